@@ -1,0 +1,176 @@
+"""FP64 CPU oracle (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA path:
+the arithmetic lives in ``oracle.cpp`` (plain double-precision loops with
+OpenMP over targets), compiled here with g++.
+
+``evaluate(problem)`` returns V, S, D at the problem's targets as the sum of
+  * the smooth part: direct O(N * N_t) sums of the smoothed kernel
+    G_H[delta](r) = -ln r/(2 pi) - E1(r^2/(4 delta))/(4 pi)   (Sec. 2,
+    eq. splitting2) and of its source-point normal derivative, and
+  * the local part: the asymptotic expansions of Sec. 4 after a closest-point
+    search on the boundary panels.
+This is the quantity the NUFFT pipeline approximates to its tolerance.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.cpp")
+_OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+
+def build(force=False):
+    """Compile oracle.cpp -> _build/liboracle.so (g++, OpenMP, -O2)."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    if not force and os.path.exists(_OUT) and os.path.getmtime(_OUT) >= os.path.getmtime(_SRC):
+        return _OUT
+    tmp = _OUT + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _OUT)
+    return _OUT
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        d, i64, vp, i32 = ctypes.c_double, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int
+        _lib.oracle_e1.restype = d
+        _lib.oracle_e1.argtypes = [d]
+        _lib.oracle_ein.restype = d
+        _lib.oracle_ein.argtypes = [d]
+        _lib.oracle_green_smooth.restype = d
+        _lib.oracle_green_smooth.argtypes = [d, d]
+        _lib.oracle_smooth_charge.argtypes = [i64, vp, vp, i64, vp, d, vp]
+        _lib.oracle_smooth_dipole.argtypes = [i64, vp, vp, vp, i64, vp, d, vp]
+        _lib.oracle_gl_nodes.argtypes = [i32, vp]
+        _lib.oracle_local.restype = i32
+        _lib.oracle_local.argtypes = [i32, i32, vp, vp, vp, i64, vp, vp, d, i32, d, vp, vp, vp, vp]
+        _lib.oracle_frame.argtypes = [i32, i32, vp, vp, vp, i32, d, vp]
+        _lib.oracle_local_formulas.argtypes = [vp, vp, d, i32, vp]
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def e1(z):
+    return lib().oracle_e1(float(z))
+
+
+def ein(z):
+    return lib().oracle_ein(float(z))
+
+
+def green_smooth(r, delta):
+    r = np.atleast_1d(np.asarray(r, dtype=np.float64))
+    return np.array([lib().oracle_green_smooth(float(x * x), float(delta)) for x in r])
+
+
+def gl_nodes(p):
+    x = np.zeros(p)
+    lib().oracle_gl_nodes(int(p), _p(x))
+    return x
+
+
+def smooth_charge(src_xy, q, tgt_xy, delta):
+    src_xy, q, tgt_xy = _c(src_xy), _c(q), _c(tgt_xy)
+    out = np.zeros(len(tgt_xy))
+    lib().oracle_smooth_charge(len(src_xy), _p(src_xy), _p(q), len(tgt_xy), _p(tgt_xy),
+                               float(delta), _p(out))
+    return out
+
+
+def smooth_dipole(src_xy, normal, m, tgt_xy, delta):
+    src_xy, normal, m, tgt_xy = _c(src_xy), _c(normal), _c(m), _c(tgt_xy)
+    out = np.zeros(len(tgt_xy))
+    lib().oracle_smooth_dipole(len(src_xy), _p(src_xy), _p(normal), _p(m), len(tgt_xy),
+                               _p(tgt_xy), float(delta), _p(out))
+    return out
+
+
+def local(bnd, sigma, mu, tgt_xy, jet, delta, order=5, on_tol=1e-12):
+    """Local part per target: returns (VL, SL, DL, info[nt,4], status)."""
+    bxy = _c(bnd["xy"]) if bnd is not None else np.zeros((0, 2))
+    npan = bnd["n_panels"] if bnd is not None else 0
+    p = bnd["order"] if bnd is not None else 0
+    tgt_xy = _c(tgt_xy)
+    nt = len(tgt_xy)
+    sigma, mu, jet = _c(sigma), _c(mu), _c(jet)
+    VL = np.zeros(nt) if jet is not None else None
+    SL = np.zeros(nt) if sigma is not None else None
+    DL = np.zeros(nt) if mu is not None else None
+    info = np.zeros((nt, 4))
+    st = lib().oracle_local(int(npan), int(p), _p(bxy), _p(sigma), _p(mu), nt, _p(tgt_xy),
+                            _p(jet), float(delta), int(order), float(on_tol), _p(VL), _p(SL),
+                            _p(DL), _p(info))
+    return VL, SL, DL, info, st
+
+
+def frame(bnd, sigma, mu, panel, t):
+    out = np.zeros(14)
+    lib().oracle_frame(bnd["n_panels"], bnd["order"], _p(_c(bnd["xy"])), _p(_c(sigma)),
+                       _p(_c(mu)), int(panel), float(t), _p(out))
+    keys = ["kappa", "g3", "g4", "s0", "s1", "s2", "m0", "m1", "m2", "m4", "Tx", "Ty", "bx", "by"]
+    return dict(zip(keys, out))
+
+
+def local_formulas(geom, jet6, delta, order=5):
+    """geom = dict(r, sgn, kappa, g3, g4, s0, s1, s2, m0, m1, m2, m4, Tx, Ty)."""
+    keys = ["r", "sgn", "kappa", "g3", "g4", "s0", "s1", "s2", "m0", "m1", "m2", "m4", "Tx", "Ty"]
+    g = np.array([float(geom.get(k, 0.0)) for k in keys])
+    j = _c(jet6 if jet6 is not None else np.zeros(6))
+    out = np.zeros(3)
+    lib().oracle_local_formulas(_p(g), _p(j), float(delta), int(order), _p(out))
+    return {"V": out[0], "S": out[1], "D": out[2]}
+
+
+def on_tolerance(problem):
+    side = max(problem["box_hi"][0] - problem["box_lo"][0], problem["box_hi"][1] - problem["box_lo"][1])
+    return 1e-12 * side
+
+
+def evaluate(problem, targets=None, order=5, want=("V", "S", "D")):
+    """V, S, D at the problem's targets (or at the given subset of target
+    indices).  Returns a dict with totals and their smooth/local parts."""
+    delta = problem["delta"]
+    idx = np.arange(len(problem["tgt_xy"])) if targets is None else np.asarray(targets)
+    txy = problem["tgt_xy"][idx]
+    jet = problem["tgt_jet"][idx] if "V" in want else None
+    bnd = problem["bnd"]
+    sigma = problem["sigma"] if "S" in want else None
+    mu = problem["mu"] if "D" in want else None
+    out = {}
+    if "V" in want:
+        q = problem["src_f"] * problem["src_w"]
+        out["VH"] = smooth_charge(problem["src_xy"], q, txy, delta) if len(q) else np.zeros(len(txy))
+    if sigma is not None:
+        out["SH"] = smooth_charge(bnd["xy"], sigma * bnd["w"], txy, delta)
+    if mu is not None:
+        out["DH"] = smooth_dipole(bnd["xy"], bnd["normal"], mu * bnd["w"], txy, delta)
+    VL, SL, DL, info, st = local(bnd, sigma, mu, txy, jet, delta, order, on_tolerance(problem))
+    if "V" in want:
+        out["VL"] = VL
+        out["V"] = out["VH"] + VL
+    if sigma is not None:
+        out["SL"] = SL
+        out["S"] = out["SH"] + SL
+    if mu is not None:
+        out["DL"] = DL
+        out["D"] = out["DH"] + DL
+    out["info"] = info
+    out["status"] = st
+    return out
