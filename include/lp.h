@@ -1,0 +1,145 @@
+/*
+ * lp.h -- C ABI of the GB300 evaluator of 2D log-kernel volume and layer
+ * potentials by heat-kernel splitting (Fryklund, Greengard, Jiang, Potter,
+ * "A lightweight, geometrically flexible fast algorithm for the evaluation
+ * of layer and volume potentials", arXiv 2409.11998).
+ *
+ * The library evaluates, at arbitrary target points x,
+ *
+ *   V[f](x) = int_Omega      G(x - x') f(x')  dx'                 (Sec. 1, eq. volpotposgreen)
+ *   S[s](x) = int_dOmega     G(x - x') s(x')  ds_x'               (Sec. 1, eq. slpot)
+ *   D[m](x) = int_dOmega  dG/dnu_x'(x - x') m(x') ds_x'           (Sec. 1, eq. dlpot)
+ *
+ * with G(x) = -log|x| / (2 pi) (eq. GreenPoisson) and nu the outward normal
+ * (so D[1] = -1 in Omega, -1/2 on dOmega, 0 outside).  Each potential is the
+ * sum of
+ *   - a smooth part: the kernel G_H[delta_1] = G - E1(|x|^2/(4 delta_1))/(4 pi)
+ *     (eq. splitting2) summed over quadrature-weighted sources, computed as
+ *     the near-history plus far-history Fourier sums of Sec. 3 (type-1 NUFFT,
+ *     diagonal multiplier of eq. vnearkspace / eq. vfarkspace, type-2 NUFFT),
+ *   - a local part: the asymptotic expansions of Sec. 4 (single-layer,
+ *     double-layer and volume lemmas), evaluated per target after a
+ *     closest-point search on the boundary panels.
+ *
+ * Discretisation (Sec. 2.2): volume sources are quadrature nodes x_j with
+ * weights w_j (any smooth rule on any triangulation, gaps allowed); the
+ * boundary is a single closed counter-clockwise curve given as n_panels
+ * consecutive panels of panel_order Gauss-Legendre nodes each, with
+ * quadrature weights (|gamma'| times the scaled Gauss weights) and outward
+ * normals.  Densities sigma, mu are given at the boundary nodes.
+ *
+ * Memory: every pointer argument may be DEVICE memory (cudaMalloc, managed)
+ * or HOST memory (pageable or pinned).  Device pointers are used in place;
+ * host inputs are copied to plan-owned device buffers and host outputs are
+ * copied back, on the plan's stream.  Caller-owned buffers must stay valid
+ * until the call's work on the stream has completed (lp_sync).  All work of
+ * a plan runs on the stream given in lp_domain (0 = legacy default stream).
+ *
+ * Errors: every call returns an lp_status.  No call launches work when it
+ * returns LP_ERR_ARG.  Problems detected on the device (a point outside the
+ * box, a band target outside the domain where V_L is undefined) set bits of a
+ * plan status word that lp_sync returns.  Calls on one plan must not be made
+ * concurrently from several host threads.
+ */
+#ifndef LP_H_
+#define LP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lp_plan_s* lp_plan_t;
+
+typedef enum {
+  LP_OK = 0,
+  LP_ERR_ARG = 1,            /* invalid argument; nothing was launched */
+  LP_ERR_OUT_OF_BOX = 2,     /* a source or target lies outside the plan's box */
+  LP_ERR_NOMEM = 3,          /* device allocation failed */
+  LP_ERR_CUDA = 4,           /* a CUDA runtime or cuFFT call failed */
+  LP_ERR_UNSUPPORTED = 5,    /* V requested at an exterior target within 12 sqrt(delta_1)
+                                of the boundary, where Sec. 4 gives no expansion */
+  LP_ERR_STATE = 6           /* call order violated (e.g. execute before lp_volume) */
+} lp_status;
+
+enum { LP_FP64 = 0, LP_FP32 = 1 };
+
+typedef struct {
+  int precision;        /* LP_FP64: all smooth-part arithmetic in double.
+                           LP_FP32: spread, FFT and interpolation in float; the
+                           multiplier table is built in double and the zero-mode
+                           (log-constant) term is summed and added in double. */
+  int order;            /* asymptotic order p in {3,4,5}: local terms through
+                           delta^{(p-1)/2} are kept (error O(delta^{p/2})); 0 -> 5 */
+  double box_lo[2];     /* box containing every source and target; the plan adds */
+  double box_hi[2];     /* its own margins for the periodic grids */
+  int64_t n_panels;     /* boundary panels (0: no boundary: free-space V only) */
+  int panel_order;      /* Gauss-Legendre nodes per panel (2..32) */
+  const double* bnd_xy;     /* [n_panels*panel_order][2] nodes, panel after panel */
+  const double* bnd_w;      /* [n_panels*panel_order] arc-length quadrature weights */
+  const double* bnd_normal; /* [n_panels*panel_order][2] outward unit normals */
+  void* stream;         /* cudaStream_t for all work of the plan */
+} lp_domain;
+
+/* Create a plan: chooses the near/far-history grids (Sec. 3: delta_2 =
+ * 32 delta_1, Fourier truncation k e^{-k^2 delta} < tol, periods that exclude
+ * aliasing for the box), builds the multiplier tables and the boundary
+ * search structures, and allocates all device workspace.
+ *   delta: delta_1 (> 0); the paper's choice is 3 * mean(w) (Sec. 6).
+ *   tol:   target accuracy of the smooth part, 1e-3 .. 1e-13 (FP32: >= 1e-6).
+ * On success *plan owns all workspace until lp_destroy. */
+lp_status lp_plan(const lp_domain* domain, double delta, double tol, lp_plan_t* plan);
+
+/* Bind volume sources: n nodes xy[n][2], quadrature weights w[n] and density
+ * f[n] (Sec. 3, input of the history algorithm: strengths f_j w_j).  The plan
+ * copies what it needs; the caller's buffers may be reused once the stream
+ * has passed this call.  n may be 0. */
+lp_status lp_volume(lp_plan_t plan, int64_t n, const double* xy, const double* w, const double* f);
+
+/* Bind the single-layer density sigma at the boundary nodes (strengths
+ * sigma_b w_b).  sigma: [n_panels*panel_order]. */
+lp_status lp_single_layer(lp_plan_t plan, const double* sigma);
+
+/* Bind the double-layer density mu at the boundary nodes (dipole strengths
+ * mu_b w_b nu_b).  mu: [n_panels*panel_order]. */
+lp_status lp_double_layer(lp_plan_t plan, const double* mu);
+
+/* Evaluate at n_t targets t_xy[n_t][2]:
+ *   V[i] = V[f](t_i)  (requires lp_volume and f_jet)
+ *   S[i] = S[sigma](t_i) (requires lp_single_layer)
+ *   D[i] = D[mu](t_i) (requires lp_double_layer)
+ * Any of V, S, D may be NULL (not requested).  f_jet[n_t][6] holds
+ * (f, f_x, f_y, f_xx, f_xy, f_yy) at each target (zero outside Omega); it
+ * feeds the volume expansion of Sec. 4 and may be NULL when V is NULL.
+ * Targets may coincide with sources or lie on the boundary (classified as
+ * on-surface when within 1e-12 * box side of it).  Asynchronous on the plan's
+ * stream; call lp_sync for completion and device-side status. */
+lp_status lp_execute(lp_plan_t plan, int64_t n_t, const double* t_xy, const double* f_jet,
+                     double* V, double* S, double* D);
+
+/* Wait for the plan's stream; return and clear the device status word. */
+lp_status lp_sync(lp_plan_t plan);
+
+/* Release all plan resources (synchronises the plan's stream first). */
+lp_status lp_destroy(lp_plan_t plan);
+
+/* Static description of a status code. */
+const char* lp_status_string(lp_status status);
+
+/* Plan parameters, for diagnostics and benchmarks:
+ * out[0..15] = {delta_1, delta_2, kernel width w, beta, g_NH, K_NH, P_NH, g_FH, K_FH,
+ *               P_FH, L_FH, band 12 sqrt(delta_1), node-gap margin, device bytes,
+ *               precision, order}. */
+lp_status lp_plan_info(lp_plan_t plan, double* out);
+
+/* Per-stage device times of the last lp_execute in milliseconds (CUDA events
+ * on the plan's stream; valid after lp_sync): out[0..7] = {spread, forward
+ * FFT, multiplier, inverse FFT, interpolation, local, total, copies}. */
+lp_status lp_stage_times(lp_plan_t plan, float* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LP_H_ */

@@ -1,0 +1,245 @@
+"""Python binding of the GB300 evaluator of 2D log-kernel volume and layer
+potentials by heat-kernel splitting (arXiv 2409.11998).
+
+Argument marshalling only: every step of the evaluation runs in the CUDA
+library ``_build/liblp.so`` behind the C ABI of ``include/lp.h``.  The
+functions below keep the C names (``lp_plan``, ``lp_volume``,
+``lp_single_layer``, ``lp_double_layer``, ``lp_execute``, ``lp_sync``,
+``lp_destroy``) and accept torch CUDA tensors (used in place) or host
+arrays (numpy / CPU tensors; the library copies them).  Importing this
+package fails loudly when the library has not been built: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblp.so")
+
+LP_FP64, LP_FP32 = 0, 1
+STATUS = {0: "LP_OK", 1: "LP_ERR_ARG", 2: "LP_ERR_OUT_OF_BOX", 3: "LP_ERR_NOMEM",
+          4: "LP_ERR_CUDA", 5: "LP_ERR_UNSUPPORTED", 6: "LP_ERR_STATE"}
+EXPORTS = ("lp_plan", "lp_volume", "lp_single_layer", "lp_double_layer", "lp_execute", "lp_sync",
+           "lp_destroy", "lp_status_string", "lp_plan_info", "lp_stage_times")
+
+
+class LpError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({_lib().lp_status_string(code).decode()})")
+
+
+class lp_domain(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("order", ctypes.c_int),
+                ("box_lo", ctypes.c_double * 2), ("box_hi", ctypes.c_double * 2),
+                ("n_panels", ctypes.c_int64), ("panel_order", ctypes.c_int),
+                ("bnd_xy", ctypes.c_void_p), ("bnd_w", ctypes.c_void_p),
+                ("bnd_normal", ctypes.c_void_p), ("stream", ctypes.c_void_p)]
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, d, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+        L.lp_plan.argtypes = [ctypes.POINTER(lp_domain), d, d, ctypes.POINTER(vp)]
+        L.lp_volume.argtypes = [vp, i64, vp, vp, vp]
+        L.lp_single_layer.argtypes = [vp, vp]
+        L.lp_double_layer.argtypes = [vp, vp]
+        L.lp_execute.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+        L.lp_sync.argtypes = [vp]
+        L.lp_destroy.argtypes = [vp]
+        L.lp_status_string.argtypes = [i32]
+        L.lp_status_string.restype = ctypes.c_char_p
+        L.lp_plan_info.argtypes = [vp, vp]
+        L.lp_stage_times.argtypes = [vp, vp]
+        for name in EXPORTS:
+            if name != "lp_status_string":
+                getattr(L, name).restype = i32
+        _LIB = L
+    return _LIB
+
+
+def library():
+    """The loaded ctypes library (raises ImportError if it is not built)."""
+    return _lib()
+
+
+def _check(code, where):
+    if code != 0:
+        raise LpError(code, where)
+
+
+def _ptr(a):
+    """Address of a contiguous float64 torch tensor or numpy array (or None)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if str(a.dtype) != "torch.float64":
+            raise ValueError("tensor must be float64")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous float64")
+        return a.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def lp_plan(box_lo, box_hi, delta, tol, *, precision=LP_FP64, order=5, n_panels=0, panel_order=16,
+            bnd_xy=None, bnd_w=None, bnd_normal=None, stream=0):
+    dom = lp_domain()
+    dom.precision = int(precision)
+    dom.order = int(order)
+    dom.box_lo[0], dom.box_lo[1] = float(box_lo[0]), float(box_lo[1])
+    dom.box_hi[0], dom.box_hi[1] = float(box_hi[0]), float(box_hi[1])
+    dom.n_panels = int(n_panels)
+    dom.panel_order = int(panel_order)
+    dom.bnd_xy = _ptr(bnd_xy)
+    dom.bnd_w = _ptr(bnd_w)
+    dom.bnd_normal = _ptr(bnd_normal)
+    dom.stream = int(stream) if stream else None
+    h = ctypes.c_void_p()
+    _check(_lib().lp_plan(ctypes.byref(dom), float(delta), float(tol), ctypes.byref(h)), "lp_plan")
+    return h
+
+
+def lp_volume(plan, n, xy, w, f):
+    _check(_lib().lp_volume(plan, int(n), _ptr(xy), _ptr(w), _ptr(f)), "lp_volume")
+
+
+def lp_single_layer(plan, sigma):
+    _check(_lib().lp_single_layer(plan, _ptr(sigma)), "lp_single_layer")
+
+
+def lp_double_layer(plan, mu):
+    _check(_lib().lp_double_layer(plan, _ptr(mu)), "lp_double_layer")
+
+
+def lp_execute(plan, n_t, t_xy, f_jet, V=None, S=None, D=None):
+    _check(_lib().lp_execute(plan, int(n_t), _ptr(t_xy), _ptr(f_jet), _ptr(V), _ptr(S), _ptr(D)),
+           "lp_execute")
+
+
+def lp_sync(plan):
+    _check(_lib().lp_sync(plan), "lp_sync")
+
+
+def lp_destroy(plan):
+    _check(_lib().lp_destroy(plan), "lp_destroy")
+
+
+def lp_plan_info(plan):
+    out = np.zeros(16)
+    _check(_lib().lp_plan_info(plan, out.ctypes.data), "lp_plan_info")
+    keys = ["delta1", "delta2", "w", "beta", "g_nh", "K_nh", "P_nh", "g_fh", "K_fh", "P_fh", "L_fh",
+            "band", "margin", "device_bytes", "precision", "order"]
+    return dict(zip(keys, out.tolist()))
+
+
+def lp_stage_times(plan):
+    out = np.zeros(8, dtype=np.float32)
+    _check(_lib().lp_stage_times(plan, out.ctypes.data), "lp_stage_times")
+    keys = ["spread", "fft_fwd", "multiplier", "fft_inv", "interp", "local", "total", "copies"]
+    return dict(zip(keys, out.tolist()))
+
+
+class Evaluator:
+    """Owns one plan.  ``problem`` is a dict as produced by ``workloads.configs``
+    (numpy arrays); arrays are moved to the device once (torch) unless
+    ``host=True``, in which case the C ABI receives host pointers."""
+
+    def __init__(self, problem, precision=None, order=5, tol=None, device="cuda", host=False,
+                 stream=None):
+        import torch
+        self.torch = torch
+        self.host = host
+        prec = problem.get("precision", "fp64") if precision is None else precision
+        self.precision = LP_FP32 if prec in ("fp32", LP_FP32) else LP_FP64
+        self.tol = problem["tol"] if tol is None else tol
+        self.device = device
+        b = problem.get("bnd")
+        self._keep = []
+
+        def dev(a):
+            if a is None:
+                return None
+            if host:
+                return np.ascontiguousarray(a, dtype=np.float64)
+            t = torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=device)
+            self._keep.append(t)
+            return t
+
+        self.stream = stream if stream is not None else (0 if host else torch.cuda.current_stream().cuda_stream)
+        kw = {}
+        if b is not None:
+            kw = dict(n_panels=b["n_panels"], panel_order=b["order"], bnd_xy=dev(b["xy"]),
+                      bnd_w=dev(b["w"]), bnd_normal=dev(b["normal"]))
+        self.plan = lp_plan(problem["box_lo"], problem["box_hi"], problem["delta"], self.tol,
+                            precision=self.precision, order=order, stream=self.stream, **kw)
+        self.problem = problem
+
+    def bind(self, src_xy=None, src_w=None, src_f=None, sigma=None, mu=None):
+        p = self.problem
+        dev = (lambda a: np.ascontiguousarray(a, dtype=np.float64)) if self.host else \
+            (lambda a: self.torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=self.device))
+        xy = p["src_xy"] if src_xy is None else src_xy
+        w = p["src_w"] if src_w is None else src_w
+        f = p["src_f"] if src_f is None else src_f
+        self._src = [dev(xy), dev(w), dev(f)]
+        lp_volume(self.plan, len(w), *self._src)
+        s = p.get("sigma") if sigma is None else sigma
+        m = p.get("mu") if mu is None else mu
+        if s is not None:
+            self._sig = dev(s)
+            lp_single_layer(self.plan, self._sig)
+        if m is not None:
+            self._mu = dev(m)
+            lp_double_layer(self.plan, self._mu)
+        return self
+
+    def evaluate(self, tgt_xy=None, tgt_jet=None, want=("V", "S", "D"), sync=True):
+        p = self.problem
+        txy = p["tgt_xy"] if tgt_xy is None else tgt_xy
+        jet = p["tgt_jet"] if tgt_jet is None else tgt_jet
+        n = len(txy)
+        if self.host:
+            t, j = np.ascontiguousarray(txy), np.ascontiguousarray(jet)
+            outs = {k: np.zeros(n) for k in want}
+        else:
+            torch = self.torch
+            t = torch.as_tensor(np.ascontiguousarray(txy), device=self.device) if not hasattr(txy, "data_ptr") else txy
+            j = torch.as_tensor(np.ascontiguousarray(jet), device=self.device) if not hasattr(jet, "data_ptr") else jet
+            outs = {k: torch.empty(n, dtype=torch.float64, device=self.device) for k in want}
+        self._tgt = (t, j)
+        lp_execute(self.plan, n, t, j if "V" in want else None, outs.get("V"), outs.get("S"), outs.get("D"))
+        if sync:
+            lp_sync(self.plan)
+        return outs
+
+    def info(self):
+        return lp_plan_info(self.plan)
+
+    def stage_times(self):
+        return lp_stage_times(self.plan)
+
+    def close(self):
+        if self.plan is not None:
+            lp_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

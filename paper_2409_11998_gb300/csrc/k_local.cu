@@ -1,0 +1,312 @@
+// Local part (Sec. 4): per target, closest boundary point (Sec. 2.2:
+// nearest node, then Newton on the panel polynomial), the tangent-line frame
+// (eq. tanparams) and the asymptotic expansions of the local single-layer,
+// double-layer and volume heat potentials, added onto the smooth part.
+//
+// Conventions (forced by the definitions of Sec. 1-2):
+//   D[mu] differentiates in the source point, so D[1] = -1 inside; with it
+//   the printed local D expansion changes sign.  The local S kernel is
+//   positive, so the printed local S expansion changes sign.  In the volume
+//   expansion, with eta the inward normal and kappa > 0 for convex
+//   boundaries, the delta^{3/2} term reads (2 f_eta - kappa f).
+#include <cmath>
+
+#include "lp_internal.cuh"
+
+namespace lpg {
+
+namespace {
+
+struct LocalArgs {
+  const double* txy;
+  const double* jet;
+  int64_t n;
+  double* out[3];  // V, S, D: local part added in place
+  const double* bxy;
+  int64_t nb;
+  int n_panels, p;
+  const double* tau;
+  const double* geo_coef;
+  const double* geo_ref;
+  const double* sig_coef;
+  const double* sig_ref;
+  const double* mu_coef;
+  const double* mu_ref;
+  double hx0, hy0, hh;
+  int hnx, hny;
+  const int* cell_start;
+  const int* cell_node;
+  double margin, band, delta, on_tol;
+  int order;
+  unsigned* status;
+};
+
+// d^j/dt^j of ref + sum_k c_k P_k(t), j = 0..nd (Legendre three-term
+// recurrence differentiated j times).
+__device__ void legendre_jet(const double* __restrict__ c, double ref, int p, double t, int nd,
+                             double* out) {
+  double pm[5] = {0, 0, 0, 0, 0}, pk[5] = {1, 0, 0, 0, 0};
+  for (int j = 0; j <= nd; ++j) out[j] = c[0] * pk[j];
+  out[0] += ref;
+  for (int k = 0; k + 1 < p; ++k) {
+    double pn[5];
+    for (int j = 0; j <= nd; ++j) {
+      double prev = j ? pk[j - 1] : 0.0;
+      pn[j] = ((2.0 * k + 1.0) * (t * pk[j] + j * prev) - k * pm[j]) / (k + 1.0);
+    }
+    for (int j = 0; j <= nd; ++j) {
+      pm[j] = pk[j];
+      pk[j] = pn[j];
+      out[j] += c[k + 1] * pk[j];
+    }
+  }
+}
+
+struct Foot {
+  int panel;
+  double t, d2;
+};
+
+__device__ Foot panel_foot(const LocalArgs& a, int ip, double t, double x, double y) {
+  const double* cx = a.geo_coef + (size_t)(2 * ip) * a.p;
+  const double* cy = cx + a.p;
+  const double rx = a.geo_ref[2 * ip], ry = a.geo_ref[2 * ip + 1];
+  double X[3], Y[3];
+  for (int it = 0; it < 20; ++it) {
+    legendre_jet(cx, rx, a.p, t, 2, X);
+    legendre_jet(cy, ry, a.p, t, 2, Y);
+    double gx = X[0] - x, gy = Y[0] - y;
+    double f = gx * X[1] + gy * Y[1];
+    double s2 = X[1] * X[1] + Y[1] * Y[1];
+    double fp = s2 + gx * X[2] + gy * Y[2];
+    if (fp < 0.1 * s2) fp = s2;
+    double tn = fmin(1.0, fmax(-1.0, t - f / fp));
+    double dt = tn - t;
+    t = tn;
+    if (fabs(dt) < 1e-14) break;
+  }
+  legendre_jet(cx, rx, a.p, t, 0, X);
+  legendre_jet(cy, ry, a.p, t, 0, Y);
+  Foot r;
+  r.panel = ip;
+  r.t = t;
+  r.d2 = (X[0] - x) * (X[0] - x) + (Y[0] - y) * (Y[0] - y);
+  return r;
+}
+
+// Coefficients of xi^1..xi^4 of F(s(xi)) with F(s) = sum_{k>=1} F[k] s^k and
+// s(xi) = sum_{k>=1} c[k] xi^k.
+__device__ void compose4(const double* F, const double* c, double* o) {
+  o[1] = F[1] * c[1];
+  o[2] = F[1] * c[2] + F[2] * c[1] * c[1];
+  o[3] = F[1] * c[3] + 2.0 * F[2] * c[1] * c[2] + F[3] * c[1] * c[1] * c[1];
+  o[4] = F[1] * c[4] + F[2] * (c[2] * c[2] + 2.0 * c[1] * c[3]) + 3.0 * F[3] * c[1] * c[1] * c[2] +
+         F[4] * c[1] * c[1] * c[1] * c[1];
+}
+
+__global__ void local_kernel(LocalArgs a) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const double x = a.txy[2 * i], y = a.txy[2 * i + 1];
+  const double dl = a.delta;
+  const double* J = a.jet ? a.jet + 6 * i : nullptr;
+  double vl = 0.0, sl = 0.0, dlv = 0.0;
+
+  // nearest boundary node (ties: lowest index) among the 3x3 hash cells
+  int best = -1;
+  double bd2 = 1e300;
+  if (a.nb > 0) {
+    int cx = (int)floor((x - a.hx0) / a.hh), cy = (int)floor((y - a.hy0) / a.hh);
+    if (cx >= 0 && cx < a.hnx && cy >= 0 && cy < a.hny) {
+      for (int oy = -1; oy <= 1; ++oy) {
+        int yy = cy + oy;
+        if (yy < 0 || yy >= a.hny) continue;
+        for (int ox = -1; ox <= 1; ++ox) {
+          int xx = cx + ox;
+          if (xx < 0 || xx >= a.hnx) continue;
+          int c = yy * a.hnx + xx;
+          for (int k = a.cell_start[c]; k < a.cell_start[c + 1]; ++k) {
+            int j = a.cell_node[k];
+            double ex = x - a.bxy[2 * j], ey = y - a.bxy[2 * j + 1];
+            double d2 = ex * ex + ey * ey;
+            if (d2 < bd2 || (d2 == bd2 && j < best)) {
+              bd2 = d2;
+              best = j;
+            }
+          }
+        }
+      }
+    }
+  }
+  bool far = best < 0 || sqrt(bd2) - a.margin >= a.band;
+  Foot ft{-1, 0.0, 1e300};
+  if (!far) {
+    const int p = a.p;
+    const int ip0 = best / p;
+    for (int d = -1; d <= 1; ++d) {
+      int ip = ((ip0 + d) % a.n_panels + a.n_panels) % a.n_panels;
+      int kb = 0;
+      double kd = 1e300;
+      for (int k = 0; k < p; ++k) {
+        const double* q = a.bxy + 2 * ((size_t)ip * p + k);
+        double d2 = (x - q[0]) * (x - q[0]) + (y - q[1]) * (y - q[1]);
+        if (d2 < kd) {
+          kd = d2;
+          kb = k;
+        }
+      }
+      Foot f = panel_foot(a, ip, a.tau[kb], x, y);
+      if (f.d2 < ft.d2) ft = f;
+    }
+    if (sqrt(ft.d2) >= a.band) far = true;
+  }
+
+  if (far) {
+    if (J) {
+      vl = dl * J[0];
+      if (a.order >= 5) vl += 0.5 * dl * dl * (J[3] + J[5]);
+    }
+  } else {
+    const int p = a.p, ip = ft.panel;
+    double X[5], Y[5];
+    const double* cgx = a.geo_coef + (size_t)(2 * ip) * p;
+    legendre_jet(cgx, a.geo_ref[2 * ip], p, ft.t, 4, X);
+    legendre_jet(cgx + p, a.geo_ref[2 * ip + 1], p, ft.t, 4, Y);
+    const double sp = hypot(X[1], Y[1]);
+    const double Tx = X[1] / sp, Ty = Y[1] / sp;
+    const double Nx = -Ty, Ny = Tx;  // inward normal of a counter-clockwise curve
+    const double r = hypot(x - X[0], y - Y[0]);
+    double sgn = 0.0;
+    if (r > a.on_tol) sgn = (-((X[0] - x) * Nx + (Y[0] - y) * Ny) > 0.0) ? 1.0 : -1.0;
+    // Taylor coefficients in s = t - t*: xi(s) = sum a_k s^k, eta(s) = sum e_k s^k
+    const double fact[5] = {1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0};
+    double A[5], E[5];
+    for (int k = 1; k <= 4; ++k) {
+      A[k] = (X[k] * Tx + Y[k] * Ty) * fact[k];
+      E[k] = (X[k] * Nx + Y[k] * Ny) * fact[k];
+    }
+    E[1] = 0.0;
+    // series reversion s(xi)
+    double C[5];
+    const double i1 = 1.0 / A[1];
+    const double i2 = i1 * i1, i3 = i2 * i1, i5 = i3 * i2, i7 = i5 * i2;
+    C[1] = i1;
+    C[2] = -A[2] * i3;
+    C[3] = (2.0 * A[2] * A[2] - A[1] * A[3]) * i5;
+    C[4] = (5.0 * A[1] * A[2] * A[3] - A[1] * A[1] * A[4] - 5.0 * A[2] * A[2] * A[2]) * i7;
+    double H[5];
+    compose4(E, C, H);
+    const double kap = 2.0 * H[2], g3 = 6.0 * H[3], g4 = 24.0 * H[4];
+    const double c = r / sqrt(dl);
+    const double sq = sqrt(dl), d15 = dl * sq, d2 = dl * dl;
+    const double Ex = exp(-0.25 * c * c) * 0.56418958354775628695;  // e^{-c^2/4}/sqrt(pi)
+    const double Cc = erfc(0.5 * c);
+    const double c2 = c * c, c3 = c2 * c;
+    if (a.out[1] && a.sig_coef) {
+      double Sv[5], F[5], o[5];
+      legendre_jet(a.sig_coef + (size_t)ip * p, a.sig_ref[ip], p, ft.t, 4, Sv);
+      for (int k = 1; k <= 4; ++k) F[k] = Sv[k] * fact[k];
+      compose4(F, C, o);
+      const double s0 = Sv[0], s1 = o[1], s2 = 2.0 * o[2];
+      const double Aq = c * Cc - 2.0 * Ex;
+      const double Q = 2.0 * (c2 - 2.0) * Ex - c3 * Cc;
+      double s = sq * 0.5 * s0 * Aq + sgn * dl * 0.25 * c * kap * s0 * Aq;
+      if (a.order >= 4)
+        s += d15 * (s0 * kap * kap / 12.0 * (2.0 * c3 * Cc - (4.0 * c2 + 1.0) * Ex) + s2 / 12.0 * Q);
+      if (a.order >= 5)
+        s += d2 * sgn * c *
+             (kap * kap * kap * s0 / 16.0 * (3.0 * c3 * Cc - (6.0 * c2 - 2.0) * Ex) +
+              (kap * s2 / 8.0 + s0 * g4 / 48.0 + s1 * g3 / 12.0) * Q);
+      sl = -s;
+    }
+    if (a.out[2] && a.mu_coef) {
+      double Mv[5], F[5], o[5];
+      legendre_jet(a.mu_coef + (size_t)ip * p, a.mu_ref[ip], p, ft.t, 4, Mv);
+      for (int k = 1; k <= 4; ++k) F[k] = Mv[k] * fact[k];
+      compose4(F, C, o);
+      const double m0 = Mv[0], m1 = o[1], m2 = 2.0 * o[2], m4 = 24.0 * o[4];
+      const double R1 = 2.0 * (c2 + 1.0) * Ex - c3 * Cc;
+      const double R4 = 2.0 * (c2 + 4.0) * Ex - c3 * Cc;
+      double s = sgn * 0.5 * m0 * Cc + sq * 0.5 * kap * m0 * Ex +
+                 dl * sgn * (0.375 * c * kap * kap * m0 * Ex + 0.25 * c * m2 * (2.0 * Ex - c * Cc));
+      if (a.order >= 4)
+        s += d15 * (5.0 / 16.0 * (c2 - 2.0) * kap * kap * kap * m0 * Ex + 0.25 * g4 * m0 * Ex +
+                    0.25 * kap * m2 * R1 + g3 * m1 / 12.0 * R4);
+      if (a.order >= 5)
+        s += d2 * sgn * c *
+             (35.0 / 128.0 * kap * kap * kap * kap * m0 * (c2 - 6.0) * Ex +
+              5.0 / 12.0 * g3 * g3 * m0 * Ex + 0.625 * kap * g4 * m0 * Ex +
+              5.0 * (kap * kap * m2 / 16.0 * R1 + kap * g3 * m1 / 24.0 * R4) +
+              m4 / 48.0 * (c3 * Cc - 2.0 * (c2 - 2.0) * Ex));
+      dlv = -s;
+    }
+    if (J) {
+      if (sgn < 0.0) {
+        atomicOr(a.status, kStatusExteriorBandV);
+      } else {
+        const double f = J[0];
+        const double fe = J[1] * Nx + J[2] * Ny;
+        const double fxx = J[3] * Tx * Tx + 2.0 * J[4] * Tx * Ty + J[5] * Ty * Ty;
+        const double fee = J[3] * Nx * Nx + 2.0 * J[4] * Nx * Ny + J[5] * Ny * Ny;
+        const double Ef = erf(0.5 * c);
+        double v = 0.25 * dl * (2.0 * Ef + 2.0 * c * Ex - c2 * Cc + 2.0) * f;
+        if (a.order >= 4) v += d15 * ((4.0 - 2.0 * c2) * Ex + c3 * Cc) * (2.0 * fe - kap * f) / 12.0;
+        if (a.order >= 5) {
+          const double c4 = c2 * c2;
+          v += d2 / 48.0 *
+               (Cc * (4.0 * c4 * kap * fe - 3.0 * (c4 + 4.0) * fee + (c4 - 12.0) * fxx -
+                      3.0 * c4 * kap * kap * f) +
+                2.0 * c * (c2 - 2.0) * Ex * (-4.0 * kap * fe + 3.0 * fee - fxx + 3.0 * kap * kap * f) +
+                24.0 * (fxx + fee));
+        }
+        vl = v;
+      }
+    }
+  }
+  if (a.out[0]) a.out[0][i] += vl;
+  if (a.out[1]) a.out[1][i] += sl;
+  if (a.out[2]) a.out[2][i] += dlv;
+}
+
+}  // namespace
+
+void launch_local(const Plan& P, int64_t nt, const double* txy, const double* jet, double* V,
+                  double* S, double* D, cudaStream_t s) {
+  if (nt <= 0) return;
+  LocalArgs a;
+  a.txy = txy;
+  a.jet = V ? jet : nullptr;
+  a.n = nt;
+  a.out[0] = V;
+  a.out[1] = S;
+  a.out[2] = D;
+  a.bxy = P.d_bxy;
+  a.nb = P.nb;
+  a.n_panels = (int)P.n_panels;
+  a.p = P.p;
+  a.tau = P.d_tau;
+  a.geo_coef = P.d_geo_coef;
+  a.geo_ref = P.d_geo_ref;
+  a.sig_coef = P.have_sigma ? P.d_sigma_coef : nullptr;
+  a.sig_ref = P.d_sigma_ref;
+  a.mu_coef = P.have_mu ? P.d_mu_coef : nullptr;
+  a.mu_ref = P.d_mu_ref;
+  a.hx0 = P.hash_x0;
+  a.hy0 = P.hash_y0;
+  a.hh = P.hash_h;
+  a.hnx = P.hash_nx;
+  a.hny = P.hash_ny;
+  a.cell_start = P.d_cell_start;
+  a.cell_node = P.d_cell_node;
+  a.margin = P.margin;
+  a.band = P.band;
+  a.delta = P.delta1;
+  a.on_tol = P.on_tol;
+  a.order = P.order;
+  a.status = P.d_status;
+  int threads = 128;
+  unsigned blocks = (unsigned)((nt + threads - 1) / threads);
+  local_kernel<<<blocks, threads, 0, s>>>(a);
+}
+
+}  // namespace lpg

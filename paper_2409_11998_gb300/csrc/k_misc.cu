@@ -1,0 +1,100 @@
+// Small device kernels: panel Legendre coefficients, source strengths
+// (Sec. 3, input: f w for volume nodes, sigma w and mu nu w for boundary
+// nodes) and FP64 strength sums.
+#include "lp_internal.cuh"
+
+namespace lpg {
+
+namespace {
+
+// coef[(ip*ncomp + comp)*p + k] = sum_i T[k][i] (v_i - v_ref), v_ref = middle
+// node; ref[ip*ncomp + comp] = v_ref.  Interpolating the centred values keeps
+// the rounding of high derivatives at the size of the panel's variation.
+__global__ void panel_coef_kernel(const double* __restrict__ vals, int stride, int ncomp, int p,
+                                  int64_t n_panels, const double* __restrict__ T, double* coef,
+                                  double* ref) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t total = n_panels * ncomp * p;
+  if (idx >= total) return;
+  int k = (int)(idx % p);
+  int64_t pc = idx / p;
+  int comp = (int)(pc % ncomp);
+  int64_t ip = pc / ncomp;
+  const double* v = vals + (size_t)ip * p * stride + comp;
+  double vr = v[(size_t)(p / 2) * stride];
+  double s = 0.0;
+  for (int i = 0; i < p; ++i) s += T[(size_t)k * p + i] * (v[(size_t)i * stride] - vr);
+  coef[idx] = s;
+  if (k == 0) ref[pc] = vr;
+}
+
+__global__ void strengths_kernel(int kind, const double* __restrict__ dens, const double* __restrict__ w,
+                                 const double* __restrict__ nrm, double* bq, int64_t nb) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  double dw = dens[j] * w[j];
+  if (kind == 0) {
+    bq[j] = dw;
+  } else {
+    bq[nb + j] = dw * nrm[2 * j];
+    bq[2 * nb + j] = dw * nrm[2 * j + 1];
+  }
+}
+
+__global__ void volume_q_kernel(const double* __restrict__ f, const double* __restrict__ w, double* q,
+                                int64_t n) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) q[j] = f[j] * w[j];
+}
+
+__global__ void sum_kernel(const double* __restrict__ x, int64_t n, double* out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x)
+    s += x[j];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) atomicAdd(out, s);
+  }
+}
+
+}  // namespace
+
+void launch_panel_coef(const Plan& P, const double* vals, int stride, int ncomp, double* coef,
+                       double* ref, cudaStream_t s) {
+  int64_t total = P.n_panels * ncomp * P.p;
+  if (total <= 0) return;
+  int threads = 128;
+  panel_coef_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, s>>>(
+      vals, stride, ncomp, P.p, P.n_panels, P.d_leg_T, coef, ref);
+}
+
+void launch_strengths(const Plan& P, int kind, cudaStream_t s) {
+  if (P.nb <= 0) return;
+  int threads = 256;
+  const double* dens = kind == 0 ? P.d_sigma : P.d_mu;
+  strengths_kernel<<<(unsigned)((P.nb + threads - 1) / threads), threads, 0, s>>>(
+      kind, dens, P.d_bw, P.d_bnrm, P.d_bq, P.nb);
+}
+
+void launch_volume_q(const double* f, const double* w, double* q, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  int threads = 256;
+  volume_q_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(f, w, q, n);
+}
+
+void launch_sum(const double* x, int64_t n, double* out, cudaStream_t s) {
+  cudaMemsetAsync(out, 0, sizeof(double), s);
+  if (n <= 0) return;
+  int threads = 256;
+  int64_t blocks = (n + threads - 1) / threads;
+  if (blocks > 1024) blocks = 1024;
+  sum_kernel<<<(unsigned)blocks, threads, 0, s>>>(x, n, out);
+}
+
+}  // namespace lpg

@@ -1,0 +1,468 @@
+// C ABI entry points (include/lp.h): plan lifetime, binding of sources and
+// densities, and the evaluation pipeline
+//   spread -> forward FFT -> multiplier -> inverse FFT -> interpolate -> local
+// of Sec. 3 (history part, two levels) and Sec. 4 (local part).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lp_internal.cuh"
+
+using namespace lpg;
+
+struct lp_plan_s {
+  Plan P;
+};
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+bool dalloc(Plan& P, void** ptr, size_t bytes) {
+  if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return false;
+  }
+  P.device_bytes += bytes;
+  return true;
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+// Device view of a caller array: used in place when it is device memory,
+// otherwise copied into plan-owned staging at byte offset *off.
+const double* device_view(Plan& P, const double* src, size_t count, size_t* off) {
+  if (!src || count == 0) return src;
+  if (is_device_ptr(src)) return src;
+  double* dst = (double*)((char*)P.d_stage + *off);
+  cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyHostToDevice, P.stream);
+  *off += ((count * sizeof(double) + 255) / 256) * 256;
+  return dst;
+}
+
+bool ensure_stage(Plan& P, size_t bytes) {
+  if (bytes <= P.stage_bytes) return true;
+  cudaStreamSynchronize(P.stream);
+  if (P.d_stage) {
+    cudaFree(P.d_stage);
+    P.device_bytes -= P.stage_bytes;
+  }
+  P.d_stage = nullptr;
+  P.stage_bytes = 0;
+  if (!dalloc(P, &P.d_stage, bytes)) return false;
+  P.stage_bytes = bytes;
+  return true;
+}
+
+size_t round256(size_t b) { return ((b + 255) / 256) * 256; }
+
+lp_status make_fft_plans(Plan& P, GridLevel& G) {
+  int n[2] = {G.g, G.g};
+  int rembed[2] = {G.g, G.pitch};
+  int cembed[2] = {G.g, G.g / 2 + 1};
+  const bool f64 = P.precision == LP_FP64;
+  int rdist = G.g * G.pitch, cdist = G.g * (G.g / 2 + 1);
+  if (cufftPlanMany(&G.fwd, 2, n, rembed, 1, rdist, cembed, 1, cdist, f64 ? CUFFT_D2Z : CUFFT_R2C, 1) !=
+      CUFFT_SUCCESS)
+    return LP_ERR_CUDA;
+  if (cufftPlanMany(&G.inv, 2, n, cembed, 1, cdist, rembed, 1, rdist, f64 ? CUFFT_Z2D : CUFFT_C2R, 1) !=
+      CUFFT_SUCCESS)
+    return LP_ERR_CUDA;
+  cufftSetStream(G.fwd, P.stream);
+  cufftSetStream(G.inv, P.stream);
+  return LP_OK;
+}
+
+void destroy_plan(Plan& P) {
+  if (P.stream) cudaStreamSynchronize(P.stream);
+  for (auto& G : P.lv) {
+    for (auto& c : G.chan) dfree(c);
+    dfree(G.mtab);
+    dfree(G.mtab32);
+    if (G.fwd) cufftDestroy(G.fwd);
+    if (G.inv) cufftDestroy(G.inv);
+  }
+  void* bufs[] = {P.d_bxy, P.d_bw, P.d_bnrm, P.d_geo_coef, P.d_geo_ref, P.d_leg_T, P.d_tau,
+                  P.d_cell_start, P.d_cell_node, P.d_vxy, P.d_vq, P.d_sigma, P.d_sigma_coef,
+                  P.d_sigma_ref, P.d_mu, P.d_mu_coef, P.d_mu_ref, P.d_bq, P.d_qsum, P.d_stage,
+                  P.d_out, P.d_status};
+  for (void* b : bufs) dfree(b);
+  if (P.h_status) cudaFreeHost(P.h_status);
+  for (auto& e : P.ev)
+    if (e) cudaEventDestroy(e);
+}
+
+lp_status status_from_cuda() {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+}
+
+// Outward normals from the panel interpolant when the caller gives none:
+// nu = (y', -x') / |gamma'| at the nodes (counter-clockwise curve).
+void derive_normals(int64_t n_panels, int p, const double* xy, double* nrm) {
+  std::vector<double> tau(p), wq(p);
+  gauss_legendre(p, tau.data(), wq.data());
+  // differentiation matrix of the Lagrange basis at the nodes
+  std::vector<double> bw(p, 1.0);
+  for (int i = 0; i < p; ++i)
+    for (int j = 0; j < p; ++j)
+      if (j != i) bw[i] /= (tau[i] - tau[j]);
+  for (int64_t ip = 0; ip < n_panels; ++ip) {
+    const double* v = xy + (size_t)ip * p * 2;
+    for (int i = 0; i < p; ++i) {
+      double dx = 0, dy = 0, diag = 0;
+      for (int j = 0; j < p; ++j) {
+        if (j == i) continue;
+        double dij = bw[j] / bw[i] / (tau[i] - tau[j]);
+        dx += dij * v[2 * j];
+        dy += dij * v[2 * j + 1];
+        diag -= dij;
+      }
+      dx += diag * v[2 * i];
+      dy += diag * v[2 * i + 1];
+      double s = std::hypot(dx, dy);
+      nrm[(size_t)(ip * p + i) * 2] = dy / s;
+      nrm[(size_t)(ip * p + i) * 2 + 1] = -dx / s;
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lp_status_string(lp_status s) {
+  switch (s) {
+    case LP_OK: return "ok";
+    case LP_ERR_ARG: return "invalid argument";
+    case LP_ERR_OUT_OF_BOX: return "a source or target lies outside the plan's box";
+    case LP_ERR_NOMEM: return "device allocation failed";
+    case LP_ERR_CUDA: return "CUDA runtime or cuFFT failure";
+    case LP_ERR_UNSUPPORTED:
+      return "volume potential requested at an exterior target inside the local band";
+    case LP_ERR_STATE: return "call order violated";
+  }
+  return "unknown status";
+}
+
+lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out) {
+  if (!dom || !out) return LP_ERR_ARG;
+  *out = nullptr;
+  if (!(delta > 0.0) || !std::isfinite(delta)) return LP_ERR_ARG;
+  if (!(tol >= 1e-13 && tol <= 1e-2)) return LP_ERR_ARG;
+  if (dom->precision != LP_FP64 && dom->precision != LP_FP32) return LP_ERR_ARG;
+  if (dom->precision == LP_FP32 && tol < 1e-6) return LP_ERR_ARG;
+  int order = dom->order == 0 ? 5 : dom->order;
+  if (order < 3 || order > 5) return LP_ERR_ARG;
+  for (int d = 0; d < 2; ++d)
+    if (!(dom->box_hi[d] > dom->box_lo[d]) || !std::isfinite(dom->box_lo[d]) ||
+        !std::isfinite(dom->box_hi[d]))
+      return LP_ERR_ARG;
+  if (dom->n_panels < 0) return LP_ERR_ARG;
+  if (dom->n_panels > 0) {
+    if (dom->panel_order < 2 || dom->panel_order > kMaxPanelOrder) return LP_ERR_ARG;
+    if (!dom->bnd_xy || !dom->bnd_w) return LP_ERR_ARG;
+    if (dom->n_panels > (int64_t)1 << 26) return LP_ERR_ARG;
+  }
+  lp_plan_s* h = new (std::nothrow) lp_plan_s();
+  if (!h) return LP_ERR_NOMEM;
+  Plan& P = h->P;
+  P.precision = dom->precision;
+  P.order = order;
+  P.delta1 = delta;
+  P.delta2 = 32.0 * delta;
+  P.tol = tol;
+  for (int d = 0; d < 2; ++d) {
+    P.box_lo[d] = dom->box_lo[d];
+    P.box_hi[d] = dom->box_hi[d];
+  }
+  P.side = std::max(P.box_hi[0] - P.box_lo[0], P.box_hi[1] - P.box_lo[1]);
+  P.on_tol = 1e-12 * P.side;
+  P.stream = (cudaStream_t)dom->stream;
+  int w = (int)std::ceil(-std::log10(tol)) + 1;
+  w = std::min(std::max(w, 3), kMaxW);
+  P.ker.w = w;
+  P.ker.beta = 2.30 * w;
+  P.ker.half_w = 0.5 * w;
+  lp_status st = choose_levels(P);
+  if (st == LP_OK) st = build_tables(P);
+  const size_t rs = P.precision == LP_FP64 ? sizeof(double) : sizeof(float);
+  for (int l = 0; l < 2 && st == LP_OK; ++l) {
+    GridLevel& G = P.lv[l];
+    G.chan_bytes = (size_t)G.g * G.pitch * rs;
+    for (int c = 0; c < 4 && st == LP_OK; ++c)
+      if (!dalloc(P, &G.chan[c], G.chan_bytes)) st = LP_ERR_NOMEM;
+    if (st == LP_OK) st = make_fft_plans(P, G);
+  }
+  if (st == LP_OK) {
+    if (!dalloc(P, (void**)&P.d_status, sizeof(unsigned)) ||
+        !dalloc(P, (void**)&P.d_qsum, 2 * sizeof(double)))
+      st = LP_ERR_NOMEM;
+    else if (cudaMallocHost((void**)&P.h_status, sizeof(unsigned)) != cudaSuccess)
+      st = LP_ERR_NOMEM;
+    else {
+      cudaMemset(P.d_status, 0, sizeof(unsigned));
+      cudaMemset(P.d_qsum, 0, 2 * sizeof(double));
+      for (auto& e : P.ev) cudaEventCreate(&e);
+    }
+  }
+  if (st == LP_OK && dom->n_panels > 0) {
+    P.n_panels = dom->n_panels;
+    P.p = dom->panel_order;
+    P.nb = P.n_panels * P.p;
+    std::vector<double> hxy(P.nb * 2), hw(P.nb), hn(P.nb * 2);
+    auto fetch = [&](const double* src, double* dst, size_t count) {
+      if (is_device_ptr(src))
+        cudaMemcpy(dst, src, count * sizeof(double), cudaMemcpyDeviceToHost);
+      else
+        std::memcpy(dst, src, count * sizeof(double));
+    };
+    fetch(dom->bnd_xy, hxy.data(), hxy.size());
+    fetch(dom->bnd_w, hw.data(), hw.size());
+    if (dom->bnd_normal)
+      fetch(dom->bnd_normal, hn.data(), hn.size());
+    else
+      derive_normals(P.n_panels, P.p, hxy.data(), hn.data());
+    bool finite = true;
+    for (double v : hxy) finite &= std::isfinite(v);
+    for (double v : hw) finite &= std::isfinite(v);
+    if (!finite) st = LP_ERR_ARG;
+    if (st == LP_OK) st = build_boundary(P, hxy.data(), hw.data(), hn.data());
+  }
+  if (st == LP_OK) st = status_from_cuda();
+  if (st != LP_OK) {
+    destroy_plan(P);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return LP_OK;
+}
+
+lp_status lp_volume(lp_plan_t h, int64_t n, const double* xy, const double* w, const double* f) {
+  if (!h || n < 0) return LP_ERR_ARG;
+  if (n > 0 && (!xy || !w || !f)) return LP_ERR_ARG;
+  Plan& P = h->P;
+  if (n > P.nv) {
+    cudaStreamSynchronize(P.stream);
+    dfree(P.d_vxy);
+    dfree(P.d_vq);
+    P.d_vxy = P.d_vq = nullptr;
+    if (!dalloc(P, (void**)&P.d_vxy, n * 2 * sizeof(double)) ||
+        !dalloc(P, (void**)&P.d_vq, n * sizeof(double)))
+      return LP_ERR_NOMEM;
+  }
+  P.nv = n;
+  if (n > 0) {
+    if (!ensure_stage(P, round256(n * 2 * sizeof(double)) + 2 * round256(n * sizeof(double))))
+      return LP_ERR_NOMEM;
+    size_t off = 0;
+    const double* dxy = device_view(P, xy, n * 2, &off);
+    const double* dw = device_view(P, w, n, &off);
+    const double* df = device_view(P, f, n, &off);
+    cudaMemcpyAsync(P.d_vxy, dxy, n * 2 * sizeof(double), cudaMemcpyDeviceToDevice, P.stream);
+    launch_volume_q(df, dw, P.d_vq, n, P.stream);
+  }
+  launch_sum(P.d_vq, n, P.d_qsum, P.stream);
+  P.have_volume = true;
+  return status_from_cuda();
+}
+
+static lp_status bind_layer(lp_plan_t h, const double* dens, int kind) {
+  if (!h || !dens) return LP_ERR_ARG;
+  Plan& P = h->P;
+  if (P.nb == 0) return LP_ERR_STATE;
+  if (!ensure_stage(P, round256(P.nb * sizeof(double)))) return LP_ERR_NOMEM;
+  size_t off = 0;
+  const double* d = device_view(P, dens, P.nb, &off);
+  double* dst = kind == 0 ? P.d_sigma : P.d_mu;
+  cudaMemcpyAsync(dst, d, P.nb * sizeof(double), cudaMemcpyDeviceToDevice, P.stream);
+  launch_panel_coef(P, dst, 1, 1, kind == 0 ? P.d_sigma_coef : P.d_mu_coef,
+                    kind == 0 ? P.d_sigma_ref : P.d_mu_ref, P.stream);
+  launch_strengths(P, kind, P.stream);
+  if (kind == 0) {
+    launch_sum(P.d_bq, P.nb, P.d_qsum + 1, P.stream);
+    P.have_sigma = true;
+  } else {
+    P.have_mu = true;
+  }
+  return status_from_cuda();
+}
+
+lp_status lp_single_layer(lp_plan_t h, const double* sigma) { return bind_layer(h, sigma, 0); }
+lp_status lp_double_layer(lp_plan_t h, const double* mu) { return bind_layer(h, mu, 1); }
+
+lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* jet, double* V,
+                     double* S, double* D) {
+  if (!h || nt < 0) return LP_ERR_ARG;
+  if (nt > 0 && !txy) return LP_ERR_ARG;
+  Plan& P = h->P;
+  const bool wv = V != nullptr, ws = S != nullptr, wd = D != nullptr;
+  if (wv && nt > 0 && !jet) return LP_ERR_ARG;
+  if ((wv && !P.have_volume) || (ws && !P.have_sigma) || (wd && !P.have_mu)) return LP_ERR_STATE;
+  if (nt == 0 || (!wv && !ws && !wd)) return LP_OK;
+  cudaStream_t s = P.stream;
+  // staging: targets, jet, and host outputs
+  size_t need = round256(nt * 2 * sizeof(double)) + round256(nt * 6 * sizeof(double));
+  if (!ensure_stage(P, need)) return LP_ERR_NOMEM;
+  double* outs[3] = {V, S, D};
+  bool host_out[3];
+  bool any_host = false;
+  for (int c = 0; c < 3; ++c) {
+    host_out[c] = outs[c] && !is_device_ptr(outs[c]);
+    any_host |= host_out[c];
+  }
+  if (any_host && (size_t)nt > P.out_cap) {
+    cudaStreamSynchronize(s);
+    dfree(P.d_out);
+    P.d_out = nullptr;
+    P.out_cap = 0;
+    if (!dalloc(P, (void**)&P.d_out, 3 * nt * sizeof(double))) return LP_ERR_NOMEM;
+    P.out_cap = nt;
+  }
+  cudaEventRecord(P.ev[0], s);
+  size_t off = 0;
+  const double* dt = device_view(P, txy, nt * 2, &off);
+  const double* dj = wv ? device_view(P, jet, nt * 6, &off) : nullptr;
+  double* dout[3];
+  for (int c = 0; c < 3; ++c) dout[c] = host_out[c] ? P.d_out + c * nt : outs[c];
+  cudaEventRecord(P.ev[1], s);
+
+  // Steps 2-3: spread every requested channel onto both history grids
+  for (int l = 0; l < 2; ++l) {
+    GridLevel& G = P.lv[l];
+    if (wv) cudaMemsetAsync(G.chan[0], 0, G.chan_bytes, s);
+    if (ws) cudaMemsetAsync(G.chan[1], 0, G.chan_bytes, s);
+    if (wd) {
+      cudaMemsetAsync(G.chan[2], 0, G.chan_bytes, s);
+      cudaMemsetAsync(G.chan[3], 0, G.chan_bytes, s);
+    }
+    if (wv && P.nv > 0) {
+      const double* q[1] = {P.d_vq};
+      void* g[1] = {G.chan[0]};
+      launch_spread(P, l, P.d_vxy, q, 1, g, P.nv, s);
+    }
+    const double* bq[3];
+    void* bg[3];
+    int nq = 0;
+    if (ws) {
+      bq[nq] = P.d_bq;
+      bg[nq++] = G.chan[1];
+    }
+    if (wd) {
+      bq[nq] = P.d_bq + P.nb;
+      bg[nq++] = G.chan[2];
+      bq[nq] = P.d_bq + 2 * P.nb;
+      bg[nq++] = G.chan[3];
+    }
+    if (nq) launch_spread(P, l, P.d_bxy, bq, nq, bg, P.nb, s);
+  }
+  cudaEventRecord(P.ev[2], s);
+  const bool f64 = P.precision == LP_FP64;
+  auto fwd = [&](GridLevel& G, int c) {
+    if (f64)
+      cufftExecD2Z(G.fwd, (cufftDoubleReal*)G.chan[c], (cufftDoubleComplex*)G.chan[c]);
+    else
+      cufftExecR2C(G.fwd, (cufftReal*)G.chan[c], (cufftComplex*)G.chan[c]);
+  };
+  auto inv = [&](GridLevel& G, int c) {
+    if (f64)
+      cufftExecZ2D(G.inv, (cufftDoubleComplex*)G.chan[c], (cufftDoubleReal*)G.chan[c]);
+    else
+      cufftExecC2R(G.inv, (cufftComplex*)G.chan[c], (cufftReal*)G.chan[c]);
+  };
+  for (int l = 0; l < 2; ++l) {
+    if (wv) fwd(P.lv[l], 0);
+    if (ws) fwd(P.lv[l], 1);
+    if (wd) {
+      fwd(P.lv[l], 2);
+      fwd(P.lv[l], 3);
+    }
+  }
+  cudaEventRecord(P.ev[3], s);
+  // Step 4: deconvolved multiplier (in place; D written to channel 2)
+  for (int l = 0; l < 2; ++l) launch_multiplier(P, l, wv, ws, wd, s);
+  cudaEventRecord(P.ev[4], s);
+  for (int l = 0; l < 2; ++l) {
+    if (wv) inv(P.lv[l], 0);
+    if (ws) inv(P.lv[l], 1);
+    if (wd) inv(P.lv[l], 2);
+  }
+  cudaEventRecord(P.ev[5], s);
+  launch_interp(P, nt, dt, dout[0], dout[1], dout[2], s);
+  cudaEventRecord(P.ev[6], s);
+  launch_local(P, nt, dt, dj, dout[0], dout[1], dout[2], s);
+  cudaEventRecord(P.ev[7], s);
+  for (int c = 0; c < 3; ++c)
+    if (host_out[c]) cudaMemcpyAsync(outs[c], dout[c], nt * sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaEventRecord(P.ev[8], s);
+  return status_from_cuda();
+}
+
+lp_status lp_sync(lp_plan_t h) {
+  if (!h) return LP_ERR_ARG;
+  Plan& P = h->P;
+  if (cudaStreamSynchronize(P.stream) != cudaSuccess) return LP_ERR_CUDA;
+  cudaMemcpy(P.h_status, P.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  unsigned st = *P.h_status;
+  cudaMemset(P.d_status, 0, sizeof(unsigned));
+  if (cudaGetLastError() != cudaSuccess) return LP_ERR_CUDA;
+  if (st & kStatusOutOfBox) return LP_ERR_OUT_OF_BOX;
+  if (st & kStatusExteriorBandV) return LP_ERR_UNSUPPORTED;
+  return LP_OK;
+}
+
+lp_status lp_destroy(lp_plan_t h) {
+  if (!h) return LP_ERR_ARG;
+  destroy_plan(h->P);
+  delete h;
+  return LP_OK;
+}
+
+lp_status lp_plan_info(lp_plan_t h, double* out) {
+  if (!h || !out) return LP_ERR_ARG;
+  const Plan& P = h->P;
+  double v[16] = {P.delta1, P.delta2, (double)P.ker.w, P.ker.beta, (double)P.lv[0].g, (double)P.lv[0].K,
+                  P.lv[0].P, (double)P.lv[1].g, (double)P.lv[1].K, P.lv[1].P, P.lv[1].L, P.band,
+                  P.margin, (double)P.device_bytes, (double)P.precision, (double)P.order};
+  std::memcpy(out, v, sizeof(v));
+  return LP_OK;
+}
+
+lp_status lp_stage_times(lp_plan_t h, float* out) {
+  if (!h || !out) return LP_ERR_ARG;
+  Plan& P = h->P;
+  // events: 0 start, 1 staged, 2 spread, 3 fwd, 4 mult, 5 inv, 6 interp, 7 local, 8 copies
+  auto el = [&](int a, int b) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, P.ev[a], P.ev[b]) != cudaSuccess) {
+      cudaGetLastError();
+      return -1.0f;
+    }
+    return ms;
+  };
+  out[0] = el(1, 2);
+  out[1] = el(2, 3);
+  out[2] = el(3, 4);
+  out[3] = el(4, 5);
+  out[4] = el(5, 6);
+  out[5] = el(6, 7);
+  out[6] = el(0, 8);
+  out[7] = el(0, 1) + el(7, 8);
+  return LP_OK;
+}
+
+}  // extern "C"

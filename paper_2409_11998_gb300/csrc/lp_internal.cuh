@@ -1,0 +1,135 @@
+// Internal declarations of the GB300 evaluator (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/lp.h"
+
+namespace lpg {
+
+constexpr int kMaxW = 16;           // widest spreading kernel (grid points)
+constexpr int kMaxPanelOrder = 32;  // Gauss-Legendre nodes per boundary panel
+constexpr int kNumStages = 8;
+
+// Device status bits (OR-ed by kernels, read by lp_sync).
+enum : unsigned {
+  kStatusOutOfBox = 1u,
+  kStatusExteriorBandV = 2u,
+};
+
+// Exponential-of-semicircle spreading kernel phi(z) = exp(beta (sqrt(1-z^2) - 1))
+// on |z| < 1, z = (u - l) / (w/2) for grid coordinate u and grid index l.
+struct Kernel {
+  int w;
+  double beta;
+  double half_w;  // w/2
+};
+
+// One periodic grid of the history part (Sec. 3): near history (kind 0,
+// multiplier (e^{-k^2 d1} - e^{-k^2 d2})/k^2) or far history (kind 1,
+// multiplier e^{-k^2 d2} W(k) with truncation radius L).
+struct GridLevel {
+  int kind = 0;
+  int g = 0;          // grid points per dimension (7-smooth, even)
+  int K = 0;          // kept modes |m| <= K per dimension
+  int pitch = 0;      // row pitch of the in-place real layout, 2 (g/2 + 1)
+  double P = 0, dk = 0, h = 0, L = 0, R = 0;
+  double x0 = 0, y0 = 0;  // coordinates of grid index 0
+  double zero_mode = 0;   // (dk/2pi)^2 M(0): the k = 0 multiplier without deconvolution
+  void* chan[4] = {nullptr, nullptr, nullptr, nullptr};  // V, S, D1, D2 in-place buffers
+  double* mtab = nullptr;  // (K+1)^2 deconvolved multiplier table, FP64
+  float* mtab32 = nullptr; // same in FP32 with the zero mode removed (FP32 path)
+  cufftHandle fwd = 0, inv = 0;
+  size_t chan_bytes = 0;
+};
+
+// Grid geometry passed to kernels by value.
+struct GridDev {
+  int g, pitch;
+  double x0, y0, inv_h;
+};
+
+struct Plan {
+  int precision = LP_FP64;
+  int order = 5;
+  double delta1 = 0, delta2 = 0, tol = 0;
+  double box_lo[2] = {0, 0}, box_hi[2] = {0, 0};
+  double side = 0;        // max box extent
+  double on_tol = 0;      // on-surface classification radius
+  Kernel ker{};
+  GridLevel lv[2];
+  cudaStream_t stream = nullptr;
+
+  // boundary
+  int64_t n_panels = 0;
+  int p = 0;              // nodes per panel
+  int64_t nb = 0;         // n_panels * p
+  double* d_bxy = nullptr;     // [nb][2]
+  double* d_bw = nullptr;      // [nb]
+  double* d_bnrm = nullptr;    // [nb][2]
+  double* d_geo_coef = nullptr;  // [n_panels][2][p] Legendre coefficients of x - xref, y - yref
+  double* d_geo_ref = nullptr;   // [n_panels][2] reference (middle node) coordinates
+  double* d_leg_T = nullptr;     // [p][p] values -> Legendre coefficients
+  double* d_tau = nullptr;       // [p] Gauss-Legendre abscissae
+  double margin = 0, band = 0;
+  // uniform hash of boundary nodes for the nearest-node search
+  double hash_x0 = 0, hash_y0 = 0, hash_h = 0;
+  int hash_nx = 0, hash_ny = 0;
+  int* d_cell_start = nullptr;  // [nx*ny + 1]
+  int* d_cell_node = nullptr;   // [nb] node ids sorted by cell
+
+  // bound sources
+  int64_t nv = 0;
+  double* d_vxy = nullptr;   // [nv][2]
+  double* d_vq = nullptr;    // [nv] f w
+  bool have_volume = false;
+  double* d_sigma = nullptr;   // [nb]
+  double* d_sigma_coef = nullptr;  // [n_panels][p] Legendre coefficients (centred)
+  double* d_sigma_ref = nullptr;   // [n_panels]
+  double* d_mu = nullptr;
+  double* d_mu_coef = nullptr;
+  double* d_mu_ref = nullptr;
+  double* d_bq = nullptr;    // [3][nb]: sigma w, mu nu1 w, mu nu2 w
+  bool have_sigma = false, have_mu = false;
+  double* d_qsum = nullptr;  // [2] FP64 sums of the V and S strengths (zero mode)
+
+  // staging for host pointers
+  void* d_stage = nullptr;
+  size_t stage_bytes = 0;
+  double* d_out = nullptr;   // [3][cap] outputs for host destinations
+  size_t out_cap = 0;
+
+  unsigned* d_status = nullptr;
+  unsigned* h_status = nullptr;  // pinned
+  cudaEvent_t ev[kNumStages + 1] = {};
+  size_t device_bytes = 0;
+};
+
+// ---- host helpers (lp_setup.cu) ----
+lp_status choose_levels(Plan& P);
+lp_status build_tables(Plan& P);
+lp_status build_boundary(Plan& P, const double* h_xy, const double* h_w, const double* h_nrm);
+void gauss_legendre(int p, double* x, double* w);
+int fft_size(int n);
+
+// ---- launches (kernels in k_*.cu) ----
+void launch_spread(const Plan& P, int level, const double* xy, const double* const* q, int nq,
+                   void* const* grids, int64_t n, cudaStream_t s);
+void launch_multiplier(const Plan& P, int level, bool want_v, bool want_s, bool want_d,
+                       cudaStream_t s);
+void launch_interp(const Plan& P, int64_t nt, const double* txy, double* V, double* S, double* D,
+                   cudaStream_t s);
+void launch_local(const Plan& P, int64_t nt, const double* txy, const double* jet, double* V,
+                  double* S, double* D, cudaStream_t s);
+void launch_panel_coef(const Plan& P, const double* vals, int stride, int ncomp, double* coef,
+                       double* ref, cudaStream_t s);
+void launch_strengths(const Plan& P, int kind, cudaStream_t s);
+void launch_volume_q(const double* f, const double* w, double* q, int64_t n, cudaStream_t s);
+void launch_sum(const double* x, int64_t n, double* out, cudaStream_t s);
+
+}  // namespace lpg

@@ -1,0 +1,287 @@
+// Plan-time host computations: history-grid sizing (Sec. 2.3 and Sec. 3,
+// Step 1, generalised to an arbitrary box), the deconvolved Fourier
+// multiplier tables (eq. vnearkspace, eq. vfarkspace, eq. Wdef), and the
+// boundary search structures used by the local part (Sec. 2.2, Sec. 4).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "lp_internal.cuh"
+
+namespace lpg {
+
+namespace {
+const double kPi = 3.14159265358979323846;
+
+// Smallest k > 1/sqrt(2 delta) (beyond the maximum of k e^{-k^2 delta}) with
+// k e^{-k^2 delta} < eps: the truncation rule of Sec. 3 (input of the
+// history algorithm), used for every channel.
+double fourier_cutoff(double delta, double eps) {
+  double lo = 1.0 / std::sqrt(2.0 * delta), hi = lo;
+  while (hi * std::exp(-hi * hi * delta) >= eps) hi *= 1.5;
+  for (int i = 0; i < 200; ++i) {
+    double mid = 0.5 * (lo + hi);
+    if (mid * std::exp(-mid * mid * delta) >= eps) lo = mid; else hi = mid;
+  }
+  return hi;
+}
+
+// 1 - J0(z) and J1(z)/z without cancellation at small z (power series),
+// glibc's j0/j1 elsewhere.
+double one_minus_j0(double z) {
+  if (z < 2.0) {
+    double q = 0.25 * z * z, term = 1.0, s = 0.0;
+    for (int k = 1; k < 40; ++k) {
+      term *= -q / ((double)k * k);   // (-q)^k / (k!)^2
+      s -= term;
+      if (std::fabs(term) < 1e-18 * std::fabs(s)) break;
+    }
+    return s;
+  }
+  return 1.0 - j0(z);
+}
+double j1_over_z(double z) {
+  if (z < 2.0) {
+    double q = 0.25 * z * z, term = 0.5, s = 0.5;
+    for (int k = 1; k < 40; ++k) {
+      term *= -q / ((double)k * (k + 1));  // (-q)^k / (2 k! (k+1)!)
+      s += term;
+      if (std::fabs(term) < 1e-18 * std::fabs(s)) break;
+    }
+    return s;
+  }
+  return j1(z) / z;
+}
+
+// ES kernel and its Fourier transform in grid-index units:
+// phihat(xi) = int_{-w/2}^{w/2} phi(2x/w) cos(xi x) dx, by Gauss-Legendre.
+double es_phi(double z, double beta) {
+  if (std::fabs(z) >= 1.0) return 0.0;
+  return std::exp(beta * (std::sqrt(1.0 - z * z) - 1.0));
+}
+}  // namespace
+
+void gauss_legendre(int p, double* x, double* w) {
+  // Newton on P_p from Chebyshev-like initial guesses; ascending order.
+  for (int i = 0; i < p; ++i) {
+    double z = std::cos(kPi * (i + 0.75) / (p + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= p; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = p * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[p - 1 - i] = z;
+    w[p - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+int fft_size(int n) {
+  int m = std::max(n, 8);
+  if (m & 1) ++m;
+  for (;; m += 2) {
+    int k = m;
+    for (int f : {2, 3, 5, 7})
+      while (k % f == 0) k /= f;
+    if (k == 1) return m;
+  }
+}
+
+lp_status choose_levels(Plan& P) {
+  const double eps = P.tol;
+  const double D = P.side;
+  const double cx = 0.5 * (P.box_lo[0] + P.box_hi[0]);
+  const double cy = 0.5 * (P.box_lo[1] + P.box_hi[1]);
+  // Reach of the Gaussian tails beyond which the history kernels are below
+  // eps: e^{-R^2 / (4 delta_2)} = eps.
+  const double R = std::sqrt(4.0 * P.delta2 * std::log(1.0 / eps));
+  for (int l = 0; l < 2; ++l) {
+    GridLevel& G = P.lv[l];
+    G.kind = l;
+    G.R = R;
+    double kmax;
+    if (l == 0) {
+      kmax = fourier_cutoff(P.delta1, 0.1 * eps);
+      G.P = D + R;                 // period excludes aliasing of F_NH over the box
+      G.L = 0.0;
+    } else {
+      kmax = fourier_cutoff(P.delta2, 0.1 * eps);
+      G.L = std::sqrt(2.0) * D + R;  // truncation radius of eq. Wdef, generalised
+      G.P = D + G.L + R;
+    }
+    G.dk = 2.0 * kPi / G.P;
+    G.K = (int)std::ceil(kmax / G.dk);
+    int g = fft_size(std::max(2 * (2 * G.K + 1), 2 * P.ker.w + 8));
+    // the spreading stencil of every point in the box must stay inside the
+    // grid (no periodic wrap): margin (P - D)/2 >= (w/2 + 2) h
+    while ((G.P - D) / 2.0 < (P.ker.half_w + 2.0) * (G.P / g)) g = fft_size(g + 2);
+    G.g = g;
+    G.h = G.P / g;
+    G.pitch = 2 * (g / 2 + 1);
+    G.x0 = cx - 0.5 * G.P;
+    G.y0 = cy - 0.5 * G.P;
+    if (G.K > g / 2 - 1) return LP_ERR_ARG;
+  }
+  return LP_OK;
+}
+
+lp_status build_tables(Plan& P) {
+  const int w = P.ker.w;
+  const double beta = P.ker.beta;
+  const int nq = 4 * w + 8;
+  std::vector<double> qx(nq), qw(nq);
+  gauss_legendre(nq, qx.data(), qw.data());
+  for (int l = 0; l < 2; ++l) {
+    GridLevel& G = P.lv[l];
+    const int K = G.K;
+    std::vector<double> ph(K + 1);
+    for (int m = 0; m <= K; ++m) {
+      double xi = 2.0 * kPi * m / G.g, s = 0.0;
+      for (int i = 0; i < nq; ++i) {
+        double x = 0.25 * w * (qx[i] + 1.0);  // [0, w/2]
+        s += qw[i] * es_phi(2.0 * x / w, beta) * std::cos(xi * x);
+      }
+      ph[m] = 2.0 * 0.25 * w * s;  // even integrand over [-w/2, w/2]
+    }
+    std::vector<double> tab((size_t)(K + 1) * (K + 1));
+    std::vector<float> tab32(tab.size());
+    const double scale = (G.dk / (2.0 * kPi)) * (G.dk / (2.0 * kPi));
+    for (int my = 0; my <= K; ++my) {
+      for (int mx = 0; mx <= K; ++mx) {
+        double k = G.dk * std::sqrt((double)mx * mx + (double)my * my);
+        double M;
+        if (l == 0) {
+          // (e^{-k^2 d1} - e^{-k^2 d2}) / k^2   (eq. vnearkspace)
+          M = (k == 0.0) ? (P.delta2 - P.delta1)
+                         : (std::expm1(-k * k * P.delta1) - std::expm1(-k * k * P.delta2)) / (k * k);
+        } else {
+          // e^{-k^2 d2} W(k), W = (1 - J0(Lk))/k^2 - L log L J1(Lk)/k   (eq. Wdef)
+          double L = G.L, z = L * k;
+          double W = L * L * (one_minus_j0(z) / (z * z > 0 ? z * z : 1.0));
+          if (z == 0.0) W = L * L * 0.25;
+          W -= L * L * std::log(L) * j1_over_z(z);
+          M = std::exp(-k * k * P.delta2) * W;
+        }
+        if (mx == 0 && my == 0) G.zero_mode = scale * M;
+        double d = ph[mx] * ph[my];
+        double v = scale * M / (d * d);
+        tab[(size_t)my * (K + 1) + mx] = v;
+        tab32[(size_t)my * (K + 1) + mx] = (mx == 0 && my == 0) ? 0.0f : (float)v;
+      }
+    }
+    if (cudaMalloc(&G.mtab, tab.size() * sizeof(double)) != cudaSuccess) return LP_ERR_NOMEM;
+    if (cudaMalloc(&G.mtab32, tab32.size() * sizeof(float)) != cudaSuccess) return LP_ERR_NOMEM;
+    P.device_bytes += tab.size() * (sizeof(double) + sizeof(float));
+    cudaMemcpy(G.mtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(G.mtab32, tab32.data(), tab32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  }
+  return LP_OK;
+}
+
+lp_status build_boundary(Plan& P, const double* h_xy, const double* h_w, const double* h_nrm) {
+  const int p = P.p;
+  const int64_t nb = P.nb;
+  // margin: longest chord between consecutive nodes along the curve; any
+  // point of the curve is within it of a node, so a target whose nearest
+  // node is farther than band + margin is outside the band.
+  double margin = 0.0;
+  for (int64_t j = 0; j < nb; ++j) {
+    int64_t k = (j + 1) % nb;
+    margin = std::max(margin, std::hypot(h_xy[2 * k] - h_xy[2 * j], h_xy[2 * k + 1] - h_xy[2 * j + 1]));
+  }
+  P.margin = margin;
+  P.band = 12.0 * std::sqrt(P.delta1);
+  // hash of nodes: cells of side >= band + margin over the box (+ one cell)
+  double hc = P.band + P.margin;
+  double lo0 = P.box_lo[0], lo1 = P.box_lo[1], hi0 = P.box_hi[0], hi1 = P.box_hi[1];
+  for (int64_t j = 0; j < nb; ++j) {
+    lo0 = std::min(lo0, h_xy[2 * j]);
+    hi0 = std::max(hi0, h_xy[2 * j]);
+    lo1 = std::min(lo1, h_xy[2 * j + 1]);
+    hi1 = std::max(hi1, h_xy[2 * j + 1]);
+  }
+  int nx = std::max(1, (int)std::ceil((hi0 - lo0) / hc) + 2);
+  int ny = std::max(1, (int)std::ceil((hi1 - lo1) / hc) + 2);
+  while ((int64_t)nx * ny > (int64_t)1 << 24) {  // bound the table for tiny deltas
+    hc *= 2.0;
+    nx = std::max(1, (int)std::ceil((hi0 - lo0) / hc) + 2);
+    ny = std::max(1, (int)std::ceil((hi1 - lo1) / hc) + 2);
+  }
+  P.hash_h = hc;
+  P.hash_x0 = lo0 - hc;
+  P.hash_y0 = lo1 - hc;
+  P.hash_nx = nx;
+  P.hash_ny = ny;
+  std::vector<int> cnt((size_t)nx * ny + 1, 0), cell(nb), order(nb);
+  for (int64_t j = 0; j < nb; ++j) {
+    int cx = (int)std::floor((h_xy[2 * j] - P.hash_x0) / hc);
+    int cy = (int)std::floor((h_xy[2 * j + 1] - P.hash_y0) / hc);
+    cx = std::min(std::max(cx, 0), nx - 1);
+    cy = std::min(std::max(cy, 0), ny - 1);
+    cell[j] = cy * nx + cx;
+    cnt[cell[j] + 1]++;
+  }
+  for (size_t c = 0; c + 1 < cnt.size(); ++c) cnt[c + 1] += cnt[c];
+  std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+  for (int64_t j = 0; j < nb; ++j) order[fill[cell[j]]++] = (int)j;  // stable: ascending ids
+
+  // Legendre transform of the panel interpolant: coef_k = (2k+1)/2 sum_i w_i v_i P_k(tau_i)
+  std::vector<double> tau(p), wq(p), T((size_t)p * p);
+  gauss_legendre(p, tau.data(), wq.data());
+  for (int i = 0; i < p; ++i) {
+    double p0 = 1.0, p1 = tau[i];
+    for (int k = 0; k < p; ++k) {
+      double pk;
+      if (k == 0) pk = 1.0;
+      else if (k == 1) pk = tau[i];
+      else {
+        double p2 = ((2.0 * k - 1.0) * tau[i] * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+        pk = p2;
+      }
+      T[(size_t)k * p + i] = 0.5 * (2.0 * k + 1.0) * wq[i] * pk;
+    }
+  }
+  auto dmalloc = [&](void** ptr, size_t bytes) -> bool {
+    if (cudaMalloc(ptr, bytes) != cudaSuccess) return false;
+    P.device_bytes += bytes;
+    return true;
+  };
+  if (!dmalloc((void**)&P.d_bxy, nb * 2 * sizeof(double)) ||
+      !dmalloc((void**)&P.d_bw, nb * sizeof(double)) ||
+      !dmalloc((void**)&P.d_bnrm, nb * 2 * sizeof(double)) ||
+      !dmalloc((void**)&P.d_geo_coef, (size_t)P.n_panels * 2 * p * sizeof(double)) ||
+      !dmalloc((void**)&P.d_geo_ref, (size_t)P.n_panels * 2 * sizeof(double)) ||
+      !dmalloc((void**)&P.d_leg_T, (size_t)p * p * sizeof(double)) ||
+      !dmalloc((void**)&P.d_tau, p * sizeof(double)) ||
+      !dmalloc((void**)&P.d_cell_start, cnt.size() * sizeof(int)) ||
+      !dmalloc((void**)&P.d_cell_node, std::max<int64_t>(nb, 1) * sizeof(int)) ||
+      !dmalloc((void**)&P.d_bq, 3 * nb * sizeof(double)) ||
+      !dmalloc((void**)&P.d_sigma, nb * sizeof(double)) ||
+      !dmalloc((void**)&P.d_mu, nb * sizeof(double)) ||
+      !dmalloc((void**)&P.d_sigma_coef, (size_t)P.n_panels * p * sizeof(double)) ||
+      !dmalloc((void**)&P.d_sigma_ref, (size_t)P.n_panels * sizeof(double)) ||
+      !dmalloc((void**)&P.d_mu_coef, (size_t)P.n_panels * p * sizeof(double)) ||
+      !dmalloc((void**)&P.d_mu_ref, (size_t)P.n_panels * sizeof(double)))
+    return LP_ERR_NOMEM;
+  cudaMemcpy(P.d_bxy, h_xy, nb * 2 * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(P.d_bw, h_w, nb * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(P.d_bnrm, h_nrm, nb * 2 * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(P.d_leg_T, T.data(), T.size() * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(P.d_tau, tau.data(), p * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(P.d_cell_start, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (nb) cudaMemcpy(P.d_cell_node, order.data(), nb * sizeof(int), cudaMemcpyHostToDevice);
+  launch_panel_coef(P, P.d_bxy, 2, 2, P.d_geo_coef, P.d_geo_ref, P.stream);
+  if (cudaStreamSynchronize(P.stream) != cudaSuccess) return LP_ERR_CUDA;
+  return LP_OK;
+}
+
+}  // namespace lpg
