@@ -1,0 +1,464 @@
+#!/usr/bin/env python
+"""Benchmark of the V + S + D evaluation (heat-kernel splitting, arXiv 2409.11998).
+
+Metric: source + target points per second, where one step evaluates V[f],
+S[sigma] and D[mu] at every target of the workload through the C ABI:
+lp_volume + lp_single_layer + lp_double_layer (bind the step's sources and
+densities) + lp_execute (spread, FFTs, multiplier, interpolation, local part).
+Points per step = N_V + N_B + N_t.
+
+Default workload: the starfish r = 1 + 0.3 cos 5t with a degraded ~190k
+triangle mesh (6 nodes per triangle), 1,024 x 16 boundary nodes, targets =
+all quadrature nodes, FP64 at tolerance 1e-9.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lp|reference]
+
+--impl reference times the FP64 CPU oracle (direct sums of the smoothed
+kernel plus the same local expansions) on the host cores, on a bounded
+sample of targets per step, and reports the same metric extrapolated to the
+whole workload.  With N > 1 (torchrun), every rank runs an independent
+replica of the workload on its own GPU (weak scaling, no collective on the
+data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "source+target points/sec at 1e-9 (FP64) / 1e-5 (FP32) rel-L2; served p50/p99 latency"
+UNIT = "points/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lp", choices=["lp", "reference"])
+    ap.add_argument("--workload", default="starfish", choices=["starfish", "disk", "square"])
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline, fp32 line")
+    return ap.parse_args()
+
+
+def make_problem(name):
+    from workloads import configs
+    if name == "starfish":
+        return configs.starfish()
+    if name == "disk":
+        return configs.disk()
+    if name == "square":
+        return configs.square(precision="fp64", tol=1e-9)
+    raise ValueError(name)
+
+
+def describe(prob):
+    m = prob["meta"]
+    nb = len(prob["bnd"]["w"]) if prob["bnd"] is not None else 0
+    desc = {
+        "starfish": "starfish r=1+0.3cos5t, degraded Delaunay mesh (slivers with aspect ratio "
+                    "log-uniform in [1,1e4], 2% non-conforming edges, 1% triangles removed), "
+                    "6-node rule, 1024x16 boundary nodes, targets = all quadrature nodes",
+        "disk": "unit disk, 2000 random-Delaunay triangles, 6-node rule, 64x16 boundary nodes, "
+                "targets = vertices + 512 exterior points",
+        "square": "[-1,1]^2, 2M jittered triangles, 6-node rule, targets = vertices",
+    }[prob["name"]]
+    return {"workload": desc, "n_triangles": m.get("n_triangles"), "n_sources": len(prob["src_w"]),
+            "n_boundary_nodes": nb, "n_targets": len(prob["tgt_xy"]), "delta1": prob["delta"],
+            "tol": prob["tol"]}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(parts)
+            except Exception:
+                pass
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_traffic(name):
+    """DRAM bytes per launch of a kernel from a committed ncu summary, valid
+    only while the kernel sources are unchanged (sha of csrc/*.cu,*.cuh)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    ent = d.get(name)
+    if not ent or ent.get("source_sha") != source_sha():
+        return None
+    return ent.get("bytes_per_launch")
+
+
+def source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2409_11998_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_lp(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import paper_2409_11998_gb300 as lp
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    prob = make_problem(args.workload)
+    nv, nb, nt = len(prob["src_w"]), len(prob["bnd"]["w"]), len(prob["tgt_xy"])
+    points = nv + nb + nt
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    sxy, sw, sf = T(prob["src_xy"]), T(prob["src_w"]), T(prob["src_f"])
+    sig, mu = T(prob["sigma"]), T(prob["mu"])
+    txy, jet = T(prob["tgt_xy"]), T(prob["tgt_jet"])
+    outs = [torch.empty(nt, dtype=torch.float64, device=dev) for _ in range(3)]
+    stream = torch.cuda.Stream(device=dev)
+    ev = lp.Evaluator(prob, precision="fp64", stream=stream.cuda_stream)
+    plan = ev.plan
+
+    def step():
+        lp.lp_volume(plan, nv, sxy, sw, sf)
+        lp.lp_single_layer(plan, sig)
+        lp.lp_double_layer(plan, mu)
+        lp.lp_execute(plan, nt, txy, jet, outs[0], outs[1], outs[2])
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        step()
+        lp.lp_sync(plan)
+    launches0 = lp.lp_plan_info(plan)["launches"]
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stages = []
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local_rank)
+    clk.start()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))          # evict L2 between steps (outside the step's events)
+            e0[k].record(stream)
+            step()
+            e1[k].record(stream)
+        lp.lp_sync(plan)
+        stages.append(lp.lp_stage_times(plan))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks = clk.stop()
+    barrier(world)
+    launches = lp.lp_plan_info(plan)["launches"] - launches0
+    step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
+    total_ms = sum(step_ms)
+    total_ms = max_over_ranks(total_ms, world)
+    value = points * args.steps * world / (total_ms / 1e3)
+    info = lp.lp_plan_info(plan)
+    st = {k: statistics.mean(s[k] for s in stages) for k in stages[0]}
+
+    # roofline of the dominant kernel stage (spread or interpolation), FP64
+    b = 8
+    g2 = info["g_nh"] ** 2 + info["g_fh"] ** 2
+    spread_bytes = (nv + nb) * 2 * b + (nv + 3 * nb) * b + g2 * b * 4
+    interp_bytes = g2 * b * 3 + nt * (2 * b + 8 * 3)
+    peak, peak_kind = peaks()
+    cand = {"spread": (st["spread"], spread_bytes), "interp": (st["interp"], interp_bytes)}
+    dom = max(cand, key=lambda k: cand[k][0])
+    ms, byts = cand[dom]
+    achieved = byts / (ms / 1e3) / 1e9
+    kname = {"spread": "spread_atomic_kernel", "interp": "interp_kernel"}[dom]
+    roof = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 2), "peak": peak,
+            "unit": "GB/s", "frac": round(achieved / peak, 5), "traffic": kernel_traffic(kname),
+            "algorithmic_bytes_per_launch": int(byts), "launch_ms": round(ms, 4),
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"}
+
+    res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded generators; no dataset)",
+           "config": {**describe(prob), "parallelism": "replicas" if world > 1 else "single",
+                      "l2": "flushed by a 512 MiB write between timed steps, outside the step events",
+                      "timing": "CUDA events on the plan stream around each step",
+                      "grids": {"g_nh": int(info["g_nh"]), "g_fh": int(info["g_fh"]), "w": int(info["w"])}},
+           "stages_ms": {k: round(v, 4) for k, v in st.items()},
+           "roofline": roof, "gpu_launches": int(launches), "wall_s_timed_region": round(wall, 3),
+           "clocks": clocks}
+
+    if rank == 0 and not args.no_extras:
+        res["parity"] = parity_sample(prob, outs)
+        res["e2e"] = run_e2e(args, prob, dev, ev, points)
+        res["fp32_same_workload"] = run_fp32(args, prob, dev, stream, points)
+        if world == 1:
+            res["cpu_baseline"] = cpu_baseline(prob, budget_s=15.0)
+    ev.close()
+    return res
+
+
+def parity_sample(prob, outs, n=48):
+    import numpy as np
+    import oracle
+    idx = np.random.default_rng(11).choice(len(prob["tgt_xy"]), n, replace=False)
+    ref = oracle.evaluate(prob, targets=idx)
+    r = {}
+    for k, o in zip("VSD", outs):
+        got = o.cpu().numpy()[idx]
+        r[f"{k}_rel_l2"] = float(np.linalg.norm(got - ref[k]) / np.linalg.norm(ref[k]))
+    r["n_sample_targets"] = n
+    return r
+
+
+def run_e2e(args, prob, dev, ev, points):
+    """Same metric through the C ABI with HOST (pinned) buffers: every step
+    copies the step's sources, densities, targets and jets to the device and
+    reads V, S, D back."""
+    import numpy as np
+    import torch
+    import paper_2409_11998_gb300 as lp
+    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
+    h = {k: pin(prob[k]) for k in ("src_xy", "src_w", "src_f", "sigma", "mu", "tgt_xy", "tgt_jet")}
+    nt = len(prob["tgt_xy"])
+    houts = [torch.empty(nt, dtype=torch.float64).pin_memory() for _ in range(3)]
+    plan = ev.plan
+    nv = len(prob["src_w"])
+
+    def step():
+        lp.lp_volume(plan, nv, h["src_xy"], h["src_w"], h["src_f"])
+        lp.lp_single_layer(plan, h["sigma"])
+        lp.lp_double_layer(plan, h["mu"])
+        lp.lp_execute(plan, nt, h["tgt_xy"], h["tgt_jet"], houts[0], houts[1], houts[2])
+        lp.lp_sync(plan)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    n = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(n):
+        step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / n
+    h2d = sum(h[k].numel() * 8 for k in h)
+    d2h = 3 * nt * 8
+    return {"value": points / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3, "steps": n,
+            "api": "lp_volume/lp_single_layer/lp_double_layer/lp_execute/lp_sync on pinned host buffers"}
+
+
+def run_fp32(args, prob, dev, stream, points):
+    import numpy as np
+    import torch
+    import oracle
+    import paper_2409_11998_gb300 as lp
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    ev = lp.Evaluator(prob, precision="fp32", tol=1e-5, stream=stream.cuda_stream)
+    nv, nt = len(prob["src_w"]), len(prob["tgt_xy"])
+    sxy, sw, sf, sig, mu, txy, jet = (T(prob[k]) for k in ("src_xy", "src_w", "src_f", "sigma", "mu", "tgt_xy", "tgt_jet"))
+    outs = [torch.empty(nt, dtype=torch.float64, device=dev) for _ in range(3)]
+    plan = ev.plan
+
+    def step():
+        lp.lp_volume(plan, nv, sxy, sw, sf)
+        lp.lp_single_layer(plan, sig)
+        lp.lp_double_layer(plan, mu)
+        lp.lp_execute(plan, nt, txy, jet, *outs)
+
+    for _ in range(3):
+        step()
+        lp.lp_sync(plan)
+    ms = []
+    for _ in range(max(3, args.steps // 2)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        lp.lp_sync(plan)
+        ms.append(a.elapsed_time(b))
+    st = lp.lp_stage_times(plan)
+    par = parity_sample(prob, outs)
+    ev.close()
+    return {"value": points / (statistics.mean(ms) / 1e3), "unit": UNIT, "dtype": "f32 (FP64 zero mode)",
+            "tol": 1e-5, "ms_per_step": statistics.mean(ms),
+            "stages_ms": {k: round(v, 4) for k, v in st.items()}, "parity": par}
+
+
+def cpu_baseline(prob, budget_s=15.0):
+    """The oracle as it stands, on the host cores, on a bounded sample of
+    targets; extrapolated to the workload's points/s."""
+    import numpy as np
+    ncores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(ncores))
+    import oracle
+    nt = len(prob["tgt_xy"])
+    rng = np.random.default_rng(5)
+    n = 32
+    while True:
+        idx = rng.choice(nt, n, replace=False)
+        t0 = time.perf_counter()
+        oracle.evaluate(prob, targets=idx)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 4 or n >= nt:
+            break
+        n = min(nt, int(n * max(2.0, budget_s / 2 / max(dt, 1e-3))))
+    per_target = dt / n
+    t_full = per_target * nt
+    points = len(prob["src_w"]) + len(prob["bnd"]["w"]) + nt
+    return {"value": points / t_full, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", ncores)),
+            "kind": "oracle", "sample": f"{n} of {nt} targets (all sources), {dt:.2f} s; "
+            f"extrapolated linearly in targets to the full workload ({t_full:.0f} s)"}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    import numpy as np
+    if rank != 0:
+        return None
+    ncores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(ncores))
+    import oracle
+    prob = make_problem(args.workload)
+    nt = len(prob["tgt_xy"])
+    points = len(prob["src_w"]) + len(prob["bnd"]["w"]) + nt
+    rng = np.random.default_rng(7)
+    # size each step so that warmup + steps take about two minutes
+    per_step = max(0.3, 120.0 / (args.steps + args.warmup))
+    n = 16
+    t0 = time.perf_counter()
+    oracle.evaluate(prob, targets=rng.choice(nt, n, replace=False))
+    per_target = (time.perf_counter() - t0) / n
+    n = int(min(nt, max(8, per_step / max(per_target, 1e-9))))
+    for _ in range(args.warmup):
+        oracle.evaluate(prob, targets=rng.choice(nt, n, replace=False))
+    times = []
+    for _ in range(args.steps):
+        idx = rng.choice(nt, n, replace=False)
+        t0 = time.perf_counter()
+        oracle.evaluate(prob, targets=idx)
+        times.append(time.perf_counter() - t0)
+    dt = statistics.mean(times)
+    t_full = dt / n * nt
+    value = points / t_full
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded generators; no dataset)",
+            "config": {**describe(prob), "parallelism": "host cores (OpenMP over targets)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+                             "kind": "oracle",
+                             "sample": f"{n} random targets per step (all {len(prob['src_w'])} sources "
+                                       f"and {len(prob['bnd']['w'])} boundary nodes); points/s "
+                                       f"extrapolated linearly in targets"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ---------------------------------------------------------------- distributed helpers
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "gloo"
+        dist.init_process_group(backend=backend, rank=rank, world_size=world)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init()
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        res = run_lp(args, rank, world, local)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

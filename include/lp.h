@@ -128,14 +128,15 @@ lp_status lp_destroy(lp_plan_t plan);
 const char* lp_status_string(lp_status status);
 
 /* Plan parameters, for diagnostics and benchmarks:
- * out[0..15] = {delta_1, delta_2, kernel width w, beta, g_NH, K_NH, P_NH, g_FH, K_FH,
+ * out[0..16] = {delta_1, delta_2, kernel width w, beta, g_NH, K_NH, P_NH, g_FH, K_FH,
  *               P_FH, L_FH, band 12 sqrt(delta_1), node-gap margin, device bytes,
- *               precision, order}. */
+ *               precision, order, kernels launched by this plan so far}. */
 lp_status lp_plan_info(lp_plan_t plan, double* out);
 
 /* Per-stage device times of the last lp_execute in milliseconds (CUDA events
- * on the plan's stream; valid after lp_sync): out[0..7] = {spread, forward
- * FFT, multiplier, inverse FFT, interpolation, local, total, copies}. */
+ * on the plan's stream; valid after lp_sync): out[0..8] = {spread, forward
+ * FFT, multiplier, inverse FFT, interpolation, local, total, copies, grid
+ * zeroing}. */
 lp_status lp_stage_times(lp_plan_t plan, float* out);
 
 #ifdef __cplusplus

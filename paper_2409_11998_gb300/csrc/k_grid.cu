@@ -206,6 +206,7 @@ void launch_spread(const Plan& P, int level, const double* xy, const double* con
   a.status = P.d_status;
   int threads = 128;
   unsigned blocks = (unsigned)((n + threads - 1) / threads);
+  ++P.launches;
   if (P.precision == LP_FP64)
     spread_atomic_kernel<double><<<blocks, threads, 0, s>>>(a);
   else
@@ -218,6 +219,7 @@ void launch_multiplier(const Plan& P, int level, bool want_v, bool want_s, bool 
   int64_t total = (int64_t)G.g * (G.g / 2 + 1);
   int threads = 256;
   unsigned blocks = (unsigned)((total + threads - 1) / threads);
+  ++P.launches;
   if (P.precision == LP_FP64) {
     using C = cufftDoubleComplex;
     multiplier_kernel<C, double><<<blocks, threads, 0, s>>>(
@@ -250,6 +252,7 @@ void launch_interp(const Plan& P, int64_t nt, const double* txy, double* V, doub
   a.zero_factor = P.lv[0].zero_mode + P.lv[1].zero_mode;
   int threads = 128;
   unsigned blocks = (unsigned)((nt + threads - 1) / threads);
+  ++P.launches;
   if (P.precision == LP_FP64) {
     interp_kernel<double><<<blocks, threads, 0, s>>>(a);
   } else {

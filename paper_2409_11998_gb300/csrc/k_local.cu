@@ -306,6 +306,7 @@ void launch_local(const Plan& P, int64_t nt, const double* txy, const double* je
   a.status = P.d_status;
   int threads = 128;
   unsigned blocks = (unsigned)((nt + threads - 1) / threads);
+  ++P.launches;
   local_kernel<<<blocks, threads, 0, s>>>(a);
 }
 

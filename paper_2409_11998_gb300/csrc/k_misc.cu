@@ -70,6 +70,7 @@ void launch_panel_coef(const Plan& P, const double* vals, int stride, int ncomp,
   int64_t total = P.n_panels * ncomp * P.p;
   if (total <= 0) return;
   int threads = 128;
+  ++P.launches;
   panel_coef_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, s>>>(
       vals, stride, ncomp, P.p, P.n_panels, P.d_leg_T, coef, ref);
 }
@@ -78,22 +79,26 @@ void launch_strengths(const Plan& P, int kind, cudaStream_t s) {
   if (P.nb <= 0) return;
   int threads = 256;
   const double* dens = kind == 0 ? P.d_sigma : P.d_mu;
+  ++P.launches;
   strengths_kernel<<<(unsigned)((P.nb + threads - 1) / threads), threads, 0, s>>>(
       kind, dens, P.d_bw, P.d_bnrm, P.d_bq, P.nb);
 }
 
-void launch_volume_q(const double* f, const double* w, double* q, int64_t n, cudaStream_t s) {
+void launch_volume_q(const Plan& P, const double* f, const double* w, double* q, int64_t n,
+                     cudaStream_t s) {
   if (n <= 0) return;
   int threads = 256;
+  ++P.launches;
   volume_q_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(f, w, q, n);
 }
 
-void launch_sum(const double* x, int64_t n, double* out, cudaStream_t s) {
+void launch_sum(const Plan& P, const double* x, int64_t n, double* out, cudaStream_t s) {
   cudaMemsetAsync(out, 0, sizeof(double), s);
   if (n <= 0) return;
   int threads = 256;
   int64_t blocks = (n + threads - 1) / threads;
   if (blocks > 1024) blocks = 1024;
+  ++P.launches;
   sum_kernel<<<(unsigned)blocks, threads, 0, s>>>(x, n, out);
 }
 

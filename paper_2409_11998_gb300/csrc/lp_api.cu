@@ -274,9 +274,9 @@ lp_status lp_volume(lp_plan_t h, int64_t n, const double* xy, const double* w, c
     const double* dw = device_view(P, w, n, &off);
     const double* df = device_view(P, f, n, &off);
     cudaMemcpyAsync(P.d_vxy, dxy, n * 2 * sizeof(double), cudaMemcpyDeviceToDevice, P.stream);
-    launch_volume_q(df, dw, P.d_vq, n, P.stream);
+    launch_volume_q(P, df, dw, P.d_vq, n, P.stream);
   }
-  launch_sum(P.d_vq, n, P.d_qsum, P.stream);
+  launch_sum(P, P.d_vq, n, P.d_qsum, P.stream);
   P.have_volume = true;
   return status_from_cuda();
 }
@@ -294,7 +294,7 @@ static lp_status bind_layer(lp_plan_t h, const double* dens, int kind) {
                     kind == 0 ? P.d_sigma_ref : P.d_mu_ref, P.stream);
   launch_strengths(P, kind, P.stream);
   if (kind == 0) {
-    launch_sum(P.d_bq, P.nb, P.d_qsum + 1, P.stream);
+    launch_sum(P, P.d_bq, P.nb, P.d_qsum + 1, P.stream);
     P.have_sigma = true;
   } else {
     P.have_mu = true;
@@ -350,6 +350,10 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
       cudaMemsetAsync(G.chan[2], 0, G.chan_bytes, s);
       cudaMemsetAsync(G.chan[3], 0, G.chan_bytes, s);
     }
+  }
+  cudaEventRecord(P.ev[2], s);
+  for (int l = 0; l < 2; ++l) {
+    GridLevel& G = P.lv[l];
     if (wv && P.nv > 0) {
       const double* q[1] = {P.d_vq};
       void* g[1] = {G.chan[0]};
@@ -370,7 +374,7 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
     }
     if (nq) launch_spread(P, l, P.d_bxy, bq, nq, bg, P.nb, s);
   }
-  cudaEventRecord(P.ev[2], s);
+  cudaEventRecord(P.ev[3], s);
   const bool f64 = P.precision == LP_FP64;
   auto fwd = [&](GridLevel& G, int c) {
     if (f64)
@@ -392,23 +396,23 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
       fwd(P.lv[l], 3);
     }
   }
-  cudaEventRecord(P.ev[3], s);
+  cudaEventRecord(P.ev[4], s);
   // Step 4: deconvolved multiplier (in place; D written to channel 2)
   for (int l = 0; l < 2; ++l) launch_multiplier(P, l, wv, ws, wd, s);
-  cudaEventRecord(P.ev[4], s);
+  cudaEventRecord(P.ev[5], s);
   for (int l = 0; l < 2; ++l) {
     if (wv) inv(P.lv[l], 0);
     if (ws) inv(P.lv[l], 1);
     if (wd) inv(P.lv[l], 2);
   }
-  cudaEventRecord(P.ev[5], s);
-  launch_interp(P, nt, dt, dout[0], dout[1], dout[2], s);
   cudaEventRecord(P.ev[6], s);
-  launch_local(P, nt, dt, dj, dout[0], dout[1], dout[2], s);
+  launch_interp(P, nt, dt, dout[0], dout[1], dout[2], s);
   cudaEventRecord(P.ev[7], s);
+  launch_local(P, nt, dt, dj, dout[0], dout[1], dout[2], s);
+  cudaEventRecord(P.ev[8], s);
   for (int c = 0; c < 3; ++c)
     if (host_out[c]) cudaMemcpyAsync(outs[c], dout[c], nt * sizeof(double), cudaMemcpyDeviceToHost, s);
-  cudaEventRecord(P.ev[8], s);
+  cudaEventRecord(P.ev[9], s);
   return status_from_cuda();
 }
 
@@ -435,9 +439,10 @@ lp_status lp_destroy(lp_plan_t h) {
 lp_status lp_plan_info(lp_plan_t h, double* out) {
   if (!h || !out) return LP_ERR_ARG;
   const Plan& P = h->P;
-  double v[16] = {P.delta1, P.delta2, (double)P.ker.w, P.ker.beta, (double)P.lv[0].g, (double)P.lv[0].K,
+  double v[17] = {P.delta1, P.delta2, (double)P.ker.w, P.ker.beta, (double)P.lv[0].g, (double)P.lv[0].K,
                   P.lv[0].P, (double)P.lv[1].g, (double)P.lv[1].K, P.lv[1].P, P.lv[1].L, P.band,
-                  P.margin, (double)P.device_bytes, (double)P.precision, (double)P.order};
+                  P.margin, (double)P.device_bytes, (double)P.precision, (double)P.order,
+                  (double)P.launches};
   std::memcpy(out, v, sizeof(v));
   return LP_OK;
 }
@@ -445,7 +450,8 @@ lp_status lp_plan_info(lp_plan_t h, double* out) {
 lp_status lp_stage_times(lp_plan_t h, float* out) {
   if (!h || !out) return LP_ERR_ARG;
   Plan& P = h->P;
-  // events: 0 start, 1 staged, 2 spread, 3 fwd, 4 mult, 5 inv, 6 interp, 7 local, 8 copies
+  // events: 0 start, 1 staged, 2 zeroed, 3 spread, 4 fwd, 5 mult, 6 inv, 7 interp,
+  // 8 local, 9 copies
   auto el = [&](int a, int b) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, P.ev[a], P.ev[b]) != cudaSuccess) {
@@ -454,14 +460,15 @@ lp_status lp_stage_times(lp_plan_t h, float* out) {
     }
     return ms;
   };
-  out[0] = el(1, 2);
-  out[1] = el(2, 3);
-  out[2] = el(3, 4);
-  out[3] = el(4, 5);
-  out[4] = el(5, 6);
-  out[5] = el(6, 7);
-  out[6] = el(0, 8);
-  out[7] = el(0, 1) + el(7, 8);
+  out[0] = el(2, 3);
+  out[1] = el(3, 4);
+  out[2] = el(4, 5);
+  out[3] = el(5, 6);
+  out[4] = el(6, 7);
+  out[5] = el(7, 8);
+  out[6] = el(0, 9);
+  out[7] = el(0, 1) + el(8, 9);
+  out[8] = el(1, 2);
   return LP_OK;
 }
 

@@ -14,7 +14,7 @@ namespace lpg {
 
 constexpr int kMaxW = 16;           // widest spreading kernel (grid points)
 constexpr int kMaxPanelOrder = 32;  // Gauss-Legendre nodes per boundary panel
-constexpr int kNumStages = 8;
+constexpr int kNumEvents = 10;
 
 // Device status bits (OR-ed by kernels, read by lp_sync).
 enum : unsigned {
@@ -106,8 +106,9 @@ struct Plan {
 
   unsigned* d_status = nullptr;
   unsigned* h_status = nullptr;  // pinned
-  cudaEvent_t ev[kNumStages + 1] = {};
+  cudaEvent_t ev[kNumEvents] = {};
   size_t device_bytes = 0;
+  mutable long long launches = 0;  // kernels launched by this plan (all calls)
 };
 
 // ---- host helpers (lp_setup.cu) ----
@@ -129,7 +130,8 @@ void launch_local(const Plan& P, int64_t nt, const double* txy, const double* je
 void launch_panel_coef(const Plan& P, const double* vals, int stride, int ncomp, double* coef,
                        double* ref, cudaStream_t s);
 void launch_strengths(const Plan& P, int kind, cudaStream_t s);
-void launch_volume_q(const double* f, const double* w, double* q, int64_t n, cudaStream_t s);
-void launch_sum(const double* x, int64_t n, double* out, cudaStream_t s);
+void launch_volume_q(const Plan& P, const double* f, const double* w, double* q, int64_t n,
+                     cudaStream_t s);
+void launch_sum(const Plan& P, const double* x, int64_t n, double* out, cudaStream_t s);
 
 }  // namespace lpg
