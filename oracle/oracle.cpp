@@ -27,7 +27,8 @@
 //   * Density and curve derivatives are with respect to the tangent-line
 //     coordinate xi (Sec. 4, eq. tanparams), obtained by series reversion.
 //   * Closest point: nearest boundary node, then Newton to |dt| < 1e-14
-//     (at most 20 steps) on that node's panel and its two neighbours.
+//     (at most 20 steps) on that node's panel; when the iterate stops at a
+//     panel end, Newton again on the adjacent panel past that end.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -458,10 +459,14 @@ int oracle_local(int n_panels, int p, const double* bxy, const double* sigma, co
     LocalGeom g;
     Foot best{-1, 0.0, 1e300};
     if (!far) {
+      // Newton on the panel of the nearest node, started at that node; if
+      // the iterate stops at a panel end, the foot lies beyond it: Newton
+      // again on the adjacent panel, started at its node nearest the target,
+      // and keep the closer foot (the first on ties).
       int ip0 = (int)(jbest / p);
-      for (int d = -1; d <= 1; ++d) {
-        int ip = ((ip0 + d) % n_panels + n_panels) % n_panels;
-        // start from the panel's node nearest to the target
+      best = newton_on_panel(P, ip0, P.tau[jbest % p], x, y);
+      if (std::fabs(best.t) == 1.0) {
+        int ip = ((ip0 + (best.t > 0 ? 1 : -1)) % n_panels + n_panels) % n_panels;
         int kbest = 0;
         double kd = 1e300;
         for (int k = 0; k < p; ++k) {

@@ -9,6 +9,7 @@ namespace lpg {
 
 namespace {
 
+template <typename T>
 struct SpreadArgs {
   const double* xy;
   const double* q[3];
@@ -16,61 +17,55 @@ struct SpreadArgs {
   int nq;
   int64_t n;
   GridDev gd;
-  Kernel ker;
   unsigned* status;
+  EsPoly<T> es;
 };
-
-__device__ __forceinline__ double es_phi(double z, double beta) {
-  double a = 1.0 - z * z;
-  return a > 0.0 ? exp(beta * (sqrt(a) - 1.0)) : 0.0;
-}
-__device__ __forceinline__ float es_phi_f(float z, float beta) {
-  float a = 1.0f - z * z;
-  return a > 0.0f ? __expf(beta * (sqrtf(a) - 1.0f)) : 0.0f;
-}
 
 // Grid coordinate split: first stencil index i0 = floor(u - w/2) + 1 and the
 // offset d0 = u - i0 of the point from it (in [w/2 - 1, w/2)).
-__device__ __forceinline__ bool stencil_origin(double u, int w, double hw, int g, int& i0, double& d0) {
+__device__ __forceinline__ bool stencil_origin(double u, int w, int g, int& i0, double& d0) {
   if (!(u > -1e9 && u < 1e9)) return false;  // rejects NaN / inf
-  double f = floor(u - hw);
+  double f = floor(u - 0.5 * w);
   i0 = (int)f + 1;
   d0 = u - (double)i0;
   return i0 >= 0 && i0 + w <= g;
 }
 
-template <typename T>
-__global__ void spread_atomic_kernel(SpreadArgs a) {
+// The W stencil weights of one dimension (Horner on the plan's polynomials).
+template <typename T, int W>
+__device__ __forceinline__ void es_weights(const EsPoly<T>& P, T v, T* out) {
+#pragma unroll
+  for (int t = 0; t < W; ++t) out[t] = P.c[P.nc - 1][t];
+  for (int k = P.nc - 2; k >= 0; --k) {
+#pragma unroll
+    for (int t = 0; t < W; ++t) out[t] = fma(out[t], v, P.c[k][t]);
+  }
+}
+
+template <typename T, int W>
+__global__ void spread_atomic_kernel(const __grid_constant__ SpreadArgs<T> a) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= a.n) return;
-  const int w = a.ker.w;
-  const double hw = a.ker.half_w;
   double ux = (a.xy[2 * j] - a.gd.x0) * a.gd.inv_h;
   double uy = (a.xy[2 * j + 1] - a.gd.y0) * a.gd.inv_h;
   int ix, iy;
   double dx, dy;
-  if (!stencil_origin(ux, w, hw, a.gd.g, ix, dx) || !stencil_origin(uy, w, hw, a.gd.g, iy, dy)) {
+  if (!stencil_origin(ux, W, a.gd.g, ix, dx) || !stencil_origin(uy, W, a.gd.g, iy, dy)) {
     atomicOr(a.status, kStatusOutOfBox);
     return;
   }
-  T kx[kMaxW], ky[kMaxW];
-  const double inv_hw = 1.0 / hw;
-  for (int t = 0; t < w; ++t) {
-    if (sizeof(T) == 8) {
-      kx[t] = (T)es_phi((dx - t) * inv_hw, a.ker.beta);
-      ky[t] = (T)es_phi((dy - t) * inv_hw, a.ker.beta);
-    } else {
-      kx[t] = (T)es_phi_f((float)((dx - t) * inv_hw), (float)a.ker.beta);
-      ky[t] = (T)es_phi_f((float)((dy - t) * inv_hw), (float)a.ker.beta);
-    }
-  }
+  T kx[W], ky[W];
+  es_weights<T, W>(a.es, (T)(dx - 0.5 * (W - 1)), kx);
+  es_weights<T, W>(a.es, (T)(dy - 0.5 * (W - 1)), ky);
   for (int c = 0; c < a.nq; ++c) {
     T qv = (T)a.q[c][j];
     T* grid = (T*)a.grid[c];
-    for (int b = 0; b < w; ++b) {
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
       T qb = qv * ky[b];
       T* row = grid + (size_t)(iy + b) * a.gd.pitch + ix;
-      for (int t = 0; t < w; ++t) atomicAdd(row + t, qb * kx[t]);
+#pragma unroll
+      for (int t = 0; t < W; ++t) atomicAdd(row + t, qb * kx[t]);
     }
   }
 }
@@ -110,6 +105,7 @@ __global__ void multiplier_kernel(int g, int K, double dk, const R* __restrict__
   }
 }
 
+template <typename T>
 struct InterpArgs {
   const double* txy;
   int64_t n;
@@ -117,17 +113,15 @@ struct InterpArgs {
   GridDev gd[2];
   const double* qsum;      // FP64 strength sums of V and S (FP32 path), or null
   double zero_factor;      // sum over levels of (dk/2pi)^2 M(0)
-  Kernel ker;
   double* out[3];
   unsigned* status;
+  EsPoly<T> es;
 };
 
-template <typename T>
-__global__ void interp_kernel(InterpArgs a) {
+template <typename T, int W>
+__global__ void interp_kernel(const __grid_constant__ InterpArgs<T> a) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
-  const int w = a.ker.w;
-  const double hw = a.ker.half_w, inv_hw = 1.0 / hw;
   // FP32 path: the k = 0 term (the log constant) is summed and added in FP64.
   double acc[3] = {0.0, 0.0, 0.0};
   if (a.qsum) {
@@ -141,29 +135,25 @@ __global__ void interp_kernel(InterpArgs a) {
     double uy = (a.txy[2 * i + 1] - gd.y0) * gd.inv_h;
     int ix, iy;
     double dx, dy;
-    if (!stencil_origin(ux, w, hw, gd.g, ix, dx) || !stencil_origin(uy, w, hw, gd.g, iy, dy)) {
+    if (!stencil_origin(ux, W, gd.g, ix, dx) || !stencil_origin(uy, W, gd.g, iy, dy)) {
       bad = true;
       break;
     }
-    T kx[kMaxW], ky[kMaxW];
-    for (int t = 0; t < w; ++t) {
-      if (sizeof(T) == 8) {
-        kx[t] = (T)es_phi((dx - t) * inv_hw, a.ker.beta);
-        ky[t] = (T)es_phi((dy - t) * inv_hw, a.ker.beta);
-      } else {
-        kx[t] = (T)es_phi_f((float)((dx - t) * inv_hw), (float)a.ker.beta);
-        ky[t] = (T)es_phi_f((float)((dy - t) * inv_hw), (float)a.ker.beta);
-      }
-    }
+    T kx[W], ky[W];
+    es_weights<T, W>(a.es, (T)(dx - 0.5 * (W - 1)), kx);
+    es_weights<T, W>(a.es, (T)(dy - 0.5 * (W - 1)), ky);
+#pragma unroll
     for (int c = 0; c < 3; ++c) {
       const T* grid = (const T*)a.grid[l][c];
       if (!grid) continue;
       T s = 0;
-      for (int b = 0; b < w; ++b) {
+#pragma unroll
+      for (int b = 0; b < W; ++b) {
         const T* row = grid + (size_t)(iy + b) * gd.pitch + ix;
         T r = 0;
-        for (int t = 0; t < w; ++t) r += row[t] * kx[t];
-        s += r * ky[b];
+#pragma unroll
+        for (int t = 0; t < W; ++t) r = fma(row[t], kx[t], r);
+        s = fma(r, ky[b], s);
       }
       acc[c] += (double)s;
     }
@@ -190,27 +180,49 @@ GridDev grid_dev(const GridLevel& G) {
 
 }  // namespace
 
+#define LP_WIDTH_CASES(X) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
+
+template <typename T>
+static void spread_dispatch(const SpreadArgs<T>& a, int w, unsigned blocks, int threads, cudaStream_t s) {
+  switch (w) {
+#define LP_CASE(W) \
+  case W:          \
+    spread_atomic_kernel<T, W><<<blocks, threads, 0, s>>>(a); \
+    break;
+    LP_WIDTH_CASES(LP_CASE)
+#undef LP_CASE
+    default: break;
+  }
+}
+
 void launch_spread(const Plan& P, int level, const double* xy, const double* const* q, int nq,
                    void* const* grids, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
-  SpreadArgs a;
-  a.xy = xy;
-  for (int c = 0; c < 3; ++c) {
-    a.q[c] = c < nq ? q[c] : nullptr;
-    a.grid[c] = c < nq ? grids[c] : nullptr;
-  }
-  a.nq = nq;
-  a.n = n;
-  a.gd = grid_dev(P.lv[level]);
-  a.ker = P.ker;
-  a.status = P.d_status;
   int threads = 128;
   unsigned blocks = (unsigned)((n + threads - 1) / threads);
   ++P.launches;
-  if (P.precision == LP_FP64)
-    spread_atomic_kernel<double><<<blocks, threads, 0, s>>>(a);
-  else
-    spread_atomic_kernel<float><<<blocks, threads, 0, s>>>(a);
+  auto fill = [&](auto& a) {
+    a.xy = xy;
+    for (int c = 0; c < 3; ++c) {
+      a.q[c] = c < nq ? q[c] : nullptr;
+      a.grid[c] = c < nq ? grids[c] : nullptr;
+    }
+    a.nq = nq;
+    a.n = n;
+    a.gd = grid_dev(P.lv[level]);
+    a.status = P.d_status;
+  };
+  if (P.precision == LP_FP64) {
+    SpreadArgs<double> a;
+    fill(a);
+    a.es = P.es;
+    spread_dispatch(a, P.ker.w, blocks, threads, s);
+  } else {
+    SpreadArgs<float> a;
+    fill(a);
+    a.es = P.es32;
+    spread_dispatch(a, P.ker.w, blocks, threads, s);
+  }
 }
 
 void launch_multiplier(const Plan& P, int level, bool want_v, bool want_s, bool want_d,
@@ -233,32 +245,51 @@ void launch_multiplier(const Plan& P, int level, bool want_v, bool want_s, bool 
   }
 }
 
+template <typename T>
+static void interp_dispatch(const InterpArgs<T>& a, int w, unsigned blocks, int threads, cudaStream_t s) {
+  switch (w) {
+#define LP_CASE(W) \
+  case W:          \
+    interp_kernel<T, W><<<blocks, threads, 0, s>>>(a); \
+    break;
+    LP_WIDTH_CASES(LP_CASE)
+#undef LP_CASE
+    default: break;
+  }
+}
+
 void launch_interp(const Plan& P, int64_t nt, const double* txy, double* V, double* S, double* D,
                    cudaStream_t s) {
   if (nt <= 0) return;
-  InterpArgs a;
-  a.txy = txy;
-  a.n = nt;
-  a.ker = P.ker;
-  a.status = P.d_status;
-  a.out[0] = V;
-  a.out[1] = S;
-  a.out[2] = D;
-  for (int l = 0; l < 2; ++l) {
-    a.gd[l] = grid_dev(P.lv[l]);
-    for (int c = 0; c < 3; ++c) a.grid[l][c] = a.out[c] ? P.lv[l].chan[c] : nullptr;
-  }
-  a.qsum = nullptr;
-  a.zero_factor = P.lv[0].zero_mode + P.lv[1].zero_mode;
+  auto fill = [&](auto& a) {
+    a.txy = txy;
+    a.n = nt;
+    a.status = P.d_status;
+    a.out[0] = V;
+    a.out[1] = S;
+    a.out[2] = D;
+    for (int l = 0; l < 2; ++l) {
+      a.gd[l] = grid_dev(P.lv[l]);
+      for (int c = 0; c < 3; ++c) a.grid[l][c] = a.out[c] ? P.lv[l].chan[c] : nullptr;
+    }
+    a.qsum = nullptr;
+    a.zero_factor = P.lv[0].zero_mode + P.lv[1].zero_mode;
+  };
   int threads = 128;
   unsigned blocks = (unsigned)((nt + threads - 1) / threads);
   ++P.launches;
   if (P.precision == LP_FP64) {
-    interp_kernel<double><<<blocks, threads, 0, s>>>(a);
+    InterpArgs<double> a;
+    fill(a);
+    a.es = P.es;
+    interp_dispatch(a, P.ker.w, blocks, threads, s);
   } else {
     // FP32 path: the zero mode was removed from the FP32 tables
+    InterpArgs<float> a;
+    fill(a);
+    a.es = P.es32;
     a.qsum = P.d_qsum;
-    interp_kernel<float><<<blocks, threads, 0, s>>>(a);
+    interp_dispatch(a, P.ker.w, blocks, threads, s);
   }
 }
 

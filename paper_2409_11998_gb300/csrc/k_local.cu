@@ -9,9 +9,14 @@
 //   positive, so the printed local S expansion changes sign.  In the volume
 //   expansion, with eta the inward normal and kappa > 0 for convex
 //   boundaries, the delta^{3/2} term reads (2 f_eta - kappa f).
+#include <cooperative_groups.h>
+
+#include <algorithm>
 #include <cmath>
 
 #include "lp_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace lpg {
 
@@ -41,23 +46,30 @@ struct LocalArgs {
   unsigned* status;
 };
 
-// d^j/dt^j of ref + sum_k c_k P_k(t), j = 0..nd (Legendre three-term
-// recurrence differentiated j times).
-__device__ void legendre_jet(const double* __restrict__ c, double ref, int p, double t, int nd,
-                             double* out) {
-  double pm[5] = {0, 0, 0, 0, 0}, pk[5] = {1, 0, 0, 0, 0};
-  for (int j = 0; j <= nd; ++j) out[j] = c[0] * pk[j];
-  out[0] += ref;
+// d^j/dt^j of ref + sum_k c_k P_k(t), j = 0..nd.  The stored coefficients are
+// c_k / k!, paired with Q_k = k! P_k, which obey the division-free recurrence
+// Q_{k+1} = (2k+1) t Q_k - k^2 Q_{k-1}; differentiating j times gives
+// Q_{k+1}^(j) = (2k+1) (t Q_k^(j) + j Q_k^(j-1)) - k^2 Q_{k-1}^(j).
+template <int ND>
+__device__ __forceinline__ void legendre_jet(const double* __restrict__ c, double ref, int p, double t,
+                                             double* out) {
+  double qm[ND + 1], qk[ND + 1];
+#pragma unroll
+  for (int j = 0; j <= ND; ++j) {
+    qm[j] = 0.0;
+    qk[j] = (j == 0) ? 1.0 : 0.0;
+    out[j] = 0.0;
+  }
+  out[0] = ref + c[0];
   for (int k = 0; k + 1 < p; ++k) {
-    double pn[5];
-    for (int j = 0; j <= nd; ++j) {
-      double prev = j ? pk[j - 1] : 0.0;
-      pn[j] = ((2.0 * k + 1.0) * (t * pk[j] + j * prev) - k * pm[j]) / (k + 1.0);
-    }
-    for (int j = 0; j <= nd; ++j) {
-      pm[j] = pk[j];
-      pk[j] = pn[j];
-      out[j] += c[k + 1] * pk[j];
+    const double a = 2.0 * k + 1.0, b = (double)k * k, ck = c[k + 1];
+#pragma unroll
+    for (int j = ND; j >= 0; --j) {
+      double prev = j ? qk[j - 1] : 0.0;
+      double qn = a * fma(t, qk[j], j * prev) - b * qm[j];
+      qm[j] = qk[j];
+      qk[j] = qn;
+      out[j] = fma(ck, qn, out[j]);
     }
   }
 }
@@ -73,8 +85,8 @@ __device__ Foot panel_foot(const LocalArgs& a, int ip, double t, double x, doubl
   const double rx = a.geo_ref[2 * ip], ry = a.geo_ref[2 * ip + 1];
   double X[3], Y[3];
   for (int it = 0; it < 20; ++it) {
-    legendre_jet(cx, rx, a.p, t, 2, X);
-    legendre_jet(cy, ry, a.p, t, 2, Y);
+    legendre_jet<2>(cx, rx, a.p, t, X);
+    legendre_jet<2>(cy, ry, a.p, t, Y);
     double gx = X[0] - x, gy = Y[0] - y;
     double f = gx * X[1] + gy * Y[1];
     double s2 = X[1] * X[1] + Y[1] * Y[1];
@@ -85,8 +97,8 @@ __device__ Foot panel_foot(const LocalArgs& a, int ip, double t, double x, doubl
     t = tn;
     if (fabs(dt) < 1e-14) break;
   }
-  legendre_jet(cx, rx, a.p, t, 0, X);
-  legendre_jet(cy, ry, a.p, t, 0, Y);
+  legendre_jet<0>(cx, rx, a.p, t, X);
+  legendre_jet<0>(cy, ry, a.p, t, Y);
   Foot r;
   r.panel = ip;
   r.t = t;
@@ -104,47 +116,22 @@ __device__ void compose4(const double* F, const double* c, double* o) {
          F[4] * c[1] * c[1] * c[1] * c[1];
 }
 
-__global__ void local_kernel(LocalArgs a) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
+__device__ __forceinline__ double far_volume(const LocalArgs& a, const double* J);
+
+__device__ void local_near_one(const LocalArgs& a, int64_t i, int best) {
   const double x = a.txy[2 * i], y = a.txy[2 * i + 1];
   const double dl = a.delta;
   const double* J = a.jet ? a.jet + 6 * i : nullptr;
   double vl = 0.0, sl = 0.0, dlv = 0.0;
-
-  // nearest boundary node (ties: lowest index) among the 3x3 hash cells
-  int best = -1;
-  double bd2 = 1e300;
-  if (a.nb > 0) {
-    int cx = (int)floor((x - a.hx0) / a.hh), cy = (int)floor((y - a.hy0) / a.hh);
-    if (cx >= 0 && cx < a.hnx && cy >= 0 && cy < a.hny) {
-      for (int oy = -1; oy <= 1; ++oy) {
-        int yy = cy + oy;
-        if (yy < 0 || yy >= a.hny) continue;
-        for (int ox = -1; ox <= 1; ++ox) {
-          int xx = cx + ox;
-          if (xx < 0 || xx >= a.hnx) continue;
-          int c = yy * a.hnx + xx;
-          for (int k = a.cell_start[c]; k < a.cell_start[c + 1]; ++k) {
-            int j = a.cell_node[k];
-            double ex = x - a.bxy[2 * j], ey = y - a.bxy[2 * j + 1];
-            double d2 = ex * ex + ey * ey;
-            if (d2 < bd2 || (d2 == bd2 && j < best)) {
-              bd2 = d2;
-              best = j;
-            }
-          }
-        }
-      }
-    }
-  }
-  bool far = best < 0 || sqrt(bd2) - a.margin >= a.band;
+  bool far = false;
   Foot ft{-1, 0.0, 1e300};
-  if (!far) {
+  {
     const int p = a.p;
     const int ip0 = best / p;
-    for (int d = -1; d <= 1; ++d) {
-      int ip = ((ip0 + d) % a.n_panels + a.n_panels) % a.n_panels;
+    ft = panel_foot(a, ip0, a.tau[best - ip0 * p], x, y);
+    if (fabs(ft.t) == 1.0) {
+      // the foot lies beyond this panel's end: continue on the adjacent panel
+      int ip = ((ip0 + (ft.t > 0.0 ? 1 : -1)) % a.n_panels + a.n_panels) % a.n_panels;
       int kb = 0;
       double kd = 1e300;
       for (int k = 0; k < p; ++k) {
@@ -162,16 +149,13 @@ __global__ void local_kernel(LocalArgs a) {
   }
 
   if (far) {
-    if (J) {
-      vl = dl * J[0];
-      if (a.order >= 5) vl += 0.5 * dl * dl * (J[3] + J[5]);
-    }
+    if (J) vl = far_volume(a, J);
   } else {
     const int p = a.p, ip = ft.panel;
     double X[5], Y[5];
     const double* cgx = a.geo_coef + (size_t)(2 * ip) * p;
-    legendre_jet(cgx, a.geo_ref[2 * ip], p, ft.t, 4, X);
-    legendre_jet(cgx + p, a.geo_ref[2 * ip + 1], p, ft.t, 4, Y);
+    legendre_jet<4>(cgx, a.geo_ref[2 * ip], p, ft.t, X);
+    legendre_jet<4>(cgx + p, a.geo_ref[2 * ip + 1], p, ft.t, Y);
     const double sp = hypot(X[1], Y[1]);
     const double Tx = X[1] / sp, Ty = Y[1] / sp;
     const double Nx = -Ty, Ny = Tx;  // inward normal of a counter-clockwise curve
@@ -204,7 +188,7 @@ __global__ void local_kernel(LocalArgs a) {
     const double c2 = c * c, c3 = c2 * c;
     if (a.out[1] && a.sig_coef) {
       double Sv[5], F[5], o[5];
-      legendre_jet(a.sig_coef + (size_t)ip * p, a.sig_ref[ip], p, ft.t, 4, Sv);
+      legendre_jet<4>(a.sig_coef + (size_t)ip * p, a.sig_ref[ip], p, ft.t, Sv);
       for (int k = 1; k <= 4; ++k) F[k] = Sv[k] * fact[k];
       compose4(F, C, o);
       const double s0 = Sv[0], s1 = o[1], s2 = 2.0 * o[2];
@@ -221,7 +205,7 @@ __global__ void local_kernel(LocalArgs a) {
     }
     if (a.out[2] && a.mu_coef) {
       double Mv[5], F[5], o[5];
-      legendre_jet(a.mu_coef + (size_t)ip * p, a.mu_ref[ip], p, ft.t, 4, Mv);
+      legendre_jet<4>(a.mu_coef + (size_t)ip * p, a.mu_ref[ip], p, ft.t, Mv);
       for (int k = 1; k <= 4; ++k) F[k] = Mv[k] * fact[k];
       compose4(F, C, o);
       const double m0 = Mv[0], m1 = o[1], m2 = 2.0 * o[2], m4 = 24.0 * o[4];
@@ -268,6 +252,64 @@ __global__ void local_kernel(LocalArgs a) {
   if (a.out[2]) a.out[2][i] += dlv;
 }
 
+__device__ __forceinline__ double far_volume(const LocalArgs& a, const double* J) {
+  // delta f + delta^2/2 lap f (Sec. 4, after eq. vplocO5)
+  double v = a.delta * J[0];
+  if (a.order >= 5) v += 0.5 * a.delta * a.delta * (J[3] + J[5]);
+  return v;
+}
+
+// Pass 1: nearest boundary node (ties: lowest index) among the 3x3 hash cells.
+// Targets whose nearest node is farther than band + margin get the far-field
+// volume term here; the others are appended to a compact list for pass 2.
+__global__ void local_classify_kernel(LocalArgs a, int2* list, int* count) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const double x = a.txy[2 * i], y = a.txy[2 * i + 1];
+  int best = -1;
+  double bd2 = 1e300;
+  if (a.nb > 0) {
+    int cx = (int)floor((x - a.hx0) / a.hh), cy = (int)floor((y - a.hy0) / a.hh);
+    if (cx >= 0 && cx < a.hnx && cy >= 0 && cy < a.hny) {
+      for (int oy = -1; oy <= 1; ++oy) {
+        int yy = cy + oy;
+        if (yy < 0 || yy >= a.hny) continue;
+        for (int ox = -1; ox <= 1; ++ox) {
+          int xx = cx + ox;
+          if (xx < 0 || xx >= a.hnx) continue;
+          int c = yy * a.hnx + xx;
+          for (int k = a.cell_start[c]; k < a.cell_start[c + 1]; ++k) {
+            int j = a.cell_node[k];
+            double ex = x - a.bxy[2 * j], ey = y - a.bxy[2 * j + 1];
+            double d2 = ex * ex + ey * ey;
+            if (d2 < bd2 || (d2 == bd2 && j < best)) {
+              bd2 = d2;
+              best = j;
+            }
+          }
+        }
+      }
+    }
+  }
+  if (best < 0 || sqrt(bd2) - a.margin >= a.band) {
+    if (a.out[0] && a.jet) a.out[0][i] += far_volume(a, a.jet + 6 * i);
+    return;
+  }
+  auto g = cg::coalesced_threads();
+  int base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(count, (int)g.size());
+  base = g.shfl(base, 0);
+  list[base + g.thread_rank()] = make_int2((int)i, best);
+}
+
+// Pass 2: closest point, frame and expansions for the listed targets.
+__global__ void local_near_kernel(LocalArgs a, const int2* __restrict__ list,
+                                  const int* __restrict__ count) {
+  const int n_near = *count;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n_near; idx += gridDim.x * blockDim.x)
+    local_near_one(a, list[idx].x, list[idx].y);
+}
+
 }  // namespace
 
 void launch_local(const Plan& P, int64_t nt, const double* txy, const double* jet, double* V,
@@ -306,8 +348,12 @@ void launch_local(const Plan& P, int64_t nt, const double* txy, const double* je
   a.status = P.d_status;
   int threads = 128;
   unsigned blocks = (unsigned)((nt + threads - 1) / threads);
+  cudaMemsetAsync(P.d_near_count, 0, sizeof(int), s);
   ++P.launches;
-  local_kernel<<<blocks, threads, 0, s>>>(a);
+  local_classify_kernel<<<blocks, threads, 0, s>>>(a, P.d_near, P.d_near_count);
+  unsigned nblk = std::min<unsigned>(blocks, 152u * 16u);
+  ++P.launches;
+  local_near_kernel<<<nblk, threads, 0, s>>>(a, P.d_near, P.d_near_count);
 }
 
 }  // namespace lpg

@@ -98,7 +98,7 @@ void destroy_plan(Plan& P) {
   void* bufs[] = {P.d_bxy, P.d_bw, P.d_bnrm, P.d_geo_coef, P.d_geo_ref, P.d_leg_T, P.d_tau,
                   P.d_cell_start, P.d_cell_node, P.d_vxy, P.d_vq, P.d_sigma, P.d_sigma_coef,
                   P.d_sigma_ref, P.d_mu, P.d_mu_coef, P.d_mu_ref, P.d_bq, P.d_qsum, P.d_stage,
-                  P.d_out, P.d_status};
+                  P.d_out, P.d_status, P.d_near, P.d_near_count};
   for (void* b : bufs) dfree(b);
   if (P.h_status) cudaFreeHost(P.h_status);
   for (auto& e : P.ev)
@@ -193,12 +193,13 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
   P.on_tol = 1e-12 * P.side;
   P.stream = (cudaStream_t)dom->stream;
   int w = (int)std::ceil(-std::log10(tol)) + 1;
-  w = std::min(std::max(w, 3), kMaxW);
+  w = std::min(std::max(w, 4), kMaxW);
   P.ker.w = w;
   P.ker.beta = 2.30 * w;
   P.ker.half_w = 0.5 * w;
   lp_status st = choose_levels(P);
   if (st == LP_OK) st = build_tables(P);
+  if (st == LP_OK) st = fit_kernel_poly(P);
   const size_t rs = P.precision == LP_FP64 ? sizeof(double) : sizeof(float);
   for (int l = 0; l < 2 && st == LP_OK; ++l) {
     GridLevel& G = P.lv[l];
@@ -307,7 +308,7 @@ lp_status lp_double_layer(lp_plan_t h, const double* mu) { return bind_layer(h, 
 
 lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* jet, double* V,
                      double* S, double* D) {
-  if (!h || nt < 0) return LP_ERR_ARG;
+  if (!h || nt < 0 || nt > (int64_t)INT32_MAX) return LP_ERR_ARG;
   if (nt > 0 && !txy) return LP_ERR_ARG;
   Plan& P = h->P;
   const bool wv = V != nullptr, ws = S != nullptr, wd = D != nullptr;
@@ -333,6 +334,15 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
     if (!dalloc(P, (void**)&P.d_out, 3 * nt * sizeof(double))) return LP_ERR_NOMEM;
     P.out_cap = nt;
   }
+  if ((size_t)nt > P.near_cap) {
+    cudaStreamSynchronize(s);
+    dfree(P.d_near);
+    P.d_near = nullptr;
+    P.near_cap = 0;
+    if (!dalloc(P, (void**)&P.d_near, nt * sizeof(int2))) return LP_ERR_NOMEM;
+    P.near_cap = nt;
+  }
+  if (!P.d_near_count && !dalloc(P, (void**)&P.d_near_count, sizeof(int))) return LP_ERR_NOMEM;
   cudaEventRecord(P.ev[0], s);
   size_t off = 0;
   const double* dt = device_view(P, txy, nt * 2, &off);
@@ -439,10 +449,10 @@ lp_status lp_destroy(lp_plan_t h) {
 lp_status lp_plan_info(lp_plan_t h, double* out) {
   if (!h || !out) return LP_ERR_ARG;
   const Plan& P = h->P;
-  double v[17] = {P.delta1, P.delta2, (double)P.ker.w, P.ker.beta, (double)P.lv[0].g, (double)P.lv[0].K,
+  double v[19] = {P.delta1, P.delta2, (double)P.ker.w, P.ker.beta, (double)P.lv[0].g, (double)P.lv[0].K,
                   P.lv[0].P, (double)P.lv[1].g, (double)P.lv[1].K, P.lv[1].P, P.lv[1].L, P.band,
                   P.margin, (double)P.device_bytes, (double)P.precision, (double)P.order,
-                  (double)P.launches};
+                  (double)P.launches, P.es_fit_err, (double)P.es.nc};
   std::memcpy(out, v, sizeof(v));
   return LP_OK;
 }

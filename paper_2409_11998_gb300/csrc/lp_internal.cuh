@@ -13,6 +13,7 @@
 namespace lpg {
 
 constexpr int kMaxW = 16;           // widest spreading kernel (grid points)
+constexpr int kMaxNC = 20;          // coefficients per piece of the kernel polynomial
 constexpr int kMaxPanelOrder = 32;  // Gauss-Legendre nodes per boundary panel
 constexpr int kNumEvents = 10;
 
@@ -28,6 +29,17 @@ struct Kernel {
   int w;
   double beta;
   double half_w;  // w/2
+};
+
+// Piecewise-polynomial form of the same kernel: for a point at grid
+// coordinate u with stencil origin i0 = floor(u - w/2) + 1 and
+// v = u - i0 - (w - 1)/2 in [-1/2, 1/2), the w stencil weights are
+// phi_t = sum_k c[k][t] v^k (t = 0..w-1), fitted at plan time to within a
+// hundredth of the plan tolerance.
+template <typename T>
+struct EsPoly {
+  int w, nc;
+  T c[kMaxNC][kMaxW];
 };
 
 // One periodic grid of the history part (Sec. 3): near history (kind 0,
@@ -62,6 +74,9 @@ struct Plan {
   double side = 0;        // max box extent
   double on_tol = 0;      // on-surface classification radius
   Kernel ker{};
+  EsPoly<double> es{};
+  EsPoly<float> es32{};
+  double es_fit_err = 0;
   GridLevel lv[2];
   cudaStream_t stream = nullptr;
 
@@ -103,6 +118,9 @@ struct Plan {
   size_t stage_bytes = 0;
   double* d_out = nullptr;   // [3][cap] outputs for host destinations
   size_t out_cap = 0;
+  int2* d_near = nullptr;    // [near_cap] (target, nearest node) of band candidates
+  int* d_near_count = nullptr;
+  size_t near_cap = 0;
 
   unsigned* d_status = nullptr;
   unsigned* h_status = nullptr;  // pinned
@@ -114,6 +132,7 @@ struct Plan {
 // ---- host helpers (lp_setup.cu) ----
 lp_status choose_levels(Plan& P);
 lp_status build_tables(Plan& P);
+lp_status fit_kernel_poly(Plan& P);
 lp_status build_boundary(Plan& P, const double* h_xy, const double* h_w, const double* h_nrm);
 void gauss_legendre(int p, double* x, double* w);
 int fft_size(int n);

@@ -185,6 +185,73 @@ lp_status build_tables(Plan& P) {
   return LP_OK;
 }
 
+// Chebyshev interpolation of each stencil weight phi_t(v), v in [-1/2, 1/2),
+// converted to monomials in v (long double on the host).  The degree grows
+// until the interior weights are within tol/100 of the kernel; the two edge
+// weights reach the support edge z = +-1, where sqrt(1 - z^2) is not smooth,
+// and are accepted once within 4 e^{-beta} (the kernel's own value there,
+// below the kernel's truncation error).
+lp_status fit_kernel_poly(Plan& P) {
+  const int w = P.ker.w;
+  const double beta = P.ker.beta, hw = P.ker.half_w;
+  auto phi = [&](int t, long double v) -> long double {
+    long double z = (v + (long double)(hw - 0.5) - t) / hw;
+    long double a = 1.0L - z * z;
+    return a > 0 ? std::exp((long double)beta * (std::sqrt(a) - 1.0L)) : 0.0L;
+  };
+  const double target = std::max(0.01 * P.tol, 1e-15);
+  const double target_edge = std::max(target, 4.0 * std::exp(-beta));
+  for (int nc = w + 1; nc <= kMaxNC; ++nc) {
+    double err = 0.0, err_edge = 0.0;
+    for (int t = 0; t < w; ++t) {
+      // Chebyshev coefficients from values at Chebyshev points on [-1,1] (x = 2 v)
+      std::vector<long double> fx(nc), cheb(nc, 0.0L);
+      for (int j = 0; j < nc; ++j) {
+        long double x = std::cos((long double)M_PI * (j + 0.5L) / nc);
+        fx[j] = phi(t, 0.5L * x);
+      }
+      for (int k = 0; k < nc; ++k) {
+        long double s = 0;
+        for (int j = 0; j < nc; ++j) s += fx[j] * std::cos((long double)M_PI * k * (j + 0.5L) / nc);
+        cheb[k] = s * (k == 0 ? 1.0L : 2.0L) / nc;
+      }
+      // monomials in x: T_0 = 1, T_1 = x, T_{k+1} = 2x T_k - T_{k-1}
+      std::vector<long double> mono(nc, 0.0L), tm(nc, 0.0L), tk(nc, 0.0L), tn(nc);
+      tm[0] = 1.0L;
+      if (nc > 1) tk[1] = 1.0L;
+      mono[0] += cheb[0];
+      for (int i = 0; i < nc; ++i) mono[i] += (nc > 1 ? cheb[1] : 0.0L) * tk[i];
+      for (int k = 1; k + 1 < nc; ++k) {
+        for (int i = 0; i < nc; ++i) tn[i] = (i ? 2.0L * tk[i - 1] : 0.0L) - tm[i];
+        for (int i = 0; i < nc; ++i) mono[i] += cheb[k + 1] * tn[i];
+        tm = tk;
+        tk = tn;
+      }
+      // x = 2 v: coefficient of v^i is mono[i] 2^i
+      long double sc = 1.0L;
+      for (int i = 0; i < nc; ++i) {
+        P.es.c[i][t] = (double)(mono[i] * sc);
+        P.es32.c[i][t] = (float)(mono[i] * sc);
+        sc *= 2.0L;
+      }
+      double e = 0.0;
+      for (int j = 0; j <= 400; ++j) {
+        double v = -0.5 + j / 400.0 * (1.0 - 1e-12);
+        double acc = P.es.c[nc - 1][t];
+        for (int i = nc - 2; i >= 0; --i) acc = acc * v + P.es.c[i][t];
+        e = std::max(e, (double)std::fabs((long double)acc - phi(t, v)));
+      }
+      if (t == 0 || t == w - 1) err_edge = std::max(err_edge, e);
+      else err = std::max(err, e);
+    }
+    P.es.w = P.es32.w = w;
+    P.es.nc = P.es32.nc = nc;
+    P.es_fit_err = std::max(err, err_edge);
+    if (err <= target && err_edge <= target_edge) return LP_OK;
+  }
+  return LP_OK;  // best effort at the maximum degree (error recorded)
+}
+
 lp_status build_boundary(Plan& P, const double* h_xy, const double* h_w, const double* h_nrm) {
   const int p = P.p;
   const int64_t nb = P.nb;
@@ -233,6 +300,7 @@ lp_status build_boundary(Plan& P, const double* h_xy, const double* h_w, const d
   for (int64_t j = 0; j < nb; ++j) order[fill[cell[j]]++] = (int)j;  // stable: ascending ids
 
   // Legendre transform of the panel interpolant: coef_k = (2k+1)/2 sum_i w_i v_i P_k(tau_i)
+  // (exact: the interpolant has degree p-1 and the Gauss rule degree 2p-1)
   std::vector<double> tau(p), wq(p), T((size_t)p * p);
   gauss_legendre(p, tau.data(), wq.data());
   for (int i = 0; i < p; ++i) {
@@ -247,7 +315,8 @@ lp_status build_boundary(Plan& P, const double* h_xy, const double* h_w, const d
         p1 = p2;
         pk = p2;
       }
-      T[(size_t)k * p + i] = 0.5 * (2.0 * k + 1.0) * wq[i] * pk;
+      // coefficients are stored divided by k!, for the recurrence of Q_k = k! P_k
+      T[(size_t)k * p + i] = 0.5 * (2.0 * k + 1.0) * wq[i] * pk / std::tgamma(k + 1.0);
     }
   }
   auto dmalloc = [&](void** ptr, size_t bytes) -> bool {
