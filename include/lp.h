@@ -118,6 +118,26 @@ lp_status lp_double_layer(lp_plan_t plan, const double* mu);
 lp_status lp_execute(lp_plan_t plan, int64_t n_t, const double* t_xy, const double* f_jet,
                      double* V, double* S, double* D);
 
+/* lp_execute without any allocation.  The paper has no counterpart: this is
+ * for callers that cannot call cudaMalloc at evaluation time -- code running
+ * while another allocator has reserved the device's memory, loops that must
+ * not take the implicit device synchronisation cudaMalloc/cudaFree can
+ * cause, or hosts where allocation after start-up is forbidden.  Such a
+ * caller creates the plan and binds sources and densities during set-up;
+ * this call then evaluates exactly what lp_execute evaluates, but it stages
+ * nothing (every pointer must be device memory, else LP_ERR_ARG) and keeps
+ * its per-call scratch -- the list of targets near the boundary -- in a
+ * static device array sized for at most 2,097,152 targets (16 MiB, held by
+ * every GPU that loads the library until the process exits); larger n_t is
+ * rejected with LP_ERR_ARG before anything is launched.  The first call on
+ * each device looks up that array's device address (with the device
+ * current), so make the first call on a device before any stream capture.
+ * All calls share the one array: calls whose work overlaps on the GPU (two
+ * plans on different streams, say) race, so serialise them.  No cudaMalloc,
+ * cudaFree or allocating library routine is called. */
+lp_status lp_execute_noalloc(lp_plan_t plan, int64_t n_t, const double* t_xy, const double* f_jet,
+                             double* V, double* S, double* D);
+
 /* Wait for the plan's stream; return and clear the device status word. */
 lp_status lp_sync(lp_plan_t plan);
 

@@ -24,7 +24,7 @@ LP_FP64, LP_FP32 = 0, 1
 STATUS = {0: "LP_OK", 1: "LP_ERR_ARG", 2: "LP_ERR_OUT_OF_BOX", 3: "LP_ERR_NOMEM",
           4: "LP_ERR_CUDA", 5: "LP_ERR_UNSUPPORTED", 6: "LP_ERR_STATE"}
 EXPORTS = ("lp_plan", "lp_volume", "lp_single_layer", "lp_double_layer", "lp_execute", "lp_sync",
-           "lp_destroy", "lp_status_string", "lp_plan_info", "lp_stage_times")
+           "lp_destroy", "lp_status_string", "lp_plan_info", "lp_stage_times", "lp_execute_noalloc")
 
 
 class LpError(RuntimeError):
@@ -56,6 +56,7 @@ def _lib():
         L.lp_single_layer.argtypes = [vp, vp]
         L.lp_double_layer.argtypes = [vp, vp]
         L.lp_execute.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+        L.lp_execute_noalloc.argtypes = [vp, i64, vp, vp, vp, vp, vp]
         L.lp_sync.argtypes = [vp]
         L.lp_destroy.argtypes = [vp]
         L.lp_status_string.argtypes = [i32]
@@ -129,6 +130,13 @@ def lp_double_layer(plan, mu):
 def lp_execute(plan, n_t, t_xy, f_jet, V=None, S=None, D=None):
     _check(_lib().lp_execute(plan, int(n_t), _ptr(t_xy), _ptr(f_jet), _ptr(V), _ptr(S), _ptr(D)),
            "lp_execute")
+
+
+def lp_execute_noalloc(plan, n_t, t_xy, f_jet, V=None, S=None, D=None):
+    """lp_execute without allocation: device buffers only, n_t <= 2**21
+    (see include/lp.h)."""
+    _check(_lib().lp_execute_noalloc(plan, int(n_t), _ptr(t_xy), _ptr(f_jet), _ptr(V), _ptr(S),
+                                     _ptr(D)), "lp_execute_noalloc")
 
 
 def lp_sync(plan):

@@ -356,4 +356,50 @@ void launch_local(const Plan& P, int64_t nt, const double* txy, const double* je
   local_near_kernel<<<nblk, threads, 0, s>>>(a, P.d_near, P.d_near_count);
 }
 
+// Same two passes with a caller-provided list and counter (the counter is
+// cleared here).
+void launch_local_list(const Plan& P, int64_t nt, const double* txy, const double* jet, double* V,
+                       double* S, double* D, int2* list, int* count, cudaStream_t s) {
+  if (nt <= 0) return;
+  LocalArgs a;
+  a.txy = txy;
+  a.jet = V ? jet : nullptr;
+  a.n = nt;
+  a.out[0] = V;
+  a.out[1] = S;
+  a.out[2] = D;
+  a.bxy = P.d_bxy;
+  a.nb = P.nb;
+  a.n_panels = (int)P.n_panels;
+  a.p = P.p;
+  a.tau = P.d_tau;
+  a.geo_coef = P.d_geo_coef;
+  a.geo_ref = P.d_geo_ref;
+  a.sig_coef = P.have_sigma ? P.d_sigma_coef : nullptr;
+  a.sig_ref = P.d_sigma_ref;
+  a.mu_coef = P.have_mu ? P.d_mu_coef : nullptr;
+  a.mu_ref = P.d_mu_ref;
+  a.hx0 = P.hash_x0;
+  a.hy0 = P.hash_y0;
+  a.hh = P.hash_h;
+  a.hnx = P.hash_nx;
+  a.hny = P.hash_ny;
+  a.cell_start = P.d_cell_start;
+  a.cell_node = P.d_cell_node;
+  a.margin = P.margin;
+  a.band = P.band;
+  a.delta = P.delta1;
+  a.on_tol = P.on_tol;
+  a.order = P.order;
+  a.status = P.d_status;
+  int threads = 128;
+  unsigned blocks = (unsigned)((nt + threads - 1) / threads);
+  cudaMemsetAsync(count, 0, sizeof(int), s);
+  ++P.launches;
+  local_classify_kernel<<<blocks, threads, 0, s>>>(a, list, count);
+  unsigned nblk = std::min<unsigned>(blocks, 152u * 16u);
+  ++P.launches;
+  local_near_kernel<<<nblk, threads, 0, s>>>(a, list, count);
+}
+
 }  // namespace lpg

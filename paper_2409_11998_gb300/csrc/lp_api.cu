@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -138,6 +139,43 @@ void derive_normals(int64_t n_panels, int p, const double* xy, double* nrm) {
       nrm[(size_t)(ip * p + i) * 2 + 1] = -dx / s;
     }
   }
+}
+
+// ---- scratch of lp_execute_noalloc -------------------------------------------
+// The near-boundary list of the local pass (one int2 per target) and its
+// counter live in this file-scope device array instead of plan memory, so
+// that the call allocates nothing.  Every GPU that loads the library holds
+// it (16 MiB + 256 B) until the process exits.
+constexpr int64_t kNoAllocMaxTargets = int64_t(1) << 21;
+constexpr size_t kNoAllocListBytes = (size_t)kNoAllocMaxTargets * sizeof(int2);
+constexpr size_t kNoAllocScratchBytes = kNoAllocListBytes + 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the scratch on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device (with that device current) and cached.
+lp_status noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return LP_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return LP_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = ptr;
+  }
+  *out = g_noalloc_addr[dev];
+  return LP_OK;
 }
 
 }  // namespace
@@ -422,6 +460,95 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
   cudaEventRecord(P.ev[8], s);
   for (int c = 0; c < 3; ++c)
     if (host_out[c]) cudaMemcpyAsync(outs[c], dout[c], nt * sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaEventRecord(P.ev[9], s);
+  return status_from_cuda();
+}
+
+lp_status lp_execute_noalloc(lp_plan_t h, int64_t nt, const double* txy, const double* jet,
+                             double* V, double* S, double* D) {
+  if (!h || nt < 0 || nt > kNoAllocMaxTargets) return LP_ERR_ARG;
+  if (nt > 0 && !txy) return LP_ERR_ARG;
+  Plan& P = h->P;
+  const bool wv = V != nullptr, ws = S != nullptr, wd = D != nullptr;
+  if (wv && nt > 0 && !jet) return LP_ERR_ARG;
+  if ((wv && !P.have_volume) || (ws && !P.have_sigma) || (wd && !P.have_mu)) return LP_ERR_STATE;
+  if (nt == 0 || (!wv && !ws && !wd)) return LP_OK;
+  // host buffers would need staging, i.e. an allocation: device memory only
+  const void* bufs[5] = {txy, wv ? jet : nullptr, V, S, D};
+  for (const void* b : bufs)
+    if (b && !is_device_ptr(b)) return LP_ERR_ARG;
+  void* scratch = nullptr;
+  lp_status st = noalloc_scratch(&scratch);
+  if (st != LP_OK) return st;
+  int2* list = (int2*)scratch;
+  int* count = (int*)((char*)scratch + kNoAllocListBytes);
+  cudaStream_t s = P.stream;
+  cudaEventRecord(P.ev[0], s);
+  cudaEventRecord(P.ev[1], s);
+  for (int l = 0; l < 2; ++l) {
+    GridLevel& G = P.lv[l];
+    if (wv) cudaMemsetAsync(G.chan[0], 0, G.chan_bytes, s);
+    if (ws) cudaMemsetAsync(G.chan[1], 0, G.chan_bytes, s);
+    if (wd) {
+      cudaMemsetAsync(G.chan[2], 0, G.chan_bytes, s);
+      cudaMemsetAsync(G.chan[3], 0, G.chan_bytes, s);
+    }
+  }
+  cudaEventRecord(P.ev[2], s);
+  for (int l = 0; l < 2; ++l) {
+    GridLevel& G = P.lv[l];
+    if (wv && P.nv > 0) {
+      const double* q[1] = {P.d_vq};
+      void* g[1] = {G.chan[0]};
+      launch_spread(P, l, P.d_vxy, q, 1, g, P.nv, s);
+    }
+    const double* bq[3];
+    void* bg[3];
+    int nq = 0;
+    if (ws) {
+      bq[nq] = P.d_bq;
+      bg[nq++] = G.chan[1];
+    }
+    if (wd) {
+      bq[nq] = P.d_bq + P.nb;
+      bg[nq++] = G.chan[2];
+      bq[nq] = P.d_bq + 2 * P.nb;
+      bg[nq++] = G.chan[3];
+    }
+    if (nq) launch_spread(P, l, P.d_bxy, bq, nq, bg, P.nb, s);
+  }
+  cudaEventRecord(P.ev[3], s);
+  const bool f64 = P.precision == LP_FP64;
+  for (int l = 0; l < 2; ++l) {
+    GridLevel& G = P.lv[l];
+    const int chans[4] = {wv ? 0 : -1, ws ? 1 : -1, wd ? 2 : -1, wd ? 3 : -1};
+    for (int c : chans) {
+      if (c < 0) continue;
+      if (f64)
+        cufftExecD2Z(G.fwd, (cufftDoubleReal*)G.chan[c], (cufftDoubleComplex*)G.chan[c]);
+      else
+        cufftExecR2C(G.fwd, (cufftReal*)G.chan[c], (cufftComplex*)G.chan[c]);
+    }
+  }
+  cudaEventRecord(P.ev[4], s);
+  for (int l = 0; l < 2; ++l) launch_multiplier(P, l, wv, ws, wd, s);
+  cudaEventRecord(P.ev[5], s);
+  for (int l = 0; l < 2; ++l) {
+    GridLevel& G = P.lv[l];
+    const int chans[3] = {wv ? 0 : -1, ws ? 1 : -1, wd ? 2 : -1};
+    for (int c : chans) {
+      if (c < 0) continue;
+      if (f64)
+        cufftExecZ2D(G.inv, (cufftDoubleComplex*)G.chan[c], (cufftDoubleReal*)G.chan[c]);
+      else
+        cufftExecC2R(G.inv, (cufftComplex*)G.chan[c], (cufftReal*)G.chan[c]);
+    }
+  }
+  cudaEventRecord(P.ev[6], s);
+  launch_interp(P, nt, txy, V, S, D, s);
+  cudaEventRecord(P.ev[7], s);
+  launch_local_list(P, nt, txy, wv ? jet : nullptr, V, S, D, list, count, s);
+  cudaEventRecord(P.ev[8], s);
   cudaEventRecord(P.ev[9], s);
   return status_from_cuda();
 }

@@ -146,6 +146,8 @@ void launch_interp(const Plan& P, int64_t nt, const double* txy, double* V, doub
                    cudaStream_t s);
 void launch_local(const Plan& P, int64_t nt, const double* txy, const double* jet, double* V,
                   double* S, double* D, cudaStream_t s);
+void launch_local_list(const Plan& P, int64_t nt, const double* txy, const double* jet, double* V,
+                       double* S, double* D, int2* list, int* count, cudaStream_t s);
 void launch_panel_coef(const Plan& P, const double* vals, int stride, int ncomp, double* coef,
                        double* ref, cudaStream_t s);
 void launch_strengths(const Plan& P, int kind, cudaStream_t s);
