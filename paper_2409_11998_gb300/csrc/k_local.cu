@@ -41,35 +41,47 @@ struct LocalArgs {
   int hnx, hny;
   const int* cell_start;
   const int* cell_node;
+  const float2* cell_xy32;   // node coordinates relative to their cell origin
+  const float* geo_coef32;   // FP32 copy of geo_coef
   double margin, band, delta, on_tol;
   int order;
   unsigned* status;
 };
 
-// d^j/dt^j of ref + sum_k c_k P_k(t), j = 0..nd.  The stored coefficients are
-// c_k / k!, paired with Q_k = k! P_k, which obey the division-free recurrence
+// d^j/dt^j of ref_s + sum_k c_s[k] P_k(t), j = 0..ND, for NS series sharing
+// one recurrence.  The stored coefficients are c_k / k!, paired with
+// Q_k = k! P_k, which obey the division-free recurrence
 // Q_{k+1} = (2k+1) t Q_k - k^2 Q_{k-1}; differentiating j times gives
 // Q_{k+1}^(j) = (2k+1) (t Q_k^(j) + j Q_k^(j-1)) - k^2 Q_{k-1}^(j).
-template <int ND>
-__device__ __forceinline__ void legendre_jet(const double* __restrict__ c, double ref, int p, double t,
-                                             double* out) {
-  double qm[ND + 1], qk[ND + 1];
+template <int ND, int NS, typename T>
+__device__ __forceinline__ void legendre_jets(const T* const* c, const T* ref, int p, T t,
+                                              T (*out)[ND + 1]) {
+  T qm[ND + 1], qk[ND + 1];
 #pragma unroll
   for (int j = 0; j <= ND; ++j) {
-    qm[j] = 0.0;
-    qk[j] = (j == 0) ? 1.0 : 0.0;
-    out[j] = 0.0;
+    qm[j] = 0;
+    qk[j] = (j == 0) ? T(1) : T(0);
   }
-  out[0] = ref + c[0];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+#pragma unroll
+    for (int j = 0; j <= ND; ++j) out[q][j] = 0;
+    out[q][0] = ref[q] + c[q][0];
+  }
   for (int k = 0; k + 1 < p; ++k) {
-    const double a = 2.0 * k + 1.0, b = (double)k * k, ck = c[k + 1];
+    const T a = T(2 * k + 1), b = T(k) * T(k);
 #pragma unroll
     for (int j = ND; j >= 0; --j) {
-      double prev = j ? qk[j - 1] : 0.0;
-      double qn = a * fma(t, qk[j], j * prev) - b * qm[j];
+      T prev = j ? qk[j - 1] : T(0);
+      T qn = a * fma(t, qk[j], T(j) * prev) - b * qm[j];
       qm[j] = qk[j];
       qk[j] = qn;
-      out[j] = fma(ck, qn, out[j]);
+    }
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      const T ck = c[q][k + 1];
+#pragma unroll
+      for (int j = 0; j <= ND; ++j) out[q][j] = fma(ck, qk[j], out[q][j]);
     }
   }
 }
@@ -80,29 +92,51 @@ struct Foot {
 };
 
 __device__ Foot panel_foot(const LocalArgs& a, int ip, double t, double x, double y) {
-  const double* cx = a.geo_coef + (size_t)(2 * ip) * a.p;
-  const double* cy = cx + a.p;
+  const size_t off = (size_t)(2 * ip) * a.p;
   const double rx = a.geo_ref[2 * ip], ry = a.geo_ref[2 * ip + 1];
-  double X[3], Y[3];
+  // single-precision Newton on the panel offsets (cheap start); the
+  // double-precision Newton below decides the foot
+  {
+    const float* c32[2] = {a.geo_coef32 + off, a.geo_coef32 + off + a.p};
+    const float zero2[2] = {0.f, 0.f};
+    const float xr = (float)(x - rx), yr = (float)(y - ry);
+    float tf = (float)t;
+    for (int it = 0; it < 8; ++it) {
+      float J[2][3];
+      legendre_jets<2, 2, float>(c32, zero2, a.p, tf, J);
+      float gx = J[0][0] - xr, gy = J[1][0] - yr;
+      float f = gx * J[0][1] + gy * J[1][1];
+      float s2 = J[0][1] * J[0][1] + J[1][1] * J[1][1];
+      float fp = s2 + gx * J[0][2] + gy * J[1][2];
+      if (fp < 0.1f * s2) fp = s2;
+      float tn = fminf(1.f, fmaxf(-1.f, tf - f / fp));
+      float dt = tn - tf;
+      tf = tn;
+      if (fabsf(dt) < 1e-6f) break;
+    }
+    if (tf == tf) t = (double)tf;  // keep the node start if the FP32 phase failed
+  }
+  const double* c64[2] = {a.geo_coef + off, a.geo_coef + off + a.p};
+  const double ref[2] = {rx, ry};
   for (int it = 0; it < 20; ++it) {
-    legendre_jet<2>(cx, rx, a.p, t, X);
-    legendre_jet<2>(cy, ry, a.p, t, Y);
-    double gx = X[0] - x, gy = Y[0] - y;
-    double f = gx * X[1] + gy * Y[1];
-    double s2 = X[1] * X[1] + Y[1] * Y[1];
-    double fp = s2 + gx * X[2] + gy * Y[2];
+    double J[2][3];
+    legendre_jets<2, 2, double>(c64, ref, a.p, t, J);
+    double gx = J[0][0] - x, gy = J[1][0] - y;
+    double f = gx * J[0][1] + gy * J[1][1];
+    double s2 = J[0][1] * J[0][1] + J[1][1] * J[1][1];
+    double fp = s2 + gx * J[0][2] + gy * J[1][2];
     if (fp < 0.1 * s2) fp = s2;
     double tn = fmin(1.0, fmax(-1.0, t - f / fp));
     double dt = tn - t;
     t = tn;
     if (fabs(dt) < 1e-14) break;
   }
-  legendre_jet<0>(cx, rx, a.p, t, X);
-  legendre_jet<0>(cy, ry, a.p, t, Y);
+  double J0[2][1];
+  legendre_jets<0, 2, double>(c64, ref, a.p, t, J0);
   Foot r;
   r.panel = ip;
   r.t = t;
-  r.d2 = (X[0] - x) * (X[0] - x) + (Y[0] - y) * (Y[0] - y);
+  r.d2 = (J0[0][0] - x) * (J0[0][0] - x) + (J0[1][0] - y) * (J0[1][0] - y);
   return r;
 }
 
@@ -152,10 +186,17 @@ __device__ void local_near_one(const LocalArgs& a, int64_t i, int best) {
     if (J) vl = far_volume(a, J);
   } else {
     const int p = a.p, ip = ft.panel;
-    double X[5], Y[5];
+    const bool want_s = a.out[1] && a.sig_coef, want_d = a.out[2] && a.mu_coef;
     const double* cgx = a.geo_coef + (size_t)(2 * ip) * p;
-    legendre_jet<4>(cgx, a.geo_ref[2 * ip], p, ft.t, X);
-    legendre_jet<4>(cgx + p, a.geo_ref[2 * ip + 1], p, ft.t, Y);
+    // value and four derivatives of x, y, sigma, mu at the foot (one recurrence)
+    const double* cs[4] = {cgx, cgx + p, want_s ? a.sig_coef + (size_t)ip * p : cgx,
+                           want_d ? a.mu_coef + (size_t)ip * p : cgx};
+    const double rs[4] = {a.geo_ref[2 * ip], a.geo_ref[2 * ip + 1], want_s ? a.sig_ref[ip] : 0.0,
+                          want_d ? a.mu_ref[ip] : 0.0};
+    double JJ[4][5];
+    legendre_jets<4, 4, double>(cs, rs, p, ft.t, JJ);
+    const double* X = JJ[0];
+    const double* Y = JJ[1];
     const double sp = hypot(X[1], Y[1]);
     const double Tx = X[1] / sp, Ty = Y[1] / sp;
     const double Nx = -Ty, Ny = Tx;  // inward normal of a counter-clockwise curve
@@ -186,9 +227,9 @@ __device__ void local_near_one(const LocalArgs& a, int64_t i, int best) {
     const double Ex = exp(-0.25 * c * c) * 0.56418958354775628695;  // e^{-c^2/4}/sqrt(pi)
     const double Cc = erfc(0.5 * c);
     const double c2 = c * c, c3 = c2 * c;
-    if (a.out[1] && a.sig_coef) {
-      double Sv[5], F[5], o[5];
-      legendre_jet<4>(a.sig_coef + (size_t)ip * p, a.sig_ref[ip], p, ft.t, Sv);
+    if (want_s) {
+      const double* Sv = JJ[2];
+      double F[5], o[5];
       for (int k = 1; k <= 4; ++k) F[k] = Sv[k] * fact[k];
       compose4(F, C, o);
       const double s0 = Sv[0], s1 = o[1], s2 = 2.0 * o[2];
@@ -203,9 +244,9 @@ __device__ void local_near_one(const LocalArgs& a, int64_t i, int best) {
               (kap * s2 / 8.0 + s0 * g4 / 48.0 + s1 * g3 / 12.0) * Q);
       sl = -s;
     }
-    if (a.out[2] && a.mu_coef) {
-      double Mv[5], F[5], o[5];
-      legendre_jet<4>(a.mu_coef + (size_t)ip * p, a.mu_ref[ip], p, ft.t, Mv);
+    if (want_d) {
+      const double* Mv = JJ[3];
+      double F[5], o[5];
       for (int k = 1; k <= 4; ++k) F[k] = Mv[k] * fact[k];
       compose4(F, C, o);
       const double m0 = Mv[0], m1 = o[1], m2 = 2.0 * o[2], m4 = 24.0 * o[4];
@@ -260,8 +301,13 @@ __device__ __forceinline__ double far_volume(const LocalArgs& a, const double* J
 }
 
 // Pass 1: nearest boundary node (ties: lowest index) among the 3x3 hash cells.
-// Targets whose nearest node is farther than band + margin get the far-field
-// volume term here; the others are appended to a compact list for pass 2.
+// A single-precision scan (node coordinates stored relative to their cell
+// origin) bounds every squared distance within err = 2e-5 h^2 (h the cell
+// side; six roundings of quantities below 3h); only nodes within 2 err of the
+// single-precision minimum are compared in double precision, which gives
+// exactly the double-precision nearest node.  Targets whose nearest node is
+// farther than band + margin get the far-field volume term here; the others
+// are appended to a compact list for pass 2.
 __global__ void local_classify_kernel(LocalArgs a, int2* list, int* count) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
@@ -271,20 +317,43 @@ __global__ void local_classify_kernel(LocalArgs a, int2* list, int* count) {
   if (a.nb > 0) {
     int cx = (int)floor((x - a.hx0) / a.hh), cy = (int)floor((y - a.hy0) / a.hh);
     if (cx >= 0 && cx < a.hnx && cy >= 0 && cy < a.hny) {
-      for (int oy = -1; oy <= 1; ++oy) {
-        int yy = cy + oy;
-        if (yy < 0 || yy >= a.hny) continue;
-        for (int ox = -1; ox <= 1; ++ox) {
-          int xx = cx + ox;
-          if (xx < 0 || xx >= a.hnx) continue;
-          int c = yy * a.hnx + xx;
-          for (int k = a.cell_start[c]; k < a.cell_start[c + 1]; ++k) {
-            int j = a.cell_node[k];
-            double ex = x - a.bxy[2 * j], ey = y - a.bxy[2 * j + 1];
-            double d2 = ex * ex + ey * ey;
-            if (d2 < bd2 || (d2 == bd2 && j < best)) {
-              bd2 = d2;
-              best = j;
+      const int x0c = max(cx - 1, 0), x1c = min(cx + 1, a.hnx - 1);
+      const int y0c = max(cy - 1, 0), y1c = min(cy + 1, a.hny - 1);
+      float m32 = 3.0e38f;
+      for (int yy = y0c; yy <= y1c; ++yy) {
+        const float ty = (float)(y - (a.hy0 + yy * a.hh));
+        for (int xx = x0c; xx <= x1c; ++xx) {
+          const float tx = (float)(x - (a.hx0 + xx * a.hh));
+          const int c = yy * a.hnx + xx;
+          const int k1 = a.cell_start[c + 1];
+          for (int k = a.cell_start[c]; k < k1; ++k) {
+            float2 q = a.cell_xy32[k];
+            float dx = tx - q.x, dy = ty - q.y;
+            m32 = fminf(m32, fmaf(dx, dx, dy * dy));
+          }
+        }
+      }
+      const float err = 2e-5f * (float)(a.hh * a.hh);
+      const double lower = sqrt(fmax((double)m32 - err, 0.0));
+      if (m32 < 1.0e38f && lower - a.margin < a.band) {
+        const float thr = m32 + 2.0f * err;
+        for (int yy = y0c; yy <= y1c; ++yy) {
+          const float ty = (float)(y - (a.hy0 + yy * a.hh));
+          for (int xx = x0c; xx <= x1c; ++xx) {
+            const float tx = (float)(x - (a.hx0 + xx * a.hh));
+            const int c = yy * a.hnx + xx;
+            const int k1 = a.cell_start[c + 1];
+            for (int k = a.cell_start[c]; k < k1; ++k) {
+              float2 q = a.cell_xy32[k];
+              float dx = tx - q.x, dy = ty - q.y;
+              if (fmaf(dx, dx, dy * dy) > thr) continue;
+              int j = a.cell_node[k];
+              double ex = x - a.bxy[2 * j], ey = y - a.bxy[2 * j + 1];
+              double d2 = ex * ex + ey * ey;
+              if (d2 < bd2 || (d2 == bd2 && j < best)) {
+                bd2 = d2;
+                best = j;
+              }
             }
           }
         }
@@ -340,6 +409,8 @@ void launch_local(const Plan& P, int64_t nt, const double* txy, const double* je
   a.hny = P.hash_ny;
   a.cell_start = P.d_cell_start;
   a.cell_node = P.d_cell_node;
+  a.cell_xy32 = P.d_cell_xy32;
+  a.geo_coef32 = P.d_geo_coef32;
   a.margin = P.margin;
   a.band = P.band;
   a.delta = P.delta1;
@@ -386,6 +457,8 @@ void launch_local_list(const Plan& P, int64_t nt, const double* txy, const doubl
   a.hny = P.hash_ny;
   a.cell_start = P.d_cell_start;
   a.cell_node = P.d_cell_node;
+  a.cell_xy32 = P.d_cell_xy32;
+  a.geo_coef32 = P.d_geo_coef32;
   a.margin = P.margin;
   a.band = P.band;
   a.delta = P.delta1;

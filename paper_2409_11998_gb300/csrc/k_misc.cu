@@ -63,7 +63,17 @@ __global__ void sum_kernel(const double* __restrict__ x, int64_t n, double* out)
   }
 }
 
+__global__ void to_float_kernel(const double* __restrict__ src, float* dst, int64_t n) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) dst[j] = (float)src[j];
+}
+
 }  // namespace
+
+void launch_to_float(const double* src, float* dst, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  to_float_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, dst, n);
+}
 
 void launch_panel_coef(const Plan& P, const double* vals, int stride, int ncomp, double* coef,
                        double* ref, cudaStream_t s) {

@@ -17,6 +17,46 @@ struct lp_plan_s {
   Plan P;
 };
 
+namespace lpg {
+
+// Forward transform of one channel: real rows [row_lo, row_hi) along x
+// (the other rows are zero), then the K + 1 kept complex columns along y.
+void fft_forward(const Plan& P, int level, int c) {
+  const GridLevel& G = P.lv[level];
+  const size_t r0 = (size_t)G.row_lo;
+  if (P.precision == LP_FP64) {
+    double* re = (double*)G.chan[c];
+    cufftDoubleComplex* cz = (cufftDoubleComplex*)G.chan[c];
+    cufftExecD2Z(G.row_fwd, re + r0 * G.pitch, cz + r0 * (G.g / 2 + 1));
+    cufftExecZ2Z(G.col, cz, cz, CUFFT_FORWARD);
+  } else {
+    float* re = (float*)G.chan[c];
+    cufftComplex* cz = (cufftComplex*)G.chan[c];
+    cufftExecR2C(G.row_fwd, re + r0 * G.pitch, cz + r0 * (G.g / 2 + 1));
+    cufftExecC2C(G.col, cz, cz, CUFFT_FORWARD);
+  }
+}
+
+// Inverse: the K + 1 columns along y (the multiplier zeroed every other
+// column), then the complex-to-real rows [row_lo, row_hi) that targets read.
+void fft_inverse(const Plan& P, int level, int c) {
+  const GridLevel& G = P.lv[level];
+  const size_t r0 = (size_t)G.row_lo;
+  if (P.precision == LP_FP64) {
+    double* re = (double*)G.chan[c];
+    cufftDoubleComplex* cz = (cufftDoubleComplex*)G.chan[c];
+    cufftExecZ2Z(G.col, cz, cz, CUFFT_INVERSE);
+    cufftExecZ2D(G.row_inv, cz + r0 * (G.g / 2 + 1), re + r0 * G.pitch);
+  } else {
+    float* re = (float*)G.chan[c];
+    cufftComplex* cz = (cufftComplex*)G.chan[c];
+    cufftExecC2C(G.col, cz, cz, CUFFT_INVERSE);
+    cufftExecC2R(G.row_inv, cz + r0 * (G.g / 2 + 1), re + r0 * G.pitch);
+  }
+}
+
+}  // namespace lpg
+
 namespace {
 
 bool is_device_ptr(const void* p) {
@@ -71,19 +111,21 @@ bool ensure_stage(Plan& P, size_t bytes) {
 size_t round256(size_t b) { return ((b + 255) / 256) * 256; }
 
 lp_status make_fft_plans(Plan& P, GridLevel& G) {
-  int n[2] = {G.g, G.g};
-  int rembed[2] = {G.g, G.pitch};
-  int cembed[2] = {G.g, G.g / 2 + 1};
+  const int g = G.g, nc = g / 2 + 1;
   const bool f64 = P.precision == LP_FP64;
-  int rdist = G.g * G.pitch, cdist = G.g * (G.g / 2 + 1);
-  if (cufftPlanMany(&G.fwd, 2, n, rembed, 1, rdist, cembed, 1, cdist, f64 ? CUFFT_D2Z : CUFFT_R2C, 1) !=
-      CUFFT_SUCCESS)
+  int n[1] = {g};
+  int rin[1] = {G.pitch}, cin[1] = {nc}, col[1] = {g};
+  const int nrows = G.row_hi - G.row_lo;
+  if (cufftPlanMany(&G.row_fwd, 1, n, rin, 1, G.pitch, cin, 1, nc, f64 ? CUFFT_D2Z : CUFFT_R2C,
+                    nrows) != CUFFT_SUCCESS ||
+      cufftPlanMany(&G.row_inv, 1, n, cin, 1, nc, rin, 1, G.pitch, f64 ? CUFFT_Z2D : CUFFT_C2R,
+                    nrows) != CUFFT_SUCCESS ||
+      cufftPlanMany(&G.col, 1, n, col, nc, 1, col, nc, 1, f64 ? CUFFT_Z2Z : CUFFT_C2C, G.K + 1) !=
+          CUFFT_SUCCESS)
     return LP_ERR_CUDA;
-  if (cufftPlanMany(&G.inv, 2, n, cembed, 1, cdist, rembed, 1, rdist, f64 ? CUFFT_Z2D : CUFFT_C2R, 1) !=
-      CUFFT_SUCCESS)
-    return LP_ERR_CUDA;
-  cufftSetStream(G.fwd, P.stream);
-  cufftSetStream(G.inv, P.stream);
+  cufftSetStream(G.row_fwd, P.stream);
+  cufftSetStream(G.row_inv, P.stream);
+  cufftSetStream(G.col, P.stream);
   return LP_OK;
 }
 
@@ -93,13 +135,15 @@ void destroy_plan(Plan& P) {
     for (auto& c : G.chan) dfree(c);
     dfree(G.mtab);
     dfree(G.mtab32);
-    if (G.fwd) cufftDestroy(G.fwd);
-    if (G.inv) cufftDestroy(G.inv);
+    if (G.row_fwd) cufftDestroy(G.row_fwd);
+    if (G.row_inv) cufftDestroy(G.row_inv);
+    if (G.col) cufftDestroy(G.col);
   }
   void* bufs[] = {P.d_bxy, P.d_bw, P.d_bnrm, P.d_geo_coef, P.d_geo_ref, P.d_leg_T, P.d_tau,
                   P.d_cell_start, P.d_cell_node, P.d_vxy, P.d_vq, P.d_sigma, P.d_sigma_coef,
                   P.d_sigma_ref, P.d_mu, P.d_mu_coef, P.d_mu_ref, P.d_bq, P.d_qsum, P.d_stage,
-                  P.d_out, P.d_status, P.d_near, P.d_near_count};
+                  P.d_out, P.d_status, P.d_near, P.d_near_count, P.d_cell_xy32,
+                  P.d_geo_coef32};
   for (void* b : bufs) dfree(b);
   if (P.h_status) cudaFreeHost(P.h_status);
   for (auto& e : P.ev)
@@ -423,25 +467,12 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
     if (nq) launch_spread(P, l, P.d_bxy, bq, nq, bg, P.nb, s);
   }
   cudaEventRecord(P.ev[3], s);
-  const bool f64 = P.precision == LP_FP64;
-  auto fwd = [&](GridLevel& G, int c) {
-    if (f64)
-      cufftExecD2Z(G.fwd, (cufftDoubleReal*)G.chan[c], (cufftDoubleComplex*)G.chan[c]);
-    else
-      cufftExecR2C(G.fwd, (cufftReal*)G.chan[c], (cufftComplex*)G.chan[c]);
-  };
-  auto inv = [&](GridLevel& G, int c) {
-    if (f64)
-      cufftExecZ2D(G.inv, (cufftDoubleComplex*)G.chan[c], (cufftDoubleReal*)G.chan[c]);
-    else
-      cufftExecC2R(G.inv, (cufftComplex*)G.chan[c], (cufftReal*)G.chan[c]);
-  };
   for (int l = 0; l < 2; ++l) {
-    if (wv) fwd(P.lv[l], 0);
-    if (ws) fwd(P.lv[l], 1);
+    if (wv) fft_forward(P, l, 0);
+    if (ws) fft_forward(P, l, 1);
     if (wd) {
-      fwd(P.lv[l], 2);
-      fwd(P.lv[l], 3);
+      fft_forward(P, l, 2);
+      fft_forward(P, l, 3);
     }
   }
   cudaEventRecord(P.ev[4], s);
@@ -449,9 +480,9 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
   for (int l = 0; l < 2; ++l) launch_multiplier(P, l, wv, ws, wd, s);
   cudaEventRecord(P.ev[5], s);
   for (int l = 0; l < 2; ++l) {
-    if (wv) inv(P.lv[l], 0);
-    if (ws) inv(P.lv[l], 1);
-    if (wd) inv(P.lv[l], 2);
+    if (wv) fft_inverse(P, l, 0);
+    if (ws) fft_inverse(P, l, 1);
+    if (wd) fft_inverse(P, l, 2);
   }
   cudaEventRecord(P.ev[6], s);
   launch_interp(P, nt, dt, dout[0], dout[1], dout[2], s);
@@ -518,31 +549,18 @@ lp_status lp_execute_noalloc(lp_plan_t h, int64_t nt, const double* txy, const d
     if (nq) launch_spread(P, l, P.d_bxy, bq, nq, bg, P.nb, s);
   }
   cudaEventRecord(P.ev[3], s);
-  const bool f64 = P.precision == LP_FP64;
   for (int l = 0; l < 2; ++l) {
-    GridLevel& G = P.lv[l];
     const int chans[4] = {wv ? 0 : -1, ws ? 1 : -1, wd ? 2 : -1, wd ? 3 : -1};
-    for (int c : chans) {
-      if (c < 0) continue;
-      if (f64)
-        cufftExecD2Z(G.fwd, (cufftDoubleReal*)G.chan[c], (cufftDoubleComplex*)G.chan[c]);
-      else
-        cufftExecR2C(G.fwd, (cufftReal*)G.chan[c], (cufftComplex*)G.chan[c]);
-    }
+    for (int c : chans)
+      if (c >= 0) fft_forward(P, l, c);
   }
   cudaEventRecord(P.ev[4], s);
   for (int l = 0; l < 2; ++l) launch_multiplier(P, l, wv, ws, wd, s);
   cudaEventRecord(P.ev[5], s);
   for (int l = 0; l < 2; ++l) {
-    GridLevel& G = P.lv[l];
     const int chans[3] = {wv ? 0 : -1, ws ? 1 : -1, wd ? 2 : -1};
-    for (int c : chans) {
-      if (c < 0) continue;
-      if (f64)
-        cufftExecZ2D(G.inv, (cufftDoubleComplex*)G.chan[c], (cufftDoubleReal*)G.chan[c]);
-      else
-        cufftExecC2R(G.inv, (cufftComplex*)G.chan[c], (cufftReal*)G.chan[c]);
-    }
+    for (int c : chans)
+      if (c >= 0) fft_inverse(P, l, c);
   }
   cudaEventRecord(P.ev[6], s);
   launch_interp(P, nt, txy, V, S, D, s);

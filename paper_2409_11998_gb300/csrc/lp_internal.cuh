@@ -56,7 +56,10 @@ struct GridLevel {
   void* chan[4] = {nullptr, nullptr, nullptr, nullptr};  // V, S, D1, D2 in-place buffers
   double* mtab = nullptr;  // (K+1)^2 deconvolved multiplier table, FP64
   float* mtab32 = nullptr; // same in FP32 with the zero mode removed (FP32 path)
-  cufftHandle fwd = 0, inv = 0;
+  // pruned transforms: real rows [row_lo, row_hi) along x, then complex
+  // columns 0..K along y (forward), and the reverse for the inverse
+  int row_lo = 0, row_hi = 0;
+  cufftHandle row_fwd = 0, row_inv = 0, col = 0;
   size_t chan_bytes = 0;
 };
 
@@ -97,6 +100,8 @@ struct Plan {
   int hash_nx = 0, hash_ny = 0;
   int* d_cell_start = nullptr;  // [nx*ny + 1]
   int* d_cell_node = nullptr;   // [nb] node ids sorted by cell
+  float2* d_cell_xy32 = nullptr;  // [nb] node coordinates relative to their cell's origin (FP32)
+  float* d_geo_coef32 = nullptr;  // FP32 copy of d_geo_coef (Newton start)
 
   // bound sources
   int64_t nv = 0;
@@ -148,9 +153,12 @@ void launch_local(const Plan& P, int64_t nt, const double* txy, const double* je
                   double* S, double* D, cudaStream_t s);
 void launch_local_list(const Plan& P, int64_t nt, const double* txy, const double* jet, double* V,
                        double* S, double* D, int2* list, int* count, cudaStream_t s);
+void fft_forward(const Plan& P, int level, int chan);
+void fft_inverse(const Plan& P, int level, int chan);
 void launch_panel_coef(const Plan& P, const double* vals, int stride, int ncomp, double* coef,
                        double* ref, cudaStream_t s);
 void launch_strengths(const Plan& P, int kind, cudaStream_t s);
+void launch_to_float(const double* src, float* dst, int64_t n, cudaStream_t s);
 void launch_volume_q(const Plan& P, const double* f, const double* w, double* q, int64_t n,
                      cudaStream_t s);
 void launch_sum(const Plan& P, const double* x, int64_t n, double* out, cudaStream_t s);
