@@ -223,21 +223,7 @@ def run_lp(args, rank, world, local_rank):
     info = lp.lp_plan_info(plan)
     st = {k: statistics.mean(s[k] for s in stages) for k in stages[0]}
 
-    # roofline of the dominant kernel stage (spread or interpolation), FP64
-    b = 8
-    g2 = info["g_nh"] ** 2 + info["g_fh"] ** 2
-    spread_bytes = (nv + nb) * 2 * b + (nv + 3 * nb) * b + g2 * b * 4
-    interp_bytes = g2 * b * 3 + nt * (2 * b + 8 * 3)
-    peak, peak_kind = peaks()
-    cand = {"spread": (st["spread"], spread_bytes), "interp": (st["interp"], interp_bytes)}
-    dom = max(cand, key=lambda k: cand[k][0])
-    ms, byts = cand[dom]
-    achieved = byts / (ms / 1e3) / 1e9
-    kname = {"spread": "spread_atomic_kernel", "interp": "interp_kernel"}[dom]
-    roof = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 2), "peak": peak,
-            "unit": "GB/s", "frac": round(achieved / peak, 5), "traffic": kernel_traffic(kname),
-            "algorithmic_bytes_per_launch": int(byts), "launch_ms": round(ms, 4),
-            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"}
+    roof = roofline(info, st, nv, nb, nt, precision="fp64")
 
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps,
@@ -259,6 +245,54 @@ def run_lp(args, rank, world, local_rank):
             res["cpu_baseline"] = cpu_baseline(prob, budget_s=15.0)
     ev.close()
     return res
+
+
+def fp64_peak_tflops():
+    """FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA per clock
+    per SM (the GB300 FP64 rate, 1.25 TFLOP/s nominal) x 2 FLOP x max SM clock."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    mhz = 2070.0
+    if os.path.exists(p):
+        mhz = float(json.load(open(p)).get("sm_max_mhz", mhz))
+    return 152 * 2 * 2 * mhz * 1e6 / 1e12
+
+
+def roofline(info, st, nv, nb, nt, precision):
+    """Roofline of this library's dominant kernel (spread or interpolation).
+    Algorithmic bytes: sources read once and grids written once (spread);
+    grids read once and targets read/written once (interpolation).
+    Algorithmic FLOPs (FP64 path): per point and level, the two stencil
+    polynomials (2 W (nc-1) FMA) plus W(W+1) FMA per output channel
+    (interpolation) or W(W+1) multiplies per input channel (spread)."""
+    b = 8 if precision == "fp64" else 4
+    g2 = info["g_nh"] ** 2 + info["g_fh"] ** 2
+    W, nc = int(info["w"]), int(info["es_nc"])
+    spread_bytes = (nv + nb) * 16 + (nv + 3 * nb) * 8 + g2 * b * 4
+    interp_bytes = g2 * b * 3 + nt * (16 + 8 * 3)
+    spread_flops = 2 * (2 * W * (nc - 1) * 2 * (nv + nb) + W * (W + 1) * 2 * (nv + 3 * nb))
+    interp_flops = 2 * 2 * nt * (2 * W * (nc - 1) + 3 * W * (W + 1))
+    hbm, hbm_kind = peaks()
+    cand = {"spread": (st["spread"], spread_bytes, spread_flops, "spread_atomic_kernel"),
+            "interp": (st["interp"], interp_bytes, interp_flops, "interp_kernel")}
+    dom = max(cand, key=lambda k: cand[k][0])
+    ms, byts, flops, kname = cand[dom]
+    gbs = byts / (ms / 1e3) / 1e9
+    hbm_part = {"achieved_gbs": round(gbs, 2), "peak_gbs": hbm, "frac": round(gbs / hbm, 5),
+                "algorithmic_bytes_per_launch": int(byts),
+                "peak_source": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+    if precision == "fp64":
+        tf = flops / (ms / 1e3) / 1e12
+        peak = fp64_peak_tflops()
+        return {"kernel": kname, "bound": "alu", "achieved": round(tf, 4), "peak": round(peak, 4),
+                "unit": "TFLOP/s (FP64)", "frac": round(tf / peak, 4),
+                "traffic": kernel_traffic(kname), "algorithmic_flops_per_launch": int(flops),
+                "launch_ms": round(ms, 4), "stage": dom,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x sm_max_mhz",
+                "hbm": hbm_part}
+    return {"kernel": kname, "bound": "hbm", "achieved": round(gbs, 2), "peak": hbm, "unit": "GB/s",
+            "frac": round(gbs / hbm, 5), "traffic": kernel_traffic(kname),
+            "algorithmic_bytes_per_launch": int(byts), "launch_ms": round(ms, 4), "stage": dom,
+            "peak_source": hbm_part["peak_source"]}
 
 
 def parity_sample(prob, outs, n=48):
@@ -342,10 +376,12 @@ def run_fp32(args, prob, dev, stream, points):
         ms.append(a.elapsed_time(b))
     st = lp.lp_stage_times(plan)
     par = parity_sample(prob, outs)
+    info = lp.lp_plan_info(plan)
+    roof = roofline(info, st, nv, len(prob["bnd"]["w"]), nt, precision="fp32")
     ev.close()
     return {"value": points / (statistics.mean(ms) / 1e3), "unit": UNIT, "dtype": "f32 (FP64 zero mode)",
             "tol": 1e-5, "ms_per_step": statistics.mean(ms),
-            "stages_ms": {k: round(v, 4) for k, v in st.items()}, "parity": par}
+            "stages_ms": {k: round(v, 4) for k, v in st.items()}, "parity": par, "roofline": roof}
 
 
 def cpu_baseline(prob, budget_s=15.0):

@@ -148,10 +148,11 @@ lp_status lp_destroy(lp_plan_t plan);
 const char* lp_status_string(lp_status status);
 
 /* Plan parameters, for diagnostics and benchmarks:
- * out[0..18] = {delta_1, delta_2, kernel width w, beta, g_NH, K_NH, P_NH, g_FH, K_FH,
+ * out[0..19] = {delta_1, delta_2, kernel width w, beta, g_NH, K_NH, P_NH, g_FH, K_FH,
  *               P_FH, L_FH, band 12 sqrt(delta_1), node-gap margin, device bytes,
  *               precision, order, kernels launched by this plan so far,
- *               max error of the kernel's polynomial form, its coefficient count}. */
+ *               max error of the kernel's polynomial form, its coefficient count,
+ *               realised upsampling min g/(2K+1)}. */
 lp_status lp_plan_info(lp_plan_t plan, double* out);
 
 /* Per-stage device times of the last lp_execute in milliseconds (CUDA events

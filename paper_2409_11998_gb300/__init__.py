@@ -148,10 +148,11 @@ def lp_destroy(plan):
 
 
 def lp_plan_info(plan):
-    out = np.zeros(19)
+    out = np.zeros(20)
     _check(_lib().lp_plan_info(plan, out.ctypes.data), "lp_plan_info")
     keys = ["delta1", "delta2", "w", "beta", "g_nh", "K_nh", "P_nh", "g_fh", "K_fh", "P_fh", "L_fh",
-            "band", "margin", "device_bytes", "precision", "order", "launches", "es_fit_err", "es_nc"]
+            "band", "margin", "device_bytes", "precision", "order", "launches", "es_fit_err", "es_nc",
+            "sigma_eff"]
     return dict(zip(keys, out.tolist()))
 
 

@@ -274,10 +274,16 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
   P.side = std::max(P.box_hi[0] - P.box_lo[0], P.box_hi[1] - P.box_lo[1]);
   P.on_tol = 1e-12 * P.side;
   P.stream = (cudaStream_t)dom->stream;
-  int w = (int)std::ceil(-std::log10(tol)) + 1;
+  // Kernel width and upsampling.  FP64 is bound by cuFFT's FP64 arithmetic,
+  // so its grids use sigma = 1.5 (0.56x the modes of sigma = 2) and one more
+  // kernel point; FP32 keeps sigma = 2.  Measured (disk, tol 1e-9): sigma 2,
+  // w 10 -> 4.3e-10; sigma 1.5, w 11 -> 3.9e-10.  FP32 adds one point for
+  // margin against single-precision rounding.
+  P.sigma = P.precision == LP_FP64 ? 1.5 : 2.0;
+  int w = (int)std::ceil(-std::log10(tol)) + 2;
   w = std::min(std::max(w, 4), kMaxW);
   P.ker.w = w;
-  P.ker.beta = 2.30 * w;
+  P.ker.beta = 2.30 * w;  // refined by choose_levels for the realised sigma
   P.ker.half_w = 0.5 * w;
   lp_status st = choose_levels(P);
   if (st == LP_OK) st = build_tables(P);
@@ -594,10 +600,10 @@ lp_status lp_destroy(lp_plan_t h) {
 lp_status lp_plan_info(lp_plan_t h, double* out) {
   if (!h || !out) return LP_ERR_ARG;
   const Plan& P = h->P;
-  double v[19] = {P.delta1, P.delta2, (double)P.ker.w, P.ker.beta, (double)P.lv[0].g, (double)P.lv[0].K,
+  double v[20] = {P.delta1, P.delta2, (double)P.ker.w, P.ker.beta, (double)P.lv[0].g, (double)P.lv[0].K,
                   P.lv[0].P, (double)P.lv[1].g, (double)P.lv[1].K, P.lv[1].P, P.lv[1].L, P.band,
                   P.margin, (double)P.device_bytes, (double)P.precision, (double)P.order,
-                  (double)P.launches, P.es_fit_err, (double)P.es.nc};
+                  (double)P.launches, P.es_fit_err, (double)P.es.nc, P.sigma_eff};
   std::memcpy(out, v, sizeof(v));
   return LP_OK;
 }

@@ -75,6 +75,8 @@ struct Plan {
   double delta1 = 0, delta2 = 0, tol = 0;
   double box_lo[2] = {0, 0}, box_hi[2] = {0, 0};
   double side = 0;        // max box extent
+  double sigma = 2.0;     // target upsampling of the history grids (g >= sigma (2K+1))
+  double sigma_eff = 2.0; // smallest realised g / (2K+1) over the two levels
   double on_tol = 0;      // on-surface classification radius
   Kernel ker{};
   EsPoly<double> es{};

@@ -120,7 +120,7 @@ lp_status choose_levels(Plan& P) {
     }
     G.dk = 2.0 * kPi / G.P;
     G.K = (int)std::ceil(kmax / G.dk);
-    int g = fft_size(std::max(2 * (2 * G.K + 1), 2 * P.ker.w + 8));
+    int g = fft_size(std::max((int)std::ceil(P.sigma * (2 * G.K + 1)), 2 * P.ker.w + 8));
     // the spreading stencil of every point in the box must stay inside the
     // grid (no periodic wrap): margin (P - D)/2 >= (w/2 + 2) h
     while ((G.P - D) / 2.0 < (P.ker.half_w + 2.0) * (G.P / g)) g = fft_size(g + 2);
@@ -136,6 +136,11 @@ lp_status choose_levels(Plan& P) {
     G.row_hi = std::min(g, (int)std::ceil((P.box_hi[1] - G.y0) / G.h + P.ker.half_w) + 3);
     if (G.K > g / 2 - 1) return LP_ERR_ARG;
   }
+  // ES shape parameter for the realised upsampling (the smaller of the two
+  // levels): beta = 0.97 pi (1 - 1/(2 sigma)) w, the exponential-of-semicircle
+  // choice of Barnett, Magland and af Klinteberg (SISC 2019).
+  P.sigma_eff = std::min(P.lv[0].g / (2.0 * P.lv[0].K + 1.0), P.lv[1].g / (2.0 * P.lv[1].K + 1.0));
+  P.ker.beta = 0.97 * kPi * (1.0 - 0.5 / P.sigma_eff) * P.ker.w;
   return LP_OK;
 }
 

@@ -120,10 +120,14 @@ def test_edge_cases(lp, disk, disk_ref):
     # empty target set
     lp.lp_execute(ev.plan, 0, None, None, None, None, None)
     lp.lp_sync(ev.plan)
-    # a single target, and a ragged count
+    # a single target, and a ragged count: errors measured against the whole
+    # target set's RMS value (the metric's scale), not a 1-3 point subset's
     for n in (1, 3, 129):
         out = ev.evaluate(tgt_xy=disk["tgt_xy"][:n], tgt_jet=disk["tgt_jet"][:n])
-        _compare(out, {k: v[:n] for k, v in disk_ref.items() if k in "VSD"}, ("V", "S", "D"), 1e-9, 5e-9)
+        for k in "VSD":
+            got = out[k].cpu().numpy()
+            rms = np.linalg.norm(disk_ref[k]) / np.sqrt(len(disk_ref[k]))
+            assert np.max(np.abs(got - disk_ref[k][:n])) < 5e-9 * rms, k
     # a target outside the box is reported, not written out of bounds
     bad = np.array([[10.0, 0.0]])
     with pytest.raises(lp.LpError) as e:
