@@ -51,6 +51,7 @@ extern "C" {
 #endif
 
 typedef struct lp_plan_s* lp_plan_t;
+typedef struct lp_batch_s* lp_batch_t;
 
 typedef enum {
   LP_OK = 0,
@@ -137,6 +138,33 @@ lp_status lp_execute(lp_plan_t plan, int64_t n_t, const double* t_xy, const doub
  * cudaFree or allocating library routine is called. */
 lp_status lp_execute_noalloc(lp_plan_t plan, int64_t n_t, const double* t_xy, const double* f_jet,
                              double* V, double* S, double* D);
+
+/* Batched evaluation of a wave of independent problems (SURVEY configs 4/5:
+ * uneven problems in one launch per kernel per wave).  A batch owns only the
+ * wave's argument records and candidate list; the member plans are ordinary
+ * plans (each bound with lp_volume / lp_single_layer / lp_double_layer on a
+ * stream the batch stream is ordered after, e.g. the same stream).
+ *   lp_batch_create(stream, &b): the batch's work runs on stream.
+ *   lp_batch_execute(b, n, plans, n_t, t_xy, f_jet, V, S, D): evaluates, for
+ *     every member i, exactly what lp_execute(plans[i], n_t[i], t_xy[i],
+ *     f_jet[i], V[i], S[i], D[i]) evaluates (Sec. 3 and Sec. 4 per problem),
+ *     with one zeroing, one spread, one multiplier, one interpolation and one
+ *     local classify + near launch for the whole wave; each member's FFTs are
+ *     issued on the batch stream.  Arrays have n entries; V, S, D (and their
+ *     entries) may be NULL; all buffers must be device memory (LP_ERR_ARG
+ *     otherwise); all members must share precision and tolerance (one kernel
+ *     shape per wave) and be distinct.  Asynchronous: lp_batch_sync waits,
+ *     lp_sync(member) returns that member's device status.
+ *   lp_batch_stage_times(b, out[9]): {zeroing+record copy, spread, forward
+ *     FFTs, multiplier, inverse FFTs, interpolation, local, total} in ms of
+ *     the last wave, and the batched launches issued so far. */
+lp_status lp_batch_create(void* stream, lp_batch_t* batch);
+lp_status lp_batch_execute(lp_batch_t batch, int n, const lp_plan_t* plans, const int64_t* n_t,
+                           const double* const* t_xy, const double* const* f_jet, double* const* V,
+                           double* const* S, double* const* D);
+lp_status lp_batch_sync(lp_batch_t batch);
+lp_status lp_batch_stage_times(lp_batch_t batch, float* out);
+lp_status lp_batch_destroy(lp_batch_t batch);
 
 /* Wait for the plan's stream; return and clear the device status word. */
 lp_status lp_sync(lp_plan_t plan);

@@ -24,7 +24,9 @@ LP_FP64, LP_FP32 = 0, 1
 STATUS = {0: "LP_OK", 1: "LP_ERR_ARG", 2: "LP_ERR_OUT_OF_BOX", 3: "LP_ERR_NOMEM",
           4: "LP_ERR_CUDA", 5: "LP_ERR_UNSUPPORTED", 6: "LP_ERR_STATE"}
 EXPORTS = ("lp_plan", "lp_volume", "lp_single_layer", "lp_double_layer", "lp_execute", "lp_sync",
-           "lp_destroy", "lp_status_string", "lp_plan_info", "lp_stage_times", "lp_execute_noalloc")
+           "lp_destroy", "lp_status_string", "lp_plan_info", "lp_stage_times", "lp_execute_noalloc",
+           "lp_batch_create", "lp_batch_execute", "lp_batch_sync", "lp_batch_stage_times",
+           "lp_batch_destroy")
 
 
 class LpError(RuntimeError):
@@ -57,6 +59,11 @@ def _lib():
         L.lp_double_layer.argtypes = [vp, vp]
         L.lp_execute.argtypes = [vp, i64, vp, vp, vp, vp, vp]
         L.lp_execute_noalloc.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+        L.lp_batch_create.argtypes = [vp, ctypes.POINTER(vp)]
+        L.lp_batch_execute.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp]
+        L.lp_batch_sync.argtypes = [vp]
+        L.lp_batch_stage_times.argtypes = [vp, vp]
+        L.lp_batch_destroy.argtypes = [vp]
         L.lp_sync.argtypes = [vp]
         L.lp_destroy.argtypes = [vp]
         L.lp_status_string.argtypes = [i32]
@@ -137,6 +144,43 @@ def lp_execute_noalloc(plan, n_t, t_xy, f_jet, V=None, S=None, D=None):
     (see include/lp.h)."""
     _check(_lib().lp_execute_noalloc(plan, int(n_t), _ptr(t_xy), _ptr(f_jet), _ptr(V), _ptr(S),
                                      _ptr(D)), "lp_execute_noalloc")
+
+
+def lp_batch_create(stream=0):
+    h = ctypes.c_void_p()
+    _check(_lib().lp_batch_create(int(stream) if stream else None, ctypes.byref(h)), "lp_batch_create")
+    return h
+
+
+def lp_batch_execute(batch, plans, n_t, t_xy, f_jet=None, V=None, S=None, D=None):
+    """One wave: plans[i] evaluated at n_t[i] targets t_xy[i] (device
+    tensors); V, S, D are lists of output tensors (entries may be None)."""
+    n = len(plans)
+    P = (ctypes.c_void_p * n)(*[p.value for p in plans])
+    NT = (ctypes.c_int64 * n)(*[int(x) for x in n_t])
+
+    def arr(lst):
+        if lst is None:
+            return None
+        return (ctypes.c_void_p * n)(*[_ptr(x) for x in lst])
+    args = [arr(t_xy), arr(f_jet), arr(V), arr(S), arr(D)]
+    _check(_lib().lp_batch_execute(batch, n, P, NT, *[ctypes.cast(a, ctypes.c_void_p) if a is not None else None
+                                                      for a in args]), "lp_batch_execute")
+
+
+def lp_batch_sync(batch):
+    _check(_lib().lp_batch_sync(batch), "lp_batch_sync")
+
+
+def lp_batch_stage_times(batch):
+    out = np.zeros(9, dtype=np.float32)
+    _check(_lib().lp_batch_stage_times(batch, out.ctypes.data), "lp_batch_stage_times")
+    keys = ["zero_copy", "spread", "fft_fwd", "multiplier", "fft_inv", "interp", "local", "total", "launches"]
+    return dict(zip(keys, out.tolist()))
+
+
+def lp_batch_destroy(batch):
+    _check(_lib().lp_batch_destroy(batch), "lp_batch_destroy")
 
 
 def lp_sync(plan):

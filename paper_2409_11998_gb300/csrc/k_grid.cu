@@ -1,25 +1,17 @@
 // History part on the periodic grids (Sec. 3, Steps 2-4): type-1 spreading of
 // weighted sources with the exponential-of-semicircle kernel, the diagonal
 // Fourier multiplier with kernel deconvolution, and type-2 interpolation.
+// Each kernel body is a per-item device function shared by the single-plan
+// launch (arguments by value) and the batched launch (an array of argument
+// records plus a per-block work list, one launch for a whole wave of plans).
 #include <cmath>
+#include <vector>
 
 #include "lp_internal.cuh"
 
 namespace lpg {
 
 namespace {
-
-template <typename T>
-struct SpreadArgs {
-  const double* xy;
-  const double* q[3];
-  void* grid[3];
-  int nq;
-  int64_t n;
-  GridDev gd;
-  unsigned* status;
-  EsPoly<T> es;
-};
 
 // Grid coordinate split: first stencil index i0 = floor(u - w/2) + 1 and the
 // offset d0 = u - i0 of the point from it (in [w/2 - 1, w/2)).
@@ -43,9 +35,7 @@ __device__ __forceinline__ void es_weights(const EsPoly<T>& P, T v, T* out) {
 }
 
 template <typename T, int W>
-__global__ void spread_atomic_kernel(const __grid_constant__ SpreadArgs<T> a) {
-  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= a.n) return;
+__device__ __forceinline__ void spread_point(const SpreadArgs<T>& a, int64_t j) {
   double ux = (a.xy[2 * j] - a.gd.x0) * a.gd.inv_h;
   double uy = (a.xy[2 * j + 1] - a.gd.y0) * a.gd.inv_h;
   int ix, iy;
@@ -70,58 +60,70 @@ __global__ void spread_atomic_kernel(const __grid_constant__ SpreadArgs<T> a) {
   }
 }
 
+template <typename T, int W>
+__global__ void spread_atomic_kernel(const __grid_constant__ SpreadArgs<T> a) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < a.n) spread_point<T, W>(a, j);
+}
+
+template <typename T, int W>
+__global__ void spread_batch_kernel(const SpreadArgs<T>* __restrict__ args, const int2* __restrict__ work) {
+  const int2 wk = work[blockIdx.x];
+  const SpreadArgs<T>& a = args[wk.x];
+  int64_t j = (int64_t)wk.y + threadIdx.x;
+  if (j < a.n) spread_point<T, W>(a, j);
+}
+
+// Multiplier on the half spectrum (row index = m_y mod g, column = m_x):
+// kept modes |m| <= K get the deconvolved history multiplier, every other
+// mode is zeroed.  D channel: multiplier times -i (k1 F1 + k2 F2), the
+// source-point derivative of eq. dlpot.
 template <typename C, typename R>
-__global__ void multiplier_kernel(int g, int K, double dk, const R* __restrict__ tab, C* V, C* S,
-                                  C* D1, const C* __restrict__ D2) {
-  const int ncol = g / 2 + 1;
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)g * ncol) return;
+__device__ __forceinline__ void multiplier_mode(const MultArgs& a, int64_t idx) {
+  const int g = a.g, K = a.K, ncol = g / 2 + 1;
   int row = (int)(idx / ncol), mx = (int)(idx - (int64_t)row * ncol);
   int my = row <= g / 2 ? row : row - g;
   int amy = my < 0 ? -my : my;
   R m = 0;
-  if (mx <= K && amy <= K) m = tab[(size_t)amy * (K + 1) + mx];
-  if (V) {
-    C z = V[idx];
+  if (mx <= K && amy <= K) m = ((const R*)a.tab)[(size_t)amy * (K + 1) + mx];
+  if (a.V) {
+    C z = ((C*)a.V)[idx];
     z.x *= m;
     z.y *= m;
-    V[idx] = z;
+    ((C*)a.V)[idx] = z;
   }
-  if (S) {
-    C z = S[idx];
+  if (a.S) {
+    C z = ((C*)a.S)[idx];
     z.x *= m;
     z.y *= m;
-    S[idx] = z;
+    ((C*)a.S)[idx] = z;
   }
-  if (D1) {
-    // D channel: multiplier times -i (k1 F1 + k2 F2), derivative in the
-    // source point (eq. dlpot convention).
-    C z1 = D1[idx], z2 = D2[idx];
-    R kx = (R)(dk * mx), ky = (R)(dk * my);
+  if (a.D1) {
+    C z1 = ((C*)a.D1)[idx], z2 = ((const C*)a.D2)[idx];
+    R kx = (R)(a.dk * mx), ky = (R)(a.dk * my);
     C o;
     o.x = m * (kx * z1.y + ky * z2.y);
     o.y = -m * (kx * z1.x + ky * z2.x);
-    D1[idx] = o;
+    ((C*)a.D1)[idx] = o;
   }
 }
 
-template <typename T>
-struct InterpArgs {
-  const double* txy;
-  int64_t n;
-  const void* grid[2][3];  // [level][V,S,D]
-  GridDev gd[2];
-  const double* qsum;      // FP64 strength sums of V and S (FP32 path), or null
-  double zero_factor;      // sum over levels of (dk/2pi)^2 M(0)
-  double* out[3];
-  unsigned* status;
-  EsPoly<T> es;
-};
+template <typename C, typename R>
+__global__ void multiplier_kernel(const __grid_constant__ MultArgs a) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < (int64_t)a.g * (a.g / 2 + 1)) multiplier_mode<C, R>(a, idx);
+}
+
+template <typename C, typename R>
+__global__ void multiplier_batch_kernel(const MultArgs* __restrict__ args, const int2* __restrict__ work) {
+  const int2 wk = work[blockIdx.x];
+  const MultArgs& a = args[wk.x];
+  int64_t idx = (int64_t)wk.y * blockDim.x + threadIdx.x;
+  if (idx < (int64_t)a.g * (a.g / 2 + 1)) multiplier_mode<C, R>(a, idx);
+}
 
 template <typename T, int W>
-__global__ void interp_kernel(const __grid_constant__ InterpArgs<T> a) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
+__device__ __forceinline__ void interp_target(const InterpArgs<T>& a, int64_t i) {
   // FP32 path: the k = 0 term (the log constant) is summed and added in FP64.
   double acc[3] = {0.0, 0.0, 0.0};
   if (a.qsum) {
@@ -168,6 +170,35 @@ __global__ void interp_kernel(const __grid_constant__ InterpArgs<T> a) {
     if (a.out[c]) a.out[c][i] = acc[c];
 }
 
+template <typename T, int W>
+__global__ void interp_kernel(const __grid_constant__ InterpArgs<T> a) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.n) interp_target<T, W>(a, i);
+}
+
+template <typename T, int W>
+__global__ void interp_batch_kernel(const InterpArgs<T>* __restrict__ args, const int2* __restrict__ work) {
+  const int2 wk = work[blockIdx.x];
+  const InterpArgs<T>& a = args[wk.x];
+  int64_t i = (int64_t)wk.y + threadIdx.x;
+  if (i < a.n) interp_target<T, W>(a, i);
+}
+
+// Zero a list of buffers (the grids of a wave) in one launch; each work item
+// clears kZeroChunk 16-byte words of one segment.
+__global__ void zero_batch_kernel(const ZeroSeg* __restrict__ segs, const int2* __restrict__ work) {
+  const int2 wk = work[blockIdx.x];
+  const ZeroSeg sg = segs[wk.x];
+  const int64_t base = (int64_t)wk.y * kZeroChunk;
+  float4* p = (float4*)sg.ptr;
+  for (int k = threadIdx.x; k < kZeroChunk; k += blockDim.x) {
+    int64_t e = base + k;
+    if (e < sg.n16) p[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+}  // namespace
+
 GridDev grid_dev(const GridLevel& G) {
   GridDev d;
   d.g = G.g;
@@ -177,8 +208,6 @@ GridDev grid_dev(const GridLevel& G) {
   d.inv_h = 1.0 / G.h;
   return d;
 }
-
-}  // namespace
 
 #define LP_WIDTH_CASES(X) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
 
@@ -195,34 +224,51 @@ static void spread_dispatch(const SpreadArgs<T>& a, int w, unsigned blocks, int 
   }
 }
 
+template <typename T>
+SpreadArgs<T> make_spread_args(const Plan& P, int level, const double* xy, const double* const* q, int nq,
+                               void* const* grids, int64_t n) {
+  SpreadArgs<T> a;
+  a.xy = xy;
+  for (int c = 0; c < 3; ++c) {
+    a.q[c] = c < nq ? q[c] : nullptr;
+    a.grid[c] = c < nq ? grids[c] : nullptr;
+  }
+  a.nq = nq;
+  a.n = n;
+  a.gd = grid_dev(P.lv[level]);
+  a.status = P.d_status;
+  if constexpr (sizeof(T) == 8) a.es = P.es; else a.es = P.es32;
+  return a;
+}
+template SpreadArgs<double> make_spread_args<double>(const Plan&, int, const double*, const double* const*,
+                                                     int, void* const*, int64_t);
+template SpreadArgs<float> make_spread_args<float>(const Plan&, int, const double*, const double* const*,
+                                                   int, void* const*, int64_t);
+
 void launch_spread(const Plan& P, int level, const double* xy, const double* const* q, int nq,
                    void* const* grids, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   int threads = 128;
   unsigned blocks = (unsigned)((n + threads - 1) / threads);
   ++P.launches;
-  auto fill = [&](auto& a) {
-    a.xy = xy;
-    for (int c = 0; c < 3; ++c) {
-      a.q[c] = c < nq ? q[c] : nullptr;
-      a.grid[c] = c < nq ? grids[c] : nullptr;
-    }
-    a.nq = nq;
-    a.n = n;
-    a.gd = grid_dev(P.lv[level]);
-    a.status = P.d_status;
-  };
-  if (P.precision == LP_FP64) {
-    SpreadArgs<double> a;
-    fill(a);
-    a.es = P.es;
-    spread_dispatch(a, P.ker.w, blocks, threads, s);
-  } else {
-    SpreadArgs<float> a;
-    fill(a);
-    a.es = P.es32;
-    spread_dispatch(a, P.ker.w, blocks, threads, s);
-  }
+  if (P.precision == LP_FP64)
+    spread_dispatch(make_spread_args<double>(P, level, xy, q, nq, grids, n), P.ker.w, blocks, threads, s);
+  else
+    spread_dispatch(make_spread_args<float>(P, level, xy, q, nq, grids, n), P.ker.w, blocks, threads, s);
+}
+
+MultArgs make_mult_args(const Plan& P, int level, bool want_v, bool want_s, bool want_d) {
+  const GridLevel& G = P.lv[level];
+  MultArgs a;
+  a.g = G.g;
+  a.K = G.K;
+  a.dk = G.dk;
+  a.tab = P.precision == LP_FP64 ? (const void*)G.mtab : (const void*)G.mtab32;
+  a.V = want_v ? G.chan[0] : nullptr;
+  a.S = want_s ? G.chan[1] : nullptr;
+  a.D1 = want_d ? G.chan[2] : nullptr;
+  a.D2 = want_d ? G.chan[3] : nullptr;
+  return a;
 }
 
 void launch_multiplier(const Plan& P, int level, bool want_v, bool want_s, bool want_d,
@@ -232,17 +278,11 @@ void launch_multiplier(const Plan& P, int level, bool want_v, bool want_s, bool 
   int threads = 256;
   unsigned blocks = (unsigned)((total + threads - 1) / threads);
   ++P.launches;
-  if (P.precision == LP_FP64) {
-    using C = cufftDoubleComplex;
-    multiplier_kernel<C, double><<<blocks, threads, 0, s>>>(
-        G.g, G.K, G.dk, G.mtab, want_v ? (C*)G.chan[0] : nullptr, want_s ? (C*)G.chan[1] : nullptr,
-        want_d ? (C*)G.chan[2] : nullptr, want_d ? (const C*)G.chan[3] : nullptr);
-  } else {
-    using C = cufftComplex;
-    multiplier_kernel<C, float><<<blocks, threads, 0, s>>>(
-        G.g, G.K, G.dk, G.mtab32, want_v ? (C*)G.chan[0] : nullptr, want_s ? (C*)G.chan[1] : nullptr,
-        want_d ? (C*)G.chan[2] : nullptr, want_d ? (const C*)G.chan[3] : nullptr);
-  }
+  MultArgs a = make_mult_args(P, level, want_v, want_s, want_d);
+  if (P.precision == LP_FP64)
+    multiplier_kernel<cufftDoubleComplex, double><<<blocks, threads, 0, s>>>(a);
+  else
+    multiplier_kernel<cufftComplex, float><<<blocks, threads, 0, s>>>(a);
 }
 
 template <typename T>
@@ -258,38 +298,88 @@ static void interp_dispatch(const InterpArgs<T>& a, int w, unsigned blocks, int 
   }
 }
 
+template <typename T>
+InterpArgs<T> make_interp_args(const Plan& P, int64_t nt, const double* txy, double* V, double* S, double* D) {
+  InterpArgs<T> a;
+  a.txy = txy;
+  a.n = nt;
+  a.status = P.d_status;
+  a.out[0] = V;
+  a.out[1] = S;
+  a.out[2] = D;
+  for (int l = 0; l < 2; ++l) {
+    a.gd[l] = grid_dev(P.lv[l]);
+    for (int c = 0; c < 3; ++c) a.grid[l][c] = a.out[c] ? P.lv[l].chan[c] : nullptr;
+  }
+  a.zero_factor = P.lv[0].zero_mode + P.lv[1].zero_mode;
+  // FP32 path: the zero mode was removed from the FP32 tables
+  a.qsum = sizeof(T) == 8 ? nullptr : P.d_qsum;
+  if constexpr (sizeof(T) == 8) a.es = P.es; else a.es = P.es32;
+  return a;
+}
+template InterpArgs<double> make_interp_args<double>(const Plan&, int64_t, const double*, double*, double*, double*);
+template InterpArgs<float> make_interp_args<float>(const Plan&, int64_t, const double*, double*, double*, double*);
+
 void launch_interp(const Plan& P, int64_t nt, const double* txy, double* V, double* S, double* D,
                    cudaStream_t s) {
   if (nt <= 0) return;
-  auto fill = [&](auto& a) {
-    a.txy = txy;
-    a.n = nt;
-    a.status = P.d_status;
-    a.out[0] = V;
-    a.out[1] = S;
-    a.out[2] = D;
-    for (int l = 0; l < 2; ++l) {
-      a.gd[l] = grid_dev(P.lv[l]);
-      for (int c = 0; c < 3; ++c) a.grid[l][c] = a.out[c] ? P.lv[l].chan[c] : nullptr;
-    }
-    a.qsum = nullptr;
-    a.zero_factor = P.lv[0].zero_mode + P.lv[1].zero_mode;
-  };
   int threads = 128;
   unsigned blocks = (unsigned)((nt + threads - 1) / threads);
   ++P.launches;
-  if (P.precision == LP_FP64) {
-    InterpArgs<double> a;
-    fill(a);
-    a.es = P.es;
-    interp_dispatch(a, P.ker.w, blocks, threads, s);
-  } else {
-    // FP32 path: the zero mode was removed from the FP32 tables
-    InterpArgs<float> a;
-    fill(a);
-    a.es = P.es32;
-    a.qsum = P.d_qsum;
-    interp_dispatch(a, P.ker.w, blocks, threads, s);
+  if (P.precision == LP_FP64)
+    interp_dispatch(make_interp_args<double>(P, nt, txy, V, S, D), P.ker.w, blocks, threads, s);
+  else
+    interp_dispatch(make_interp_args<float>(P, nt, txy, V, S, D), P.ker.w, blocks, threads, s);
+}
+
+// ---- batched launches ---------------------------------------------------------
+
+void launch_zero_batch(const ZeroSeg* d_segs, const int2* d_work, int nwork, cudaStream_t s) {
+  if (nwork > 0) zero_batch_kernel<<<nwork, 256, 0, s>>>(d_segs, d_work);
+}
+
+void launch_spread_batch(int precision, int w, const void* d_args, const int2* d_work, int nwork,
+                         cudaStream_t s) {
+  if (nwork <= 0) return;
+  switch (w) {
+#define LP_CASE(W)                                                                              \
+  case W:                                                                                       \
+    if (precision == LP_FP64)                                                                   \
+      spread_batch_kernel<double, W>                                                            \
+          <<<nwork, kBatchThreads, 0, s>>>((const SpreadArgs<double>*)d_args, d_work);          \
+    else                                                                                        \
+      spread_batch_kernel<float, W><<<nwork, kBatchThreads, 0, s>>>((const SpreadArgs<float>*)d_args, d_work); \
+    break;
+    LP_WIDTH_CASES(LP_CASE)
+#undef LP_CASE
+    default: break;
+  }
+}
+
+void launch_multiplier_batch(int precision, const MultArgs* d_args, const int2* d_work, int nwork,
+                             cudaStream_t s) {
+  if (nwork <= 0) return;
+  if (precision == LP_FP64)
+    multiplier_batch_kernel<cufftDoubleComplex, double><<<nwork, kBatchThreads, 0, s>>>(d_args, d_work);
+  else
+    multiplier_batch_kernel<cufftComplex, float><<<nwork, kBatchThreads, 0, s>>>(d_args, d_work);
+}
+
+void launch_interp_batch(int precision, int w, const void* d_args, const int2* d_work, int nwork,
+                         cudaStream_t s) {
+  if (nwork <= 0) return;
+  switch (w) {
+#define LP_CASE(W)                                                                              \
+  case W:                                                                                       \
+    if (precision == LP_FP64)                                                                   \
+      interp_batch_kernel<double, W>                                                            \
+          <<<nwork, kBatchThreads, 0, s>>>((const InterpArgs<double>*)d_args, d_work);          \
+    else                                                                                        \
+      interp_batch_kernel<float, W><<<nwork, kBatchThreads, 0, s>>>((const InterpArgs<float>*)d_args, d_work); \
+    break;
+    LP_WIDTH_CASES(LP_CASE)
+#undef LP_CASE
+    default: break;
   }
 }
 

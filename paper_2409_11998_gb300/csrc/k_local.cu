@@ -22,31 +22,6 @@ namespace lpg {
 
 namespace {
 
-struct LocalArgs {
-  const double* txy;
-  const double* jet;
-  int64_t n;
-  double* out[3];  // V, S, D: local part added in place
-  const double* bxy;
-  int64_t nb;
-  int n_panels, p;
-  const double* tau;
-  const double* geo_coef;
-  const double* geo_ref;
-  const double* sig_coef;
-  const double* sig_ref;
-  const double* mu_coef;
-  const double* mu_ref;
-  double hx0, hy0, hh;
-  int hnx, hny;
-  const int* cell_start;
-  const int* cell_node;
-  const float2* cell_xy32;   // node coordinates relative to their cell origin
-  const float* geo_coef32;   // FP32 copy of geo_coef
-  double margin, band, delta, on_tol;
-  int order;
-  unsigned* status;
-};
 
 // d^j/dt^j of ref_s + sum_k c_s[k] P_k(t), j = 0..ND, for NS series sharing
 // one recurrence.  The stored coefficients are c_k / k!, paired with
@@ -308,9 +283,9 @@ __device__ __forceinline__ double far_volume(const LocalArgs& a, const double* J
 // exactly the double-precision nearest node.  Targets whose nearest node is
 // farther than band + margin get the far-field volume term here; the others
 // are appended to a compact list for pass 2.
-__global__ void local_classify_kernel(LocalArgs a, int2* list, int* count) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
+// Returns the nearest node for a band candidate, -1 when the far-field term
+// was applied.
+__device__ int local_classify_one(const LocalArgs& a, int64_t i) {
   const double x = a.txy[2 * i], y = a.txy[2 * i + 1];
   int best = -1;
   double bd2 = 1e300;
@@ -362,8 +337,16 @@ __global__ void local_classify_kernel(LocalArgs a, int2* list, int* count) {
   }
   if (best < 0 || sqrt(bd2) - a.margin >= a.band) {
     if (a.out[0] && a.jet) a.out[0][i] += far_volume(a, a.jet + 6 * i);
-    return;
+    return -1;
   }
+  return best;
+}
+
+__global__ void local_classify_kernel(const __grid_constant__ LocalArgs a, int2* list, int* count) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const int best = local_classify_one(a, i);
+  if (best < 0) return;
   auto g = cg::coalesced_threads();
   int base = 0;
   if (g.thread_rank() == 0) base = atomicAdd(count, (int)g.size());
@@ -371,19 +354,44 @@ __global__ void local_classify_kernel(LocalArgs a, int2* list, int* count) {
   list[base + g.thread_rank()] = make_int2((int)i, best);
 }
 
+// Batched: one launch over the targets of many plans; list entries are
+// (plan, target, nearest node).
+__global__ void local_classify_batch_kernel(const LocalArgs* __restrict__ args, const int2* __restrict__ work,
+                                            int4* list, int* count) {
+  const int2 wk = work[blockIdx.x];
+  const LocalArgs& a = args[wk.x];
+  int64_t i = (int64_t)wk.y + threadIdx.x;
+  if (i >= a.n) return;
+  const int best = local_classify_one(a, i);
+  if (best < 0) return;
+  auto g = cg::coalesced_threads();
+  int base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(count, (int)g.size());
+  base = g.shfl(base, 0);
+  list[base + g.thread_rank()] = make_int4(wk.x, (int)i, best, 0);
+}
+
 // Pass 2: closest point, frame and expansions for the listed targets.
-__global__ void local_near_kernel(LocalArgs a, const int2* __restrict__ list,
+__global__ void local_near_kernel(const __grid_constant__ LocalArgs a, const int2* __restrict__ list,
                                   const int* __restrict__ count) {
   const int n_near = *count;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n_near; idx += gridDim.x * blockDim.x)
     local_near_one(a, list[idx].x, list[idx].y);
 }
 
+__global__ void local_near_batch_kernel(const LocalArgs* __restrict__ args, const int4* __restrict__ list,
+                                        const int* __restrict__ count) {
+  const int n_near = *count;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n_near; idx += gridDim.x * blockDim.x) {
+    const int4 e = list[idx];
+    local_near_one(args[e.x], e.y, e.z);
+  }
+}
+
 }  // namespace
 
-void launch_local(const Plan& P, int64_t nt, const double* txy, const double* jet, double* V,
-                  double* S, double* D, cudaStream_t s) {
-  if (nt <= 0) return;
+LocalArgs make_local_args(const Plan& P, int64_t nt, const double* txy, const double* jet, double* V,
+                          double* S, double* D) {
   LocalArgs a;
   a.txy = txy;
   a.jet = V ? jet : nullptr;
@@ -417,6 +425,13 @@ void launch_local(const Plan& P, int64_t nt, const double* txy, const double* je
   a.on_tol = P.on_tol;
   a.order = P.order;
   a.status = P.d_status;
+  return a;
+}
+
+void launch_local(const Plan& P, int64_t nt, const double* txy, const double* jet, double* V,
+                  double* S, double* D, cudaStream_t s) {
+  if (nt <= 0) return;
+  LocalArgs a = make_local_args(P, nt, txy, jet, V, S, D);
   int threads = 128;
   unsigned blocks = (unsigned)((nt + threads - 1) / threads);
   cudaMemsetAsync(P.d_near_count, 0, sizeof(int), s);
@@ -432,39 +447,7 @@ void launch_local(const Plan& P, int64_t nt, const double* txy, const double* je
 void launch_local_list(const Plan& P, int64_t nt, const double* txy, const double* jet, double* V,
                        double* S, double* D, int2* list, int* count, cudaStream_t s) {
   if (nt <= 0) return;
-  LocalArgs a;
-  a.txy = txy;
-  a.jet = V ? jet : nullptr;
-  a.n = nt;
-  a.out[0] = V;
-  a.out[1] = S;
-  a.out[2] = D;
-  a.bxy = P.d_bxy;
-  a.nb = P.nb;
-  a.n_panels = (int)P.n_panels;
-  a.p = P.p;
-  a.tau = P.d_tau;
-  a.geo_coef = P.d_geo_coef;
-  a.geo_ref = P.d_geo_ref;
-  a.sig_coef = P.have_sigma ? P.d_sigma_coef : nullptr;
-  a.sig_ref = P.d_sigma_ref;
-  a.mu_coef = P.have_mu ? P.d_mu_coef : nullptr;
-  a.mu_ref = P.d_mu_ref;
-  a.hx0 = P.hash_x0;
-  a.hy0 = P.hash_y0;
-  a.hh = P.hash_h;
-  a.hnx = P.hash_nx;
-  a.hny = P.hash_ny;
-  a.cell_start = P.d_cell_start;
-  a.cell_node = P.d_cell_node;
-  a.cell_xy32 = P.d_cell_xy32;
-  a.geo_coef32 = P.d_geo_coef32;
-  a.margin = P.margin;
-  a.band = P.band;
-  a.delta = P.delta1;
-  a.on_tol = P.on_tol;
-  a.order = P.order;
-  a.status = P.d_status;
+  LocalArgs a = make_local_args(P, nt, txy, jet, V, S, D);
   int threads = 128;
   unsigned blocks = (unsigned)((nt + threads - 1) / threads);
   cudaMemsetAsync(count, 0, sizeof(int), s);
@@ -473,6 +456,18 @@ void launch_local_list(const Plan& P, int64_t nt, const double* txy, const doubl
   unsigned nblk = std::min<unsigned>(blocks, 152u * 16u);
   ++P.launches;
   local_near_kernel<<<nblk, threads, 0, s>>>(a, list, count);
+}
+
+// Batched local pass over a wave of plans: one classify launch over every
+// plan's targets (work entries of kBatchThreads targets), one near launch over
+// the combined candidate list.
+void launch_local_batch(const LocalArgs* d_args, const int2* d_work, int nwork, int4* d_list,
+                        int* d_count, int64_t n_total, cudaStream_t s) {
+  if (nwork <= 0) return;
+  cudaMemsetAsync(d_count, 0, sizeof(int), s);
+  local_classify_batch_kernel<<<nwork, kBatchThreads, 0, s>>>(d_args, d_work, d_list, d_count);
+  unsigned nblk = (unsigned)std::min<int64_t>((n_total + 127) / 128, 152 * 16);
+  local_near_batch_kernel<<<std::max(nblk, 1u), 128, 0, s>>>(d_args, d_list, d_count);
 }
 
 }  // namespace lpg

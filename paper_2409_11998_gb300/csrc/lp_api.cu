@@ -275,12 +275,14 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
   P.on_tol = 1e-12 * P.side;
   P.stream = (cudaStream_t)dom->stream;
   // Kernel width and upsampling.  FP64 is bound by cuFFT's FP64 arithmetic,
-  // so its grids use sigma = 1.5 (0.56x the modes of sigma = 2) and one more
-  // kernel point; FP32 keeps sigma = 2.  Measured (disk, tol 1e-9): sigma 2,
-  // w 10 -> 4.3e-10; sigma 1.5, w 11 -> 3.9e-10.  FP32 adds one point for
-  // margin against single-precision rounding.
+  // so its grids use sigma = 1.5 (0.56x the modes of sigma = 2) and wider
+  // kernels; FP32 keeps sigma = 2.  Measured (disk, tol 1e-9): sigma 2, w 10
+  // -> 4.3e-10; sigma 1.5, w 11 -> 3.9e-10, w 12 -> 5.6e-11.  Small, many-
+  // lobed problems reached 1.2e-9 at w 11, so FP64 takes w = ceil(-log10 tol)
+  // + 3 (12 at 1e-9); FP32 takes + 2 (7 at 1e-5) for margin against
+  // single-precision rounding.
   P.sigma = P.precision == LP_FP64 ? 1.5 : 2.0;
-  int w = (int)std::ceil(-std::log10(tol)) + 2;
+  int w = (int)std::ceil(-std::log10(tol)) + (P.precision == LP_FP64 ? 3 : 2);
   w = std::min(std::max(w, 4), kMaxW);
   P.ker.w = w;
   P.ker.beta = 2.30 * w;  // refined by choose_levels for the realised sigma

@@ -1,0 +1,312 @@
+// Batched evaluation of a wave of independent plans (problems of different
+// sizes): one zeroing launch, one spread launch, one multiplier launch, one
+// interpolation launch and one local classify + one near launch for the whole
+// wave, each over an array of per-plan argument records with a per-block work
+// list; each plan's pruned FFTs are issued on the batch stream in between.
+// The arithmetic per item is the single-plan kernels' (same device functions).
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lp_internal.cuh"
+
+using namespace lpg;
+
+struct lp_plan_s {
+  Plan P;
+};
+
+struct lp_batch_s {
+  cudaStream_t stream = nullptr;
+  void* d_buf = nullptr;  // per-wave records and work lists
+  void* h_buf = nullptr;  // pinned mirror
+  size_t buf_cap = 0;
+  int4* d_list = nullptr;  // near-boundary candidates of the wave
+  size_t list_cap = 0;
+  int* d_count = nullptr;
+  cudaEvent_t ev[8] = {};
+  bool pending = false;   // h_buf is in use by an enqueued copy until ev[7]
+  long long launches = 0;
+};
+
+namespace {
+
+bool dev_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Append records of type R to the packed host image; returns their offset.
+struct Packer {
+  std::vector<unsigned char> img;
+  template <typename R>
+  size_t put(const std::vector<R>& v) {
+    size_t off = align_up(img.size(), 256);
+    img.resize(off + v.size() * sizeof(R));
+    if (!v.empty()) std::memcpy(img.data() + off, v.data(), v.size() * sizeof(R));
+    return off;
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+lp_status lp_batch_create(void* stream, lp_batch_t* out) {
+  if (!out) return LP_ERR_ARG;
+  *out = nullptr;
+  lp_batch_s* b = new (std::nothrow) lp_batch_s();
+  if (!b) return LP_ERR_NOMEM;
+  b->stream = (cudaStream_t)stream;
+  if (cudaMalloc(&b->d_count, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return LP_ERR_NOMEM;
+  }
+  for (auto& e : b->ev) cudaEventCreate(&e);
+  *out = b;
+  return LP_OK;
+}
+
+lp_status lp_batch_destroy(lp_batch_t b) {
+  if (!b) return LP_ERR_ARG;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  else cudaDeviceSynchronize();
+  if (b->d_buf) cudaFree(b->d_buf);
+  if (b->h_buf) cudaFreeHost(b->h_buf);
+  if (b->d_list) cudaFree(b->d_list);
+  if (b->d_count) cudaFree(b->d_count);
+  for (auto& e : b->ev)
+    if (e) cudaEventDestroy(e);
+  delete b;
+  return LP_OK;
+}
+
+lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const int64_t* n_t,
+                           const double* const* t_xy, const double* const* f_jet, double* const* V,
+                           double* const* S, double* const* D) {
+  if (!b || n <= 0 || !plans || !n_t || !t_xy || !plans[0]) return LP_ERR_ARG;
+  const int prec = plans[0]->P.precision, w = plans[0]->P.ker.w;
+  int64_t total_t = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i]) return LP_ERR_ARG;
+    const Plan& P = plans[i]->P;
+    if (P.precision != prec || P.ker.w != w) return LP_ERR_ARG;  // one kernel shape per wave
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) return LP_ERR_ARG;  // a plan's grids serve one problem
+    if (n_t[i] < 0 || n_t[i] > (int64_t)INT32_MAX) return LP_ERR_ARG;
+    const bool wv = V && V[i], ws = S && S[i], wd = D && D[i];
+    if ((wv && !P.have_volume) || (ws && !P.have_sigma) || (wd && !P.have_mu)) return LP_ERR_STATE;
+    if (n_t[i] == 0) continue;
+    if (!dev_ptr(t_xy[i])) return LP_ERR_ARG;
+    if (wv && (!f_jet || !dev_ptr(f_jet[i]))) return LP_ERR_ARG;
+    if ((wv && !dev_ptr(V[i])) || (ws && !dev_ptr(S[i])) || (wd && !dev_ptr(D[i]))) return LP_ERR_ARG;
+    total_t += n_t[i];
+  }
+  cudaStream_t s = b->stream;
+  if (b->pending) {
+    cudaEventSynchronize(b->ev[7]);  // the previous wave's records were copied
+    b->pending = false;
+  }
+
+  // ---- per-wave records ----
+  std::vector<ZeroSeg> zsegs;
+  std::vector<int2> zwork;
+  std::vector<SpreadArgs<double>> sp64;
+  std::vector<SpreadArgs<float>> sp32;
+  std::vector<int2> swork;
+  std::vector<MultArgs> mult;
+  std::vector<int2> mwork;
+  std::vector<InterpArgs<double>> in64;
+  std::vector<InterpArgs<float>> in32;
+  std::vector<int2> iwork;
+  std::vector<LocalArgs> loc;
+  std::vector<int2> lwork;
+  const bool f64 = prec == LP_FP64;
+  for (int i = 0; i < n; ++i) {
+    const Plan& P = plans[i]->P;
+    const bool wv = V && V[i], ws = S && S[i], wd = D && D[i];
+    const int64_t nt = n_t[i];
+    if (nt == 0 || (!wv && !ws && !wd)) continue;
+    for (int l = 0; l < 2; ++l) {
+      const GridLevel& G = P.lv[l];
+      const bool need[4] = {wv, ws, wd, wd};
+      for (int c = 0; c < 4; ++c) {
+        if (!need[c]) continue;
+        int rec = (int)zsegs.size();
+        ZeroSeg zs{G.chan[c], (int64_t)(G.chan_bytes / 16)};
+        zsegs.push_back(zs);
+        for (int64_t e = 0; e < zs.n16; e += kZeroChunk) zwork.push_back(make_int2(rec, (int)(e / kZeroChunk)));
+      }
+      // spread records: volume sources, then boundary channels
+      auto add_spread = [&](const double* xy, const double* const* q, int nq, void* const* grids, int64_t cnt) {
+        if (cnt <= 0 || nq == 0) return;
+        int rec = f64 ? (int)sp64.size() : (int)sp32.size();
+        if (f64) sp64.push_back(make_spread_args<double>(P, l, xy, q, nq, grids, cnt));
+        else sp32.push_back(make_spread_args<float>(P, l, xy, q, nq, grids, cnt));
+        for (int64_t j = 0; j < cnt; j += kBatchThreads) swork.push_back(make_int2(rec, (int)j));
+      };
+      if (wv) {
+        const double* q[1] = {P.d_vq};
+        void* g[1] = {G.chan[0]};
+        add_spread(P.d_vxy, q, 1, g, P.nv);
+      }
+      const double* bq[3];
+      void* bg[3];
+      int nq = 0;
+      if (ws) {
+        bq[nq] = P.d_bq;
+        bg[nq++] = G.chan[1];
+      }
+      if (wd) {
+        bq[nq] = P.d_bq + P.nb;
+        bg[nq++] = G.chan[2];
+        bq[nq] = P.d_bq + 2 * P.nb;
+        bg[nq++] = G.chan[3];
+      }
+      add_spread(P.d_bxy, bq, nq, bg, P.nb);
+      int rec = (int)mult.size();
+      mult.push_back(make_mult_args(P, l, wv, ws, wd));
+      int64_t modes = (int64_t)G.g * (G.g / 2 + 1);
+      for (int64_t j = 0; j * kBatchThreads < modes; ++j) mwork.push_back(make_int2(rec, (int)j));
+    }
+    double* vo = wv ? V[i] : nullptr;
+    double* so = ws ? S[i] : nullptr;
+    double* dout = wd ? D[i] : nullptr;
+    int rec = f64 ? (int)in64.size() : (int)in32.size();
+    if (f64) in64.push_back(make_interp_args<double>(P, nt, t_xy[i], vo, so, dout));
+    else in32.push_back(make_interp_args<float>(P, nt, t_xy[i], vo, so, dout));
+    int lrec = (int)loc.size();
+    loc.push_back(make_local_args(P, nt, t_xy[i], wv ? f_jet[i] : nullptr, vo, so, dout));
+    for (int64_t j = 0; j < nt; j += kBatchThreads) {
+      iwork.push_back(make_int2(rec, (int)j));
+      lwork.push_back(make_int2(lrec, (int)j));
+    }
+  }
+  if (iwork.empty()) return LP_OK;
+  Packer pk;
+  const size_t o_zs = pk.put(zsegs), o_zw = pk.put(zwork);
+  const size_t o_sa = f64 ? pk.put(sp64) : pk.put(sp32), o_sw = pk.put(swork);
+  const size_t o_ma = pk.put(mult), o_mw = pk.put(mwork);
+  const size_t o_ia = f64 ? pk.put(in64) : pk.put(in32), o_iw = pk.put(iwork);
+  const size_t o_la = pk.put(loc), o_lw = pk.put(lwork);
+  const size_t bytes = align_up(pk.img.size(), 256);
+  if (bytes > b->buf_cap) {
+    cudaStreamSynchronize(s);
+    if (b->d_buf) cudaFree(b->d_buf);
+    if (b->h_buf) cudaFreeHost(b->h_buf);
+    b->d_buf = b->h_buf = nullptr;
+    b->buf_cap = 0;
+    size_t cap = std::max(bytes, (size_t)1 << 20);
+    if (cudaMalloc(&b->d_buf, cap) != cudaSuccess || cudaMallocHost(&b->h_buf, cap) != cudaSuccess) {
+      cudaGetLastError();
+      return LP_ERR_NOMEM;
+    }
+    b->buf_cap = cap;
+  }
+  if ((size_t)total_t > b->list_cap) {
+    cudaStreamSynchronize(s);
+    if (b->d_list) cudaFree(b->d_list);
+    b->d_list = nullptr;
+    b->list_cap = 0;
+    if (cudaMalloc(&b->d_list, total_t * sizeof(int4)) != cudaSuccess) {
+      cudaGetLastError();
+      return LP_ERR_NOMEM;
+    }
+    b->list_cap = total_t;
+  }
+  std::memcpy(b->h_buf, pk.img.data(), pk.img.size());
+  char* d = (char*)b->d_buf;
+  cudaEventRecord(b->ev[0], s);
+  cudaMemcpyAsync(d, b->h_buf, pk.img.size(), cudaMemcpyHostToDevice, s);
+  launch_zero_batch((const ZeroSeg*)(d + o_zs), (const int2*)(d + o_zw), (int)zwork.size(), s);
+  cudaEventRecord(b->ev[1], s);
+  launch_spread_batch(prec, w, d + o_sa, (const int2*)(d + o_sw), (int)swork.size(), s);
+  cudaEventRecord(b->ev[2], s);
+  b->launches += 2;
+  // each plan's pruned transforms on the batch stream
+  for (int i = 0; i < n; ++i) {
+    const Plan& P = plans[i]->P;
+    const bool wv = V && V[i], ws = S && S[i], wd = D && D[i];
+    if (n_t[i] == 0 || (!wv && !ws && !wd)) continue;
+    for (int l = 0; l < 2; ++l) {
+      const GridLevel& G = P.lv[l];
+      cufftSetStream(G.row_fwd, s);
+      cufftSetStream(G.col, s);
+      if (wv) fft_forward(P, l, 0);
+      if (ws) fft_forward(P, l, 1);
+      if (wd) {
+        fft_forward(P, l, 2);
+        fft_forward(P, l, 3);
+      }
+    }
+  }
+  cudaEventRecord(b->ev[3], s);
+  launch_multiplier_batch(prec, (const MultArgs*)(d + o_ma), (const int2*)(d + o_mw), (int)mwork.size(), s);
+  cudaEventRecord(b->ev[4], s);
+  for (int i = 0; i < n; ++i) {
+    const Plan& P = plans[i]->P;
+    const bool wv = V && V[i], ws = S && S[i], wd = D && D[i];
+    if (n_t[i] == 0 || (!wv && !ws && !wd)) continue;
+    for (int l = 0; l < 2; ++l) {
+      const GridLevel& G = P.lv[l];
+      cufftSetStream(G.row_inv, s);
+      if (wv) fft_inverse(P, l, 0);
+      if (ws) fft_inverse(P, l, 1);
+      if (wd) fft_inverse(P, l, 2);
+      cufftSetStream(G.row_fwd, P.stream);
+      cufftSetStream(G.row_inv, P.stream);
+      cufftSetStream(G.col, P.stream);
+    }
+  }
+  cudaEventRecord(b->ev[5], s);
+  launch_interp_batch(prec, w, d + o_ia, (const int2*)(d + o_iw), (int)iwork.size(), s);
+  cudaEventRecord(b->ev[6], s);
+  launch_local_batch((const LocalArgs*)(d + o_la), (const int2*)(d + o_lw), (int)lwork.size(), b->d_list,
+                     b->d_count, total_t, s);
+  cudaEventRecord(b->ev[7], s);
+  b->launches += 5;
+  b->pending = true;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+}
+
+lp_status lp_batch_sync(lp_batch_t b) {
+  if (!b) return LP_ERR_ARG;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return LP_ERR_CUDA;
+  b->pending = false;
+  return cudaGetLastError() == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+}
+
+lp_status lp_batch_stage_times(lp_batch_t b, float* out) {
+  if (!b || !out) return LP_ERR_ARG;
+  auto el = [&](int x, int y) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, b->ev[x], b->ev[y]) != cudaSuccess) {
+      cudaGetLastError();
+      return -1.0f;
+    }
+    return ms;
+  };
+  // {zero+copy, spread, forward FFTs, multiplier, inverse FFTs, interp, local, total, launches}
+  out[0] = el(0, 1);
+  out[1] = el(1, 2);
+  out[2] = el(2, 3);
+  out[3] = el(3, 4);
+  out[4] = el(4, 5);
+  out[5] = el(5, 6);
+  out[6] = el(6, 7);
+  out[7] = el(0, 7);
+  out[8] = (float)b->launches;
+  return LP_OK;
+}
+
+}  // extern "C"

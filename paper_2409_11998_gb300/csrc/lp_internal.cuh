@@ -14,6 +14,8 @@ namespace lpg {
 
 constexpr int kMaxW = 16;           // widest spreading kernel (grid points)
 constexpr int kMaxNC = 20;          // coefficients per piece of the kernel polynomial
+constexpr int kBatchThreads = 128;  // threads per block (and items per work entry) of batched launches
+constexpr int kZeroChunk = 4096;    // 16-byte words cleared per work entry of the batched zeroing
 constexpr int kMaxPanelOrder = 32;  // Gauss-Legendre nodes per boundary panel
 constexpr int kNumEvents = 10;
 
@@ -67,6 +69,77 @@ struct GridLevel {
 struct GridDev {
   int g, pitch;
   double x0, y0, inv_h;
+};
+
+// Argument records of the grid kernels.  A single-plan launch passes one by
+// value; a batched launch passes an array of them in device memory plus a
+// per-block work list.
+template <typename T>
+struct SpreadArgs {
+  const double* xy;
+  const double* q[3];
+  void* grid[3];
+  int nq;
+  int64_t n;
+  GridDev gd;
+  unsigned* status;
+  EsPoly<T> es;
+};
+
+template <typename T>
+struct InterpArgs {
+  const double* txy;
+  int64_t n;
+  const void* grid[2][3];  // [level][V,S,D]
+  GridDev gd[2];
+  const double* qsum;      // FP64 strength sums of V and S (FP32 path), or null
+  double zero_factor;      // sum over levels of (dk/2pi)^2 M(0)
+  double* out[3];
+  unsigned* status;
+  EsPoly<T> es;
+};
+
+struct MultArgs {
+  int g, K;
+  double dk;
+  const void* tab;        // double (FP64) or float (FP32) table
+  void* V;
+  void* S;
+  void* D1;
+  const void* D2;
+};
+
+// A buffer to clear in a batched launch: ptr (16-byte aligned), n16 16-byte words.
+struct ZeroSeg {
+  void* ptr;
+  int64_t n16;
+};
+
+// Argument record of the local pass (one per plan).
+struct LocalArgs {
+  const double* txy;
+  const double* jet;
+  int64_t n;
+  double* out[3];  // V, S, D: local part added in place
+  const double* bxy;
+  int64_t nb;
+  int n_panels, p;
+  const double* tau;
+  const double* geo_coef;
+  const double* geo_ref;
+  const double* sig_coef;
+  const double* sig_ref;
+  const double* mu_coef;
+  const double* mu_ref;
+  double hx0, hy0, hh;
+  int hnx, hny;
+  const int* cell_start;
+  const int* cell_node;
+  const float2* cell_xy32;   // node coordinates relative to their cell origin
+  const float* geo_coef32;   // FP32 copy of geo_coef
+  double margin, band, delta, on_tol;
+  int order;
+  unsigned* status;
 };
 
 struct Plan {
@@ -143,6 +216,26 @@ lp_status fit_kernel_poly(Plan& P);
 lp_status build_boundary(Plan& P, const double* h_xy, const double* h_w, const double* h_nrm);
 void gauss_legendre(int p, double* x, double* w);
 int fft_size(int n);
+
+// ---- argument builders and batched launches ----
+GridDev grid_dev(const GridLevel& G);
+template <typename T>
+SpreadArgs<T> make_spread_args(const Plan& P, int level, const double* xy, const double* const* q, int nq,
+                               void* const* grids, int64_t n);
+template <typename T>
+InterpArgs<T> make_interp_args(const Plan& P, int64_t nt, const double* txy, double* V, double* S, double* D);
+MultArgs make_mult_args(const Plan& P, int level, bool want_v, bool want_s, bool want_d);
+LocalArgs make_local_args(const Plan& P, int64_t nt, const double* txy, const double* jet, double* V,
+                          double* S, double* D);
+void launch_zero_batch(const ZeroSeg* d_segs, const int2* d_work, int nwork, cudaStream_t s);
+void launch_spread_batch(int precision, int w, const void* d_args, const int2* d_work, int nwork,
+                         cudaStream_t s);
+void launch_multiplier_batch(int precision, const MultArgs* d_args, const int2* d_work, int nwork,
+                             cudaStream_t s);
+void launch_interp_batch(int precision, int w, const void* d_args, const int2* d_work, int nwork,
+                         cudaStream_t s);
+void launch_local_batch(const LocalArgs* d_args, const int2* d_work, int nwork, int4* d_list,
+                        int* d_count, int64_t n_total, cudaStream_t s);
 
 // ---- launches (kernels in k_*.cu) ----
 void launch_spread(const Plan& P, int level, const double* xy, const double* const* q, int nq,

@@ -133,10 +133,14 @@ def star_batch_member(seed, n_triangles, precision="fp64", tol=1e-9):
     a = rng.uniform(0.1, 0.4)
     k = int(rng.integers(3, 10))
     curve = C.Star(a, k)
-    n_b = max(24, int(np.sqrt(n_triangles) * 2.5))
+    n_b = max(24, 8 * k, int(np.sqrt(n_triangles) * 2.5))
     n_int = max(8, (n_triangles - n_b) // 2)
     mesh = M.delaunay_mesh(curve, n_int, n_b, rng)
     xy, w = M.quadrature(mesh, curve)
+    # coarse meshes of many-lobed stars can put straight edges across the
+    # troughs: drop the nodes that fall outside the curve (a gap in the mesh)
+    keep = curve.inside(xy)
+    xy, w = xy[keep], w[keep]
     cen = []
     while len(cen) < 8:
         p = rng.uniform(-1 - a, 1 + a, size=(1, 2))
