@@ -46,8 +46,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lp", choices=["lp", "reference"])
-    ap.add_argument("--workload", default="starfish", choices=["starfish", "disk", "square"])
-    ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline, fp32 line")
+    ap.add_argument("--workload", default="starfish", choices=["starfish", "disk", "square", "batch", "serve"])
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline, fp32 and serving lines")
+    ap.add_argument("--batch-size", type=int, default=256, help="problems per wave (--workload batch)")
+    ap.add_argument("--serve-seconds", type=float, default=8.0, help="seconds per arrival rate (--workload serve)")
     return ap.parse_args()
 
 
@@ -241,6 +243,10 @@ def run_lp(args, rank, world, local_rank):
         res["parity"] = parity_sample(prob, outs)
         res["e2e"] = run_e2e(args, prob, dev, ev, points)
         res["fp32_same_workload"] = run_fp32(args, prob, dev, stream, points)
+        from workloads import configs as _cfg
+        small_pool = _cfg.serving_pool(n_meshes=6, t_min=10_000, t_max=300_000, seed=5300)
+        res["served"] = run_serve(args, rank, world, local_rank, pool=small_pool, rates=(100, 400),
+                                  seconds=3.0)
         if world == 1:
             res["cpu_baseline"] = cpu_baseline(prob, budget_s=15.0)
     ev.close()
@@ -410,6 +416,119 @@ def cpu_baseline(prob, budget_s=15.0):
             f"extrapolated linearly in targets to the full workload ({t_full:.0f} s)"}
 
 
+# ---------------------------------------------------------------- batched waves (config 4)
+def run_batch(args, rank, world, local_rank):
+    """256 star domains r = 1 + a cos kt (a ~ U[0.1, 0.4], k in 3..9) of
+    log-uniform 1k..200k triangles in one wave: one launch per kernel for
+    the whole wave, against the same problems one lp_execute at a time."""
+    import numpy as np
+    import torch
+    import paper_2409_11998_gb300 as lp
+    from workloads import configs
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    rng = np.random.default_rng(4000)
+    sizes = np.exp(rng.uniform(np.log(1000), np.log(200000), args.batch_size)).astype(int)
+    probs = [configs.star_batch_member(4000 + i, int(n)) for i, n in enumerate(sizes)]
+    points = sum(len(p["src_w"]) + len(p["bnd"]["w"]) + len(p["tgt_xy"]) for p in probs)
+    out = {}
+    stream = torch.cuda.Stream(device=dev)
+    for prec, tol in (("fp64", 1e-9), ("fp32", 1e-5)):
+        evs = [lp.Evaluator(p, precision=prec, tol=tol, stream=stream.cuda_stream).bind() for p in probs]
+        T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+        txy = [T(p["tgt_xy"]) for p in probs]
+        jet = [T(p["tgt_jet"]) for p in probs]
+        o = {k: [torch.empty(len(p["tgt_xy"]), dtype=torch.float64, device=dev) for p in probs] for k in "VSD"}
+        b = lp.lp_batch_create(stream.cuda_stream)
+        plans = [e.plan for e in evs]
+        nts = [len(p["tgt_xy"]) for p in probs]
+
+        def wave():
+            lp.lp_batch_execute(b, plans, nts, txy, jet, o["V"], o["S"], o["D"])
+
+        def seq():
+            for i, e in enumerate(evs):
+                lp.lp_execute(e.plan, nts[i], txy[i], jet[i], o["V"][i], o["S"][i], o["D"][i])
+
+        res = {}
+        for name, fn in (("batched", wave), ("one_at_a_time", seq)):
+            for _ in range(max(args.warmup, 2)):
+                fn()
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(max(3, args.steps // 5)):
+                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a_.record(stream)
+                fn()
+                b_.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a_.elapsed_time(b_))
+            res[name] = {"ms_per_wave": statistics.mean(ms), "points_per_s": points / (statistics.mean(ms) / 1e3)}
+        wave()
+        torch.cuda.synchronize()
+        res["stages_ms"] = {k: round(v, 4) for k, v in lp.lp_batch_stage_times(b).items()}
+        # parity on a sample of problems
+        import oracle
+        errs = []
+        for i in rng.choice(len(probs), 4, replace=False):
+            idx = np.random.default_rng(int(i)).choice(nts[i], min(64, nts[i]), replace=False)
+            ref = oracle.evaluate(probs[i], targets=idx)
+            for k in "VSD":
+                got = o[k][i].cpu().numpy()[idx]
+                errs.append(float(np.linalg.norm(got - ref[k]) / np.linalg.norm(ref[k])))
+        res["parity_max_rel_l2_sampled"] = max(errs)
+        res["tol"] = tol
+        out[prec] = res
+        lp.lp_batch_destroy(b)
+        for e in evs:
+            e.close()
+    r64 = out["fp64"]
+    return {"metric": METRIC, "value": r64["batched"]["points_per_s"], "unit": UNIT, "n_gpus": world,
+            "steps": max(3, args.steps // 5), "warmup": max(args.warmup, 2),
+            "ms_per_step": r64["batched"]["ms_per_wave"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generators; no dataset)",
+            "config": {"workload": f"{len(probs)} star domains r=1+a cos kt, a~U[0.1,0.4], k in 3..9, "
+                                   "log-uniform 1k..200k triangles, one wave",
+                       "n_problems": len(probs), "points_per_wave": points,
+                       "triangles_total": int(sum(p["meta"]["n_triangles"] for p in probs))},
+            "batch": out}
+
+
+# ---------------------------------------------------------------- serving (config 5)
+def run_serve(args, rank, world, local_rank, pool=None, rates=(25, 50, 100, 200), seconds=None):
+    """Poisson arrivals of V+S+D requests over a resident mesh pool (10k..5M
+    triangles on the disk, starfish and square domains), FP32 at 1e-5 with
+    continuous batching, against one request at a time in FP64."""
+    import torch
+    from paper_2409_11998_gb300 import serve
+    from workloads import configs
+    torch.cuda.set_device(local_rank)
+    seconds = args.serve_seconds if seconds is None else seconds
+    if pool is None:
+        pool = configs.serving_pool()
+    pool64 = [dict(p, precision="fp64", tol=1e-9) for p in pool]
+    out = {"pool": [{"name": p["name"], "triangles": p["meta"]["n_triangles"],
+                     "points": len(p["src_w"]) + len(p["bnd"]["w"]) + len(p["tgt_xy"])} for p in pool],
+           "rates": {}}
+    srv = serve.Server(pool, precision="fp32", tol=1e-5, n_slots=2, max_wave=32)
+    one = serve.Server(pool64, precision="fp64", tol=1e-9, one_at_a_time=True)
+    srv.prewarm()
+    one.prewarm()
+    srv.run(serve.poisson_arrivals(20, 1.0, len(pool), seed=1))   # warm-up
+    one.run(serve.poisson_arrivals(5, 1.0, len(pool), seed=2))
+    for lam in rates:
+        arr = serve.poisson_arrivals(lam, seconds, len(pool), seed=int(lam))
+        a = serve.latency_stats(srv.run(arr))
+        b = serve.latency_stats(one.run(arr))
+        out["rates"][str(lam)] = {"batched_fp32": a, "one_at_a_time_fp64": b}
+    out["resident_bytes"] = srv.resident
+    out["plans_created"] = srv.created
+    out["plans_evicted"] = srv.evicted
+    srv.close()
+    one.close()
+    return out
+
+
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     import numpy as np
@@ -487,6 +606,19 @@ def main():
     rank, world, local = dist_init()
     if args.impl == "reference":
         res = run_reference(args, rank, world)
+    elif args.workload == "batch":
+        res = run_batch(args, rank, world, local)
+    elif args.workload == "serve":
+        sv = run_serve(args, rank, world, local)
+        top = sv["rates"][max(sv["rates"], key=float)]
+        res = {"metric": METRIC, "value": top["batched_fp32"]["points_per_s"], "unit": UNIT, "n_gpus": world,
+               "steps": None, "warmup": None, "ms_per_step": None, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 zero mode)",
+               "data": "synthetic (seeded generators; no dataset)",
+               "config": {"workload": "Poisson V+S+D request stream over 12 resident meshes (10k..5M "
+                                      "triangles, disk/starfish/square), FP32 tol 1e-5, continuous batching",
+                          "seconds_per_rate": args.serve_seconds},
+               "served": sv}
     else:
         res = run_lp(args, rank, world, local)
     if rank == 0 and res is not None:

@@ -9,6 +9,13 @@
 //   positive, so the printed local S expansion changes sign.  In the volume
 //   expansion, with eta the inward normal and kappa > 0 for convex
 //   boundaries, the delta^{3/2} term reads (2 f_eta - kappa f).
+//
+// The passes are templated on the arithmetic type of the plan.  FP64 plans
+// decide the nearest node exactly and run Newton to |dt| < 1e-14.  FP32 plans
+// (tolerance >= 1e-6) take the single-precision nearest node and foot and
+// evaluate the expansions in single precision in coordinates relative to the
+// panel's reference node; the foot offset, hence the distance and the side of
+// the boundary, is still evaluated in double precision.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -61,22 +68,29 @@ __device__ __forceinline__ void legendre_jets(const T* const* c, const T* ref, i
   }
 }
 
+// Foot of the perpendicular: panel, parameter, and the offset from the target
+// to the foot (gx, gy) with its squared length, always evaluated in double
+// precision so that the side of the boundary and the distance are exact to
+// rounding whatever the arithmetic type of the expansions.
 struct Foot {
   int panel;
-  double t, d2;
+  double t, d2, gx, gy;
 };
 
+// Newton for the foot on panel ip from parameter t.  A single-precision phase
+// in coordinates relative to the panel's reference node runs always; FP64
+// plans (full = true) continue with the double-precision Newton to
+// |dt| < 1e-14, FP32 plans take one double-precision step.
+template <bool full>
 __device__ Foot panel_foot(const LocalArgs& a, int ip, double t, double x, double y) {
   const size_t off = (size_t)(2 * ip) * a.p;
   const double rx = a.geo_ref[2 * ip], ry = a.geo_ref[2 * ip + 1];
-  // single-precision Newton on the panel offsets (cheap start); the
-  // double-precision Newton below decides the foot
   {
     const float* c32[2] = {a.geo_coef32 + off, a.geo_coef32 + off + a.p};
     const float zero2[2] = {0.f, 0.f};
     const float xr = (float)(x - rx), yr = (float)(y - ry);
     float tf = (float)t;
-    for (int it = 0; it < 8; ++it) {
+    for (int it = 0; it < (full ? 8 : 16); ++it) {
       float J[2][3];
       legendre_jets<2, 2, float>(c32, zero2, a.p, tf, J);
       float gx = J[0][0] - xr, gy = J[1][0] - yr;
@@ -87,57 +101,93 @@ __device__ Foot panel_foot(const LocalArgs& a, int ip, double t, double x, doubl
       float tn = fminf(1.f, fmaxf(-1.f, tf - f / fp));
       float dt = tn - tf;
       tf = tn;
-      if (fabsf(dt) < 1e-6f) break;
+      if (fabsf(dt) < (full ? 1e-6f : 2e-7f)) break;
     }
-    if (tf == tf) t = (double)tf;  // keep the node start if the FP32 phase failed
+    if (tf == tf) t = (double)tf;  // keep the node start if the phase failed
   }
   const double* c64[2] = {a.geo_coef + off, a.geo_coef + off + a.p};
   const double ref[2] = {rx, ry};
-  for (int it = 0; it < 20; ++it) {
-    double J[2][3];
-    legendre_jets<2, 2, double>(c64, ref, a.p, t, J);
-    double gx = J[0][0] - x, gy = J[1][0] - y;
-    double f = gx * J[0][1] + gy * J[1][1];
-    double s2 = J[0][1] * J[0][1] + J[1][1] * J[1][1];
-    double fp = s2 + gx * J[0][2] + gy * J[1][2];
-    if (fp < 0.1 * s2) fp = s2;
-    double tn = fmin(1.0, fmax(-1.0, t - f / fp));
-    double dt = tn - t;
-    t = tn;
-    if (fabs(dt) < 1e-14) break;
-  }
-  double J0[2][1];
-  legendre_jets<0, 2, double>(c64, ref, a.p, t, J0);
   Foot r;
   r.panel = ip;
+  if (full) {
+    for (int it = 0; it < 20; ++it) {
+      double J[2][3];
+      legendre_jets<2, 2, double>(c64, ref, a.p, t, J);
+      double gx = J[0][0] - x, gy = J[1][0] - y;
+      double f = gx * J[0][1] + gy * J[1][1];
+      double s2 = J[0][1] * J[0][1] + J[1][1] * J[1][1];
+      double fp = s2 + gx * J[0][2] + gy * J[1][2];
+      if (fp < 0.1 * s2) fp = s2;
+      double tn = fmin(1.0, fmax(-1.0, t - f / fp));
+      double dt = tn - t;
+      t = tn;
+      if (fabs(dt) < 1e-14) break;
+    }
+    double J0[2][1];
+    legendre_jets<0, 2, double>(c64, ref, a.p, t, J0);
+    r.gx = J0[0][0] - x;
+    r.gy = J0[1][0] - y;
+  } else {
+    // one double-precision Newton step from the single-precision foot
+    // (|dt| ~ 1e-7, leaving an error ~ dt^2); the offset at the new parameter
+    // from the second-order Taylor expansion (error ~ dt^3 times the third
+    // derivative), so that the distance of on-boundary targets is resolved
+    // to rounding
+    double J[2][3];
+    legendre_jets<2, 2, double>(c64, ref, a.p, t, J);
+    const double gx = J[0][0] - x, gy = J[1][0] - y;
+    const double f = gx * J[0][1] + gy * J[1][1];
+    const double s2 = J[0][1] * J[0][1] + J[1][1] * J[1][1];
+    double fp = s2 + gx * J[0][2] + gy * J[1][2];
+    if (fp < 0.1 * s2) fp = s2;
+    const double tn = fmin(1.0, fmax(-1.0, t - f / fp));
+    const double dt = tn - t;
+    t = tn;
+    r.gx = gx + dt * (J[0][1] + 0.5 * dt * J[0][2]);
+    r.gy = gy + dt * (J[1][1] + 0.5 * dt * J[1][2]);
+  }
   r.t = t;
-  r.d2 = (J0[0][0] - x) * (J0[0][0] - x) + (J0[1][0] - y) * (J0[1][0] - y);
+  r.d2 = r.gx * r.gx + r.gy * r.gy;
   return r;
 }
 
+template <typename T>
+__device__ __forceinline__ const T* coef_ptr(const double* c64, const float* c32);
+template <>
+__device__ __forceinline__ const double* coef_ptr<double>(const double* c64, const float*) { return c64; }
+template <>
+__device__ __forceinline__ const float* coef_ptr<float>(const double*, const float* c32) { return c32; }
+
 // Coefficients of xi^1..xi^4 of F(s(xi)) with F(s) = sum_{k>=1} F[k] s^k and
 // s(xi) = sum_{k>=1} c[k] xi^k.
-__device__ void compose4(const double* F, const double* c, double* o) {
+template <typename T>
+__device__ void compose4(const T* F, const T* c, T* o) {
   o[1] = F[1] * c[1];
   o[2] = F[1] * c[2] + F[2] * c[1] * c[1];
-  o[3] = F[1] * c[3] + 2.0 * F[2] * c[1] * c[2] + F[3] * c[1] * c[1] * c[1];
-  o[4] = F[1] * c[4] + F[2] * (c[2] * c[2] + 2.0 * c[1] * c[3]) + 3.0 * F[3] * c[1] * c[1] * c[2] +
+  o[3] = F[1] * c[3] + T(2) * F[2] * c[1] * c[2] + F[3] * c[1] * c[1] * c[1];
+  o[4] = F[1] * c[4] + F[2] * (c[2] * c[2] + T(2) * c[1] * c[3]) + T(3) * F[3] * c[1] * c[1] * c[2] +
          F[4] * c[1] * c[1] * c[1] * c[1];
 }
 
-__device__ __forceinline__ double far_volume(const LocalArgs& a, const double* J);
+__device__ __forceinline__ double far_volume(const LocalArgs& a, const double* J) {
+  // delta f + delta^2/2 lap f (Sec. 4, after eq. vplocO5)
+  double v = a.delta * J[0];
+  if (a.order >= 5) v += 0.5 * a.delta * a.delta * (J[3] + J[5]);
+  return v;
+}
 
+template <typename T>
 __device__ void local_near_one(const LocalArgs& a, int64_t i, int best) {
   const double x = a.txy[2 * i], y = a.txy[2 * i + 1];
-  const double dl = a.delta;
+  const T dl = (T)a.delta;
   const double* J = a.jet ? a.jet + 6 * i : nullptr;
-  double vl = 0.0, sl = 0.0, dlv = 0.0;
+  T vl = 0, sl = 0, dlv = 0;
   bool far = false;
-  Foot ft{-1, 0.0, 1e300};
+  Foot ft{-1, 0.0, 1e300, 0.0, 0.0};
   {
     const int p = a.p;
     const int ip0 = best / p;
-    ft = panel_foot(a, ip0, a.tau[best - ip0 * p], x, y);
+    ft = panel_foot<sizeof(T) == 8>(a, ip0, a.tau[best - ip0 * p], x, y);
     if (fabs(ft.t) == 1.0) {
       // the foot lies beyond this panel's end: continue on the adjacent panel
       int ip = ((ip0 + (ft.t > 0.0 ? 1 : -1)) % a.n_panels + a.n_panels) % a.n_panels;
@@ -151,140 +201,139 @@ __device__ void local_near_one(const LocalArgs& a, int64_t i, int best) {
           kb = k;
         }
       }
-      Foot f = panel_foot(a, ip, a.tau[kb], x, y);
+      Foot f = panel_foot<sizeof(T) == 8>(a, ip, a.tau[kb], x, y);
       if (f.d2 < ft.d2) ft = f;
     }
     if (sqrt(ft.d2) >= a.band) far = true;
   }
 
   if (far) {
-    if (J) vl = far_volume(a, J);
+    if (J) vl = (T)far_volume(a, J);
   } else {
     const int p = a.p, ip = ft.panel;
     const bool want_s = a.out[1] && a.sig_coef, want_d = a.out[2] && a.mu_coef;
-    const double* cgx = a.geo_coef + (size_t)(2 * ip) * p;
-    // value and four derivatives of x, y, sigma, mu at the foot (one recurrence)
-    const double* cs[4] = {cgx, cgx + p, want_s ? a.sig_coef + (size_t)ip * p : cgx,
-                           want_d ? a.mu_coef + (size_t)ip * p : cgx};
-    const double rs[4] = {a.geo_ref[2 * ip], a.geo_ref[2 * ip + 1], want_s ? a.sig_ref[ip] : 0.0,
-                          want_d ? a.mu_ref[ip] : 0.0};
-    double JJ[4][5];
-    legendre_jets<4, 4, double>(cs, rs, p, ft.t, JJ);
-    const double* X = JJ[0];
-    const double* Y = JJ[1];
-    const double sp = hypot(X[1], Y[1]);
-    const double Tx = X[1] / sp, Ty = Y[1] / sp;
-    const double Nx = -Ty, Ny = Tx;  // inward normal of a counter-clockwise curve
-    const double r = hypot(x - X[0], y - Y[0]);
-    double sgn = 0.0;
-    if (r > a.on_tol) sgn = (-((X[0] - x) * Nx + (Y[0] - y) * Ny) > 0.0) ? 1.0 : -1.0;
+    const T* cgx = coef_ptr<T>(a.geo_coef, a.geo_coef32) + (size_t)(2 * ip) * p;
+    // value and four derivatives of x, y (relative to the panel's reference
+    // node), sigma, mu at the foot (one recurrence)
+    const T* cs[4] = {cgx, cgx + p, want_s ? coef_ptr<T>(a.sig_coef, a.sig_coef32) + (size_t)ip * p : cgx,
+                      want_d ? coef_ptr<T>(a.mu_coef, a.mu_coef32) + (size_t)ip * p : cgx};
+    const T rs[4] = {T(0), T(0), want_s ? (T)a.sig_ref[ip] : T(0), want_d ? (T)a.mu_ref[ip] : T(0)};
+    T JJ[4][5];
+    legendre_jets<4, 4, T>(cs, rs, p, (T)ft.t, JJ);
+    const T* X = JJ[0];
+    const T* Y = JJ[1];
+    const T sp = hypot(X[1], Y[1]);
+    const T Tx = X[1] / sp, Ty = Y[1] / sp;
+    const T Nx = -Ty, Ny = Tx;  // inward normal of a counter-clockwise curve
+    const double rd = sqrt(ft.d2);
+    const T r = (T)rd;
+    T sgn = 0;
+    if (rd > a.on_tol) sgn = (-(ft.gx * (double)Nx + ft.gy * (double)Ny) > 0.0) ? T(1) : T(-1);
     // Taylor coefficients in s = t - t*: xi(s) = sum a_k s^k, eta(s) = sum e_k s^k
-    const double fact[5] = {1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0};
-    double A[5], E[5];
+    const T fact[5] = {T(1), T(1), T(0.5), T(1.0 / 6.0), T(1.0 / 24.0)};
+    T A[5], E[5];
     for (int k = 1; k <= 4; ++k) {
       A[k] = (X[k] * Tx + Y[k] * Ty) * fact[k];
       E[k] = (X[k] * Nx + Y[k] * Ny) * fact[k];
     }
-    E[1] = 0.0;
+    E[1] = 0;
     // series reversion s(xi)
-    double C[5];
-    const double i1 = 1.0 / A[1];
-    const double i2 = i1 * i1, i3 = i2 * i1, i5 = i3 * i2, i7 = i5 * i2;
+    T C[5];
+    const T i1 = T(1.0) / A[1];
+    const T i2 = i1 * i1, i3 = i2 * i1, i5 = i3 * i2, i7 = i5 * i2;
     C[1] = i1;
     C[2] = -A[2] * i3;
-    C[3] = (2.0 * A[2] * A[2] - A[1] * A[3]) * i5;
-    C[4] = (5.0 * A[1] * A[2] * A[3] - A[1] * A[1] * A[4] - 5.0 * A[2] * A[2] * A[2]) * i7;
-    double H[5];
-    compose4(E, C, H);
-    const double kap = 2.0 * H[2], g3 = 6.0 * H[3], g4 = 24.0 * H[4];
-    const double c = r / sqrt(dl);
-    const double sq = sqrt(dl), d15 = dl * sq, d2 = dl * dl;
-    const double Ex = exp(-0.25 * c * c) * 0.56418958354775628695;  // e^{-c^2/4}/sqrt(pi)
-    const double Cc = erfc(0.5 * c);
-    const double c2 = c * c, c3 = c2 * c;
+    C[3] = (T(2.0) * A[2] * A[2] - A[1] * A[3]) * i5;
+    C[4] = (T(5.0) * A[1] * A[2] * A[3] - A[1] * A[1] * A[4] - T(5.0) * A[2] * A[2] * A[2]) * i7;
+    T H[5];
+    compose4<T>(E, C, H);
+    const T kap = T(2.0) * H[2], g3 = T(6.0) * H[3], g4 = T(24.0) * H[4];
+    const T c = r / sqrt(dl);
+    const T sq = sqrt(dl), d15 = dl * sq, d2 = dl * dl;
+    const T Ex = exp(-T(0.25) * c * c) * T(0.56418958354775628695);  // e^{-c^2/4}/sqrt(pi)
+    const T Cc = erfc(T(0.5) * c);
+    const T c2 = c * c, c3 = c2 * c;
     if (want_s) {
-      const double* Sv = JJ[2];
-      double F[5], o[5];
+      const T* Sv = JJ[2];
+      T F[5], o[5];
       for (int k = 1; k <= 4; ++k) F[k] = Sv[k] * fact[k];
-      compose4(F, C, o);
-      const double s0 = Sv[0], s1 = o[1], s2 = 2.0 * o[2];
-      const double Aq = c * Cc - 2.0 * Ex;
-      const double Q = 2.0 * (c2 - 2.0) * Ex - c3 * Cc;
-      double s = sq * 0.5 * s0 * Aq + sgn * dl * 0.25 * c * kap * s0 * Aq;
+      compose4<T>(F, C, o);
+      const T s0 = Sv[0], s1 = o[1], s2 = T(2.0) * o[2];
+      const T Aq = c * Cc - T(2.0) * Ex;
+      const T Q = T(2.0) * (c2 - T(2.0)) * Ex - c3 * Cc;
+      T s = sq * T(0.5) * s0 * Aq + sgn * dl * T(0.25) * c * kap * s0 * Aq;
       if (a.order >= 4)
-        s += d15 * (s0 * kap * kap / 12.0 * (2.0 * c3 * Cc - (4.0 * c2 + 1.0) * Ex) + s2 / 12.0 * Q);
+        s += d15 * (s0 * kap * kap / T(12.0) * (T(2.0) * c3 * Cc - (T(4.0) * c2 + T(1.0)) * Ex) + s2 / T(12.0) * Q);
       if (a.order >= 5)
         s += d2 * sgn * c *
-             (kap * kap * kap * s0 / 16.0 * (3.0 * c3 * Cc - (6.0 * c2 - 2.0) * Ex) +
-              (kap * s2 / 8.0 + s0 * g4 / 48.0 + s1 * g3 / 12.0) * Q);
+             (kap * kap * kap * s0 / T(16.0) * (T(3.0) * c3 * Cc - (T(6.0) * c2 - T(2.0)) * Ex) +
+              (kap * s2 / T(8.0) + s0 * g4 / T(48.0) + s1 * g3 / T(12.0)) * Q);
       sl = -s;
     }
     if (want_d) {
-      const double* Mv = JJ[3];
-      double F[5], o[5];
+      const T* Mv = JJ[3];
+      T F[5], o[5];
       for (int k = 1; k <= 4; ++k) F[k] = Mv[k] * fact[k];
-      compose4(F, C, o);
-      const double m0 = Mv[0], m1 = o[1], m2 = 2.0 * o[2], m4 = 24.0 * o[4];
-      const double R1 = 2.0 * (c2 + 1.0) * Ex - c3 * Cc;
-      const double R4 = 2.0 * (c2 + 4.0) * Ex - c3 * Cc;
-      double s = sgn * 0.5 * m0 * Cc + sq * 0.5 * kap * m0 * Ex +
-                 dl * sgn * (0.375 * c * kap * kap * m0 * Ex + 0.25 * c * m2 * (2.0 * Ex - c * Cc));
+      compose4<T>(F, C, o);
+      const T m0 = Mv[0], m1 = o[1], m2 = T(2.0) * o[2], m4 = T(24.0) * o[4];
+      const T R1 = T(2.0) * (c2 + T(1.0)) * Ex - c3 * Cc;
+      const T R4 = T(2.0) * (c2 + T(4.0)) * Ex - c3 * Cc;
+      T s = sgn * T(0.5) * m0 * Cc + sq * T(0.5) * kap * m0 * Ex +
+            dl * sgn * (T(0.375) * c * kap * kap * m0 * Ex + T(0.25) * c * m2 * (T(2.0) * Ex - c * Cc));
       if (a.order >= 4)
-        s += d15 * (5.0 / 16.0 * (c2 - 2.0) * kap * kap * kap * m0 * Ex + 0.25 * g4 * m0 * Ex +
-                    0.25 * kap * m2 * R1 + g3 * m1 / 12.0 * R4);
+        s += d15 * (T(5.0 / 16.0) * (c2 - T(2.0)) * kap * kap * kap * m0 * Ex + T(0.25) * g4 * m0 * Ex +
+                    T(0.25) * kap * m2 * R1 + g3 * m1 / T(12.0) * R4);
       if (a.order >= 5)
         s += d2 * sgn * c *
-             (35.0 / 128.0 * kap * kap * kap * kap * m0 * (c2 - 6.0) * Ex +
-              5.0 / 12.0 * g3 * g3 * m0 * Ex + 0.625 * kap * g4 * m0 * Ex +
-              5.0 * (kap * kap * m2 / 16.0 * R1 + kap * g3 * m1 / 24.0 * R4) +
-              m4 / 48.0 * (c3 * Cc - 2.0 * (c2 - 2.0) * Ex));
+             (T(35.0 / 128.0) * kap * kap * kap * kap * m0 * (c2 - T(6.0)) * Ex +
+              T(5.0 / 12.0) * g3 * g3 * m0 * Ex + T(0.625) * kap * g4 * m0 * Ex +
+              T(5.0) * (kap * kap * m2 / T(16.0) * R1 + kap * g3 * m1 / T(24.0) * R4) +
+              m4 / T(48.0) * (c3 * Cc - T(2.0) * (c2 - T(2.0)) * Ex));
       dlv = -s;
     }
     if (J) {
-      if (sgn < 0.0) {
+      if (sgn < T(0.0)) {
         atomicOr(a.status, kStatusExteriorBandV);
       } else {
-        const double f = J[0];
-        const double fe = J[1] * Nx + J[2] * Ny;
-        const double fxx = J[3] * Tx * Tx + 2.0 * J[4] * Tx * Ty + J[5] * Ty * Ty;
-        const double fee = J[3] * Nx * Nx + 2.0 * J[4] * Nx * Ny + J[5] * Ny * Ny;
-        const double Ef = erf(0.5 * c);
-        double v = 0.25 * dl * (2.0 * Ef + 2.0 * c * Ex - c2 * Cc + 2.0) * f;
-        if (a.order >= 4) v += d15 * ((4.0 - 2.0 * c2) * Ex + c3 * Cc) * (2.0 * fe - kap * f) / 12.0;
+        T Jt[6];
+        for (int k = 0; k < 6; ++k) Jt[k] = (T)J[k];
+        const T f = Jt[0];
+        const T fe = Jt[1] * Nx + Jt[2] * Ny;
+        const T fxx = Jt[3] * Tx * Tx + T(2.0) * Jt[4] * Tx * Ty + Jt[5] * Ty * Ty;
+        const T fee = Jt[3] * Nx * Nx + T(2.0) * Jt[4] * Nx * Ny + Jt[5] * Ny * Ny;
+        const T Ef = erf(T(0.5) * c);
+        T v = T(0.25) * dl * (T(2.0) * Ef + T(2.0) * c * Ex - c2 * Cc + T(2.0)) * f;
+        if (a.order >= 4) v += d15 * ((T(4.0) - T(2.0) * c2) * Ex + c3 * Cc) * (T(2.0) * fe - kap * f) / T(12.0);
         if (a.order >= 5) {
-          const double c4 = c2 * c2;
-          v += d2 / 48.0 *
-               (Cc * (4.0 * c4 * kap * fe - 3.0 * (c4 + 4.0) * fee + (c4 - 12.0) * fxx -
-                      3.0 * c4 * kap * kap * f) +
-                2.0 * c * (c2 - 2.0) * Ex * (-4.0 * kap * fe + 3.0 * fee - fxx + 3.0 * kap * kap * f) +
-                24.0 * (fxx + fee));
+          const T c4 = c2 * c2;
+          v += d2 / T(48.0) *
+               (Cc * (T(4.0) * c4 * kap * fe - T(3.0) * (c4 + T(4.0)) * fee + (c4 - T(12.0)) * fxx -
+                      T(3.0) * c4 * kap * kap * f) +
+                T(2.0) * c * (c2 - T(2.0)) * Ex * (-T(4.0) * kap * fe + T(3.0) * fee - fxx + T(3.0) * kap * kap * f) +
+                T(24.0) * (fxx + fee));
         }
         vl = v;
       }
     }
   }
-  if (a.out[0]) a.out[0][i] += vl;
-  if (a.out[1]) a.out[1][i] += sl;
-  if (a.out[2]) a.out[2][i] += dlv;
+  if (a.out[0]) a.out[0][i] += (double)vl;
+  if (a.out[1]) a.out[1][i] += (double)sl;
+  if (a.out[2]) a.out[2][i] += (double)dlv;
 }
 
-__device__ __forceinline__ double far_volume(const LocalArgs& a, const double* J) {
-  // delta f + delta^2/2 lap f (Sec. 4, after eq. vplocO5)
-  double v = a.delta * J[0];
-  if (a.order >= 5) v += 0.5 * a.delta * a.delta * (J[3] + J[5]);
-  return v;
-}
-
-// Pass 1: nearest boundary node (ties: lowest index) among the 3x3 hash cells.
-// A single-precision scan (node coordinates stored relative to their cell
+// Pass 1: nearest boundary node among the 3x3 hash cells.  A
+// single-precision scan (node coordinates stored relative to their cell
 // origin) bounds every squared distance within err = 2e-5 h^2 (h the cell
-// side; six roundings of quantities below 3h); only nodes within 2 err of the
-// single-precision minimum are compared in double precision, which gives
-// exactly the double-precision nearest node.  Targets whose nearest node is
-// farther than band + margin get the far-field volume term here; the others
-// are appended to a compact list for pass 2.
-// Returns the nearest node for a band candidate, -1 when the far-field term
-// was applied.
+// side; six roundings of quantities below 3h).  FP64 plans (exact = true) then
+// compare in double precision only the nodes within 2 err of the
+// single-precision minimum, which gives exactly the double-precision nearest
+// node (ties: lowest index); FP32 plans keep the single-precision choice,
+// which only seeds the foot search (an error of err at the band edge, where
+// the near and far expansions agree, is harmless).  Targets whose nearest
+// node is farther than band + margin get the far-field volume term here; the
+// others are appended to a compact list for pass 2.  Returns the nearest node
+// for a band candidate, -1 when the far-field term was applied.
+template <bool exact>
 __device__ int local_classify_one(const LocalArgs& a, int64_t i) {
   const double x = a.txy[2 * i], y = a.txy[2 * i + 1];
   int best = -1;
@@ -295,6 +344,7 @@ __device__ int local_classify_one(const LocalArgs& a, int64_t i) {
       const int x0c = max(cx - 1, 0), x1c = min(cx + 1, a.hnx - 1);
       const int y0c = max(cy - 1, 0), y1c = min(cy + 1, a.hny - 1);
       float m32 = 3.0e38f;
+      int k32 = -1;
       for (int yy = y0c; yy <= y1c; ++yy) {
         const float ty = (float)(y - (a.hy0 + yy * a.hh));
         for (int xx = x0c; xx <= x1c; ++xx) {
@@ -304,30 +354,43 @@ __device__ int local_classify_one(const LocalArgs& a, int64_t i) {
           for (int k = a.cell_start[c]; k < k1; ++k) {
             float2 q = a.cell_xy32[k];
             float dx = tx - q.x, dy = ty - q.y;
-            m32 = fminf(m32, fmaf(dx, dx, dy * dy));
+            const float d2 = fmaf(dx, dx, dy * dy);
+            if (exact) {
+              m32 = fminf(m32, d2);
+            } else if (d2 < m32) {
+              m32 = d2;
+              k32 = k;
+            }
           }
         }
       }
-      const float err = 2e-5f * (float)(a.hh * a.hh);
-      const double lower = sqrt(fmax((double)m32 - err, 0.0));
-      if (m32 < 1.0e38f && lower - a.margin < a.band) {
-        const float thr = m32 + 2.0f * err;
-        for (int yy = y0c; yy <= y1c; ++yy) {
-          const float ty = (float)(y - (a.hy0 + yy * a.hh));
-          for (int xx = x0c; xx <= x1c; ++xx) {
-            const float tx = (float)(x - (a.hx0 + xx * a.hh));
-            const int c = yy * a.hnx + xx;
-            const int k1 = a.cell_start[c + 1];
-            for (int k = a.cell_start[c]; k < k1; ++k) {
-              float2 q = a.cell_xy32[k];
-              float dx = tx - q.x, dy = ty - q.y;
-              if (fmaf(dx, dx, dy * dy) > thr) continue;
-              int j = a.cell_node[k];
-              double ex = x - a.bxy[2 * j], ey = y - a.bxy[2 * j + 1];
-              double d2 = ex * ex + ey * ey;
-              if (d2 < bd2 || (d2 == bd2 && j < best)) {
-                bd2 = d2;
-                best = j;
+      if (!exact) {
+        if (k32 >= 0) {
+          best = a.cell_node[k32];
+          bd2 = (double)m32;
+        }
+      } else {
+        const float err = 2e-5f * (float)(a.hh * a.hh);
+        const double lower = sqrt(fmax((double)m32 - err, 0.0));
+        if (m32 < 1.0e38f && lower - a.margin < a.band) {
+          const float thr = m32 + 2.0f * err;
+          for (int yy = y0c; yy <= y1c; ++yy) {
+            const float ty = (float)(y - (a.hy0 + yy * a.hh));
+            for (int xx = x0c; xx <= x1c; ++xx) {
+              const float tx = (float)(x - (a.hx0 + xx * a.hh));
+              const int c = yy * a.hnx + xx;
+              const int k1 = a.cell_start[c + 1];
+              for (int k = a.cell_start[c]; k < k1; ++k) {
+                float2 q = a.cell_xy32[k];
+                float dx = tx - q.x, dy = ty - q.y;
+                if (fmaf(dx, dx, dy * dy) > thr) continue;
+                int j = a.cell_node[k];
+                double ex = x - a.bxy[2 * j], ey = y - a.bxy[2 * j + 1];
+                double d2 = ex * ex + ey * ey;
+                if (d2 < bd2 || (d2 == bd2 && j < best)) {
+                  bd2 = d2;
+                  best = j;
+                }
               }
             }
           }
@@ -342,10 +405,11 @@ __device__ int local_classify_one(const LocalArgs& a, int64_t i) {
   return best;
 }
 
+template <typename T>
 __global__ void local_classify_kernel(const __grid_constant__ LocalArgs a, int2* list, int* count) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
-  const int best = local_classify_one(a, i);
+  const int best = local_classify_one<sizeof(T) == 8>(a, i);
   if (best < 0) return;
   auto g = cg::coalesced_threads();
   int base = 0;
@@ -356,13 +420,14 @@ __global__ void local_classify_kernel(const __grid_constant__ LocalArgs a, int2*
 
 // Batched: one launch over the targets of many plans; list entries are
 // (plan, target, nearest node).
+template <typename T>
 __global__ void local_classify_batch_kernel(const LocalArgs* __restrict__ args, const int2* __restrict__ work,
                                             int4* list, int* count) {
   const int2 wk = work[blockIdx.x];
   const LocalArgs& a = args[wk.x];
   int64_t i = (int64_t)wk.y + threadIdx.x;
   if (i >= a.n) return;
-  const int best = local_classify_one(a, i);
+  const int best = local_classify_one<sizeof(T) == 8>(a, i);
   if (best < 0) return;
   auto g = cg::coalesced_threads();
   int base = 0;
@@ -372,20 +437,32 @@ __global__ void local_classify_batch_kernel(const LocalArgs* __restrict__ args, 
 }
 
 // Pass 2: closest point, frame and expansions for the listed targets.
+template <typename T>
 __global__ void local_near_kernel(const __grid_constant__ LocalArgs a, const int2* __restrict__ list,
                                   const int* __restrict__ count) {
   const int n_near = *count;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n_near; idx += gridDim.x * blockDim.x)
-    local_near_one(a, list[idx].x, list[idx].y);
+    local_near_one<T>(a, list[idx].x, list[idx].y);
 }
 
+template <typename T>
 __global__ void local_near_batch_kernel(const LocalArgs* __restrict__ args, const int4* __restrict__ list,
                                         const int* __restrict__ count) {
   const int n_near = *count;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n_near; idx += gridDim.x * blockDim.x) {
     const int4 e = list[idx];
-    local_near_one(args[e.x], e.y, e.z);
+    local_near_one<T>(args[e.x], e.y, e.z);
   }
+}
+
+template <typename T>
+void local_two_pass(const LocalArgs& a, int64_t nt, int2* list, int* count, cudaStream_t s) {
+  const int threads = 128;
+  const unsigned blocks = (unsigned)((nt + threads - 1) / threads);
+  cudaMemsetAsync(count, 0, sizeof(int), s);
+  local_classify_kernel<T><<<blocks, threads, 0, s>>>(a, list, count);
+  const unsigned nblk = std::min<unsigned>(blocks, 152u * 16u);
+  local_near_kernel<T><<<nblk, threads, 0, s>>>(a, list, count);
 }
 
 }  // namespace
@@ -419,6 +496,8 @@ LocalArgs make_local_args(const Plan& P, int64_t nt, const double* txy, const do
   a.cell_node = P.d_cell_node;
   a.cell_xy32 = P.d_cell_xy32;
   a.geo_coef32 = P.d_geo_coef32;
+  a.sig_coef32 = P.d_sigma_coef32;
+  a.mu_coef32 = P.d_mu_coef32;
   a.margin = P.margin;
   a.band = P.band;
   a.delta = P.delta1;
@@ -430,16 +509,7 @@ LocalArgs make_local_args(const Plan& P, int64_t nt, const double* txy, const do
 
 void launch_local(const Plan& P, int64_t nt, const double* txy, const double* jet, double* V,
                   double* S, double* D, cudaStream_t s) {
-  if (nt <= 0) return;
-  LocalArgs a = make_local_args(P, nt, txy, jet, V, S, D);
-  int threads = 128;
-  unsigned blocks = (unsigned)((nt + threads - 1) / threads);
-  cudaMemsetAsync(P.d_near_count, 0, sizeof(int), s);
-  ++P.launches;
-  local_classify_kernel<<<blocks, threads, 0, s>>>(a, P.d_near, P.d_near_count);
-  unsigned nblk = std::min<unsigned>(blocks, 152u * 16u);
-  ++P.launches;
-  local_near_kernel<<<nblk, threads, 0, s>>>(a, P.d_near, P.d_near_count);
+  launch_local_list(P, nt, txy, jet, V, S, D, P.d_near, P.d_near_count, s);
 }
 
 // Same two passes with a caller-provided list and counter (the counter is
@@ -448,26 +518,28 @@ void launch_local_list(const Plan& P, int64_t nt, const double* txy, const doubl
                        double* S, double* D, int2* list, int* count, cudaStream_t s) {
   if (nt <= 0) return;
   LocalArgs a = make_local_args(P, nt, txy, jet, V, S, D);
-  int threads = 128;
-  unsigned blocks = (unsigned)((nt + threads - 1) / threads);
-  cudaMemsetAsync(count, 0, sizeof(int), s);
-  ++P.launches;
-  local_classify_kernel<<<blocks, threads, 0, s>>>(a, list, count);
-  unsigned nblk = std::min<unsigned>(blocks, 152u * 16u);
-  ++P.launches;
-  local_near_kernel<<<nblk, threads, 0, s>>>(a, list, count);
+  P.launches += 2;
+  if (P.precision == LP_FP64)
+    local_two_pass<double>(a, nt, list, count, s);
+  else
+    local_two_pass<float>(a, nt, list, count, s);
 }
 
 // Batched local pass over a wave of plans: one classify launch over every
 // plan's targets (work entries of kBatchThreads targets), one near launch over
 // the combined candidate list.
-void launch_local_batch(const LocalArgs* d_args, const int2* d_work, int nwork, int4* d_list,
+void launch_local_batch(int precision, const LocalArgs* d_args, const int2* d_work, int nwork, int4* d_list,
                         int* d_count, int64_t n_total, cudaStream_t s) {
   if (nwork <= 0) return;
   cudaMemsetAsync(d_count, 0, sizeof(int), s);
-  local_classify_batch_kernel<<<nwork, kBatchThreads, 0, s>>>(d_args, d_work, d_list, d_count);
-  unsigned nblk = (unsigned)std::min<int64_t>((n_total + 127) / 128, 152 * 16);
-  local_near_batch_kernel<<<std::max(nblk, 1u), 128, 0, s>>>(d_args, d_list, d_count);
+  const unsigned nblk = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_total + 127) / 128, 152 * 16));
+  if (precision == LP_FP64) {
+    local_classify_batch_kernel<double><<<nwork, kBatchThreads, 0, s>>>(d_args, d_work, d_list, d_count);
+    local_near_batch_kernel<double><<<nblk, 128, 0, s>>>(d_args, d_list, d_count);
+  } else {
+    local_classify_batch_kernel<float><<<nwork, kBatchThreads, 0, s>>>(d_args, d_work, d_list, d_count);
+    local_near_batch_kernel<float><<<nblk, 128, 0, s>>>(d_args, d_list, d_count);
+  }
 }
 
 }  // namespace lpg

@@ -63,12 +63,69 @@ __global__ void sum_kernel(const double* __restrict__ x, int64_t n, double* out)
   }
 }
 
+// Deconvolved history multiplier (eq. vnearkspace; eq. vfarkspace with W of
+// eq. Wdef) on the kept modes, tab[my][mx] = scale M(dk |m|) / (ph[mx] ph[my])^2;
+// the FP32 copy omits the k = 0 entry (its term is added in FP64).
+__device__ double one_minus_j0_dev(double z) {
+  if (z < 2.0) {  // power series: no cancellation at small z
+    double q = 0.25 * z * z, term = 1.0, s = 0.0;
+    for (int k = 1; k < 40; ++k) {
+      term *= -q / ((double)k * k);
+      s -= term;
+      if (fabs(term) < 1e-18 * fabs(s)) break;
+    }
+    return s;
+  }
+  return 1.0 - j0(z);
+}
+__device__ double j1_over_z_dev(double z) {
+  if (z < 2.0) {
+    double q = 0.25 * z * z, term = 0.5, s = 0.5;
+    for (int k = 1; k < 40; ++k) {
+      term *= -q / ((double)k * (k + 1));
+      s += term;
+      if (fabs(term) < 1e-18 * fabs(s)) break;
+    }
+    return s;
+  }
+  return j1(z) / z;
+}
+
+__global__ void mult_table_kernel(int kind, int K, double dk, double d1, double d2, double L, double scale,
+                                  const double* __restrict__ ph, double* tab, float* tab32) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t n = (int64_t)(K + 1) * (K + 1);
+  if (idx >= n) return;
+  int my = (int)(idx / (K + 1)), mx = (int)(idx - (int64_t)my * (K + 1));
+  double k = dk * sqrt((double)mx * mx + (double)my * my);
+  double M;
+  if (kind == 0) {
+    M = (k == 0.0) ? (d2 - d1) : (expm1(-k * k * d1) - expm1(-k * k * d2)) / (k * k);
+  } else {
+    double z = L * k;
+    double W = (z == 0.0) ? 0.25 * L * L : L * L * (one_minus_j0_dev(z) / (z * z));
+    W -= L * L * log(L) * j1_over_z_dev(z);
+    M = exp(-k * k * d2) * W;
+  }
+  double d = ph[mx] * ph[my];
+  double v = scale * M / (d * d);
+  tab[idx] = v;
+  tab32[idx] = (idx == 0) ? 0.0f : (float)v;
+}
+
 __global__ void to_float_kernel(const double* __restrict__ src, float* dst, int64_t n) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j < n) dst[j] = (float)src[j];
 }
 
 }  // namespace
+
+void launch_mult_table(int kind, int K, double dk, double d1, double d2, double L, double scale,
+                       const double* d_ph, double* tab, float* tab32, cudaStream_t s) {
+  int64_t n = (int64_t)(K + 1) * (K + 1);
+  mult_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(kind, K, dk, d1, d2, L, scale, d_ph, tab,
+                                                                 tab32);
+}
 
 void launch_to_float(const double* src, float* dst, int64_t n, cudaStream_t s) {
   if (n <= 0) return;

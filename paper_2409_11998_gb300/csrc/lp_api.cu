@@ -143,7 +143,8 @@ void destroy_plan(Plan& P) {
                   P.d_cell_start, P.d_cell_node, P.d_vxy, P.d_vq, P.d_sigma, P.d_sigma_coef,
                   P.d_sigma_ref, P.d_mu, P.d_mu_coef, P.d_mu_ref, P.d_bq, P.d_qsum, P.d_stage,
                   P.d_out, P.d_status, P.d_near, P.d_near_count, P.d_cell_xy32,
-                  P.d_geo_coef32};
+                  P.d_geo_coef32, P.d_keys, P.d_counts, P.d_cursor, P.d_vrel_s, P.d_vperm, P.d_vq_s,
+                  P.d_vstart, P.d_sigma_coef32, P.d_mu_coef32};
   for (void* b : bufs) dfree(b);
   if (P.h_status) cudaFreeHost(P.h_status);
   for (auto& e : P.ev)
@@ -220,6 +221,72 @@ lp_status noalloc_scratch(void** out) {
   }
   *out = g_noalloc_addr[dev];
   return LP_OK;
+}
+
+// Bins of the binned volume spread (FP32 plans): squares of kTile
+// near-history cells.  Plans whose kernel fit needs more coefficients than
+// the binned kernel holds keep the point-parallel spread.
+lp_status setup_bins(Plan& P) {
+  const GridLevel& N = P.lv[0];
+  const int w = P.ker.w;
+  if (w < 4 || w > 10 || P.es32.nc > sub_ncw(w)) return LP_OK;
+  P.bins.x0 = N.x0;
+  P.bins.y0 = N.y0;
+  P.bins.inv_bt = 1.0 / (kTile * N.h);
+  P.bins.nbx = P.bins.nby = (N.g + kTile - 1) / kTile;
+  // Patch side per level: the bin, the stencil halo and a cell of rounding
+  // slack; among the next 16 sizes, the one whose row pitch gives the fewest
+  // shared-memory wavefronts for the w^2 stencil cells taken 32 at a time.
+  for (int l = 0; l < 2; ++l) {
+    const double cells = kTile * N.h / P.lv[l].h;
+    const int m0 = (int)std::ceil(cells) + w + 3;
+    int best = m0, best_wf = 1 << 30;
+    for (int m = m0; m < m0 + 16; ++m) {
+      int wf = 0;
+      for (int p0 = 0; p0 < w * w; p0 += 32) {
+        int hits[32] = {0}, mx = 0;
+        for (int i = p0; i < std::min(p0 + 32, w * w); ++i) mx = std::max(mx, ++hits[((i / w) * m + i % w) % 32]);
+        wf += mx;
+      }
+      if (wf < best_wf) {
+        best_wf = wf;
+        best = m;
+      }
+    }
+    P.sub_M[l] = best;
+    const size_t smem = (size_t)(((sub_ncw(w) * w + 3) & ~3) + (kSubThreads / 32) * best * best) * sizeof(float);
+    if (smem > 200 * 1024) return LP_OK;
+  }
+  if (!spread_sub_configure(w)) return LP_ERR_CUDA;
+  const size_t nbins = (size_t)P.bins.nbx * P.bins.nby + 1;
+  if (!dalloc(P, (void**)&P.d_counts, nbins * sizeof(int)) ||
+      !dalloc(P, (void**)&P.d_cursor, nbins * sizeof(int)) ||
+      !dalloc(P, (void**)&P.d_vstart, (nbins + 1) * sizeof(int)))
+    return LP_ERR_NOMEM;
+  cudaMemset(P.d_vstart, 0, (nbins + 1) * sizeof(int));
+  P.binned = true;
+  return LP_OK;
+}
+
+// FP32 spread of the volume channel on one level from the sorted nodes.
+void spread_binned(const Plan& P, int l, cudaStream_t s) {
+  const GridLevel& G = P.lv[l];
+  SubArgs a;
+  a.gd = grid_dev(G);
+  a.es = P.es32;
+  a.rel = P.d_vrel_s;
+  a.q = P.d_vq_s;
+  a.start = P.d_vstart;
+  a.grid = G.chan[0];
+  a.org_x = P.bins.x0;
+  a.org_y = P.bins.y0;
+  a.bt = 1.0 / P.bins.inv_bt;
+  a.nbx = P.bins.nbx;
+  a.nby = P.bins.nby;
+  a.M = P.sub_M[l];
+  a.status = P.d_status;
+  ++P.launches;
+  launch_spread_sub(a, P.ker.w, s);
 }
 
 }  // namespace
@@ -333,6 +400,7 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
     if (!finite) st = LP_ERR_ARG;
     if (st == LP_OK) st = build_boundary(P, hxy.data(), hw.data(), hn.data());
   }
+  if (st == LP_OK && P.precision == LP_FP32) st = setup_bins(P);
   if (st == LP_OK) st = status_from_cuda();
   if (st != LP_OK) {
     destroy_plan(P);
@@ -367,6 +435,34 @@ lp_status lp_volume(lp_plan_t h, int64_t n, const double* xy, const double* w, c
     cudaMemcpyAsync(P.d_vxy, dxy, n * 2 * sizeof(double), cudaMemcpyDeviceToDevice, P.stream);
     launch_volume_q(P, df, dw, P.d_vq, n, P.stream);
   }
+  if (P.binned && n > 0) {
+    // sort the volume nodes into the spread's bins
+    if ((size_t)n > P.key_cap || !P.d_vrel_s || (size_t)n > P.vsort_cap) {
+      cudaStreamSynchronize(P.stream);
+      if ((size_t)n > P.key_cap) {
+        dfree(P.d_keys);
+        P.d_keys = nullptr;
+        if (!dalloc(P, (void**)&P.d_keys, n * sizeof(int))) return LP_ERR_NOMEM;
+        P.key_cap = n;
+      }
+      if ((size_t)n > P.vsort_cap) {
+        dfree(P.d_vrel_s);
+        dfree(P.d_vperm);
+        dfree(P.d_vq_s);
+        P.d_vrel_s = nullptr;
+        P.d_vperm = nullptr;
+        P.d_vq_s = nullptr;
+        if (!dalloc(P, (void**)&P.d_vrel_s, n * sizeof(float2)) ||
+            !dalloc(P, (void**)&P.d_vperm, n * sizeof(int)) || !dalloc(P, (void**)&P.d_vq_s, n * sizeof(float)))
+          return LP_ERR_NOMEM;
+        P.vsort_cap = n;
+      }
+    }
+    launch_bin_sort(P.d_vxy, n, P.bins, P.d_keys, P.d_counts, P.d_cursor, P.d_vstart, P.d_vrel_s, P.d_vperm,
+                    P.d_status, P.stream);
+    launch_gather_q(P.d_vq, n, 1, P.d_vperm, n, P.d_vq_s, P.stream);
+    P.launches += 4;
+  }
   launch_sum(P, P.d_vq, n, P.d_qsum, P.stream);
   P.have_volume = true;
   return status_from_cuda();
@@ -383,6 +479,11 @@ static lp_status bind_layer(lp_plan_t h, const double* dens, int kind) {
   cudaMemcpyAsync(dst, d, P.nb * sizeof(double), cudaMemcpyDeviceToDevice, P.stream);
   launch_panel_coef(P, dst, 1, 1, kind == 0 ? P.d_sigma_coef : P.d_mu_coef,
                     kind == 0 ? P.d_sigma_ref : P.d_mu_ref, P.stream);
+  if (P.precision == LP_FP32) {
+    launch_to_float(kind == 0 ? P.d_sigma_coef : P.d_mu_coef, kind == 0 ? P.d_sigma_coef32 : P.d_mu_coef32,
+                    P.n_panels * P.p, P.stream);
+    ++P.launches;
+  }
   launch_strengths(P, kind, P.stream);
   if (kind == 0) {
     launch_sum(P, P.d_bq, P.nb, P.d_qsum + 1, P.stream);
@@ -441,7 +542,9 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
   for (int c = 0; c < 3; ++c) dout[c] = host_out[c] ? P.d_out + c * nt : outs[c];
   cudaEventRecord(P.ev[1], s);
 
-  // Steps 2-3: spread every requested channel onto both history grids
+  // Steps 2-3: spread every requested channel onto both history grids:
+  // volume nodes through the bins (FP32 plans) or point-parallel with global
+  // atomics; boundary nodes point-parallel.
   for (int l = 0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
     if (wv) cudaMemsetAsync(G.chan[0], 0, G.chan_bytes, s);
@@ -455,9 +558,13 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
   for (int l = 0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
     if (wv && P.nv > 0) {
-      const double* q[1] = {P.d_vq};
-      void* g[1] = {G.chan[0]};
-      launch_spread(P, l, P.d_vxy, q, 1, g, P.nv, s);
+      if (P.binned) {
+        spread_binned(P, l, s);
+      } else {
+        const double* q[1] = {P.d_vq};
+        void* g[1] = {G.chan[0]};
+        launch_spread(P, l, P.d_vxy, q, 1, g, P.nv, s);
+      }
     }
     const double* bq[3];
     void* bg[3];

@@ -270,7 +270,7 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
   cudaEventRecord(b->ev[5], s);
   launch_interp_batch(prec, w, d + o_ia, (const int2*)(d + o_iw), (int)iwork.size(), s);
   cudaEventRecord(b->ev[6], s);
-  launch_local_batch((const LocalArgs*)(d + o_la), (const int2*)(d + o_lw), (int)lwork.size(), b->d_list,
+  launch_local_batch(prec, (const LocalArgs*)(d + o_la), (const int2*)(d + o_lw), (int)lwork.size(), b->d_list,
                      b->d_count, total_t, s);
   cudaEventRecord(b->ev[7], s);
   b->launches += 5;

@@ -16,6 +16,12 @@ constexpr int kMaxW = 16;           // widest spreading kernel (grid points)
 constexpr int kMaxNC = 20;          // coefficients per piece of the kernel polynomial
 constexpr int kBatchThreads = 128;  // threads per block (and items per work entry) of batched launches
 constexpr int kZeroChunk = 4096;    // 16-byte words cleared per work entry of the batched zeroing
+constexpr int kTile = 32;           // bin side (near-history cells) of the binned spread
+constexpr int kSubThreads = 256;    // threads per CTA of the binned spread
+// Coefficient count of the binned spread's weight polynomials for width w
+// (the plan's fit is zero-padded; plans whose fit needs more use the
+// point-parallel spread).
+constexpr int sub_ncw(int w) { return w + 3; }
 constexpr int kMaxPanelOrder = 32;  // Gauss-Legendre nodes per boundary panel
 constexpr int kNumEvents = 10;
 
@@ -115,6 +121,26 @@ struct ZeroSeg {
   int64_t n16;
 };
 
+// Bins of the sorted-source spread: squares of side kTile near-history cells
+// from the near-history grid origin (physical, so both levels use them).
+struct BinGeom {
+  double x0, y0, inv_bt;  // origin and 1 / (kTile h_NH)
+  int nbx, nby;
+};
+
+// One level of the binned spread of the volume nodes: one CTA per bin.
+struct SubArgs {
+  GridDev gd;
+  const float2* rel;  // positions relative to their bin's corner, in bin order
+  const float* q;     // strengths in the same order
+  const int* start;   // [nbins + 2] bin starts (last bin: overflow)
+  void* grid;
+  double org_x, org_y, bt;  // bin grid origin and bin side
+  int nbx, nby, M;          // bins per dimension; patch side (row pitch)
+  unsigned* status;
+  EsPoly<float> es;
+};
+
 // Argument record of the local pass (one per plan).
 struct LocalArgs {
   const double* txy;
@@ -137,6 +163,8 @@ struct LocalArgs {
   const int* cell_node;
   const float2* cell_xy32;   // node coordinates relative to their cell origin
   const float* geo_coef32;   // FP32 copy of geo_coef
+  const float* sig_coef32;   // FP32 copies of sig_coef / mu_coef (FP32 plans)
+  const float* mu_coef32;
   double margin, band, delta, on_tol;
   int order;
   unsigned* status;
@@ -177,6 +205,22 @@ struct Plan {
   int* d_cell_node = nullptr;   // [nb] node ids sorted by cell
   float2* d_cell_xy32 = nullptr;  // [nb] node coordinates relative to their cell's origin (FP32)
   float* d_geo_coef32 = nullptr;  // FP32 copy of d_geo_coef (Newton start)
+  float* d_sigma_coef32 = nullptr;  // FP32 copies of the density coefficients (FP32 local pass)
+  float* d_mu_coef32 = nullptr;
+
+  // sorted-bin spread (FP32 path)
+  BinGeom bins{};
+  int sub_M[2] = {0, 0};           // shared-memory patch side (row pitch), per level
+  int* d_keys = nullptr;           // scratch [max(nv, nb)]
+  int* d_counts = nullptr;         // scratch [nbins + 1]
+  int* d_cursor = nullptr;         // scratch [nbins + 1]
+  float2* d_vrel_s = nullptr;      // volume nodes sorted by bin (offsets from the bin corner)
+  int* d_vperm = nullptr;
+  float* d_vq_s = nullptr;
+  int* d_vstart = nullptr;         // [nbins + 2]
+  bool binned = false;             // volume spread through the bins (FP32 plans)
+  size_t key_cap = 0;
+  size_t vsort_cap = 0;
 
   // bound sources
   int64_t nv = 0;
@@ -234,7 +278,7 @@ void launch_multiplier_batch(int precision, const MultArgs* d_args, const int2* 
                              cudaStream_t s);
 void launch_interp_batch(int precision, int w, const void* d_args, const int2* d_work, int nwork,
                          cudaStream_t s);
-void launch_local_batch(const LocalArgs* d_args, const int2* d_work, int nwork, int4* d_list,
+void launch_local_batch(int precision, const LocalArgs* d_args, const int2* d_work, int nwork, int4* d_list,
                         int* d_count, int64_t n_total, cudaStream_t s);
 
 // ---- launches (kernels in k_*.cu) ----
@@ -248,12 +292,21 @@ void launch_local(const Plan& P, int64_t nt, const double* txy, const double* je
                   double* S, double* D, cudaStream_t s);
 void launch_local_list(const Plan& P, int64_t nt, const double* txy, const double* jet, double* V,
                        double* S, double* D, int2* list, int* count, cudaStream_t s);
+void launch_bin_sort(const double* xy, int64_t n, const BinGeom& bg, int* keys, int* counts, int* cursor,
+                     int* starts, float2* rel_s, int* perm, unsigned* status, cudaStream_t s);
+void launch_gather_q(const double* q, int64_t stride, int nq, const int* perm, int64_t n, float* q_s,
+                     cudaStream_t s);
+bool spread_sub_configure(int w);
+size_t spread_sub_smem(const SubArgs& a, int w);
+void launch_spread_sub(const SubArgs& a, int w, cudaStream_t s);
 void fft_forward(const Plan& P, int level, int chan);
 void fft_inverse(const Plan& P, int level, int chan);
 void launch_panel_coef(const Plan& P, const double* vals, int stride, int ncomp, double* coef,
                        double* ref, cudaStream_t s);
 void launch_strengths(const Plan& P, int kind, cudaStream_t s);
 void launch_to_float(const double* src, float* dst, int64_t n, cudaStream_t s);
+void launch_mult_table(int kind, int K, double dk, double d1, double d2, double L, double scale,
+                       const double* d_ph, double* tab, float* tab32, cudaStream_t s);
 void launch_volume_q(const Plan& P, const double* f, const double* w, double* q, int64_t n,
                      cudaStream_t s);
 void launch_sum(const Plan& P, const double* x, int64_t n, double* out, cudaStream_t s);

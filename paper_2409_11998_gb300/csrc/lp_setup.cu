@@ -27,33 +27,6 @@ double fourier_cutoff(double delta, double eps) {
   return hi;
 }
 
-// 1 - J0(z) and J1(z)/z without cancellation at small z (power series),
-// glibc's j0/j1 elsewhere.
-double one_minus_j0(double z) {
-  if (z < 2.0) {
-    double q = 0.25 * z * z, term = 1.0, s = 0.0;
-    for (int k = 1; k < 40; ++k) {
-      term *= -q / ((double)k * k);   // (-q)^k / (k!)^2
-      s -= term;
-      if (std::fabs(term) < 1e-18 * std::fabs(s)) break;
-    }
-    return s;
-  }
-  return 1.0 - j0(z);
-}
-double j1_over_z(double z) {
-  if (z < 2.0) {
-    double q = 0.25 * z * z, term = 0.5, s = 0.5;
-    for (int k = 1; k < 40; ++k) {
-      term *= -q / ((double)k * (k + 1));  // (-q)^k / (2 k! (k+1)!)
-      s += term;
-      if (std::fabs(term) < 1e-18 * std::fabs(s)) break;
-    }
-    return s;
-  }
-  return j1(z) / z;
-}
-
 // ES kernel and its Fourier transform in grid-index units:
 // phihat(xi) = int_{-w/2}^{w/2} phi(2x/w) cos(xi x) dx, by Gauss-Legendre.
 double es_phi(double z, double beta) {
@@ -162,37 +135,23 @@ lp_status build_tables(Plan& P) {
       }
       ph[m] = 2.0 * 0.25 * w * s;  // even integrand over [-w/2, w/2]
     }
-    std::vector<double> tab((size_t)(K + 1) * (K + 1));
-    std::vector<float> tab32(tab.size());
     const double scale = (G.dk / (2.0 * kPi)) * (G.dk / (2.0 * kPi));
-    for (int my = 0; my <= K; ++my) {
-      for (int mx = 0; mx <= K; ++mx) {
-        double k = G.dk * std::sqrt((double)mx * mx + (double)my * my);
-        double M;
-        if (l == 0) {
-          // (e^{-k^2 d1} - e^{-k^2 d2}) / k^2   (eq. vnearkspace)
-          M = (k == 0.0) ? (P.delta2 - P.delta1)
-                         : (std::expm1(-k * k * P.delta1) - std::expm1(-k * k * P.delta2)) / (k * k);
-        } else {
-          // e^{-k^2 d2} W(k), W = (1 - J0(Lk))/k^2 - L log L J1(Lk)/k   (eq. Wdef)
-          double L = G.L, z = L * k;
-          double W = L * L * (one_minus_j0(z) / (z * z > 0 ? z * z : 1.0));
-          if (z == 0.0) W = L * L * 0.25;
-          W -= L * L * std::log(L) * j1_over_z(z);
-          M = std::exp(-k * k * P.delta2) * W;
-        }
-        if (mx == 0 && my == 0) G.zero_mode = scale * M;
-        double d = ph[mx] * ph[my];
-        double v = scale * M / (d * d);
-        tab[(size_t)my * (K + 1) + mx] = v;
-        tab32[(size_t)my * (K + 1) + mx] = (mx == 0 && my == 0) ? 0.0f : (float)v;
-      }
+    // the k = 0 multiplier without deconvolution (FP32 path adds it in FP64)
+    G.zero_mode = scale * (l == 0 ? (P.delta2 - P.delta1) : G.L * G.L * (1.0 - 2.0 * std::log(G.L)) / 4.0);
+    const size_t n = (size_t)(K + 1) * (K + 1);
+    double* d_ph = nullptr;
+    if (cudaMalloc(&G.mtab, n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&G.mtab32, n * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&d_ph, (K + 1) * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      if (d_ph) cudaFree(d_ph);
+      return LP_ERR_NOMEM;
     }
-    if (cudaMalloc(&G.mtab, tab.size() * sizeof(double)) != cudaSuccess) return LP_ERR_NOMEM;
-    if (cudaMalloc(&G.mtab32, tab32.size() * sizeof(float)) != cudaSuccess) return LP_ERR_NOMEM;
-    P.device_bytes += tab.size() * (sizeof(double) + sizeof(float));
-    cudaMemcpy(G.mtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
-    cudaMemcpy(G.mtab32, tab32.data(), tab32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    P.device_bytes += n * (sizeof(double) + sizeof(float));
+    cudaMemcpy(d_ph, ph.data(), (K + 1) * sizeof(double), cudaMemcpyHostToDevice);
+    launch_mult_table(l, K, G.dk, P.delta1, P.delta2, G.L, scale, d_ph, G.mtab, G.mtab32, P.stream);
+    cudaStreamSynchronize(P.stream);
+    cudaFree(d_ph);
   }
   return LP_OK;
 }
@@ -362,7 +321,9 @@ lp_status build_boundary(Plan& P, const double* h_xy, const double* h_w, const d
       !dmalloc((void**)&P.d_sigma_coef, (size_t)P.n_panels * p * sizeof(double)) ||
       !dmalloc((void**)&P.d_sigma_ref, (size_t)P.n_panels * sizeof(double)) ||
       !dmalloc((void**)&P.d_mu_coef, (size_t)P.n_panels * p * sizeof(double)) ||
-      !dmalloc((void**)&P.d_mu_ref, (size_t)P.n_panels * sizeof(double)))
+      !dmalloc((void**)&P.d_mu_ref, (size_t)P.n_panels * sizeof(double)) ||
+      !dmalloc((void**)&P.d_sigma_coef32, (size_t)P.n_panels * p * sizeof(float)) ||
+      !dmalloc((void**)&P.d_mu_coef32, (size_t)P.n_panels * p * sizeof(float)))
     return LP_ERR_NOMEM;
   cudaMemcpy(P.d_bxy, h_xy, nb * 2 * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemcpy(P.d_bw, h_w, nb * sizeof(double), cudaMemcpyHostToDevice);

@@ -1,0 +1,57 @@
+"""Continuous batching: every request's V, S, D are the same as the request
+evaluated alone, whether it ran in a wave with others or not."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lp():
+    from paper_2409_11998_gb300 import build
+    build.build()
+    import paper_2409_11998_gb300 as lp
+    return lp
+
+
+def test_results_same_alone_and_in_the_mix(lp):
+    from paper_2409_11998_gb300 import serve
+    from workloads import configs
+    pool = configs.serving_pool(n_meshes=4, t_min=1500, t_max=12000, seed=5100)
+    # bursts of overlapping arrivals on every mesh, so waves mix meshes and
+    # repeat a mesh within one wave
+    arrivals = [(0.001 * (i // 5), i % 4, 0.6 + 0.05 * i) for i in range(20)]
+    srv = serve.Server(pool, precision="fp32", tol=1e-5, n_slots=2, max_wave=8, keep_outputs=True)
+    srv.prewarm()
+    reqs = srv.run(arrivals)
+    stats = serve.latency_stats(reqs)
+    assert stats["requests"] == 20 and stats["p99_ms"] >= stats["p50_ms"] > 0
+    waves_with_many = srv.created > len(pool) * 2  # extra plans were needed for repeated meshes
+    for r in reqs:
+        p = pool[r.mesh]
+        ev = lp.Evaluator(p, precision="fp32", tol=1e-5).bind(src_f=p["src_f"] * r.scale,
+                                                             sigma=p["sigma"] * r.scale,
+                                                             mu=p["mu"] * r.scale)
+        alone = ev.evaluate(tgt_jet=p["tgt_jet"] * r.scale)
+        for k in "VSD":
+            a = alone[k].cpu().numpy()
+            b = r.outputs[k].cpu().numpy()
+            assert np.max(np.abs(a - b)) <= 5e-6 * np.max(np.abs(a)), (r.rid, k)
+        ev.close()
+    srv.close()
+    assert waves_with_many
+
+
+def test_one_at_a_time_path(lp):
+    from paper_2409_11998_gb300 import serve
+    from workloads import configs
+    pool = configs.serving_pool(n_meshes=2, t_min=1500, t_max=4000, seed=5200, precision="fp64", tol=1e-9)
+    srv = serve.Server(pool, precision="fp64", tol=1e-9, one_at_a_time=True, keep_outputs=True)
+    srv.prewarm()
+    reqs = srv.run([(0.0, 0, 1.0), (0.0, 1, 1.0), (0.001, 0, 2.0)])
+    a = reqs[0].outputs["V"].cpu().numpy()
+    c = reqs[2].outputs["V"].cpu().numpy()
+    assert np.allclose(2.0 * a, c, rtol=1e-12, atol=1e-14 * np.max(np.abs(a)))  # linear in the densities
+    srv.close()

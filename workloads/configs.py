@@ -171,3 +171,50 @@ def circle_layer_problem(n_panels=256, order=16, n_targets=64, delta=1e-4, mode=
     return _finish("circle-layer", "fp64", tol, z, np.zeros(0), np.zeros(0), bnd, dens, dens.copy(),
                    tgt, np.zeros((n_targets, 6)), {"radii": list(radii)}, delta=delta,
                    box=([-1.6, -1.6], [1.6, 1.6]))
+
+
+def serving_pool(n_meshes=12, t_min=10_000, t_max=5_000_000, seed=5000, precision="fp32", tol=1e-5,
+                 max_delaunay=300_000):
+    """Meshes for the serving workload: sizes log-uniform in [t_min, t_max]
+    triangles on the disk, starfish and square domains (in turn); sizes above
+    max_delaunay use the jittered structured square (fast to generate).
+    Every problem carries sigma and mu; targets are the mesh vertices."""
+    out = []
+    sizes = np.exp(np.linspace(np.log(t_min), np.log(t_max), n_meshes))
+    for i, T in enumerate(sizes):
+        T = int(T)
+        rng = np.random.default_rng(seed + i)
+        dom = ("disk", "starfish", "square")[i % 3] if T <= max_delaunay else "square"
+        if dom == "square":
+            n = max(8, int(np.sqrt(T / 2)))
+            mesh = M.square_mesh(n, rng, jitter=0.3)
+            xy, w = M.quadrature(mesh)
+            bnd = make_square_panels(1.0, max(8, n // 16), 16)
+            s = bnd["xy"]
+            sigma = 1.0 + 0.5 * np.sin(np.pi * s[:, 0]) * np.cos(np.pi * s[:, 1])
+            mu = np.cos(0.5 * np.pi * s[:, 0]) + 0.3 * s[:, 1]
+            field = GaussianSum(rng.uniform(-0.9, 0.9, size=(8, 2)), rng.uniform(0.02, 0.2, 8), background=1.0)
+        else:
+            curve = C.Circle(1.0) if dom == "disk" else C.Star(0.3, 5)
+            n_b = max(64, int(np.sqrt(T) * 2.5))
+            mesh = M.delaunay_mesh(curve, max(8, (T - n_b) // 2), n_b, rng)
+            xy, w = M.quadrature(mesh, curve)
+            keep = curve.inside(xy)
+            xy, w = xy[keep], w[keep]
+            n_pan = int(np.clip(2 ** np.round(np.log2(max(64, n_b / 2))), 64, 4096))
+            bnd = make_panels(curve, n_pan, 16)
+            sigma = random_smooth_density(bnd["t"], rng)
+            mu = random_smooth_density(bnd["t"], rng)
+            cen = []
+            while len(cen) < 8:
+                p = rng.uniform(-1.3, 1.3, size=(1, 2))
+                if curve.inside(p)[0]:
+                    cen.append(p[0])
+            field = GaussianSum(np.array(cen), rng.uniform(0.02, 0.2, 8))
+        tgt = mesh["P"]
+        if dom != "square":
+            tgt = tgt[(curve.inside(tgt)) | (np.arange(len(tgt)) < mesh["nbv"])]
+        meta = {"n_triangles": int(len(mesh["T"])), "domain": dom}
+        out.append(_finish(f"serve{i}-{dom}", precision, tol, xy, w, field.value(xy), bnd, sigma, mu,
+                           tgt, field.jet(tgt), meta))
+    return out

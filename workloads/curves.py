@@ -76,6 +76,14 @@ class PolarCurve(Curve):
         th = np.arctan2(p[:, 1], p[:, 0])
         return np.hypot(p[:, 0], p[:, 1]) < self.rho(th, 0)
 
+    def wall_distance(self, p):
+        """Approximate distance to the curve along its normal: the radial gap
+        times the cosine between the radial direction and the normal."""
+        p = np.asarray(p, dtype=np.float64) - self.center
+        th = np.arctan2(p[:, 1], p[:, 0])
+        r0, r1 = self.rho(th, 0), self.rho(th, 1)
+        return np.abs(r0 - np.hypot(p[:, 0], p[:, 1])) * r0 / np.sqrt(r0 * r0 + r1 * r1)
+
 
 class Circle(PolarCurve):
     def __init__(self, radius=1.0, center=(0.0, 0.0)):

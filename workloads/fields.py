@@ -47,8 +47,18 @@ class GaussianSum:
                 o[:, 5] += -A * ky * ky * sx * cy_
         return out
 
-    def value(self, xy):
-        return self.jet(xy)[:, 0]
+    def value(self, xy, chunk=1 << 21):
+        xy = np.asarray(xy, dtype=np.float64)
+        out = np.full(len(xy), self.bg)
+        for s0 in range(0, len(xy), chunk):
+            p = xy[s0:s0 + chunk]
+            o = out[s0:s0 + chunk]
+            for (cx, cy), s, a in zip(self.c, self.s, self.a):
+                o += a * np.exp(-((p[:, 0] - cx) ** 2 + (p[:, 1] - cy) ** 2) / (s * s))
+            if self.sincos is not None:
+                A, kx, ky = self.sincos
+                o += A * np.sin(kx * p[:, 0]) * np.cos(ky * p[:, 1])
+        return out
 
 
 class PolyField:

@@ -47,7 +47,10 @@ def delaunay_mesh(curve, n_interior, n_boundary, rng, min_wall_frac=0.5):
         cand = cand[curve.inside(cand)]
         if cand.size:
             # keep interior points away from the wall to avoid needle triangles there
-            d = _dist_to_polyline(cand, B)
+            if hasattr(curve, "wall_distance"):
+                d = curve.wall_distance(cand)
+            else:
+                d = _dist_to_polyline(cand, B)
             cand = cand[d > min_wall_frac * h * 0.5]
         pts.append(cand[:need])
         need -= len(pts[-1])
