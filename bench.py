@@ -179,17 +179,19 @@ def run_lp(args, rank, world, local_rank):
     points = nv + nb + nt
     T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
     sxy, sw, sf = T(prob["src_xy"]), T(prob["src_w"]), T(prob["src_f"])
-    sig, mu = T(prob["sigma"]), T(prob["mu"])
+    sig, mu = layer_densities(prob, T)
     txy, jet = T(prob["tgt_xy"]), T(prob["tgt_jet"])
-    outs = [torch.empty(nt, dtype=torch.float64, device=dev) for _ in range(3)]
+    outs = output_buffers(prob, nt, lambda: torch.empty(nt, dtype=torch.float64, device=dev))
     stream = torch.cuda.Stream(device=dev)
     ev = lp.Evaluator(prob, precision="fp64", stream=stream.cuda_stream)
     plan = ev.plan
 
     def step():
         lp.lp_volume(plan, nv, sxy, sw, sf)
-        lp.lp_single_layer(plan, sig)
-        lp.lp_double_layer(plan, mu)
+        if sig is not None:
+            lp.lp_single_layer(plan, sig)
+        if mu is not None:
+            lp.lp_double_layer(plan, mu)
         lp.lp_execute(plan, nt, txy, jet, outs[0], outs[1], outs[2])
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -243,10 +245,11 @@ def run_lp(args, rank, world, local_rank):
         res["parity"] = parity_sample(prob, outs)
         res["e2e"] = run_e2e(args, prob, dev, ev, points)
         res["fp32_same_workload"] = run_fp32(args, prob, dev, stream, points)
-        from workloads import configs as _cfg
-        small_pool = _cfg.serving_pool(n_meshes=6, t_min=10_000, t_max=300_000, seed=5300)
-        res["served"] = run_serve(args, rank, world, local_rank, pool=small_pool, rates=(100, 400),
-                                  seconds=3.0)
+        if args.workload == "starfish":
+            from workloads import configs as _cfg
+            small_pool = _cfg.serving_pool(n_meshes=6, t_min=10_000, t_max=300_000, seed=5300)
+            res["served"] = run_serve(args, rank, world, local_rank, pool=small_pool, rates=(100, 400),
+                                      seconds=3.0)
         if world == 1:
             res["cpu_baseline"] = cpu_baseline(prob, budget_s=15.0)
     ev.close()
@@ -301,13 +304,30 @@ def roofline(info, st, nv, nb, nt, precision):
             "peak_source": hbm_part["peak_source"]}
 
 
+def layer_densities(prob, conv):
+    """sigma and mu on the device (None where the workload carries none)."""
+    return tuple(None if prob.get(k) is None else conv(prob[k]) for k in ("sigma", "mu"))
+
+
+def output_buffers(prob, nt, make):
+    """V, S, D output buffers; S and D only where the workload has sigma, mu."""
+    return [make(), make() if prob.get("sigma") is not None else None,
+            make() if prob.get("mu") is not None else None]
+
+
+def wanted(prob):
+    return tuple(k for k, o in zip("VSD", output_buffers(prob, 0, lambda: 1)) if o is not None)
+
+
 def parity_sample(prob, outs, n=48):
     import numpy as np
     import oracle
     idx = np.random.default_rng(11).choice(len(prob["tgt_xy"]), n, replace=False)
-    ref = oracle.evaluate(prob, targets=idx)
+    ref = oracle.evaluate(prob, targets=idx, want=wanted(prob))
     r = {}
     for k, o in zip("VSD", outs):
+        if o is None:
+            continue
         got = o.cpu().numpy()[idx]
         r[f"{k}_rel_l2"] = float(np.linalg.norm(got - ref[k]) / np.linalg.norm(ref[k]))
     r["n_sample_targets"] = n
@@ -322,16 +342,19 @@ def run_e2e(args, prob, dev, ev, points):
     import torch
     import paper_2409_11998_gb300 as lp
     pin = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
-    h = {k: pin(prob[k]) for k in ("src_xy", "src_w", "src_f", "sigma", "mu", "tgt_xy", "tgt_jet")}
+    h = {k: pin(prob[k]) for k in ("src_xy", "src_w", "src_f", "sigma", "mu", "tgt_xy", "tgt_jet")
+         if prob.get(k) is not None}
     nt = len(prob["tgt_xy"])
-    houts = [torch.empty(nt, dtype=torch.float64).pin_memory() for _ in range(3)]
+    houts = output_buffers(prob, nt, lambda: torch.empty(nt, dtype=torch.float64).pin_memory())
     plan = ev.plan
     nv = len(prob["src_w"])
 
     def step():
         lp.lp_volume(plan, nv, h["src_xy"], h["src_w"], h["src_f"])
-        lp.lp_single_layer(plan, h["sigma"])
-        lp.lp_double_layer(plan, h["mu"])
+        if "sigma" in h:
+            lp.lp_single_layer(plan, h["sigma"])
+        if "mu" in h:
+            lp.lp_double_layer(plan, h["mu"])
         lp.lp_execute(plan, nt, h["tgt_xy"], h["tgt_jet"], houts[0], houts[1], houts[2])
         lp.lp_sync(plan)
 
@@ -345,7 +368,7 @@ def run_e2e(args, prob, dev, ev, points):
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / n
     h2d = sum(h[k].numel() * 8 for k in h)
-    d2h = 3 * nt * 8
+    d2h = sum(o is not None for o in houts) * nt * 8
     return {"value": points / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3, "steps": n,
             "api": "lp_volume/lp_single_layer/lp_double_layer/lp_execute/lp_sync on pinned host buffers"}
@@ -359,14 +382,17 @@ def run_fp32(args, prob, dev, stream, points):
     T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
     ev = lp.Evaluator(prob, precision="fp32", tol=1e-5, stream=stream.cuda_stream)
     nv, nt = len(prob["src_w"]), len(prob["tgt_xy"])
-    sxy, sw, sf, sig, mu, txy, jet = (T(prob[k]) for k in ("src_xy", "src_w", "src_f", "sigma", "mu", "tgt_xy", "tgt_jet"))
-    outs = [torch.empty(nt, dtype=torch.float64, device=dev) for _ in range(3)]
+    sxy, sw, sf, txy, jet = (T(prob[k]) for k in ("src_xy", "src_w", "src_f", "tgt_xy", "tgt_jet"))
+    sig, mu = layer_densities(prob, T)
+    outs = output_buffers(prob, nt, lambda: torch.empty(nt, dtype=torch.float64, device=dev))
     plan = ev.plan
 
     def step():
         lp.lp_volume(plan, nv, sxy, sw, sf)
-        lp.lp_single_layer(plan, sig)
-        lp.lp_double_layer(plan, mu)
+        if sig is not None:
+            lp.lp_single_layer(plan, sig)
+        if mu is not None:
+            lp.lp_double_layer(plan, mu)
         lp.lp_execute(plan, nt, txy, jet, *outs)
 
     for _ in range(3):

@@ -1,0 +1,72 @@
+"""Parity at the benchmark's full sizes, in the configuration the benchmark
+times (device-resident inputs, one plan, V + S + D in one lp_execute), on
+sampled targets the oracle evaluates one by one.
+
+Workloads: the 1.2M-node starfish (FP64 at 1e-9 and FP32 at 1e-5) and the
+12M-node square with 1M vertex targets (geometry-only boundary, V only; FP64
+at 1e-9 and FP32 at 1e-5).  The sample mixes uniformly drawn targets with the
+targets closest to the boundary (local expansions, on-surface points and, on
+the square, the corners).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lp():
+    from paper_2409_11998_gb300 import build
+    build.build()
+    import paper_2409_11998_gb300 as lp
+    return lp
+
+
+def _sample(prob, n_random=40, n_near=24, seed=17):
+    from scipy.spatial import cKDTree
+    txy = prob["tgt_xy"]
+    rng = np.random.default_rng(seed)
+    rand = rng.choice(len(txy), n_random, replace=False)
+    d, _ = cKDTree(prob["bnd"]["xy"]).query(txy)
+    near = np.argsort(d, kind="stable")[::max(1, len(txy) // 4000)][:n_near]
+    return np.unique(np.concatenate([rand, near]))
+
+
+def _run(lp, prob, precision, tol, oracle_lib):
+    want = tuple(k for k in "VSD" if k == "V" or prob.get({"S": "sigma", "D": "mu"}[k]) is not None)
+    ev = lp.Evaluator(prob, precision=precision, tol=tol).bind()
+    out = ev.evaluate(want=want)
+    idx = _sample(prob)
+    ref = oracle_lib.evaluate(prob, targets=idx, want=want)
+    for k in want:
+        got = out[k].cpu().numpy()[idx]
+        l2 = np.linalg.norm(got - ref[k]) / np.linalg.norm(ref[k])
+        mx = np.max(np.abs(got - ref[k])) / np.max(np.abs(ref[k]))
+        assert l2 < tol, f"{k}: rel-L2 {l2:.3e} over {len(idx)} sampled targets"
+        assert mx < 5 * tol, f"{k}: rel-max {mx:.3e}"
+        assert np.all(np.isfinite(out[k].cpu().numpy()))
+    ev.close()
+
+
+@pytest.fixture(scope="module")
+def starfish():
+    from workloads import configs
+    return configs.starfish()
+
+
+@pytest.fixture(scope="module")
+def square():
+    from workloads import configs
+    return configs.square()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 1e-5)])
+def test_starfish_full_size(lp, starfish, oracle_lib, precision, tol):
+    _run(lp, starfish, precision, tol, oracle_lib)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 1e-5)])
+def test_square_12M_full_size(lp, square, oracle_lib, precision, tol):
+    _run(lp, square, precision, tol, oracle_lib)
