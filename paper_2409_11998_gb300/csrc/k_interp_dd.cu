@@ -1,0 +1,123 @@
+// Type-2 interpolation of the FP64 plans in double-float arithmetic (Sec. 3,
+// Step 4): u(x) = sum over both history grids of the w x w stencil weights
+// times the grid values, which the df64 FFT chain left as (hi, lo) pairs.
+// The stencil weights are the plan's per-offset polynomials evaluated by
+// Horner's rule in df64 (coefficients split from the FP64 fit); products are
+// accumulated with error-free transforms and the three outputs are converted
+// to double once per target.
+#include <cmath>
+
+#include "df64.cuh"
+#include "lp_internal.cuh"
+
+namespace lpg {
+
+namespace {
+
+// acc * v + c with one renormalisation
+__device__ __forceinline__ dd dd_horner_step(dd acc, dd v, dd c) {
+  const float p = __fmul_rn(acc.hi, v.hi);
+  float e = __fmaf_rn(acc.hi, v.hi, -p);
+  e = __fmaf_rn(acc.hi, v.lo, e);
+  e = __fmaf_rn(acc.lo, v.hi, e);
+  float s, t;
+  two_sum(p, c.hi, s, t);
+  t = __fadd_rn(t, __fadd_rn(e, c.lo));
+  dd r;
+  quick_two_sum(s, t, r.hi, r.lo);
+  return r;
+}
+
+// Stencil origin i0 = floor(u - W/2) + 1 of a df64 grid coordinate, and the
+// offset v = u - i0 - (W-1)/2 in [-1/2, 1/2).
+template <int W>
+__device__ __forceinline__ bool dd_stencil(dd u, int g, int& i0, dd& v) {
+  const dd t = dd_add(u, dd{-0.5f * W, 0.f});
+  float f = floorf(t.hi);
+  if (t.hi == f && t.lo < 0.f) f -= 1.f;
+  if (!(f > -1e7f && f < 1e7f)) return false;
+  i0 = (int)f + 1;
+  v = dd_add(u, dd{-((float)i0 + 0.5f * (W - 1)), 0.f});
+  return i0 >= 0 && i0 + W <= g;
+}
+
+template <int W>
+__device__ __forceinline__ void dd_weights(const InterpDDArgs& a, dd v, dd* w) {
+  const int nc = a.nc;
+#pragma unroll
+  for (int t = 0; t < W; ++t) {
+    const float2 c = a.coef[nc - 1][t];
+    w[t] = dd{c.x, c.y};
+  }
+  for (int k = nc - 2; k >= 0; --k) {
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+      const float2 c = a.coef[k][t];
+      w[t] = dd_horner_step(w[t], v, dd{c.x, c.y});
+    }
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(128) interp_dd_kernel(const __grid_constant__ InterpDDArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const dd X = dd_from_double(a.txy[2 * i]), Y = dd_from_double(a.txy[2 * i + 1]);
+  dd_acc acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  bool bad = false;
+  for (int l = 0; l < 2; ++l) {
+    const InterpDDLevel& L = a.lv[l];
+    const dd ux = dd_mul(dd_sub(X, dd{L.x0.x, L.x0.y}), dd{L.inv_h.x, L.inv_h.y});
+    const dd uy = dd_mul(dd_sub(Y, dd{L.y0.x, L.y0.y}), dd{L.inv_h.x, L.inv_h.y});
+    int ix, iy;
+    dd vx, vy;
+    if (!dd_stencil<W>(ux, L.g, ix, vx) || !dd_stencil<W>(uy, L.g, iy, vy)) {
+      bad = true;
+      continue;
+    }
+    dd wx[W], wy[W];
+    dd_weights<W>(a, vx, wx);
+    dd_weights<W>(a, vy, wy);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (!a.out[c]) continue;
+      const float2* base = (const float2*)L.grid[c] + (size_t)iy * L.pitch + ix;
+#pragma unroll
+      for (int b = 0; b < W; ++b) {
+        const float2* row = base + (size_t)b * L.pitch;
+        dd_acc r = {0.f, 0.f};
+#pragma unroll
+        for (int t = 0; t < W; ++t) {
+          const float2 gv = __ldg(row + t);
+          acc_fma(r, wx[t], dd{gv.x, gv.y});
+        }
+        acc_fma(acc[c], wy[b], acc_value(r));
+      }
+    }
+  }
+  if (bad) {
+    atomicOr(a.status, kStatusOutOfBox);
+    return;
+  }
+  for (int c = 0; c < 3; ++c)
+    if (a.out[c]) a.out[c][i] = dd_to_double(acc_value(acc[c]));
+}
+
+}  // namespace
+
+void launch_interp_dd(const InterpDDArgs& a, int w, cudaStream_t s) {
+  if (a.n <= 0) return;
+  const unsigned blocks = (unsigned)((a.n + 127) / 128);
+  switch (w) {
+#define LP_CASE(W)                                         \
+  case W:                                                  \
+    interp_dd_kernel<W><<<blocks, 128, 0, s>>>(a);         \
+    break;
+    LP_CASE(4) LP_CASE(5) LP_CASE(6) LP_CASE(7) LP_CASE(8) LP_CASE(9) LP_CASE(10) LP_CASE(11) LP_CASE(12)
+    LP_CASE(13) LP_CASE(14) LP_CASE(15) LP_CASE(16)
+#undef LP_CASE
+    default: break;
+  }
+}
+
+}  // namespace lpg

@@ -133,6 +133,9 @@ void destroy_plan(Plan& P) {
   if (P.stream) cudaStreamSynchronize(P.stream);
   for (auto& G : P.lv) {
     for (auto& c : G.chan) dfree(c);
+    for (auto& c : G.spec) dfree(c);
+    dfree(G.tw_dd);
+    dfree(G.mtab_dd);
     dfree(G.mtab);
     dfree(G.mtab32);
     if (G.row_fwd) cufftDestroy(G.row_fwd);
@@ -289,6 +292,127 @@ void spread_binned(const Plan& P, int l, cudaStream_t s) {
   launch_spread_sub(a, P.ker.w, s);
 }
 
+float2 split_host(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+
+// df64 FFT chain and interpolation of FP64 plans: radix plans, twiddles, the
+// multiplier tables as (hi, lo) pairs and the per-channel spectrum columns.
+// Plans whose grids are not 3-smooth or whose columns do not fit in shared
+// memory keep cuFFT.
+lp_status setup_fft_dd(Plan& P) {
+  const size_t limit = 220 * 1024;
+  for (int l = 0; l < 2; ++l) {
+    GridLevel& G = P.lv[l];
+    G.full = fft_shape(G.g);
+    G.half = fft_shape(G.g / 2);
+    if (G.full.nst <= 0 || G.half.nst <= 0 || (G.g & 1)) return LP_OK;
+    if (fft_cols_smem(G.g) > limit || fft_rows_smem(G.g) > limit) return LP_OK;
+  }
+  if (!fft_dd_configure()) return LP_ERR_CUDA;
+  for (int l = 0; l < 2; ++l) {
+    GridLevel& G = P.lv[l];
+    G.kp = (G.K + 2) & ~1;
+    const size_t spec_bytes = (size_t)G.g * G.kp * sizeof(float4);
+    for (int c = 0; c < 4; ++c)
+      if (!dalloc(P, (void**)&G.spec[c], spec_bytes)) return LP_ERR_NOMEM;
+    const std::vector<float4> tw = fft_twiddles(G.g);
+    const size_t ntab = (size_t)(G.K + 1) * (G.K + 1);
+    if (!dalloc(P, (void**)&G.tw_dd, tw.size() * sizeof(float4)) ||
+        !dalloc(P, (void**)&G.mtab_dd, ntab * sizeof(float2)))
+      return LP_ERR_NOMEM;
+    cudaMemcpy(G.tw_dd, tw.data(), tw.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    launch_split_table(G.mtab, G.mtab_dd, (int64_t)ntab, P.stream);
+  }
+  for (int k = 0; k < P.es.nc; ++k)
+    for (int t = 0; t < P.es.w; ++t) P.es_dd[k][t] = split_host(P.es.c[k][t]);
+  if (cudaStreamSynchronize(P.stream) != cudaSuccess) return LP_ERR_CUDA;
+  P.dd_fft = true;
+  return LP_OK;
+}
+
+// Steps 2-4 of the FP64 plans in df64: forward row transforms of the spread
+// grids, the fused column pass (transform, multiplier, inverse transform) and
+// the inverse row transforms, then the interpolation.
+void history_dd(const Plan& P, int64_t nt, const double* txy, double* const* dout, bool wv, bool ws, bool wd,
+                cudaStream_t s) {
+  int fch[4], nf = 0;
+  if (wv) fch[nf++] = 0;
+  if (ws) fch[nf++] = 1;
+  if (wd) {
+    fch[nf++] = 2;
+    fch[nf++] = 3;
+  }
+  int ich[3], ni = 0;
+  if (wv) ich[ni++] = 0;
+  if (ws) ich[ni++] = 1;
+  if (wd) ich[ni++] = 2;
+  auto row_args = [&](const GridLevel& G, const int* ch, int n) {
+    FftRowArgs a{};
+    a.half = G.half;
+    a.tw = G.tw_dd;
+    for (int i = 0; i < n; ++i) {
+      a.grid[i] = G.chan[ch[i]];
+      a.spec[i] = G.spec[ch[i]];
+    }
+    a.pitch = G.pitch;
+    a.kp = G.kp;
+    a.K = G.K;
+    a.row_lo = G.row_lo;
+    a.row_hi = G.row_hi;
+    return a;
+  };
+  for (int l = 0; l < 2; ++l) {
+    launch_fft_rows_fwd(row_args(P.lv[l], fch, nf), nf, s);
+    ++P.launches;
+  }
+  cudaEventRecord(P.ev[4], s);
+  for (int l = 0; l < 2; ++l) {
+    const GridLevel& G = P.lv[l];
+    FftColArgs a{};
+    a.full = G.full;
+    a.tw = G.tw_dd;
+    a.tab = G.mtab_dd;
+    a.dk = split_host(G.dk);
+    int nj = 0;
+    if (wv) a.job[nj++] = FftColJob{0, {G.spec[0], nullptr}, G.spec[0]};
+    if (ws) a.job[nj++] = FftColJob{0, {G.spec[1], nullptr}, G.spec[1]};
+    if (wd) a.job[nj++] = FftColJob{1, {G.spec[2], G.spec[3]}, G.spec[2]};
+    a.kp = G.kp;
+    a.K = G.K;
+    a.row_lo = G.row_lo;
+    a.row_hi = G.row_hi;
+    launch_fft_cols(a, nj, s);
+    ++P.launches;
+  }
+  cudaEventRecord(P.ev[5], s);
+  for (int l = 0; l < 2; ++l) {
+    launch_fft_rows_inv(row_args(P.lv[l], ich, ni), ni, s);
+    ++P.launches;
+  }
+  cudaEventRecord(P.ev[6], s);
+  InterpDDArgs a{};
+  a.txy = txy;
+  a.n = nt;
+  for (int l = 0; l < 2; ++l) {
+    const GridLevel& G = P.lv[l];
+    InterpDDLevel& L = a.lv[l];
+    for (int c = 0; c < 3; ++c) L.grid[c] = G.chan[c];
+    L.g = G.g;
+    L.pitch = G.pitch;
+    L.x0 = split_host(G.x0);
+    L.y0 = split_host(G.y0);
+    L.inv_h = split_host(1.0 / G.h);
+  }
+  for (int c = 0; c < 3; ++c) a.out[c] = dout[c];
+  a.status = P.d_status;
+  a.nc = P.es.nc;
+  std::memcpy(a.coef, P.es_dd, sizeof(a.coef));
+  launch_interp_dd(a, P.ker.w, s);
+  ++P.launches;
+}
+
 }  // namespace
 
 extern "C" {
@@ -401,6 +525,7 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
     if (st == LP_OK) st = build_boundary(P, hxy.data(), hw.data(), hn.data());
   }
   if (st == LP_OK && P.precision == LP_FP32) st = setup_bins(P);
+  if (st == LP_OK && P.precision == LP_FP64) st = setup_fft_dd(P);
   if (st == LP_OK) st = status_from_cuda();
   if (st != LP_OK) {
     destroy_plan(P);
@@ -582,25 +707,29 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
     if (nq) launch_spread(P, l, P.d_bxy, bq, nq, bg, P.nb, s);
   }
   cudaEventRecord(P.ev[3], s);
-  for (int l = 0; l < 2; ++l) {
-    if (wv) fft_forward(P, l, 0);
-    if (ws) fft_forward(P, l, 1);
-    if (wd) {
-      fft_forward(P, l, 2);
-      fft_forward(P, l, 3);
+  if (P.dd_fft) {
+    history_dd(P, nt, dt, dout, wv, ws, wd, s);
+  } else {
+    for (int l = 0; l < 2; ++l) {
+      if (wv) fft_forward(P, l, 0);
+      if (ws) fft_forward(P, l, 1);
+      if (wd) {
+        fft_forward(P, l, 2);
+        fft_forward(P, l, 3);
+      }
     }
+    cudaEventRecord(P.ev[4], s);
+    // Step 4: deconvolved multiplier (in place; D written to channel 2)
+    for (int l = 0; l < 2; ++l) launch_multiplier(P, l, wv, ws, wd, s);
+    cudaEventRecord(P.ev[5], s);
+    for (int l = 0; l < 2; ++l) {
+      if (wv) fft_inverse(P, l, 0);
+      if (ws) fft_inverse(P, l, 1);
+      if (wd) fft_inverse(P, l, 2);
+    }
+    cudaEventRecord(P.ev[6], s);
+    launch_interp(P, nt, dt, dout[0], dout[1], dout[2], s);
   }
-  cudaEventRecord(P.ev[4], s);
-  // Step 4: deconvolved multiplier (in place; D written to channel 2)
-  for (int l = 0; l < 2; ++l) launch_multiplier(P, l, wv, ws, wd, s);
-  cudaEventRecord(P.ev[5], s);
-  for (int l = 0; l < 2; ++l) {
-    if (wv) fft_inverse(P, l, 0);
-    if (ws) fft_inverse(P, l, 1);
-    if (wd) fft_inverse(P, l, 2);
-  }
-  cudaEventRecord(P.ev[6], s);
-  launch_interp(P, nt, dt, dout[0], dout[1], dout[2], s);
   cudaEventRecord(P.ev[7], s);
   launch_local(P, nt, dt, dj, dout[0], dout[1], dout[2], s);
   cudaEventRecord(P.ev[8], s);

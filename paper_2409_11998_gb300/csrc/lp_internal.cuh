@@ -24,6 +24,8 @@ constexpr int kSubThreads = 256;    // threads per CTA of the binned spread
 constexpr int sub_ncw(int w) { return w + 3; }
 constexpr int kMaxPanelOrder = 32;  // Gauss-Legendre nodes per boundary panel
 constexpr int kNumEvents = 10;
+constexpr int kFftThreads = 256;    // threads per CTA of the df64 FFT kernels
+constexpr int kMaxFftStages = 24;   // radix stages of one df64 transform
 
 // Device status bits (OR-ed by kernels, read by lp_sync).
 enum : unsigned {
@@ -50,6 +52,12 @@ struct EsPoly {
   T c[kMaxNC][kMaxW];
 };
 
+// Radix plan of one df64 transform of length n (n = 2^a 3^b).
+struct FftShape {
+  int n, nst;
+  int radix[kMaxFftStages];
+};
+
 // One periodic grid of the history part (Sec. 3): near history (kind 0,
 // multiplier (e^{-k^2 d1} - e^{-k^2 d2})/k^2) or far history (kind 1,
 // multiplier e^{-k^2 d2} W(k) with truncation radius L).
@@ -69,6 +77,14 @@ struct GridLevel {
   int row_lo = 0, row_hi = 0;
   cufftHandle row_fwd = 0, row_inv = 0, col = 0;
   size_t chan_bytes = 0;
+  // df64 FFT chain (FP64 plans): twiddles e^{-2 pi i k/g}, the multiplier
+  // table as (hi, lo) pairs, and per channel the kept half-spectrum columns
+  // [g][kp] (kp = K + 1 rounded up to even) as df64 complex
+  FftShape full{}, half{};
+  float4* tw_dd = nullptr;
+  float2* mtab_dd = nullptr;
+  float4* spec[4] = {nullptr, nullptr, nullptr, nullptr};
+  int kp = 0;
 };
 
 // Grid geometry passed to kernels by value.
@@ -141,6 +157,47 @@ struct SubArgs {
   EsPoly<float> es;
 };
 
+// df64 FFT chain (k_fft.cu)
+struct FftRowArgs {
+  FftShape half;
+  const float4* tw;
+  void* grid[4];      // FP64 grids (forward input) / df64 grids (inverse output)
+  float4* spec[4];    // kept half spectra
+  int pitch, kp, K, row_lo, row_hi;
+};
+
+struct FftColJob {
+  int kind;           // 0: M F (V, S); 1: M (-i)(k1 F1 + k2 F2) (D)
+  const float4* in[2];
+  float4* out;
+};
+
+struct FftColArgs {
+  FftShape full;
+  const float4* tw;
+  const float2* tab;  // deconvolved multiplier, (K+1)^2, df64
+  float2 dk;          // mode spacing, df64
+  FftColJob job[3];
+  int kp, K, row_lo, row_hi;
+};
+
+// df64 interpolation (k_interp_dd.cu)
+struct InterpDDLevel {
+  const void* grid[3];  // V, S, D grids as df64 (hi, lo) pairs
+  int g, pitch;
+  float2 x0, y0, inv_h;
+};
+
+struct InterpDDArgs {
+  const double* txy;
+  int64_t n;
+  InterpDDLevel lv[2];
+  double* out[3];
+  unsigned* status;
+  int nc;
+  float2 coef[kMaxNC][kMaxW];  // weight polynomials, df64
+};
+
 // Argument record of the local pass (one per plan).
 struct LocalArgs {
   const double* txy;
@@ -182,6 +239,8 @@ struct Plan {
   Kernel ker{};
   EsPoly<double> es{};
   EsPoly<float> es32{};
+  float2 es_dd[kMaxNC][kMaxW] = {};  // es as df64 (hi, lo) pairs
+  bool dd_fft = false;               // FP64 plan runs the df64 FFT chain and interpolation
   double es_fit_err = 0;
   GridLevel lv[2];
   cudaStream_t stream = nullptr;
@@ -299,6 +358,16 @@ void launch_gather_q(const double* q, int64_t stride, int nq, const int* perm, i
 bool spread_sub_configure(int w);
 size_t spread_sub_smem(const SubArgs& a, int w);
 void launch_spread_sub(const SubArgs& a, int w, cudaStream_t s);
+FftShape fft_shape(int n);
+std::vector<float4> fft_twiddles(int g);
+bool fft_dd_configure();
+size_t fft_rows_smem(int g);
+size_t fft_cols_smem(int g);
+void launch_fft_rows_fwd(const FftRowArgs& a, int nchan, cudaStream_t s);
+void launch_fft_rows_inv(const FftRowArgs& a, int nchan, cudaStream_t s);
+void launch_fft_cols(const FftColArgs& a, int njobs, cudaStream_t s);
+void launch_split_table(const double* src, float2* dst, int64_t n, cudaStream_t s);
+void launch_interp_dd(const InterpDDArgs& a, int w, cudaStream_t s);
 void fft_forward(const Plan& P, int level, int chan);
 void fft_inverse(const Plan& P, int level, int chan);
 void launch_panel_coef(const Plan& P, const double* vals, int stride, int ncomp, double* coef,
