@@ -1,15 +1,17 @@
-// Volume nodes sorted into square bins of kTile near-history cells
-// (counting sort), and the single-precision spread that uses them.  One CTA
-// owns one bin on each level's grid: it accumulates every point of the bin
-// into shared-memory copies of the grid patch their stencils cover (the bin
-// plus a w-cell halo), then adds the patch to the grid with global atomics.
-// Each point is read once per level, its stencil weights are evaluated once,
-// and the w^2 updates hit shared memory only.  Positions are stored relative
-// to their bin's corner in single precision (bins are ~0.03 wide, so ~2e-9
-// absolute).
+// Volume nodes sorted into square bins of near-history cells (counting
+// sort; 32 cells for FP32 plans, 24 for FP64 plans), and the binned spreads
+// that use them.  One CTA owns one bin on each level's grid: it accumulates
+// every point of the bin into shared-memory copies of the grid patch their
+// stencils cover (the bin plus a w-cell halo), then adds the patch to the
+// grid with global atomics.  Each point is read once per level, its stencil
+// weights are evaluated once, and the w^2 updates hit shared memory only.
+// Positions are stored relative to their bin's corner: in single precision
+// for FP32 plans (bins are ~0.03 wide, so ~2e-9 absolute), as df64 pairs for
+// FP64 plans.
 #include <algorithm>
 #include <cmath>
 
+#include "df64.cuh"
 #include "lp_internal.cuh"
 
 namespace lpg {
@@ -181,6 +183,182 @@ __global__ void __launch_bounds__(kSubThreads) spread_sub_kernel(const __grid_co
   }
 }
 
+// Scatter of the FP64 plans: offsets from the bin corner as df64 pairs
+// (x.hi, x.lo, y.hi, y.lo), exact to ~2^-48 of the bin side.
+__global__ void scatter_dd_kernel(const double* __restrict__ xy, int64_t n, const int* __restrict__ keys,
+                                  const int* __restrict__ starts, int* cursor, BinGeom bg, float4* rel_s,
+                                  int* perm) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int key = keys[j];
+  const int pos = starts[key] + atomicAdd(&cursor[key], 1);
+  const int bx = key % bg.nbx, by = key / bg.nbx;  // overflow bin: never read
+  const double bt = 1.0 / bg.inv_bt;
+  const dd rx = dd_from_double(xy[2 * j] - (bg.x0 + bx * bt));
+  const dd ry = dd_from_double(xy[2 * j + 1] - (bg.y0 + by * bt));
+  rel_s[pos] = make_float4(rx.hi, rx.lo, ry.hi, ry.lo);
+  perm[pos] = (int)j;
+}
+
+// q_s[k] = q[perm[k]] as a df64 pair
+__global__ void gather_q_dd_kernel(const double* __restrict__ q, const int* __restrict__ perm, int64_t n,
+                                   float2* q_s) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const dd v = dd_from_double(q[perm[k]]);
+  q_s[k] = make_float2(v.hi, v.lo);
+}
+
+// acc * v + c with one renormalisation
+__device__ __forceinline__ dd horner_dd(dd acc, dd v, float2 c) {
+  const float p = __fmul_rn(acc.hi, v.hi);
+  float e = __fmaf_rn(acc.hi, v.hi, -p);
+  e = __fmaf_rn(acc.hi, v.lo, e);
+  e = __fmaf_rn(acc.lo, v.hi, e);
+  float s, t;
+  two_sum(p, c.x, s, t);
+  t = __fadd_rn(t, __fadd_rn(e, c.y));
+  dd r;
+  quick_two_sum(s, t, r.hi, r.lo);
+  return r;
+}
+
+// Stencil origin of a df64 patch coordinate u (see dd_stencil of the
+// interpolation): i0 = floor(u - W/2) + 1 and v = u - i0 - (W-1)/2.
+template <int W>
+__device__ __forceinline__ bool stencil_dd(dd u, int M, int& i0, dd& v) {
+  const dd t = dd_add(u, dd{-0.5f * W, 0.f});
+  float f = floorf(t.hi);
+  if (t.hi == f && t.lo < 0.f) f -= 1.f;
+  if (!(f > -1e6f && f < 1e6f)) return false;
+  i0 = (int)f + 1;
+  v = dd_add(u, dd{-((float)i0 + 0.5f * (W - 1)), 0.f});
+  return i0 >= 0 && i0 + W <= M;
+}
+
+// Binned spread of the volume nodes of FP64 plans, in df64.  As the
+// single-precision kernel (one CTA per bin, warp-private patches, one warp
+// per point when updating cells), except that the stencil weights are
+// evaluated with lane = point first -- each lane runs the 2w df64 Horner
+// chains of its own point, x weights and q times y weights, into shared
+// memory -- and that patch cells hold df64 sums.  The CTA adds its patch to
+// the FP64 grid with FP64 atomics.
+template <int W>
+__global__ void __launch_bounds__(kSubDDThreads) spread_sub_dd_kernel(const __grid_constant__ SubDDArgs a) {
+  extern __shared__ float2 smd[];
+  constexpr int NC = W * W, NP = (NC + 31) / 32, NWARP = kSubDDThreads / 32;
+  constexpr int WS = 2 * W + 1;  // weight row stride (odd: conflict-free lane = point stores)
+  const int M = a.M, MM = M * M, nc = a.nc;
+  const int bx = blockIdx.x, by = blockIdx.y;
+  const int key = by * a.nbx + bx;
+  const int k0 = a.start[key], n_here = a.start[key + 1] - k0;
+  if (n_here == 0) return;
+  float2* coef = smd;                          // [nc][W]
+  float2* wbuf = coef + kMaxNC * W;            // [NWARP][32][WS]
+  float2* patch = wbuf + NWARP * 32 * WS;      // [NWARP][MM] (sum, correction)
+  for (int e = threadIdx.x; e < nc * W; e += blockDim.x) coef[e] = a.coef[e / W][e % W];
+  for (int e = threadIdx.x; e < NWARP * MM; e += blockDim.x) patch[e] = make_float2(0.f, 0.f);
+  const double ux = (a.org_x + bx * a.bt - a.gd.x0) * a.gd.inv_h;
+  const double uy = (a.org_y + by * a.bt - a.gd.y0) * a.gd.inv_h;
+  const int ox = (int)floor(ux - 0.5 * W), oy = (int)floor(uy - 0.5 * W);
+  const dd u0 = dd_from_double(ux - ox), v0 = dd_from_double(uy - oy);
+  const dd inv_h = dd{a.inv_h.x, a.inv_h.y};
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int cell[NP], wxo[NP], wyo[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const int i = lane + 32 * p;
+    const int r = i / W, c = i % W;
+    cell[p] = i < NC ? r * M + c : -1;
+    wxo[p] = c;
+    wyo[p] = W + (r < W ? r : 0);
+  }
+  float2* wb = wbuf + warp * 32 * WS;
+  float2* mine = patch + warp * MM;
+  __syncthreads();
+  const int n_warp = n_here > warp ? (n_here - warp + NWARP - 1) / NWARP : 0;
+  for (int j0 = 0; j0 < n_warp; j0 += 32) {
+    // weights, lane = point
+    const int jl = j0 + lane;
+    int ix = 0, iy = 0;
+    bool ok = false;
+    if (jl < n_warp) {
+      const int kk = k0 + warp + NWARP * jl;
+      const float4 r = a.rel[kk];
+      const float2 q = a.q[kk];
+      const dd u = dd_add(u0, dd_mul(dd{r.x, r.y}, inv_h));
+      const dd v = dd_add(v0, dd_mul(dd{r.z, r.w}, inv_h));
+      dd vx, vy;
+      ok = stencil_dd<W>(u, M, ix, vx) && stencil_dd<W>(v, M, iy, vy);
+      if (ok) {
+        float2* out = wb + lane * WS;
+        dd w[W];
+#pragma unroll
+        for (int t = 0; t < W; ++t) w[t] = dd{coef[(nc - 1) * W + t].x, coef[(nc - 1) * W + t].y};
+        for (int k = nc - 2; k >= 0; --k) {
+#pragma unroll
+          for (int t = 0; t < W; ++t) w[t] = horner_dd(w[t], vx, coef[k * W + t]);
+        }
+#pragma unroll
+        for (int t = 0; t < W; ++t) out[t] = make_float2(w[t].hi, w[t].lo);
+#pragma unroll
+        for (int t = 0; t < W; ++t) w[t] = dd{coef[(nc - 1) * W + t].x, coef[(nc - 1) * W + t].y};
+        for (int k = nc - 2; k >= 0; --k) {
+#pragma unroll
+          for (int t = 0; t < W; ++t) w[t] = horner_dd(w[t], vy, coef[k * W + t]);
+        }
+        const dd qd = dd{q.x, q.y};
+#pragma unroll
+        for (int t = 0; t < W; ++t) {
+          const dd qw = dd_mul(w[t], qd);
+          out[W + t] = make_float2(qw.hi, qw.lo);
+        }
+      } else {
+        atomicOr(a.status, kStatusOutOfBox);
+      }
+    }
+    __syncwarp();
+    // cells, one point at a time
+    const int cnt = min(32, n_warp - j0);
+    for (int jj = 0; jj < cnt; ++jj) {
+      if (!__shfl_sync(0xffffffffu, (int)ok, jj)) continue;
+      const int pix = __shfl_sync(0xffffffffu, ix, jj), piy = __shfl_sync(0xffffffffu, iy, jj);
+      float2* dst = mine + piy * M + pix;
+      const float2* wrow = wb + jj * WS;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        if (cell[p] < 0) continue;
+        const float2 wx = wrow[wxo[p]], qwy = wrow[wyo[p]];
+        const dd prod = dd_mul(dd{qwy.x, qwy.y}, dd{wx.x, wx.y});
+        float2 cur = dst[cell[p]];
+        float s, t;
+        two_sum(cur.x, prod.hi, s, t);
+        cur.y = __fadd_rn(cur.y, __fadd_rn(t, prod.lo));
+        cur.x = s;
+        dst[cell[p]] = cur;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  double* grid = (double*)a.grid;
+  for (int e = threadIdx.x; e < MM; e += blockDim.x) {
+    dd acc = dd{0.f, 0.f};
+#pragma unroll
+    for (int w = 0; w < NWARP; ++w) {
+      const float2 pv = patch[w * MM + e];
+      acc = dd_add(acc, dd_add(dd{pv.x, 0.f}, dd{pv.y, 0.f}));
+    }
+    if (acc.hi == 0.f) continue;
+    const int gy = oy + e / M, gx = ox + e % M;
+    if (gx < 0 || gy < 0 || gx >= a.gd.g || gy >= a.gd.g) {
+      atomicOr(a.status, kStatusOutOfBox);
+      continue;
+    }
+    atomicAdd(grid + (size_t)gy * a.gd.pitch + gx, dd_to_double(acc));
+  }
+}
+
 }  // namespace
 
 void launch_bin_sort(const double* xy, int64_t n, const BinGeom& bg, int* keys, int* counts, int* cursor,
@@ -194,6 +372,58 @@ void launch_bin_sort(const double* xy, int64_t n, const BinGeom& bg, int* keys, 
   scan_kernel<<<1, 1024, 0, s>>>(counts, nbins, starts);
   if (n > 0)
     scatter_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(xy, n, keys, starts, cursor, bg, rel_s, perm);
+}
+
+void launch_bin_sort_dd(const double* xy, int64_t n, const BinGeom& bg, int* keys, int* counts, int* cursor,
+                        int* starts, float4* rel_s, int* perm, unsigned* status, cudaStream_t s) {
+  const int nbins = bg.nbx * bg.nby + 1;  // + overflow bin
+  cudaMemsetAsync(counts, 0, nbins * sizeof(int), s);
+  cudaMemsetAsync(cursor, 0, nbins * sizeof(int), s);
+  if (n > 0)
+    bin_keys_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(xy, n, bg.x0, bg.y0, bg.inv_bt, bg.nbx, bg.nby,
+                                                                keys, counts, status);
+  scan_kernel<<<1, 1024, 0, s>>>(counts, nbins, starts);
+  if (n > 0)
+    scatter_dd_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(xy, n, keys, starts, cursor, bg, rel_s, perm);
+}
+
+void launch_gather_q_dd(const double* q, const int* perm, int64_t n, float2* q_s, cudaStream_t s) {
+  if (n > 0) gather_q_dd_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(q, perm, n, q_s);
+}
+
+size_t spread_sub_dd_smem(int M, int w) {
+  return (size_t)(kMaxNC * w + (kSubDDThreads / 32) * 32 * (2 * w + 1) + (kSubDDThreads / 32) * M * M) *
+         sizeof(float2);
+}
+
+#define LP_SUB_DD_CASES LP_CASE(4) LP_CASE(5) LP_CASE(6) LP_CASE(7) LP_CASE(8) LP_CASE(9) LP_CASE(10) \
+  LP_CASE(11) LP_CASE(12) LP_CASE(13) LP_CASE(14) LP_CASE(15) LP_CASE(16)
+
+bool spread_sub_dd_configure(int w) {
+  const int bytes = 220 * 1024;
+  switch (w) {
+#define LP_CASE(W)                                                                                     \
+  case W:                                                                                              \
+    return cudaFuncSetAttribute(spread_sub_dd_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                bytes) == cudaSuccess;
+    LP_SUB_DD_CASES
+#undef LP_CASE
+    default: return false;
+  }
+}
+
+void launch_spread_sub_dd(const SubDDArgs& a, int w, cudaStream_t s) {
+  dim3 grid(a.nbx, a.nby);
+  const size_t smem = spread_sub_dd_smem(a.M, w);
+  switch (w) {
+#define LP_CASE(W)                                                    \
+  case W:                                                             \
+    spread_sub_dd_kernel<W><<<grid, kSubDDThreads, smem, s>>>(a);     \
+    break;
+    LP_SUB_DD_CASES
+#undef LP_CASE
+    default: break;
+  }
 }
 
 void launch_gather_q(const double* q, int64_t stride, int nq, const int* perm, int64_t n, float* q_s,

@@ -10,12 +10,11 @@
 //   expansion, with eta the inward normal and kappa > 0 for convex
 //   boundaries, the delta^{3/2} term reads (2 f_eta - kappa f).
 //
-// The passes are templated on the arithmetic type of the plan.  FP64 plans
-// decide the nearest node exactly and run Newton to |dt| < 1e-14.  FP32 plans
-// (tolerance >= 1e-6) take the single-precision nearest node and foot and
-// evaluate the expansions in single precision in coordinates relative to the
-// panel's reference node; the foot offset, hence the distance and the side of
-// the boundary, is still evaluated in double precision.
+// The passes are templated on the arithmetic type of the expansions: double
+// for FP64 plans, float for FP32 plans (tolerance >= 1e-6; coordinates
+// relative to the panel's reference node).  Both take the single-precision
+// nearest node and foot search finished in double precision (panel_foot), so
+// the distance and the side of the boundary are resolved to rounding.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -77,20 +76,24 @@ struct Foot {
   double t, d2, gx, gy;
 };
 
-// Newton for the foot on panel ip from parameter t.  A single-precision phase
-// in coordinates relative to the panel's reference node runs always; FP64
-// plans (full = true) continue with the double-precision Newton to
-// |dt| < 1e-14, FP32 plans take one double-precision step.
-template <bool full>
+// Newton for the foot on panel ip from parameter t: a single-precision phase
+// in coordinates relative to the panel's reference node, then one
+// double-precision step, whose offset at the new parameter comes from the
+// second-order Taylor expansion (the step leaves ~|dt|^2 in t and ~|dt|^3
+// times the third derivative in the offset), so the distance of on-boundary
+// targets and the side of the boundary are resolved to rounding.  If the
+// single-precision phase does not settle, the double-precision Newton runs to
+// |dt| < 1e-14 (at most 20 steps) as in the closest-point rule.
 __device__ Foot panel_foot(const LocalArgs& a, int ip, double t, double x, double y) {
   const size_t off = (size_t)(2 * ip) * a.p;
   const double rx = a.geo_ref[2 * ip], ry = a.geo_ref[2 * ip + 1];
+  bool settled = false;
   {
     const float* c32[2] = {a.geo_coef32 + off, a.geo_coef32 + off + a.p};
     const float zero2[2] = {0.f, 0.f};
     const float xr = (float)(x - rx), yr = (float)(y - ry);
     float tf = (float)t;
-    for (int it = 0; it < (full ? 8 : 16); ++it) {
+    for (int it = 0; it < 16; ++it) {
       float J[2][3];
       legendre_jets<2, 2, float>(c32, zero2, a.p, tf, J);
       float gx = J[0][0] - xr, gy = J[1][0] - yr;
@@ -101,15 +104,21 @@ __device__ Foot panel_foot(const LocalArgs& a, int ip, double t, double x, doubl
       float tn = fminf(1.f, fmaxf(-1.f, tf - f / fp));
       float dt = tn - tf;
       tf = tn;
-      if (fabsf(dt) < (full ? 1e-6f : 2e-7f)) break;
+      if (fabsf(dt) < 2e-7f) {
+        settled = true;
+        break;
+      }
     }
-    if (tf == tf) t = (double)tf;  // keep the node start if the phase failed
+    if (tf == tf)
+      t = (double)tf;
+    else
+      settled = false;  // keep the node start if the phase failed
   }
   const double* c64[2] = {a.geo_coef + off, a.geo_coef + off + a.p};
   const double ref[2] = {rx, ry};
   Foot r;
   r.panel = ip;
-  if (full) {
+  if (!settled) {
     for (int it = 0; it < 20; ++it) {
       double J[2][3];
       legendre_jets<2, 2, double>(c64, ref, a.p, t, J);
@@ -128,11 +137,6 @@ __device__ Foot panel_foot(const LocalArgs& a, int ip, double t, double x, doubl
     r.gx = J0[0][0] - x;
     r.gy = J0[1][0] - y;
   } else {
-    // one double-precision Newton step from the single-precision foot
-    // (|dt| ~ 1e-7, leaving an error ~ dt^2); the offset at the new parameter
-    // from the second-order Taylor expansion (error ~ dt^3 times the third
-    // derivative), so that the distance of on-boundary targets is resolved
-    // to rounding
     double J[2][3];
     legendre_jets<2, 2, double>(c64, ref, a.p, t, J);
     const double gx = J[0][0] - x, gy = J[1][0] - y;
@@ -187,7 +191,7 @@ __device__ void local_near_one(const LocalArgs& a, int64_t i, int best) {
   {
     const int p = a.p;
     const int ip0 = best / p;
-    ft = panel_foot<sizeof(T) == 8>(a, ip0, a.tau[best - ip0 * p], x, y);
+    ft = panel_foot(a, ip0, a.tau[best - ip0 * p], x, y);
     if (fabs(ft.t) == 1.0) {
       // the foot lies beyond this panel's end: continue on the adjacent panel
       int ip = ((ip0 + (ft.t > 0.0 ? 1 : -1)) % a.n_panels + a.n_panels) % a.n_panels;
@@ -201,7 +205,7 @@ __device__ void local_near_one(const LocalArgs& a, int64_t i, int best) {
           kb = k;
         }
       }
-      Foot f = panel_foot<sizeof(T) == 8>(a, ip, a.tau[kb], x, y);
+      Foot f = panel_foot(a, ip, a.tau[kb], x, y);
       if (f.d2 < ft.d2) ft = f;
     }
     if (sqrt(ft.d2) >= a.band) far = true;
@@ -321,19 +325,15 @@ __device__ void local_near_one(const LocalArgs& a, int64_t i, int best) {
   if (a.out[2]) a.out[2][i] += (double)dlv;
 }
 
-// Pass 1: nearest boundary node among the 3x3 hash cells.  A
-// single-precision scan (node coordinates stored relative to their cell
-// origin) bounds every squared distance within err = 2e-5 h^2 (h the cell
-// side; six roundings of quantities below 3h).  FP64 plans (exact = true) then
-// compare in double precision only the nodes within 2 err of the
-// single-precision minimum, which gives exactly the double-precision nearest
-// node (ties: lowest index); FP32 plans keep the single-precision choice,
-// which only seeds the foot search (an error of err at the band edge, where
-// the near and far expansions agree, is harmless).  Targets whose nearest
-// node is farther than band + margin get the far-field volume term here; the
-// others are appended to a compact list for pass 2.  Returns the nearest node
-// for a band candidate, -1 when the far-field term was applied.
-template <bool exact>
+// Pass 1: nearest boundary node among the 3x3 hash cells, by a single-
+// precision scan over node coordinates stored relative to their cell origin
+// (every squared distance within 2e-5 h^2, h the cell side).  The node only
+// seeds the foot search; at the band edge, where a rounding-level error can
+// move a target between the near and far branches, the near and far
+// expansions agree.  Targets whose nearest node is farther than band + margin
+// get the far-field volume term here; the others are appended to a compact
+// list for pass 2.  Returns the nearest node for a band candidate, -1 when
+// the far-field term was applied.
 __device__ int local_classify_one(const LocalArgs& a, int64_t i) {
   const double x = a.txy[2 * i], y = a.txy[2 * i + 1];
   int best = -1;
@@ -355,46 +355,16 @@ __device__ int local_classify_one(const LocalArgs& a, int64_t i) {
             float2 q = a.cell_xy32[k];
             float dx = tx - q.x, dy = ty - q.y;
             const float d2 = fmaf(dx, dx, dy * dy);
-            if (exact) {
-              m32 = fminf(m32, d2);
-            } else if (d2 < m32) {
+            if (d2 < m32) {
               m32 = d2;
               k32 = k;
             }
           }
         }
       }
-      if (!exact) {
-        if (k32 >= 0) {
-          best = a.cell_node[k32];
-          bd2 = (double)m32;
-        }
-      } else {
-        const float err = 2e-5f * (float)(a.hh * a.hh);
-        const double lower = sqrt(fmax((double)m32 - err, 0.0));
-        if (m32 < 1.0e38f && lower - a.margin < a.band) {
-          const float thr = m32 + 2.0f * err;
-          for (int yy = y0c; yy <= y1c; ++yy) {
-            const float ty = (float)(y - (a.hy0 + yy * a.hh));
-            for (int xx = x0c; xx <= x1c; ++xx) {
-              const float tx = (float)(x - (a.hx0 + xx * a.hh));
-              const int c = yy * a.hnx + xx;
-              const int k1 = a.cell_start[c + 1];
-              for (int k = a.cell_start[c]; k < k1; ++k) {
-                float2 q = a.cell_xy32[k];
-                float dx = tx - q.x, dy = ty - q.y;
-                if (fmaf(dx, dx, dy * dy) > thr) continue;
-                int j = a.cell_node[k];
-                double ex = x - a.bxy[2 * j], ey = y - a.bxy[2 * j + 1];
-                double d2 = ex * ex + ey * ey;
-                if (d2 < bd2 || (d2 == bd2 && j < best)) {
-                  bd2 = d2;
-                  best = j;
-                }
-              }
-            }
-          }
-        }
+      if (k32 >= 0) {
+        best = a.cell_node[k32];
+        bd2 = (double)m32;
       }
     }
   }
@@ -405,11 +375,10 @@ __device__ int local_classify_one(const LocalArgs& a, int64_t i) {
   return best;
 }
 
-template <typename T>
 __global__ void local_classify_kernel(const __grid_constant__ LocalArgs a, int2* list, int* count) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
-  const int best = local_classify_one<sizeof(T) == 8>(a, i);
+  const int best = local_classify_one(a, i);
   if (best < 0) return;
   auto g = cg::coalesced_threads();
   int base = 0;
@@ -420,14 +389,13 @@ __global__ void local_classify_kernel(const __grid_constant__ LocalArgs a, int2*
 
 // Batched: one launch over the targets of many plans; list entries are
 // (plan, target, nearest node).
-template <typename T>
 __global__ void local_classify_batch_kernel(const LocalArgs* __restrict__ args, const int2* __restrict__ work,
                                             int4* list, int* count) {
   const int2 wk = work[blockIdx.x];
   const LocalArgs& a = args[wk.x];
   int64_t i = (int64_t)wk.y + threadIdx.x;
   if (i >= a.n) return;
-  const int best = local_classify_one<sizeof(T) == 8>(a, i);
+  const int best = local_classify_one(a, i);
   if (best < 0) return;
   auto g = cg::coalesced_threads();
   int base = 0;
@@ -460,7 +428,7 @@ void local_two_pass(const LocalArgs& a, int64_t nt, int2* list, int* count, cuda
   const int threads = 128;
   const unsigned blocks = (unsigned)((nt + threads - 1) / threads);
   cudaMemsetAsync(count, 0, sizeof(int), s);
-  local_classify_kernel<T><<<blocks, threads, 0, s>>>(a, list, count);
+  local_classify_kernel<<<blocks, threads, 0, s>>>(a, list, count);
   const unsigned nblk = std::min<unsigned>(blocks, 152u * 16u);
   local_near_kernel<T><<<nblk, threads, 0, s>>>(a, list, count);
 }
@@ -533,13 +501,11 @@ void launch_local_batch(int precision, const LocalArgs* d_args, const int2* d_wo
   if (nwork <= 0) return;
   cudaMemsetAsync(d_count, 0, sizeof(int), s);
   const unsigned nblk = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_total + 127) / 128, 152 * 16));
-  if (precision == LP_FP64) {
-    local_classify_batch_kernel<double><<<nwork, kBatchThreads, 0, s>>>(d_args, d_work, d_list, d_count);
+  local_classify_batch_kernel<<<nwork, kBatchThreads, 0, s>>>(d_args, d_work, d_list, d_count);
+  if (precision == LP_FP64)
     local_near_batch_kernel<double><<<nblk, 128, 0, s>>>(d_args, d_list, d_count);
-  } else {
-    local_classify_batch_kernel<float><<<nwork, kBatchThreads, 0, s>>>(d_args, d_work, d_list, d_count);
+  else
     local_near_batch_kernel<float><<<nblk, 128, 0, s>>>(d_args, d_list, d_count);
-  }
 }
 
 }  // namespace lpg

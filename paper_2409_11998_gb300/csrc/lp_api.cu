@@ -147,7 +147,7 @@ void destroy_plan(Plan& P) {
                   P.d_sigma_ref, P.d_mu, P.d_mu_coef, P.d_mu_ref, P.d_bq, P.d_qsum, P.d_stage,
                   P.d_out, P.d_status, P.d_near, P.d_near_count, P.d_cell_xy32,
                   P.d_geo_coef32, P.d_keys, P.d_counts, P.d_cursor, P.d_vrel_s, P.d_vperm, P.d_vq_s,
-                  P.d_vstart, P.d_sigma_coef32, P.d_mu_coef32};
+                  P.d_vstart, P.d_sigma_coef32, P.d_mu_coef32, P.d_vrel_dd, P.d_vq_dd};
   for (void* b : bufs) dfree(b);
   if (P.h_status) cudaFreeHost(P.h_status);
   for (auto& e : P.ev)
@@ -226,29 +226,35 @@ lp_status noalloc_scratch(void** out) {
   return LP_OK;
 }
 
-// Bins of the binned volume spread (FP32 plans): squares of kTile
-// near-history cells.  Plans whose kernel fit needs more coefficients than
+// Bins of the binned volume spread: squares of bin_cells near-history cells
+// (32 for FP32 plans; 24 for FP64 plans, whose df64 patches take twice the
+// shared memory).  FP32 plans whose kernel fit needs more coefficients than
 // the binned kernel holds keep the point-parallel spread.
 lp_status setup_bins(Plan& P) {
   const GridLevel& N = P.lv[0];
   const int w = P.ker.w;
-  if (w < 4 || w > 10 || P.es32.nc > sub_ncw(w)) return LP_OK;
+  const bool f64 = P.precision == LP_FP64;
+  if (w < 4 || (!f64 && (w > 10 || P.es32.nc > sub_ncw(w)))) return LP_OK;
+  P.bin_cells = f64 ? 24 : kTile;
   P.bins.x0 = N.x0;
   P.bins.y0 = N.y0;
-  P.bins.inv_bt = 1.0 / (kTile * N.h);
-  P.bins.nbx = P.bins.nby = (N.g + kTile - 1) / kTile;
+  P.bins.inv_bt = 1.0 / (P.bin_cells * N.h);
+  P.bins.nbx = P.bins.nby = (N.g + P.bin_cells - 1) / P.bin_cells;
   // Patch side per level: the bin, the stencil halo and a cell of rounding
   // slack; among the next 16 sizes, the one whose row pitch gives the fewest
-  // shared-memory wavefronts for the w^2 stencil cells taken 32 at a time.
+  // shared-memory wavefronts for the w^2 stencil cells taken 32 at a time
+  // (4-byte cells: 32 banks per warp; 8-byte cells: 16 per half warp).
+  const int banks = f64 ? 16 : 32, group = f64 ? 16 : 32;
   for (int l = 0; l < 2; ++l) {
-    const double cells = kTile * N.h / P.lv[l].h;
+    const double cells = P.bin_cells * N.h / P.lv[l].h;
     const int m0 = (int)std::ceil(cells) + w + 3;
     int best = m0, best_wf = 1 << 30;
     for (int m = m0; m < m0 + 16; ++m) {
       int wf = 0;
-      for (int p0 = 0; p0 < w * w; p0 += 32) {
+      for (int p0 = 0; p0 < w * w; p0 += group) {
         int hits[32] = {0}, mx = 0;
-        for (int i = p0; i < std::min(p0 + 32, w * w); ++i) mx = std::max(mx, ++hits[((i / w) * m + i % w) % 32]);
+        for (int i = p0; i < std::min(p0 + group, w * w); ++i)
+          mx = std::max(mx, ++hits[((i / w) * m + i % w) % banks]);
         wf += mx;
       }
       if (wf < best_wf) {
@@ -257,10 +263,11 @@ lp_status setup_bins(Plan& P) {
       }
     }
     P.sub_M[l] = best;
-    const size_t smem = (size_t)(((sub_ncw(w) * w + 3) & ~3) + (kSubThreads / 32) * best * best) * sizeof(float);
+    const size_t smem = f64 ? spread_sub_dd_smem(best, w)
+                            : (size_t)(((sub_ncw(w) * w + 3) & ~3) + (kSubThreads / 32) * best * best) * sizeof(float);
     if (smem > 200 * 1024) return LP_OK;
   }
-  if (!spread_sub_configure(w)) return LP_ERR_CUDA;
+  if (!(f64 ? spread_sub_dd_configure(w) : spread_sub_configure(w))) return LP_ERR_CUDA;
   const size_t nbins = (size_t)P.bins.nbx * P.bins.nby + 1;
   if (!dalloc(P, (void**)&P.d_counts, nbins * sizeof(int)) ||
       !dalloc(P, (void**)&P.d_cursor, nbins * sizeof(int)) ||
@@ -269,6 +276,36 @@ lp_status setup_bins(Plan& P) {
   cudaMemset(P.d_vstart, 0, (nbins + 1) * sizeof(int));
   P.binned = true;
   return LP_OK;
+}
+
+// FP64 plans: df64 spread of the volume channel on one level.
+void spread_binned_dd(const Plan& P, int l, cudaStream_t s) {
+  const GridLevel& G = P.lv[l];
+  SubDDArgs a{};
+  a.gd = grid_dev(G);
+  a.rel = P.d_vrel_dd;
+  a.q = P.d_vq_dd;
+  a.start = P.d_vstart;
+  a.grid = G.chan[0];
+  a.org_x = P.bins.x0;
+  a.org_y = P.bins.y0;
+  a.bt = 1.0 / P.bins.inv_bt;
+  const double ih = 1.0 / G.h;
+  const float ihh = (float)ih;
+  a.inv_h = make_float2(ihh, (float)(ih - (double)ihh));
+  a.nbx = P.bins.nbx;
+  a.nby = P.bins.nby;
+  a.M = P.sub_M[l];
+  a.nc = P.es.nc;
+  a.status = P.d_status;
+  for (int k = 0; k < P.es.nc; ++k)
+    for (int t = 0; t < P.es.w; ++t) {
+      const double c = P.es.c[k][t];
+      const float ch = (float)c;
+      a.coef[k][t] = make_float2(ch, (float)(c - (double)ch));
+    }
+  ++P.launches;
+  launch_spread_sub_dd(a, P.ker.w, s);
 }
 
 // FP32 spread of the volume channel on one level from the sorted nodes.
@@ -524,7 +561,7 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
     if (!finite) st = LP_ERR_ARG;
     if (st == LP_OK) st = build_boundary(P, hxy.data(), hw.data(), hn.data());
   }
-  if (st == LP_OK && P.precision == LP_FP32) st = setup_bins(P);
+  if (st == LP_OK) st = setup_bins(P);
   if (st == LP_OK && P.precision == LP_FP64) st = setup_fft_dd(P);
   if (st == LP_OK) st = status_from_cuda();
   if (st != LP_OK) {
@@ -562,7 +599,8 @@ lp_status lp_volume(lp_plan_t h, int64_t n, const double* xy, const double* w, c
   }
   if (P.binned && n > 0) {
     // sort the volume nodes into the spread's bins
-    if ((size_t)n > P.key_cap || !P.d_vrel_s || (size_t)n > P.vsort_cap) {
+    const bool f64 = P.precision == LP_FP64;
+    if ((size_t)n > P.key_cap || (size_t)n > P.vsort_cap) {
       cudaStreamSynchronize(P.stream);
       if ((size_t)n > P.key_cap) {
         dfree(P.d_keys);
@@ -571,21 +609,31 @@ lp_status lp_volume(lp_plan_t h, int64_t n, const double* xy, const double* w, c
         P.key_cap = n;
       }
       if ((size_t)n > P.vsort_cap) {
-        dfree(P.d_vrel_s);
-        dfree(P.d_vperm);
-        dfree(P.d_vq_s);
-        P.d_vrel_s = nullptr;
-        P.d_vperm = nullptr;
-        P.d_vq_s = nullptr;
-        if (!dalloc(P, (void**)&P.d_vrel_s, n * sizeof(float2)) ||
-            !dalloc(P, (void**)&P.d_vperm, n * sizeof(int)) || !dalloc(P, (void**)&P.d_vq_s, n * sizeof(float)))
-          return LP_ERR_NOMEM;
+        void** bufs[5] = {(void**)&P.d_vrel_s, (void**)&P.d_vperm, (void**)&P.d_vq_s, (void**)&P.d_vrel_dd,
+                          (void**)&P.d_vq_dd};
+        for (void** b : bufs) {
+          dfree(*b);
+          *b = nullptr;
+        }
+        P.vsort_cap = 0;
+        const bool ok = dalloc(P, (void**)&P.d_vperm, n * sizeof(int)) &&
+                        (f64 ? dalloc(P, (void**)&P.d_vrel_dd, n * sizeof(float4)) &&
+                                   dalloc(P, (void**)&P.d_vq_dd, n * sizeof(float2))
+                             : dalloc(P, (void**)&P.d_vrel_s, n * sizeof(float2)) &&
+                                   dalloc(P, (void**)&P.d_vq_s, n * sizeof(float)));
+        if (!ok) return LP_ERR_NOMEM;
         P.vsort_cap = n;
       }
     }
-    launch_bin_sort(P.d_vxy, n, P.bins, P.d_keys, P.d_counts, P.d_cursor, P.d_vstart, P.d_vrel_s, P.d_vperm,
-                    P.d_status, P.stream);
-    launch_gather_q(P.d_vq, n, 1, P.d_vperm, n, P.d_vq_s, P.stream);
+    if (f64) {
+      launch_bin_sort_dd(P.d_vxy, n, P.bins, P.d_keys, P.d_counts, P.d_cursor, P.d_vstart, P.d_vrel_dd,
+                         P.d_vperm, P.d_status, P.stream);
+      launch_gather_q_dd(P.d_vq, P.d_vperm, n, P.d_vq_dd, P.stream);
+    } else {
+      launch_bin_sort(P.d_vxy, n, P.bins, P.d_keys, P.d_counts, P.d_cursor, P.d_vstart, P.d_vrel_s, P.d_vperm,
+                      P.d_status, P.stream);
+      launch_gather_q(P.d_vq, n, 1, P.d_vperm, n, P.d_vq_s, P.stream);
+    }
     P.launches += 4;
   }
   launch_sum(P, P.d_vq, n, P.d_qsum, P.stream);
@@ -604,11 +652,10 @@ static lp_status bind_layer(lp_plan_t h, const double* dens, int kind) {
   cudaMemcpyAsync(dst, d, P.nb * sizeof(double), cudaMemcpyDeviceToDevice, P.stream);
   launch_panel_coef(P, dst, 1, 1, kind == 0 ? P.d_sigma_coef : P.d_mu_coef,
                     kind == 0 ? P.d_sigma_ref : P.d_mu_ref, P.stream);
-  if (P.precision == LP_FP32) {
-    launch_to_float(kind == 0 ? P.d_sigma_coef : P.d_mu_coef, kind == 0 ? P.d_sigma_coef32 : P.d_mu_coef32,
-                    P.n_panels * P.p, P.stream);
-    ++P.launches;
-  }
+  // single-precision copy for the local expansions (both precisions)
+  launch_to_float(kind == 0 ? P.d_sigma_coef : P.d_mu_coef, kind == 0 ? P.d_sigma_coef32 : P.d_mu_coef32,
+                  P.n_panels * P.p, P.stream);
+  ++P.launches;
   launch_strengths(P, kind, P.stream);
   if (kind == 0) {
     launch_sum(P, P.d_bq, P.nb, P.d_qsum + 1, P.stream);
@@ -684,7 +731,10 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
     GridLevel& G = P.lv[l];
     if (wv && P.nv > 0) {
       if (P.binned) {
-        spread_binned(P, l, s);
+        if (P.precision == LP_FP64)
+          spread_binned_dd(P, l, s);
+        else
+          spread_binned(P, l, s);
       } else {
         const double* q[1] = {P.d_vq};
         void* g[1] = {G.chan[0]};

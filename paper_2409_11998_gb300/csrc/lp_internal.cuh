@@ -18,6 +18,7 @@ constexpr int kBatchThreads = 128;  // threads per block (and items per work ent
 constexpr int kZeroChunk = 4096;    // 16-byte words cleared per work entry of the batched zeroing
 constexpr int kTile = 32;           // bin side (near-history cells) of the binned spread
 constexpr int kSubThreads = 256;    // threads per CTA of the binned spread
+constexpr int kSubDDThreads = 128;  // threads per CTA of the binned df64 spread (FP64 plans)
 // Coefficient count of the binned spread's weight polynomials for width w
 // (the plan's fit is zero-padded; plans whose fit needs more use the
 // point-parallel spread).
@@ -157,6 +158,20 @@ struct SubArgs {
   EsPoly<float> es;
 };
 
+// One level of the binned df64 spread of the volume nodes (FP64 plans).
+struct SubDDArgs {
+  GridDev gd;
+  const float4* rel;  // offsets from the bin corner, df64 (x.hi, x.lo, y.hi, y.lo), in bin order
+  const float2* q;    // strengths, df64, same order
+  const int* start;   // [nbins + 2] bin starts
+  void* grid;         // FP64 grid
+  double org_x, org_y, bt;
+  float2 inv_h;       // 1 / h, df64
+  int nbx, nby, M, nc;
+  unsigned* status;
+  float2 coef[kMaxNC][kMaxW];  // weight polynomials, df64
+};
+
 // df64 FFT chain (k_fft.cu)
 struct FftRowArgs {
   FftShape half;
@@ -277,7 +292,10 @@ struct Plan {
   int* d_vperm = nullptr;
   float* d_vq_s = nullptr;
   int* d_vstart = nullptr;         // [nbins + 2]
-  bool binned = false;             // volume spread through the bins (FP32 plans)
+  bool binned = false;             // volume spread through the bins
+  int bin_cells = kTile;           // bin side in near-history cells (FP32 32, FP64 24)
+  float4* d_vrel_dd = nullptr;     // FP64 plans: offsets from the bin corner, df64
+  float2* d_vq_dd = nullptr;       // FP64 plans: strengths in bin order, df64
   size_t key_cap = 0;
   size_t vsort_cap = 0;
 
@@ -356,6 +374,12 @@ void launch_bin_sort(const double* xy, int64_t n, const BinGeom& bg, int* keys, 
 void launch_gather_q(const double* q, int64_t stride, int nq, const int* perm, int64_t n, float* q_s,
                      cudaStream_t s);
 bool spread_sub_configure(int w);
+bool spread_sub_dd_configure(int w);
+size_t spread_sub_dd_smem(int M, int w);
+void launch_spread_sub_dd(const SubDDArgs& a, int w, cudaStream_t s);
+void launch_bin_sort_dd(const double* xy, int64_t n, const BinGeom& bg, int* keys, int* counts, int* cursor,
+                        int* starts, float4* rel_s, int* perm, unsigned* status, cudaStream_t s);
+void launch_gather_q_dd(const double* q, const int* perm, int64_t n, float2* q_s, cudaStream_t s);
 size_t spread_sub_smem(const SubArgs& a, int w);
 void launch_spread_sub(const SubArgs& a, int w, cudaStream_t s);
 FftShape fft_shape(int n);
