@@ -158,11 +158,15 @@ __global__ void __launch_bounds__(kSubThreads) spread_sub_kernel(const __grid_co
 #pragma unroll
       for (int j = NCW - 2; j >= 0; --j) wgt = fmaf(wgt, z, cf[j]);
       float* dst = my + iy * M + ix;
+      float cur[NP];
+#pragma unroll
+      for (int p = 0; p < NP; ++p)
+        if (cell[p] >= 0) cur[p] = dst[cell[p]];
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
         const float wx = __shfl_sync(0xffffffffu, wgt, src_x[p]);
         const float wy = __shfl_sync(0xffffffffu, wgt, src_y[p]);
-        if (cell[p] >= 0) dst[cell[p]] = fmaf(qv * wy, wx, dst[cell[p]]);
+        if (cell[p] >= 0) dst[cell[p]] = fmaf(qv * wy, wx, cur[p]);
       }
       __syncwarp();
     }
@@ -325,18 +329,25 @@ __global__ void __launch_bounds__(kSubDDThreads) spread_sub_dd_kernel(const __gr
       const int pix = __shfl_sync(0xffffffffu, ix, jj), piy = __shfl_sync(0xffffffffu, iy, jj);
       float2* dst = mine + piy * M + pix;
       const float2* wrow = wb + jj * WS;
+      // the lane's cells are distinct: load them all, update, store them all
+      // (keeps the shared-memory loads from waiting on earlier stores)
+      float2 cur[NP];
+#pragma unroll
+      for (int p = 0; p < NP; ++p)
+        if (cell[p] >= 0) cur[p] = dst[cell[p]];
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
         if (cell[p] < 0) continue;
         const float2 wx = wrow[wxo[p]], qwy = wrow[wyo[p]];
         const dd prod = dd_mul(dd{qwy.x, qwy.y}, dd{wx.x, wx.y});
-        float2 cur = dst[cell[p]];
         float s, t;
-        two_sum(cur.x, prod.hi, s, t);
-        cur.y = __fadd_rn(cur.y, __fadd_rn(t, prod.lo));
-        cur.x = s;
-        dst[cell[p]] = cur;
+        two_sum(cur[p].x, prod.hi, s, t);
+        cur[p].y = __fadd_rn(cur[p].y, __fadd_rn(t, prod.lo));
+        cur[p].x = s;
       }
+#pragma unroll
+      for (int p = 0; p < NP; ++p)
+        if (cell[p] >= 0) dst[cell[p]] = cur[p];
       __syncwarp();
     }
   }

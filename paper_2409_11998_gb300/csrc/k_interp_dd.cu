@@ -78,19 +78,21 @@ __global__ void __launch_bounds__(128) interp_dd_kernel(const __grid_constant__ 
     dd wx[W], wy[W];
     dd_weights<W>(a, vx, wx);
     dd_weights<W>(a, vy, wy);
-#pragma unroll
+    // rows and channels stay rolled (wy spills to L1-resident local memory):
+    // unrolling all w^2 C products overflows the instruction cache
+#pragma unroll 1
     for (int c = 0; c < 3; ++c) {
       if (!a.out[c]) continue;
       const float2* base = (const float2*)L.grid[c] + (size_t)iy * L.pitch + ix;
-#pragma unroll
+#pragma unroll 1
       for (int b = 0; b < W; ++b) {
         const float2* row = base + (size_t)b * L.pitch;
+        float2 gv[W];
+#pragma unroll
+        for (int t = 0; t < W; ++t) gv[t] = __ldg(row + t);
         dd_acc r = {0.f, 0.f};
 #pragma unroll
-        for (int t = 0; t < W; ++t) {
-          const float2 gv = __ldg(row + t);
-          acc_fma(r, wx[t], dd{gv.x, gv.y});
-        }
+        for (int t = 0; t < W; ++t) acc_fma(r, wx[t], dd{gv[t].x, gv[t].y});
         acc_fma(acc[c], wy[b], acc_value(r));
       }
     }

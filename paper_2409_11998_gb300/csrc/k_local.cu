@@ -77,17 +77,16 @@ struct Foot {
 };
 
 // Newton for the foot on panel ip from parameter t: a single-precision phase
-// in coordinates relative to the panel's reference node, then one
-// double-precision step, whose offset at the new parameter comes from the
-// second-order Taylor expansion (the step leaves ~|dt|^2 in t and ~|dt|^3
-// times the third derivative in the offset), so the distance of on-boundary
-// targets and the side of the boundary are resolved to rounding.  If the
-// single-precision phase does not settle, the double-precision Newton runs to
-// |dt| < 1e-14 (at most 20 steps) as in the closest-point rule.
+// in coordinates relative to the panel's reference node (it ends within
+// single-precision noise of the root, or after 16 steps), then double-
+// precision steps until one moves t by less than 1e-6 -- Newton's quadratic
+// convergence leaves ~1e-12 in t after it -- with the foot offset at the last
+// parameter from the second-order Taylor expansion of that step (error ~|dt|^3
+// times the third derivative), so that the distance of on-boundary targets
+// and the side of the boundary are resolved to rounding.
 __device__ Foot panel_foot(const LocalArgs& a, int ip, double t, double x, double y) {
   const size_t off = (size_t)(2 * ip) * a.p;
   const double rx = a.geo_ref[2 * ip], ry = a.geo_ref[2 * ip + 1];
-  bool settled = false;
   {
     const float* c32[2] = {a.geo_coef32 + off, a.geo_coef32 + off + a.p};
     const float zero2[2] = {0.f, 0.f};
@@ -104,39 +103,15 @@ __device__ Foot panel_foot(const LocalArgs& a, int ip, double t, double x, doubl
       float tn = fminf(1.f, fmaxf(-1.f, tf - f / fp));
       float dt = tn - tf;
       tf = tn;
-      if (fabsf(dt) < 2e-7f) {
-        settled = true;
-        break;
-      }
+      if (fabsf(dt) < 2e-7f) break;
     }
-    if (tf == tf)
-      t = (double)tf;
-    else
-      settled = false;  // keep the node start if the phase failed
+    if (tf == tf) t = (double)tf;  // keep the node start if the phase failed
   }
   const double* c64[2] = {a.geo_coef + off, a.geo_coef + off + a.p};
   const double ref[2] = {rx, ry};
   Foot r;
   r.panel = ip;
-  if (!settled) {
-    for (int it = 0; it < 20; ++it) {
-      double J[2][3];
-      legendre_jets<2, 2, double>(c64, ref, a.p, t, J);
-      double gx = J[0][0] - x, gy = J[1][0] - y;
-      double f = gx * J[0][1] + gy * J[1][1];
-      double s2 = J[0][1] * J[0][1] + J[1][1] * J[1][1];
-      double fp = s2 + gx * J[0][2] + gy * J[1][2];
-      if (fp < 0.1 * s2) fp = s2;
-      double tn = fmin(1.0, fmax(-1.0, t - f / fp));
-      double dt = tn - t;
-      t = tn;
-      if (fabs(dt) < 1e-14) break;
-    }
-    double J0[2][1];
-    legendre_jets<0, 2, double>(c64, ref, a.p, t, J0);
-    r.gx = J0[0][0] - x;
-    r.gy = J0[1][0] - y;
-  } else {
+  for (int it = 0; it < 20; ++it) {
     double J[2][3];
     legendre_jets<2, 2, double>(c64, ref, a.p, t, J);
     const double gx = J[0][0] - x, gy = J[1][0] - y;
@@ -149,6 +124,7 @@ __device__ Foot panel_foot(const LocalArgs& a, int ip, double t, double x, doubl
     t = tn;
     r.gx = gx + dt * (J[0][1] + 0.5 * dt * J[0][2]);
     r.gy = gy + dt * (J[1][1] + 0.5 * dt * J[1][2]);
+    if (fabs(dt) < 1e-6) break;
   }
   r.t = t;
   r.d2 = r.gx * r.gx + r.gy * r.gy;
