@@ -145,8 +145,9 @@ def peaks():
 
 
 def kernel_traffic(name):
-    """DRAM bytes per launch of a kernel from a committed ncu summary, valid
-    only while the kernel sources are unchanged (sha of csrc/*.cu,*.cuh)."""
+    """DRAM bytes (read + write) of a kernel per bench step, summed over its
+    launches in the step, from a committed ncu summary; valid only while the
+    kernel sources are unchanged (sha of csrc/*.cu,*.cuh)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -154,7 +155,7 @@ def kernel_traffic(name):
     ent = d.get(name)
     if not ent or ent.get("source_sha") != source_sha():
         return None
-    return ent.get("bytes_per_launch")
+    return ent.get("bytes_per_step")
 
 
 def source_sha():
@@ -227,11 +228,15 @@ def run_lp(args, rank, world, local_rank):
     info = lp.lp_plan_info(plan)
     st = {k: statistics.mean(s[k] for s in stages) for k in stages[0]}
 
-    roof = roofline(info, st, nv, nb, nt, precision="fp64")
+    roof = roofline(info, st, nv, nb, nt, precision="fp64", n_out=sum(o is not None for o in outs))
 
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "df64+f64" if (info.get("own_fft") and info.get("precision") == 0) else "f64",
+           "dtype_detail": ("volume spread, transforms, multiplier and interpolation in double-float "
+                            "(FP32 pairs, ~48-bit); boundary spread, local expansions and outputs in FP64")
+           if (info.get("own_fft") and info.get("precision") == 0) else "FP64 throughout",
            "data": "synthetic (seeded generators; no dataset)",
            "config": {**describe(prob), "parallelism": "replicas" if world > 1 else "single",
                       "l2": "flushed by a 512 MiB write between timed steps, outside the step events",
@@ -256,52 +261,84 @@ def run_lp(args, rank, world, local_rank):
     return res
 
 
-def fp64_peak_tflops():
-    """FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA per clock
-    per SM (the GB300 FP64 rate, 1.25 TFLOP/s nominal) x 2 FLOP x max SM clock."""
+def sm_max_mhz():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     mhz = 2070.0
     if os.path.exists(p):
         mhz = float(json.load(open(p)).get("sm_max_mhz", mhz))
-    return 152 * 2 * 2 * mhz * 1e6 / 1e12
+    return mhz
 
 
-def roofline(info, st, nv, nb, nt, precision):
-    """Roofline of this library's dominant kernel (spread or interpolation).
-    Algorithmic bytes: sources read once and grids written once (spread);
-    grids read once and targets read/written once (interpolation).
-    Algorithmic FLOPs (FP64 path): per point and level, the two stencil
-    polynomials (2 W (nc-1) FMA) plus W(W+1) FMA per output channel
-    (interpolation) or W(W+1) multiplies per input channel (spread)."""
+def fp64_peak_tflops():
+    """FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA per clock
+    per SM (the GB300 FP64 rate, 1.25 TFLOP/s nominal) x 2 FLOP x max SM clock."""
+    return 152 * 2 * 2 * sm_max_mhz() * 1e6 / 1e12
+
+
+# FP32 instructions of one double-float multiply-add as the kernels implement
+# it: two-product (multiply + 3 fused multiply-adds), two-sum (6), two adds and
+# the renormalising fast two-sum (3).
+DF64_FMA_INSTR = 15
+
+
+def df64_peak_t():
+    """Double-float multiply-adds per second the FP32 units can issue: 152 SMs
+    x 128 FP32 lanes x max SM clock / DF64_FMA_INSTR (T/s)."""
+    return 152 * 128 * sm_max_mhz() * 1e6 / DF64_FMA_INSTR / 1e12
+
+
+def roofline(info, st, nv, nb, nt, precision, n_out=3):
+    """Roofline of this library's dominant kernel.
+
+    FP64 plans with the double-float chain: the volume spread
+    (spread_sub_dd_kernel, both levels) or the interpolation
+    (interp_dd_kernel), whichever takes longer, bound by FP32 issue.  Work per
+    point and level, in double-float multiply-adds: 2 w (nc - 1) for the two
+    weight polynomials plus w (w + 1) per channel (w q*wy products and w^2
+    cell updates for the spread; w^2 products and w row combinations per
+    output for the interpolation).
+
+    FP32 plans: the binned volume spread (spread_sub_kernel, both levels)
+    against HBM bandwidth, with algorithmic bytes: positions (2b) and
+    strengths (b) of every volume node read once, the V grids of both levels
+    written once (b per cell)."""
     b = 8 if precision == "fp64" else 4
-    g2 = info["g_nh"] ** 2 + info["g_fh"] ** 2
     W, nc = int(info["w"]), int(info["es_nc"])
-    spread_bytes = (nv + nb) * 16 + (nv + 3 * nb) * 8 + g2 * b * 4
-    interp_bytes = g2 * b * 3 + nt * (16 + 8 * 3)
-    spread_flops = 2 * (2 * W * (nc - 1) * 2 * (nv + nb) + W * (W + 1) * 2 * (nv + 3 * nb))
-    interp_flops = 2 * 2 * nt * (2 * W * (nc - 1) + 3 * W * (W + 1))
+    g2 = info["g_nh"] ** 2 + info["g_fh"] ** 2
     hbm, hbm_kind = peaks()
-    cand = {"spread": (st["spread"], spread_bytes, spread_flops, "spread_atomic_kernel"),
-            "interp": (st["interp"], interp_bytes, interp_flops, "interp_kernel")}
-    dom = max(cand, key=lambda k: cand[k][0])
-    ms, byts, flops, kname = cand[dom]
-    gbs = byts / (ms / 1e3) / 1e9
-    hbm_part = {"achieved_gbs": round(gbs, 2), "peak_gbs": hbm, "frac": round(gbs / hbm, 5),
-                "algorithmic_bytes_per_launch": int(byts),
-                "peak_source": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+    vol_ms = st.get("spread_volume", st["spread"])
+    if precision == "fp64" and (info.get("own_fft") and info.get("precision") == 0):
+        cand = {"spread": (vol_ms, nv * 2 * (2 * W * (nc - 1) + W * (W + 1)),
+                           "spread_sub_dd_kernel" if info.get("binned") else "spread_atomic_kernel"),
+                "interp": (st["interp"], nt * 2 * (2 * W * (nc - 1) + n_out * W * (W + 1)), "interp_dd_kernel")}
+        dom = max(cand, key=lambda k: cand[k][0])
+        ms, ops, kname = cand[dom]
+        ach = ops / (ms / 1e3) / 1e12
+        peak = df64_peak_t()
+        return {"kernel": kname, "bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 4),
+                "unit": "T df64-FMA/s (FP32 units)", "frac": round(ach / peak, 4),
+                "traffic": kernel_traffic(kname), "traffic_unit": "DRAM bytes per step (both launches)",
+                "algorithmic_df64_fma_per_step": int(ops), "launch_ms": round(ms, 4), "stage": dom,
+                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x sm_max_mhz / {DF64_FMA_INSTR} "
+                               "FP32 instructions per df64 multiply-add"}
     if precision == "fp64":
+        flops = 2 * (2 * W * (nc - 1) * 2 * (nv + nb) + W * (W + 1) * 2 * (nv + 3 * nb))
+        ms = st["spread"]
         tf = flops / (ms / 1e3) / 1e12
         peak = fp64_peak_tflops()
-        return {"kernel": kname, "bound": "alu", "achieved": round(tf, 4), "peak": round(peak, 4),
-                "unit": "TFLOP/s (FP64)", "frac": round(tf / peak, 4),
-                "traffic": kernel_traffic(kname), "algorithmic_flops_per_launch": int(flops),
-                "launch_ms": round(ms, 4), "stage": dom,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x sm_max_mhz",
-                "hbm": hbm_part}
+        return {"kernel": "spread_atomic_kernel", "bound": "alu", "achieved": round(tf, 4),
+                "peak": round(peak, 4), "unit": "TFLOP/s (FP64)", "frac": round(tf / peak, 4),
+                "traffic": kernel_traffic("spread_atomic_kernel"), "algorithmic_flops_per_step": int(flops),
+                "launch_ms": round(ms, 4), "stage": "spread",
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x sm_max_mhz"}
+    kname = "spread_sub_kernel" if info.get("binned") else "spread_atomic_kernel"
+    byts = nv * 3 * b + g2 * b
+    gbs = byts / (vol_ms / 1e3) / 1e9
     return {"kernel": kname, "bound": "hbm", "achieved": round(gbs, 2), "peak": hbm, "unit": "GB/s",
             "frac": round(gbs / hbm, 5), "traffic": kernel_traffic(kname),
-            "algorithmic_bytes_per_launch": int(byts), "launch_ms": round(ms, 4), "stage": dom,
-            "peak_source": hbm_part["peak_source"]}
+            "traffic_unit": "DRAM bytes per step (both launches)",
+            "algorithmic_bytes_per_step": int(byts), "launch_ms": round(vol_ms, 4), "stage": "spread_volume",
+            "peak_source": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)"}
 
 
 def layer_densities(prob, conv):
@@ -409,7 +446,8 @@ def run_fp32(args, prob, dev, stream, points):
     st = lp.lp_stage_times(plan)
     par = parity_sample(prob, outs)
     info = lp.lp_plan_info(plan)
-    roof = roofline(info, st, nv, len(prob["bnd"]["w"]), nt, precision="fp32")
+    roof = roofline(info, st, nv, len(prob["bnd"]["w"]), nt, precision="fp32",
+                    n_out=sum(o is not None for o in outs))
     ev.close()
     return {"value": points / (statistics.mean(ms) / 1e3), "unit": UNIT, "dtype": "f32 (FP64 zero mode)",
             "tol": 1e-5, "ms_per_step": statistics.mean(ms),

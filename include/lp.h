@@ -67,10 +67,14 @@ typedef enum {
 enum { LP_FP64 = 0, LP_FP32 = 1 };
 
 typedef struct {
-  int precision;        /* LP_FP64: all smooth-part arithmetic in double.
-                           LP_FP32: spread, FFT and interpolation in float; the
-                           multiplier table is built in double and the zero-mode
-                           (log-constant) term is summed and added in double. */
+  int precision;        /* LP_FP64: tolerances down to ~1e-12.  The volume spread,
+                           FFTs, multiplier and interpolation run in double-float
+                           arithmetic (pairs of floats, ~48 bits); the boundary
+                           spread, the local expansions and all outputs in double.
+                           LP_FP32: spread, FFT, interpolation and local
+                           expansions in float; the multiplier table is built in
+                           double and the zero-mode (log-constant) term is summed
+                           and added in double. */
   int order;            /* asymptotic order p in {3,4,5}: local terms through
                            delta^{(p-1)/2} are kept (error O(delta^{p/2})); 0 -> 5 */
   double box_lo[2];     /* box containing every source and target; the plan adds */
@@ -176,17 +180,24 @@ lp_status lp_destroy(lp_plan_t plan);
 const char* lp_status_string(lp_status status);
 
 /* Plan parameters, for diagnostics and benchmarks:
- * out[0..19] = {delta_1, delta_2, kernel width w, beta, g_NH, K_NH, P_NH, g_FH, K_FH,
+ * out[0..22] = {delta_1, delta_2, kernel width w, beta, g_NH, K_NH, P_NH, g_FH, K_FH,
  *               P_FH, L_FH, band 12 sqrt(delta_1), node-gap margin, device bytes,
  *               precision, order, kernels launched by this plan so far,
  *               max error of the kernel's polynomial form, its coefficient count,
- *               realised upsampling min g/(2K+1)}. */
+ *               realised upsampling min g/(2K+1), 1 if the transforms run in
+ *               the library's own FFT kernels (for FP64 plans in double-float
+ *               arithmetic, with the double-float interpolation), 0 for cuFFT,
+ *               1 if volume sources are spread through bins, bin side in
+ *               near-history cells}.  out must hold 23 doubles. */
 lp_status lp_plan_info(lp_plan_t plan, double* out);
 
 /* Per-stage device times of the last lp_execute in milliseconds (CUDA events
- * on the plan's stream; valid after lp_sync): out[0..8] = {spread, forward
+ * on the plan's stream; valid after lp_sync): out[0..9] = {spread, forward
  * FFT, multiplier, inverse FFT, interpolation, local, total, copies, grid
- * zeroing}. */
+ * zeroing, spread of the volume sources alone (part of out[0])}.  With the
+ * double-float transforms, "forward FFT" is the row transforms, "multiplier"
+ * the fused column pass (forward transform, multiplier, inverse transform)
+ * and "inverse FFT" the inverse row transforms.  out must hold 10 floats. */
 lp_status lp_stage_times(lp_plan_t plan, float* out);
 
 #ifdef __cplusplus

@@ -192,18 +192,19 @@ def lp_destroy(plan):
 
 
 def lp_plan_info(plan):
-    out = np.zeros(20)
+    out = np.zeros(23)
     _check(_lib().lp_plan_info(plan, out.ctypes.data), "lp_plan_info")
     keys = ["delta1", "delta2", "w", "beta", "g_nh", "K_nh", "P_nh", "g_fh", "K_fh", "P_fh", "L_fh",
             "band", "margin", "device_bytes", "precision", "order", "launches", "es_fit_err", "es_nc",
-            "sigma_eff"]
+            "sigma_eff", "own_fft", "binned", "bin_cells"]
     return dict(zip(keys, out.tolist()))
 
 
 def lp_stage_times(plan):
-    out = np.zeros(9, dtype=np.float32)
+    out = np.zeros(10, dtype=np.float32)
     _check(_lib().lp_stage_times(plan, out.ctypes.data), "lp_stage_times")
-    keys = ["spread", "fft_fwd", "multiplier", "fft_inv", "interp", "local", "total", "copies", "zero"]
+    keys = ["spread", "fft_fwd", "multiplier", "fft_inv", "interp", "local", "total", "copies", "zero",
+            "spread_volume"]
     return dict(zip(keys, out.tolist()))
 
 

@@ -1,6 +1,7 @@
-// FFT chain of the FP64 plans in double-float arithmetic (Sec. 3, Steps 2-4:
-// forward transform of the spread grids, diagonal multiplier, inverse
-// transform), replacing FP64 cuFFT, which on GB300 is bound by the FP64 units.
+// FFT chain of the history part (Sec. 3, Steps 2-4: forward transform of the
+// spread grids, diagonal multiplier, inverse transform): in double-float
+// arithmetic for FP64 plans (FP64 cuFFT is bound by GB300's FP64 units) and
+// in single precision for FP32 plans, with the same structure.
 //
 //   rows_fwd  real grid rows [row_lo, row_hi) (FP64, as spread) -> kept modes
 //             0..K of each row's half spectrum, df64 complex, [g][Kp]
@@ -9,7 +10,8 @@
 //             inverse transform along y -- the column never leaves shared
 //             memory between the two transforms
 //   rows_inv  rows [row_lo, row_hi) of the half spectrum -> real grid rows,
-//             written in place over the FP64 grid as df64 (hi, lo) pairs
+//             written in place over the grid (FP64 plans: as df64 (hi, lo)
+//             pairs over the FP64 values)
 //
 // Transforms are unnormalised with the signs of the forward (e^{-i}) and
 // inverse (e^{+i}) DFT, as the multiplier tables expect.  Each 1D transform
@@ -35,75 +37,123 @@ namespace {
 constexpr float kS3h = 0.8660253882408142f;
 constexpr float kS3l = 1.5543625053737742e-08f;
 
-template <int R>
-__device__ __forceinline__ void dft_small(cdd* v, bool inv) {
+// Arithmetic of one chain: DD = double-float complex values (float4 in
+// memory: re.hi, re.lo, im.hi, im.lo), F32 = single-precision complex
+// (float2).  Twiddles come from one df64 table; F32 uses its high parts.
+struct DD {
+  using V = cdd;
+  using S = float4;
+  __device__ static V load(const S* p) { return cdd_load(p); }
+  __device__ static void store(S* p, V a) { cdd_store(p, a); }
+  __device__ static V zero() { return cdd{dd{0.f, 0.f}, dd{0.f, 0.f}}; }
+  __device__ static V add(V a, V b) { return cdd_add(a, b); }
+  __device__ static V sub(V a, V b) { return cdd_sub(a, b); }
+  __device__ static V conj(V a) { return cdd_conj(a); }
+  __device__ static V mi(V a) { return cdd_mul_mi(a); }
+  __device__ static V pi(V a) { return cdd_mul_pi(a); }
+  __device__ static V half(V a) {
+    return cdd{dd_scale(a.re, 0.5f), dd_scale(a.im, 0.5f)};
+  }
+  __device__ static V s3(V a) {
+    const dd c = dd_make(kS3h, kS3l);
+    return cdd{dd_mul(a.re, c), dd_mul(a.im, c)};
+  }
+  __device__ static V tw(const float4* t, int k) { return cdd_load(t + k); }
+  __device__ static V mul(V a, V t) { return cdd_mul(a, t); }
+  __device__ static V mul_conj(V a, V t) { return cdd_mul_conj(a, t); }
+};
+
+struct F32 {
+  using V = float2;
+  using S = float2;
+  __device__ static V load(const S* p) { return *p; }
+  __device__ static void store(S* p, V a) { *p = a; }
+  __device__ static V zero() { return make_float2(0.f, 0.f); }
+  __device__ static V add(V a, V b) { return make_float2(a.x + b.x, a.y + b.y); }
+  __device__ static V sub(V a, V b) { return make_float2(a.x - b.x, a.y - b.y); }
+  __device__ static V conj(V a) { return make_float2(a.x, -a.y); }
+  __device__ static V mi(V a) { return make_float2(a.y, -a.x); }
+  __device__ static V pi(V a) { return make_float2(-a.y, a.x); }
+  __device__ static V half(V a) { return make_float2(0.5f * a.x, 0.5f * a.y); }
+  __device__ static V s3(V a) { return make_float2(kS3h * a.x, kS3h * a.y); }
+  __device__ static V tw(const float4* t, int k) {
+    const float4 v = t[k];
+    return make_float2(v.x, v.z);
+  }
+  __device__ static V mul(V a, V t) { return make_float2(a.x * t.x - a.y * t.y, a.x * t.y + a.y * t.x); }
+  __device__ static V mul_conj(V a, V t) { return make_float2(a.x * t.x + a.y * t.y, a.y * t.x - a.x * t.y); }
+};
+
+template <class A, int R>
+__device__ __forceinline__ void dft_small(typename A::V* v, bool inv) {
+  using V = typename A::V;
   if (R == 2) {
-    const cdd a = v[0], b = v[1];
-    v[0] = cdd_add(a, b);
-    v[1] = cdd_sub(a, b);
+    const V a = v[0], b = v[1];
+    v[0] = A::add(a, b);
+    v[1] = A::sub(a, b);
   } else if (R == 4) {
-    const cdd t0 = cdd_add(v[0], v[2]), t1 = cdd_sub(v[0], v[2]);
-    const cdd t2 = cdd_add(v[1], v[3]);
-    const cdd d = cdd_sub(v[1], v[3]);
-    const cdd t3 = inv ? cdd_mul_pi(d) : cdd_mul_mi(d);
-    v[0] = cdd_add(t0, t2);
-    v[1] = cdd_add(t1, t3);
-    v[2] = cdd_sub(t0, t2);
-    v[3] = cdd_sub(t1, t3);
+    const V t0 = A::add(v[0], v[2]), t1 = A::sub(v[0], v[2]);
+    const V t2 = A::add(v[1], v[3]);
+    const V d = A::sub(v[1], v[3]);
+    const V t3 = inv ? A::pi(d) : A::mi(d);
+    v[0] = A::add(t0, t2);
+    v[1] = A::add(t1, t3);
+    v[2] = A::sub(t0, t2);
+    v[3] = A::sub(t1, t3);
   } else {  // R == 3
-    const cdd t1 = cdd_add(v[1], v[2]);
-    const cdd t2 = cdd_sub(v[0], cdd{dd_scale(t1.re, 0.5f), dd_scale(t1.im, 0.5f)});
-    const cdd d = cdd_sub(v[1], v[2]);
-    const dd s3 = dd_make(kS3h, kS3l);
-    const cdd ds = cdd{dd_mul(d.re, s3), dd_mul(d.im, s3)};
-    const cdd t3 = inv ? cdd_mul_pi(ds) : cdd_mul_mi(ds);
-    v[0] = cdd_add(v[0], t1);
-    v[1] = cdd_add(t2, t3);
-    v[2] = cdd_sub(t2, t3);
+    const V t1 = A::add(v[1], v[2]);
+    const V t2 = A::sub(v[0], A::half(t1));
+    const V ds = A::s3(A::sub(v[1], v[2]));
+    const V t3 = inv ? A::pi(ds) : A::mi(ds);
+    v[0] = A::add(v[0], t1);
+    v[1] = A::add(t2, t3);
+    v[2] = A::sub(t2, t3);
   }
 }
 
-template <int R>
-__device__ __forceinline__ void stockham_butterfly(const float4* in, float4* out, int j, int N, int Ns,
-                                                   const float4* __restrict__ tw, int tws, bool inv) {
+template <class A, int R>
+__device__ __forceinline__ void stockham_butterfly(const typename A::S* in, typename A::S* out, int j, int N,
+                                                   int Ns, const float4* __restrict__ tw, int tws, bool inv) {
+  using V = typename A::V;
   const int stride = N / R;
-  cdd v[R];
+  V v[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) v[r] = cdd_load(in + j + r * stride);
+  for (int r = 0; r < R; ++r) v[r] = A::load(in + j + r * stride);
   const int k = j % Ns;
   if (k != 0) {
     const int step = (N / (Ns * R)) * tws;
 #pragma unroll
     for (int r = 1; r < R; ++r) {
-      const cdd t = cdd_load(tw + k * r * step);
-      v[r] = inv ? cdd_mul_conj(v[r], t) : cdd_mul(v[r], t);
+      const V t = A::tw(tw, k * r * step);
+      v[r] = inv ? A::mul_conj(v[r], t) : A::mul(v[r], t);
     }
   }
-  dft_small<R>(v, inv);
+  dft_small<A, R>(v, inv);
   const int base = (j - k) * R + k;
 #pragma unroll
-  for (int r = 0; r < R; ++r) cdd_store(out + base + r * Ns, v[r]);
+  for (int r = 0; r < R; ++r) A::store(out + base + r * Ns, v[r]);
 }
 
 // Transform of length N held in a (scratch b); returns the buffer holding
 // the result.  All threads of the CTA take part; the caller synchronises
 // before (data in a) and the function synchronises after every stage.
-__device__ float4* fft_smem(float4* a, float4* b, const FftShape& sh, const float4* __restrict__ tw, int tws,
-                            bool inv) {
+template <class A>
+__device__ typename A::S* fft_smem(typename A::S* a, typename A::S* b, const FftShape& sh,
+                                   const float4* __restrict__ tw, int tws, bool inv) {
   const int N = sh.n;
   int Ns = 1;
   for (int s = 0; s < sh.nst; ++s) {
     const int R = sh.radix[s];
     const int nb = N / R;
     if (R == 4) {
-      for (int j = threadIdx.x; j < nb; j += blockDim.x) stockham_butterfly<4>(a, b, j, N, Ns, tw, tws, inv);
+      for (int j = threadIdx.x; j < nb; j += blockDim.x) stockham_butterfly<A, 4>(a, b, j, N, Ns, tw, tws, inv);
     } else if (R == 2) {
-      for (int j = threadIdx.x; j < nb; j += blockDim.x) stockham_butterfly<2>(a, b, j, N, Ns, tw, tws, inv);
+      for (int j = threadIdx.x; j < nb; j += blockDim.x) stockham_butterfly<A, 2>(a, b, j, N, Ns, tw, tws, inv);
     } else {
-      for (int j = threadIdx.x; j < nb; j += blockDim.x) stockham_butterfly<3>(a, b, j, N, Ns, tw, tws, inv);
+      for (int j = threadIdx.x; j < nb; j += blockDim.x) stockham_butterfly<A, 3>(a, b, j, N, Ns, tw, tws, inv);
     }
     __syncthreads();
-    float4* t = a;
+    typename A::S* t = a;
     a = b;
     b = t;
     Ns *= R;
@@ -111,29 +161,62 @@ __device__ float4* fft_smem(float4* a, float4* b, const FftShape& sh, const floa
   return a;
 }
 
-__device__ __forceinline__ cdd cdd_zero() { return cdd{dd{0.f, 0.f}, dd{0.f, 0.f}}; }
+// grid row -> complex sequence z_n = x_2n + i x_2n+1
+__device__ __forceinline__ cdd load_pair(const void* row, int n, DD) {
+  const double2 x = *((const double2*)row + n);
+  return cdd{dd_from_double(x.x), dd_from_double(x.y)};
+}
+__device__ __forceinline__ float2 load_pair(const void* row, int n, F32) { return *((const float2*)row + n); }
+
+// complex z_n -> grid row values x_2n, x_2n+1 (df64 pairs, or floats)
+__device__ __forceinline__ void store_pair(void* row, int n, cdd z, DD) { cdd_store((float4*)row + n, z); }
+__device__ __forceinline__ void store_pair(void* row, int n, float2 z, F32) { *((float2*)row + n) = z; }
+
+// multiplier table entry: df64 pair, or float
+__device__ __forceinline__ dd mult_value(const void* tab, size_t i, DD) {
+  const float2 m = ((const float2*)tab)[i];
+  return dd_make(m.x, m.y);
+}
+__device__ __forceinline__ float mult_value(const void* tab, size_t i, F32) { return ((const float*)tab)[i]; }
+
+__device__ __forceinline__ cdd scale_real(cdd a, dd m) { return cdd_scale_dd(a, m); }
+__device__ __forceinline__ float2 scale_real(float2 a, float m) { return make_float2(a.x * m, a.y * m); }
+
+// m (-i)(kx f1 + ky f2), kx = dk mx, ky = dk my
+__device__ __forceinline__ cdd dipole_mode(cdd f1, cdd f2, dd m, float2 dk2, int mx, int my) {
+  const dd dk = dd_make(dk2.x, dk2.y);
+  const dd kx = dd_mul_f(dk, (float)mx), ky = dd_mul_f(dk, (float)my);
+  const dd re = dd_dot2(kx, f1.im, ky, f2.im);
+  const dd im = dd_dot2(kx, f1.re, ky, f2.re);
+  return cdd{dd_mul(m, re), dd_neg(dd_mul(m, im))};
+}
+__device__ __forceinline__ float2 dipole_mode(float2 f1, float2 f2, float m, float2 dk2, int mx, int my) {
+  const float kx = dk2.x * (float)mx, ky = dk2.x * (float)my;
+  return make_float2(m * (kx * f1.y + ky * f2.y), -m * (kx * f1.x + ky * f2.x));
+}
 
 // Forward transform of real rows: one CTA per (row, channel).
+template <class A>
 __global__ void __launch_bounds__(kFftThreads) fft_rows_fwd_kernel(const __grid_constant__ FftRowArgs a) {
-  extern __shared__ float4 sm[];
+  using V = typename A::V;
+  using S = typename A::S;
+  extern __shared__ float4 sm_raw[];
+  S* sm = (S*)sm_raw;
   const int N = a.half.n;
   const int row = a.row_lo + blockIdx.x, c = blockIdx.y;
-  const double* src = (const double*)a.grid[c] + (size_t)row * a.pitch;
-  float4* buf0 = sm;
-  float4* buf1 = sm + N;
-  for (int n = threadIdx.x; n < N; n += blockDim.x) {
-    const double2 x = *(const double2*)(src + 2 * n);
-    cdd_store(buf0 + n, cdd{dd_from_double(x.x), dd_from_double(x.y)});
-  }
+  // a complex value of the chain takes twice the bytes of a real grid element
+  const char* src = (const char*)a.grid[c] + (size_t)row * a.pitch * (sizeof(S) / 2);
+  S* buf0 = sm;
+  S* buf1 = sm + N;
+  for (int n = threadIdx.x; n < N; n += blockDim.x) A::store(buf0 + n, load_pair(src, n, A()));
   __syncthreads();
-  const float4* Z = fft_smem(buf0, buf1, a.half, a.tw, 2, false);
-  float4* dst = a.spec[c] + (size_t)row * a.kp;
+  const S* Z = fft_smem<A>(buf0, buf1, a.half, a.tw, 2, false);
+  S* dst = (S*)a.spec[c] + (size_t)row * a.kp;
   for (int k = threadIdx.x; k <= a.K; k += blockDim.x) {
-    const cdd zk = cdd_load(Z + k), zn = cdd_conj(cdd_load(Z + (k == 0 ? 0 : N - k)));
-    const cdd s = cdd_add(zk, zn), d = cdd_sub(zk, zn);
-    const cdd e = cdd{dd_scale(s.re, 0.5f), dd_scale(s.im, 0.5f)};
-    const cdd o = cdd_mul_mi(cdd{dd_scale(d.re, 0.5f), dd_scale(d.im, 0.5f)});
-    cdd_store(dst + k, cdd_add(e, cdd_mul(cdd_load(a.tw + k), o)));
+    const V zk = A::load(Z + k), zn = A::conj(A::load(Z + (k == 0 ? 0 : N - k)));
+    const V e = A::half(A::add(zk, zn));
+    const V o = A::mi(A::half(A::sub(zk, zn)));
+    A::store(dst + k, A::add(e, A::mul(o, A::tw(a.tw, k))));
   }
 }
 
@@ -141,89 +224,86 @@ __global__ void __launch_bounds__(kFftThreads) fft_rows_fwd_kernel(const __grid_
 // one spectrum and multiply by M; kind 1 (D) transforms two and combines
 // them, parking the first transform in its own (global) column meanwhile so
 // that every job needs only two shared-memory buffers of g values.
+template <class A>
 __global__ void __launch_bounds__(kFftThreads) fft_cols_kernel(const __grid_constant__ FftColArgs a) {
-  extern __shared__ float4 sm[];
+  using V = typename A::V;
+  using S = typename A::S;
+  extern __shared__ float4 sm_raw[];
+  S* sm = (S*)sm_raw;
   const int g = a.full.n, K = a.K, mx = blockIdx.x;
   const FftColJob& job = a.job[blockIdx.y];
-  float4* buf0 = sm;
-  float4* buf1 = sm + g;
-  auto load_col = [&](const float4* spec) {
+  S* buf0 = sm;
+  S* buf1 = sm + g;
+  auto load_col = [&](const void* spec) {
+    const S* sp = (const S*)spec;
     for (int r = threadIdx.x; r < g; r += blockDim.x) {
       if (r >= a.row_lo && r < a.row_hi)
-        buf0[r] = spec[(size_t)r * a.kp + mx];
+        buf0[r] = sp[(size_t)r * a.kp + mx];
       else
-        cdd_store(buf0 + r, cdd_zero());
+        A::store(buf0 + r, A::zero());
     }
     __syncthreads();
   };
-  const dd dk = dd_make(a.dk.x, a.dk.y);
-  float4* X;
+  S* X;
   if (job.kind == 1) {
     load_col(job.in[0]);
-    const float4* F1 = fft_smem(buf0, buf1, a.full, a.tw, 1, false);
-    float4* park = job.out;  // the D1 spectrum column, all g rows
+    const S* F1 = fft_smem<A>(buf0, buf1, a.full, a.tw, 1, false);
+    S* park = (S*)job.out;  // the D1 spectrum column, all g rows
     for (int r = threadIdx.x; r < g; r += blockDim.x) park[(size_t)r * a.kp + mx] = F1[r];
     __syncthreads();
     load_col(job.in[1]);
-    X = fft_smem(buf0, buf1, a.full, a.tw, 1, false);
-    const dd kx = dd_mul_f(dk, (float)mx);
+    X = fft_smem<A>(buf0, buf1, a.full, a.tw, 1, false);
     for (int r = threadIdx.x; r < g; r += blockDim.x) {
       const int my = r <= g / 2 ? r : r - g;
       const int amy = my < 0 ? -my : my;
-      cdd o = cdd_zero();
-      if (amy <= K) {
-        const float2 mt = a.tab[(size_t)amy * (K + 1) + mx];
-        const dd m = dd_make(mt.x, mt.y);
-        const dd ky = dd_mul_f(dk, (float)my);
-        const cdd f1 = cdd_load(park + (size_t)r * a.kp + mx), f2 = cdd_load(X + r);
-        // m (-i)(kx f1 + ky f2)
-        const dd re = dd_dot2(kx, f1.im, ky, f2.im);
-        const dd im = dd_dot2(kx, f1.re, ky, f2.re);
-        o = cdd{dd_mul(m, re), dd_neg(dd_mul(m, im))};
-      }
-      cdd_store(X + r, o);
+      V o = A::zero();
+      if (amy <= K)
+        o = dipole_mode(A::load(park + (size_t)r * a.kp + mx), A::load(X + r),
+                        mult_value(a.tab, (size_t)amy * (K + 1) + mx, A()), a.dk, mx, my);
+      A::store(X + r, o);
     }
   } else {
     load_col(job.in[0]);
-    X = fft_smem(buf0, buf1, a.full, a.tw, 1, false);
+    X = fft_smem<A>(buf0, buf1, a.full, a.tw, 1, false);
     for (int r = threadIdx.x; r < g; r += blockDim.x) {
       const int my = r <= g / 2 ? r : r - g;
       const int amy = my < 0 ? -my : my;
-      cdd o = cdd_zero();
-      if (amy <= K) {
-        const float2 mt = a.tab[(size_t)amy * (K + 1) + mx];
-        o = cdd_scale_dd(cdd_load(X + r), dd_make(mt.x, mt.y));
-      }
-      cdd_store(X + r, o);
+      V o = A::zero();
+      if (amy <= K) o = scale_real(A::load(X + r), mult_value(a.tab, (size_t)amy * (K + 1) + mx, A()));
+      A::store(X + r, o);
     }
   }
   __syncthreads();
-  const float4* Y = fft_smem(X, X == buf0 ? buf1 : buf0, a.full, a.tw, 1, true);
-  for (int r = a.row_lo + threadIdx.x; r < a.row_hi; r += blockDim.x) job.out[(size_t)r * a.kp + mx] = Y[r];
+  const S* Y = fft_smem<A>(X, X == buf0 ? buf1 : buf0, a.full, a.tw, 1, true);
+  S* out = (S*)job.out;
+  for (int r = a.row_lo + threadIdx.x; r < a.row_hi; r += blockDim.x) out[(size_t)r * a.kp + mx] = Y[r];
 }
 
-// Inverse transform of rows: one CTA per (row, job); writes g df64 values
-// over the row of the job's FP64 grid.
+// Inverse transform of rows: one CTA per (row, job); writes the g values of
+// the row over the job's grid row (df64 pairs over the FP64 grid, or floats).
+template <class A>
 __global__ void __launch_bounds__(kFftThreads) fft_rows_inv_kernel(const __grid_constant__ FftRowArgs a) {
-  extern __shared__ float4 sm[];
+  using V = typename A::V;
+  using S = typename A::S;
+  extern __shared__ float4 sm_raw[];
+  S* sm = (S*)sm_raw;
   const int N = a.half.n;
   const int row = a.row_lo + blockIdx.x, c = blockIdx.y;
-  const float4* spec = a.spec[c] + (size_t)row * a.kp;
-  float4* buf0 = sm;
-  float4* buf1 = sm + N;
+  const S* spec = (const S*)a.spec[c] + (size_t)row * a.kp;
+  S* buf0 = sm;
+  S* buf1 = sm + N;
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
-    cdd xk = k <= a.K ? cdd_load(spec + k) : cdd_zero();
-    if (k == 0) xk.im = dd{0.f, 0.f};
+    V xk = k <= a.K ? A::load(spec + k) : A::zero();
+    if (k == 0) xk = A::add(A::half(xk), A::half(A::conj(xk)));  // drop the imaginary part
     const int nk = N - k;
-    const cdd xn = nk <= a.K ? cdd_conj(cdd_load(spec + nk)) : cdd_zero();
-    const cdd A = cdd_add(xk, xn);
-    const cdd B = cdd_mul_conj(cdd_sub(xk, xn), cdd_load(a.tw + k));
-    cdd_store(buf0 + k, cdd_add(A, cdd_mul_pi(B)));
+    const V xn = nk <= a.K ? A::conj(A::load(spec + nk)) : A::zero();
+    const V B = A::mul_conj(A::sub(xk, xn), A::tw(a.tw, k));
+    A::store(buf0 + k, A::add(A::add(xk, xn), A::pi(B)));
   }
   __syncthreads();
-  const float4* z = fft_smem(buf0, buf1, a.half, a.tw, 2, true);
-  float4* dst = (float4*)((float2*)a.grid[c] + (size_t)row * a.pitch);  // 2 df64 values per float4
-  for (int n = threadIdx.x; n < N; n += blockDim.x) dst[n] = z[n];
+  const S* z = fft_smem<A>(buf0, buf1, a.half, a.tw, 2, true);
+  char* dst = (char*)a.grid[c] + (size_t)row * a.pitch * (sizeof(S) / 2);
+  for (int n = threadIdx.x; n < N; n += blockDim.x) store_pair(dst, n, A::load(z + n), A());
 }
 
 __global__ void split_table_kernel(const double* __restrict__ src, float2* dst, int64_t n) {
@@ -273,34 +353,46 @@ std::vector<float4> fft_twiddles(int g) {
   return t;
 }
 
-size_t fft_rows_smem(int g) { return (size_t)2 * (g / 2) * sizeof(float4); }
-size_t fft_cols_smem(int g) { return (size_t)2 * g * sizeof(float4); }
+size_t fft_rows_smem(int g, bool f64) { return (size_t)2 * (g / 2) * (f64 ? sizeof(float4) : sizeof(float2)); }
+size_t fft_cols_smem(int g, bool f64) { return (size_t)2 * g * (f64 ? sizeof(float4) : sizeof(float2)); }
 
 bool fft_dd_configure() {
   const int bytes = 220 * 1024;
-  return cudaFuncSetAttribute(fft_rows_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
-             cudaSuccess &&
-         cudaFuncSetAttribute(fft_rows_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
-             cudaSuccess &&
-         cudaFuncSetAttribute(fft_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
-             cudaSuccess;
+  const void* fns[6] = {(const void*)fft_rows_fwd_kernel<DD>, (const void*)fft_rows_inv_kernel<DD>,
+                        (const void*)fft_cols_kernel<DD>,      (const void*)fft_rows_fwd_kernel<F32>,
+                        (const void*)fft_rows_inv_kernel<F32>, (const void*)fft_cols_kernel<F32>};
+  for (const void* f : fns)
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return false;
+  return true;
 }
 
-void launch_fft_rows_fwd(const FftRowArgs& a, int nchan, cudaStream_t s) {
+void launch_fft_rows_fwd(const FftRowArgs& a, int nchan, bool f64, cudaStream_t s) {
   const int nrows = a.row_hi - a.row_lo;
   if (nrows <= 0 || nchan <= 0) return;
-  fft_rows_fwd_kernel<<<dim3(nrows, nchan), kFftThreads, fft_rows_smem(2 * a.half.n), s>>>(a);
+  const size_t smem = fft_rows_smem(2 * a.half.n, f64);
+  if (f64)
+    fft_rows_fwd_kernel<DD><<<dim3(nrows, nchan), kFftThreads, smem, s>>>(a);
+  else
+    fft_rows_fwd_kernel<F32><<<dim3(nrows, nchan), kFftThreads, smem, s>>>(a);
 }
 
-void launch_fft_rows_inv(const FftRowArgs& a, int nchan, cudaStream_t s) {
+void launch_fft_rows_inv(const FftRowArgs& a, int nchan, bool f64, cudaStream_t s) {
   const int nrows = a.row_hi - a.row_lo;
   if (nrows <= 0 || nchan <= 0) return;
-  fft_rows_inv_kernel<<<dim3(nrows, nchan), kFftThreads, fft_rows_smem(2 * a.half.n), s>>>(a);
+  const size_t smem = fft_rows_smem(2 * a.half.n, f64);
+  if (f64)
+    fft_rows_inv_kernel<DD><<<dim3(nrows, nchan), kFftThreads, smem, s>>>(a);
+  else
+    fft_rows_inv_kernel<F32><<<dim3(nrows, nchan), kFftThreads, smem, s>>>(a);
 }
 
-void launch_fft_cols(const FftColArgs& a, int njobs, cudaStream_t s) {
+void launch_fft_cols(const FftColArgs& a, int njobs, bool f64, cudaStream_t s) {
   if (njobs <= 0) return;
-  fft_cols_kernel<<<dim3(a.K + 1, njobs), kFftThreads, fft_cols_smem(a.full.n), s>>>(a);
+  const size_t smem = fft_cols_smem(a.full.n, f64);
+  if (f64)
+    fft_cols_kernel<DD><<<dim3(a.K + 1, njobs), kFftThreads, smem, s>>>(a);
+  else
+    fft_cols_kernel<F32><<<dim3(a.K + 1, njobs), kFftThreads, smem, s>>>(a);
 }
 
 }  // namespace lpg

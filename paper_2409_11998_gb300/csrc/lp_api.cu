@@ -334,46 +334,49 @@ float2 split_host(double x) {
   return make_float2(h, (float)(x - (double)h));
 }
 
-// df64 FFT chain and interpolation of FP64 plans: radix plans, twiddles, the
-// multiplier tables as (hi, lo) pairs and the per-channel spectrum columns.
-// Plans whose grids are not 3-smooth or whose columns do not fit in shared
-// memory keep cuFFT.
-lp_status setup_fft_dd(Plan& P) {
+// FFT chain of both precisions (k_fft.cu): radix plans, twiddles, the
+// multiplier tables as (hi, lo) pairs (FP64) and the per-channel spectrum
+// columns.  Plans whose grids are not 3-smooth or whose columns do not fit in
+// shared memory keep cuFFT.
+lp_status setup_fft_chain(Plan& P) {
   const size_t limit = 220 * 1024;
+  const bool f64 = P.precision == LP_FP64;
   for (int l = 0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
     G.full = fft_shape(G.g);
     G.half = fft_shape(G.g / 2);
     if (G.full.nst <= 0 || G.half.nst <= 0 || (G.g & 1)) return LP_OK;
-    if (fft_cols_smem(G.g) > limit || fft_rows_smem(G.g) > limit) return LP_OK;
+    if (fft_cols_smem(G.g, f64) > limit || fft_rows_smem(G.g, f64) > limit) return LP_OK;
   }
   if (!fft_dd_configure()) return LP_ERR_CUDA;
   for (int l = 0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
     G.kp = (G.K + 2) & ~1;
-    const size_t spec_bytes = (size_t)G.g * G.kp * sizeof(float4);
+    const size_t spec_bytes = (size_t)G.g * G.kp * (f64 ? sizeof(float4) : sizeof(float2));
     for (int c = 0; c < 4; ++c)
-      if (!dalloc(P, (void**)&G.spec[c], spec_bytes)) return LP_ERR_NOMEM;
+      if (!dalloc(P, &G.spec[c], spec_bytes)) return LP_ERR_NOMEM;
     const std::vector<float4> tw = fft_twiddles(G.g);
-    const size_t ntab = (size_t)(G.K + 1) * (G.K + 1);
-    if (!dalloc(P, (void**)&G.tw_dd, tw.size() * sizeof(float4)) ||
-        !dalloc(P, (void**)&G.mtab_dd, ntab * sizeof(float2)))
-      return LP_ERR_NOMEM;
+    if (!dalloc(P, (void**)&G.tw_dd, tw.size() * sizeof(float4))) return LP_ERR_NOMEM;
     cudaMemcpy(G.tw_dd, tw.data(), tw.size() * sizeof(float4), cudaMemcpyHostToDevice);
-    launch_split_table(G.mtab, G.mtab_dd, (int64_t)ntab, P.stream);
+    if (f64) {
+      const size_t ntab = (size_t)(G.K + 1) * (G.K + 1);
+      if (!dalloc(P, (void**)&G.mtab_dd, ntab * sizeof(float2))) return LP_ERR_NOMEM;
+      launch_split_table(G.mtab, G.mtab_dd, (int64_t)ntab, P.stream);
+    }
   }
   for (int k = 0; k < P.es.nc; ++k)
     for (int t = 0; t < P.es.w; ++t) P.es_dd[k][t] = split_host(P.es.c[k][t]);
   if (cudaStreamSynchronize(P.stream) != cudaSuccess) return LP_ERR_CUDA;
-  P.dd_fft = true;
+  P.own_fft = true;
   return LP_OK;
 }
 
-// Steps 2-4 of the FP64 plans in df64: forward row transforms of the spread
-// grids, the fused column pass (transform, multiplier, inverse transform) and
-// the inverse row transforms, then the interpolation.
-void history_dd(const Plan& P, int64_t nt, const double* txy, double* const* dout, bool wv, bool ws, bool wd,
-                cudaStream_t s) {
+// Steps 2-4 with the FFT chain: forward row transforms of the spread grids,
+// the fused column pass (transform, multiplier, inverse transform), the
+// inverse row transforms, then the interpolation (df64 for FP64 plans).
+void history_chain(const Plan& P, int64_t nt, const double* txy, double* const* dout, bool wv, bool ws,
+                   bool wd, cudaStream_t s) {
+  const bool f64 = P.precision == LP_FP64;
   int fch[4], nf = 0;
   if (wv) fch[nf++] = 0;
   if (ws) fch[nf++] = 1;
@@ -401,7 +404,7 @@ void history_dd(const Plan& P, int64_t nt, const double* txy, double* const* dou
     return a;
   };
   for (int l = 0; l < 2; ++l) {
-    launch_fft_rows_fwd(row_args(P.lv[l], fch, nf), nf, s);
+    launch_fft_rows_fwd(row_args(P.lv[l], fch, nf), nf, f64, s);
     ++P.launches;
   }
   cudaEventRecord(P.ev[4], s);
@@ -410,8 +413,8 @@ void history_dd(const Plan& P, int64_t nt, const double* txy, double* const* dou
     FftColArgs a{};
     a.full = G.full;
     a.tw = G.tw_dd;
-    a.tab = G.mtab_dd;
-    a.dk = split_host(G.dk);
+    a.tab = f64 ? (const void*)G.mtab_dd : (const void*)G.mtab32;
+    a.dk = f64 ? split_host(G.dk) : make_float2((float)G.dk, 0.f);
     int nj = 0;
     if (wv) a.job[nj++] = FftColJob{0, {G.spec[0], nullptr}, G.spec[0]};
     if (ws) a.job[nj++] = FftColJob{0, {G.spec[1], nullptr}, G.spec[1]};
@@ -420,15 +423,19 @@ void history_dd(const Plan& P, int64_t nt, const double* txy, double* const* dou
     a.K = G.K;
     a.row_lo = G.row_lo;
     a.row_hi = G.row_hi;
-    launch_fft_cols(a, nj, s);
+    launch_fft_cols(a, nj, f64, s);
     ++P.launches;
   }
   cudaEventRecord(P.ev[5], s);
   for (int l = 0; l < 2; ++l) {
-    launch_fft_rows_inv(row_args(P.lv[l], ich, ni), ni, s);
+    launch_fft_rows_inv(row_args(P.lv[l], ich, ni), ni, f64, s);
     ++P.launches;
   }
   cudaEventRecord(P.ev[6], s);
+  if (!f64) {
+    launch_interp(P, nt, txy, dout[0], dout[1], dout[2], s);
+    return;
+  }
   InterpDDArgs a{};
   a.txy = txy;
   a.n = nt;
@@ -562,7 +569,7 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
     if (st == LP_OK) st = build_boundary(P, hxy.data(), hw.data(), hn.data());
   }
   if (st == LP_OK) st = setup_bins(P);
-  if (st == LP_OK && P.precision == LP_FP64) st = setup_fft_dd(P);
+  if (st == LP_OK) st = setup_fft_chain(P);
   if (st == LP_OK) st = status_from_cuda();
   if (st != LP_OK) {
     destroy_plan(P);
@@ -741,6 +748,10 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
         launch_spread(P, l, P.d_vxy, q, 1, g, P.nv, s);
       }
     }
+  }
+  cudaEventRecord(P.ev[10], s);
+  for (int l = 0; l < 2; ++l) {
+    GridLevel& G = P.lv[l];
     const double* bq[3];
     void* bg[3];
     int nq = 0;
@@ -757,8 +768,8 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
     if (nq) launch_spread(P, l, P.d_bxy, bq, nq, bg, P.nb, s);
   }
   cudaEventRecord(P.ev[3], s);
-  if (P.dd_fft) {
-    history_dd(P, nt, dt, dout, wv, ws, wd, s);
+  if (P.own_fft) {
+    history_chain(P, nt, dt, dout, wv, ws, wd, s);
   } else {
     for (int l = 0; l < 2; ++l) {
       if (wv) fft_forward(P, l, 0);
@@ -827,6 +838,10 @@ lp_status lp_execute_noalloc(lp_plan_t h, int64_t nt, const double* txy, const d
       void* g[1] = {G.chan[0]};
       launch_spread(P, l, P.d_vxy, q, 1, g, P.nv, s);
     }
+  }
+  cudaEventRecord(P.ev[10], s);
+  for (int l = 0; l < 2; ++l) {
+    GridLevel& G = P.lv[l];
     const double* bq[3];
     void* bg[3];
     int nq = 0;
@@ -888,10 +903,11 @@ lp_status lp_destroy(lp_plan_t h) {
 lp_status lp_plan_info(lp_plan_t h, double* out) {
   if (!h || !out) return LP_ERR_ARG;
   const Plan& P = h->P;
-  double v[20] = {P.delta1, P.delta2, (double)P.ker.w, P.ker.beta, (double)P.lv[0].g, (double)P.lv[0].K,
+  double v[23] = {P.delta1, P.delta2, (double)P.ker.w, P.ker.beta, (double)P.lv[0].g, (double)P.lv[0].K,
                   P.lv[0].P, (double)P.lv[1].g, (double)P.lv[1].K, P.lv[1].P, P.lv[1].L, P.band,
                   P.margin, (double)P.device_bytes, (double)P.precision, (double)P.order,
-                  (double)P.launches, P.es_fit_err, (double)P.es.nc, P.sigma_eff};
+                  (double)P.launches, P.es_fit_err, (double)P.es.nc, P.sigma_eff,
+                  P.own_fft ? 1.0 : 0.0, P.binned ? 1.0 : 0.0, (double)P.bin_cells};
   std::memcpy(out, v, sizeof(v));
   return LP_OK;
 }
@@ -899,8 +915,8 @@ lp_status lp_plan_info(lp_plan_t h, double* out) {
 lp_status lp_stage_times(lp_plan_t h, float* out) {
   if (!h || !out) return LP_ERR_ARG;
   Plan& P = h->P;
-  // events: 0 start, 1 staged, 2 zeroed, 3 spread, 4 fwd, 5 mult, 6 inv, 7 interp,
-  // 8 local, 9 copies
+  // events: 0 start, 1 staged, 2 zeroed, 10 volume spread, 3 spread, 4 fwd,
+  // 5 mult, 6 inv, 7 interp, 8 local, 9 copies
   auto el = [&](int a, int b) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, P.ev[a], P.ev[b]) != cudaSuccess) {
@@ -918,6 +934,7 @@ lp_status lp_stage_times(lp_plan_t h, float* out) {
   out[6] = el(0, 9);
   out[7] = el(0, 1) + el(8, 9);
   out[8] = el(1, 2);
+  out[9] = el(2, 10);
   return LP_OK;
 }
 

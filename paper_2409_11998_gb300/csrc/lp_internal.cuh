@@ -24,7 +24,7 @@ constexpr int kSubDDThreads = 128;  // threads per CTA of the binned df64 spread
 // point-parallel spread).
 constexpr int sub_ncw(int w) { return w + 3; }
 constexpr int kMaxPanelOrder = 32;  // Gauss-Legendre nodes per boundary panel
-constexpr int kNumEvents = 10;
+constexpr int kNumEvents = 11;
 constexpr int kFftThreads = 256;    // threads per CTA of the df64 FFT kernels
 constexpr int kMaxFftStages = 24;   // radix stages of one df64 transform
 
@@ -78,13 +78,13 @@ struct GridLevel {
   int row_lo = 0, row_hi = 0;
   cufftHandle row_fwd = 0, row_inv = 0, col = 0;
   size_t chan_bytes = 0;
-  // df64 FFT chain (FP64 plans): twiddles e^{-2 pi i k/g}, the multiplier
-  // table as (hi, lo) pairs, and per channel the kept half-spectrum columns
-  // [g][kp] (kp = K + 1 rounded up to even) as df64 complex
+  // FFT chain: twiddles e^{-2 pi i k/g} as df64, the multiplier table as
+  // (hi, lo) pairs (FP64 plans), and per channel the kept half-spectrum
+  // columns [g][kp] (kp = K + 1 rounded up to even), df64 or FP32 complex
   FftShape full{}, half{};
   float4* tw_dd = nullptr;
   float2* mtab_dd = nullptr;
-  float4* spec[4] = {nullptr, nullptr, nullptr, nullptr};
+  void* spec[4] = {nullptr, nullptr, nullptr, nullptr};
   int kp = 0;
 };
 
@@ -176,22 +176,22 @@ struct SubDDArgs {
 struct FftRowArgs {
   FftShape half;
   const float4* tw;
-  void* grid[4];      // FP64 grids (forward input) / df64 grids (inverse output)
-  float4* spec[4];    // kept half spectra
+  void* grid[4];      // grids: forward input (FP64 or FP32), inverse output (df64 pairs or FP32)
+  void* spec[4];      // kept half spectra (df64 or FP32 complex)
   int pitch, kp, K, row_lo, row_hi;
 };
 
 struct FftColJob {
   int kind;           // 0: M F (V, S); 1: M (-i)(k1 F1 + k2 F2) (D)
-  const float4* in[2];
-  float4* out;
+  const void* in[2];
+  void* out;
 };
 
 struct FftColArgs {
   FftShape full;
   const float4* tw;
-  const float2* tab;  // deconvolved multiplier, (K+1)^2, df64
-  float2 dk;          // mode spacing, df64
+  const void* tab;    // deconvolved multiplier, (K+1)^2: df64 pairs (FP64) or floats without k = 0 (FP32)
+  float2 dk;          // mode spacing (df64 pair; FP32 uses .x)
   FftColJob job[3];
   int kp, K, row_lo, row_hi;
 };
@@ -255,7 +255,8 @@ struct Plan {
   EsPoly<double> es{};
   EsPoly<float> es32{};
   float2 es_dd[kMaxNC][kMaxW] = {};  // es as df64 (hi, lo) pairs
-  bool dd_fft = false;               // FP64 plan runs the df64 FFT chain and interpolation
+  bool own_fft = false;              // transforms run in this library's FFT chain (df64 for FP64 plans,
+                                     // with the df64 interpolation), not cuFFT
   double es_fit_err = 0;
   GridLevel lv[2];
   cudaStream_t stream = nullptr;
@@ -385,11 +386,11 @@ void launch_spread_sub(const SubArgs& a, int w, cudaStream_t s);
 FftShape fft_shape(int n);
 std::vector<float4> fft_twiddles(int g);
 bool fft_dd_configure();
-size_t fft_rows_smem(int g);
-size_t fft_cols_smem(int g);
-void launch_fft_rows_fwd(const FftRowArgs& a, int nchan, cudaStream_t s);
-void launch_fft_rows_inv(const FftRowArgs& a, int nchan, cudaStream_t s);
-void launch_fft_cols(const FftColArgs& a, int njobs, cudaStream_t s);
+size_t fft_rows_smem(int g, bool f64);
+size_t fft_cols_smem(int g, bool f64);
+void launch_fft_rows_fwd(const FftRowArgs& a, int nchan, bool f64, cudaStream_t s);
+void launch_fft_rows_inv(const FftRowArgs& a, int nchan, bool f64, cudaStream_t s);
+void launch_fft_cols(const FftColArgs& a, int njobs, bool f64, cudaStream_t s);
 void launch_split_table(const double* src, float2* dst, int64_t n, cudaStream_t s);
 void launch_interp_dd(const InterpDDArgs& a, int w, cudaStream_t s);
 void fft_forward(const Plan& P, int level, int chan);
