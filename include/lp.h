@@ -161,7 +161,11 @@ lp_status lp_execute_noalloc(lp_plan_t plan, int64_t n_t, const double* t_xy, co
  *     lp_sync(member) returns that member's device status.
  *   lp_batch_stage_times(b, out[9]): {zeroing+record copy, spread, forward
  *     FFTs, multiplier, inverse FFTs, interpolation, local, total} in ms of
- *     the last wave, and the batched launches issued so far. */
+ *     the last wave, and the launches issued so far.  Zeroing, the boundary
+ *     spread, the local pass and (for plans on cuFFT) the multiplier and
+ *     interpolation are one launch each per wave; binned volume spreads, the
+ *     library's FFT chain (timed as forward FFTs) and the double-float
+ *     interpolation run per member on the batch stream. */
 lp_status lp_batch_create(void* stream, lp_batch_t* batch);
 lp_status lp_batch_execute(lp_batch_t batch, int n, const lp_plan_t* plans, const int64_t* n_t,
                            const double* const* t_xy, const double* const* f_jet, double* const* V,

@@ -226,6 +226,10 @@ lp_status noalloc_scratch(void** out) {
   return LP_OK;
 }
 
+}  // namespace
+
+namespace lpg {
+
 // Bins of the binned volume spread: squares of bin_cells near-history cells
 // (32 for FP32 plans; 24 for FP64 plans, whose df64 patches take twice the
 // shared memory).  FP32 plans whose kernel fit needs more coefficients than
@@ -308,6 +312,16 @@ void spread_binned_dd(const Plan& P, int l, cudaStream_t s) {
   launch_spread_sub_dd(a, P.ker.w, s);
 }
 
+void spread_binned(const Plan& P, int l, cudaStream_t s);
+
+// Spread of the volume channel on one level from the sorted nodes.
+void spread_volume_binned(const Plan& P, int l, cudaStream_t s) {
+  if (P.precision == LP_FP64)
+    spread_binned_dd(P, l, s);
+  else
+    spread_binned(P, l, s);
+}
+
 // FP32 spread of the volume channel on one level from the sorted nodes.
 void spread_binned(const Plan& P, int l, cudaStream_t s) {
   const GridLevel& G = P.lv[l];
@@ -372,10 +386,9 @@ lp_status setup_fft_chain(Plan& P) {
 }
 
 // Steps 2-4 with the FFT chain: forward row transforms of the spread grids,
-// the fused column pass (transform, multiplier, inverse transform), the
-// inverse row transforms, then the interpolation (df64 for FP64 plans).
-void history_chain(const Plan& P, int64_t nt, const double* txy, double* const* dout, bool wv, bool ws,
-                   bool wd, cudaStream_t s) {
+// the fused column pass (transform, multiplier, inverse transform) and the
+// inverse row transforms (stage events recorded when `events`).
+void history_transforms(const Plan& P, bool wv, bool ws, bool wd, cudaStream_t s, bool events) {
   const bool f64 = P.precision == LP_FP64;
   int fch[4], nf = 0;
   if (wv) fch[nf++] = 0;
@@ -407,7 +420,7 @@ void history_chain(const Plan& P, int64_t nt, const double* txy, double* const* 
     launch_fft_rows_fwd(row_args(P.lv[l], fch, nf), nf, f64, s);
     ++P.launches;
   }
-  cudaEventRecord(P.ev[4], s);
+  if (events) cudaEventRecord(P.ev[4], s);
   for (int l = 0; l < 2; ++l) {
     const GridLevel& G = P.lv[l];
     FftColArgs a{};
@@ -426,13 +439,18 @@ void history_chain(const Plan& P, int64_t nt, const double* txy, double* const* 
     launch_fft_cols(a, nj, f64, s);
     ++P.launches;
   }
-  cudaEventRecord(P.ev[5], s);
+  if (events) cudaEventRecord(P.ev[5], s);
   for (int l = 0; l < 2; ++l) {
     launch_fft_rows_inv(row_args(P.lv[l], ich, ni), ni, f64, s);
     ++P.launches;
   }
-  cudaEventRecord(P.ev[6], s);
-  if (!f64) {
+  if (events) cudaEventRecord(P.ev[6], s);
+}
+
+// Step 4 after the FFT chain: interpolation from the chain's grids (df64
+// pairs for FP64 plans, floats for FP32 plans).
+void history_interp(const Plan& P, int64_t nt, const double* txy, double* const* dout, cudaStream_t s) {
+  if (P.precision != LP_FP64) {
     launch_interp(P, nt, txy, dout[0], dout[1], dout[2], s);
     return;
   }
@@ -457,7 +475,7 @@ void history_chain(const Plan& P, int64_t nt, const double* txy, double* const* 
   ++P.launches;
 }
 
-}  // namespace
+}  // namespace lpg
 
 extern "C" {
 
@@ -738,10 +756,7 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
     GridLevel& G = P.lv[l];
     if (wv && P.nv > 0) {
       if (P.binned) {
-        if (P.precision == LP_FP64)
-          spread_binned_dd(P, l, s);
-        else
-          spread_binned(P, l, s);
+        spread_volume_binned(P, l, s);
       } else {
         const double* q[1] = {P.d_vq};
         void* g[1] = {G.chan[0]};
@@ -769,7 +784,8 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
   }
   cudaEventRecord(P.ev[3], s);
   if (P.own_fft) {
-    history_chain(P, nt, dt, dout, wv, ws, wd, s);
+    history_transforms(P, wv, ws, wd, s, true);
+    history_interp(P, nt, dt, dout, s);
   } else {
     for (int l = 0; l < 2; ++l) {
       if (wv) fft_forward(P, l, 0);

@@ -90,6 +90,12 @@ lp_status lp_batch_destroy(lp_batch_t b) {
   return LP_OK;
 }
 
+static long long sum_launches(const lp_plan_t* plans, int n) {
+  long long t = 0;
+  for (int i = 0; i < n; ++i) t += plans[i]->P.launches;
+  return t;
+}
+
 lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const int64_t* n_t,
                            const double* const* t_xy, const double* const* f_jet, double* const* V,
                            double* const* S, double* const* D) {
@@ -154,7 +160,7 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
         else sp32.push_back(make_spread_args<float>(P, l, xy, q, nq, grids, cnt));
         for (int64_t j = 0; j < cnt; j += kBatchThreads) swork.push_back(make_int2(rec, (int)j));
       };
-      if (wv) {
+      if (wv && !P.binned) {  // binned plans spread their volume nodes per plan below
         const double* q[1] = {P.d_vq};
         void* g[1] = {G.chan[0]};
         add_spread(P.d_vxy, q, 1, g, P.nv);
@@ -173,25 +179,28 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
         bg[nq++] = G.chan[3];
       }
       add_spread(P.d_bxy, bq, nq, bg, P.nb);
-      int rec = (int)mult.size();
-      mult.push_back(make_mult_args(P, l, wv, ws, wd));
-      int64_t modes = (int64_t)G.g * (G.g / 2 + 1);
-      for (int64_t j = 0; j * kBatchThreads < modes; ++j) mwork.push_back(make_int2(rec, (int)j));
+      if (!P.own_fft) {  // plans on the FFT chain apply the multiplier inside it
+        int rec = (int)mult.size();
+        mult.push_back(make_mult_args(P, l, wv, ws, wd));
+        int64_t modes = (int64_t)G.g * (G.g / 2 + 1);
+        for (int64_t j = 0; j * kBatchThreads < modes; ++j) mwork.push_back(make_int2(rec, (int)j));
+      }
     }
     double* vo = wv ? V[i] : nullptr;
     double* so = ws ? S[i] : nullptr;
     double* dout = wd ? D[i] : nullptr;
-    int rec = f64 ? (int)in64.size() : (int)in32.size();
-    if (f64) in64.push_back(make_interp_args<double>(P, nt, t_xy[i], vo, so, dout));
-    else in32.push_back(make_interp_args<float>(P, nt, t_xy[i], vo, so, dout));
+    // FP64 plans on the FFT chain interpolate from df64 grids, per plan below
+    if (!(f64 && P.own_fft)) {
+      int rec = f64 ? (int)in64.size() : (int)in32.size();
+      if (f64) in64.push_back(make_interp_args<double>(P, nt, t_xy[i], vo, so, dout));
+      else in32.push_back(make_interp_args<float>(P, nt, t_xy[i], vo, so, dout));
+      for (int64_t j = 0; j < nt; j += kBatchThreads) iwork.push_back(make_int2(rec, (int)j));
+    }
     int lrec = (int)loc.size();
     loc.push_back(make_local_args(P, nt, t_xy[i], wv ? f_jet[i] : nullptr, vo, so, dout));
-    for (int64_t j = 0; j < nt; j += kBatchThreads) {
-      iwork.push_back(make_int2(rec, (int)j));
-      lwork.push_back(make_int2(lrec, (int)j));
-    }
+    for (int64_t j = 0; j < nt; j += kBatchThreads) lwork.push_back(make_int2(lrec, (int)j));
   }
-  if (iwork.empty()) return LP_OK;
+  if (lwork.empty()) return LP_OK;
   Packer pk;
   const size_t o_zs = pk.put(zsegs), o_zw = pk.put(zwork);
   const size_t o_sa = f64 ? pk.put(sp64) : pk.put(sp32), o_sw = pk.put(swork);
@@ -230,13 +239,24 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
   launch_zero_batch((const ZeroSeg*)(d + o_zs), (const int2*)(d + o_zw), (int)zwork.size(), s);
   cudaEventRecord(b->ev[1], s);
   launch_spread_batch(prec, w, d + o_sa, (const int2*)(d + o_sw), (int)swork.size(), s);
-  cudaEventRecord(b->ev[2], s);
   b->launches += 2;
-  // each plan's pruned transforms on the batch stream
+  const long long before = sum_launches(plans, n);
+  for (int i = 0; i < n; ++i) {
+    const Plan& P = plans[i]->P;
+    if (n_t[i] > 0 && V && V[i] && P.binned && P.nv > 0)
+      for (int l = 0; l < 2; ++l) spread_volume_binned(P, l, s);
+  }
+  cudaEventRecord(b->ev[2], s);
+  // each plan's transforms on the batch stream: the whole FFT chain for plans
+  // on it (counted as forward transforms), else pruned cuFFT transforms
   for (int i = 0; i < n; ++i) {
     const Plan& P = plans[i]->P;
     const bool wv = V && V[i], ws = S && S[i], wd = D && D[i];
     if (n_t[i] == 0 || (!wv && !ws && !wd)) continue;
+    if (P.own_fft) {
+      history_transforms(P, wv, ws, wd, s, false);
+      continue;
+    }
     for (int l = 0; l < 2; ++l) {
       const GridLevel& G = P.lv[l];
       cufftSetStream(G.row_fwd, s);
@@ -255,7 +275,7 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
   for (int i = 0; i < n; ++i) {
     const Plan& P = plans[i]->P;
     const bool wv = V && V[i], ws = S && S[i], wd = D && D[i];
-    if (n_t[i] == 0 || (!wv && !ws && !wd)) continue;
+    if (n_t[i] == 0 || (!wv && !ws && !wd) || P.own_fft) continue;
     for (int l = 0; l < 2; ++l) {
       const GridLevel& G = P.lv[l];
       cufftSetStream(G.row_inv, s);
@@ -269,11 +289,18 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
   }
   cudaEventRecord(b->ev[5], s);
   launch_interp_batch(prec, w, d + o_ia, (const int2*)(d + o_iw), (int)iwork.size(), s);
+  for (int i = 0; i < n; ++i) {
+    const Plan& P = plans[i]->P;
+    const bool wv = V && V[i], ws = S && S[i], wd = D && D[i];
+    if (n_t[i] == 0 || (!wv && !ws && !wd) || !(f64 && P.own_fft)) continue;
+    double* outs[3] = {wv ? V[i] : nullptr, ws ? S[i] : nullptr, wd ? D[i] : nullptr};
+    history_interp(P, n_t[i], t_xy[i], outs, s);
+  }
   cudaEventRecord(b->ev[6], s);
   launch_local_batch(prec, (const LocalArgs*)(d + o_la), (const int2*)(d + o_lw), (int)lwork.size(), b->d_list,
                      b->d_count, total_t, s);
   cudaEventRecord(b->ev[7], s);
-  b->launches += 5;
+  b->launches += 5 + (sum_launches(plans, n) - before);
   b->pending = true;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LP_OK : LP_ERR_CUDA;

@@ -393,6 +393,10 @@ void launch_fft_rows_inv(const FftRowArgs& a, int nchan, bool f64, cudaStream_t 
 void launch_fft_cols(const FftColArgs& a, int njobs, bool f64, cudaStream_t s);
 void launch_split_table(const double* src, float2* dst, int64_t n, cudaStream_t s);
 void launch_interp_dd(const InterpDDArgs& a, int w, cudaStream_t s);
+// pipeline pieces shared by lp_execute and lp_batch_execute (lp_api.cu)
+void spread_volume_binned(const Plan& P, int l, cudaStream_t s);
+void history_transforms(const Plan& P, bool wv, bool ws, bool wd, cudaStream_t s, bool events);
+void history_interp(const Plan& P, int64_t nt, const double* txy, double* const* dout, cudaStream_t s);
 void fft_forward(const Plan& P, int level, int chan);
 void fft_inverse(const Plan& P, int level, int chan);
 void launch_panel_coef(const Plan& P, const double* vals, int stride, int ncomp, double* coef,
