@@ -144,27 +144,21 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_traffic(name):
+def kernel_traffic(name, workload):
     """DRAM bytes (read + write) of a kernel per bench step, summed over its
-    launches in the step, from a committed ncu summary; valid only while the
-    kernel sources are unchanged (sha of csrc/*.cu,*.cuh)."""
+    launches in the step, from the committed ncu summary profiles/traffic.json
+    (entries kernel@workload); valid only while the kernel's source file is
+    unchanged (its sha256 prefix is stored with the entry)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p))
-    ent = d.get(name)
-    if not ent or ent.get("source_sha") != source_sha():
+    ent = json.load(open(p)).get(f"{name}@{workload}")
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2409_11998_gb300", "csrc", ent["file"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != ent["file_sha"]:
         return None
     return ent.get("bytes_per_step")
-
-
-def source_sha():
-    h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2409_11998_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
-    return h.hexdigest()[:16]
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -228,7 +222,8 @@ def run_lp(args, rank, world, local_rank):
     info = lp.lp_plan_info(plan)
     st = {k: statistics.mean(s[k] for s in stages) for k in stages[0]}
 
-    roof = roofline(info, st, nv, nb, nt, precision="fp64", n_out=sum(o is not None for o in outs))
+    roof = roofline(info, st, nv, nb, nt, precision="fp64", n_out=sum(o is not None for o in outs),
+                    workload=args.workload)
 
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps,
@@ -287,7 +282,7 @@ def df64_peak_t():
     return 152 * 128 * sm_max_mhz() * 1e6 / DF64_FMA_INSTR / 1e12
 
 
-def roofline(info, st, nv, nb, nt, precision, n_out=3):
+def roofline(info, st, nv, nb, nt, precision, n_out=3, workload="starfish"):
     """Roofline of this library's dominant kernel.
 
     FP64 plans with the double-float chain: the volume spread
@@ -317,7 +312,7 @@ def roofline(info, st, nv, nb, nt, precision, n_out=3):
         peak = df64_peak_t()
         return {"kernel": kname, "bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 4),
                 "unit": "T df64-FMA/s (FP32 units)", "frac": round(ach / peak, 4),
-                "traffic": kernel_traffic(kname), "traffic_unit": "DRAM bytes per step (both launches)",
+                "traffic": kernel_traffic(kname, workload), "traffic_unit": "DRAM bytes per step (both launches)",
                 "algorithmic_df64_fma_per_step": int(ops), "launch_ms": round(ms, 4), "stage": dom,
                 "peak_source": f"derived: 152 SMs x 128 FP32 lanes x sm_max_mhz / {DF64_FMA_INSTR} "
                                "FP32 instructions per df64 multiply-add"}
@@ -328,14 +323,14 @@ def roofline(info, st, nv, nb, nt, precision, n_out=3):
         peak = fp64_peak_tflops()
         return {"kernel": "spread_atomic_kernel", "bound": "alu", "achieved": round(tf, 4),
                 "peak": round(peak, 4), "unit": "TFLOP/s (FP64)", "frac": round(tf / peak, 4),
-                "traffic": kernel_traffic("spread_atomic_kernel"), "algorithmic_flops_per_step": int(flops),
+                "traffic": kernel_traffic("spread_atomic_kernel", workload), "algorithmic_flops_per_step": int(flops),
                 "launch_ms": round(ms, 4), "stage": "spread",
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x sm_max_mhz"}
     kname = "spread_sub_kernel" if info.get("binned") else "spread_atomic_kernel"
     byts = nv * 3 * b + g2 * b
     gbs = byts / (vol_ms / 1e3) / 1e9
     return {"kernel": kname, "bound": "hbm", "achieved": round(gbs, 2), "peak": hbm, "unit": "GB/s",
-            "frac": round(gbs / hbm, 5), "traffic": kernel_traffic(kname),
+            "frac": round(gbs / hbm, 5), "traffic": kernel_traffic(kname, workload),
             "traffic_unit": "DRAM bytes per step (both launches)",
             "algorithmic_bytes_per_step": int(byts), "launch_ms": round(vol_ms, 4), "stage": "spread_volume",
             "peak_source": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)"}
@@ -447,7 +442,7 @@ def run_fp32(args, prob, dev, stream, points):
     par = parity_sample(prob, outs)
     info = lp.lp_plan_info(plan)
     roof = roofline(info, st, nv, len(prob["bnd"]["w"]), nt, precision="fp32",
-                    n_out=sum(o is not None for o in outs))
+                    n_out=sum(o is not None for o in outs), workload=args.workload)
     ev.close()
     return {"value": points / (statistics.mean(ms) / 1e3), "unit": UNIT, "dtype": "f32 (FP64 zero mode)",
             "tol": 1e-5, "ms_per_step": statistics.mean(ms),
