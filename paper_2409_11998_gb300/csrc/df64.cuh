@@ -119,6 +119,53 @@ __device__ __forceinline__ dd acc_value(dd_acc a) {
   return r;
 }
 
+// acc * v + c with one renormalisation (Horner step)
+__device__ __forceinline__ dd dd_horner(dd acc, dd v, float2 c) {
+  const float p = __fmul_rn(acc.hi, v.hi);
+  float e = __fmaf_rn(acc.hi, v.hi, -p);
+  e = __fmaf_rn(acc.hi, v.lo, e);
+  e = __fmaf_rn(acc.lo, v.hi, e);
+  float s, t;
+  two_sum(p, c.x, s, t);
+  t = __fadd_rn(t, __fadd_rn(e, c.y));
+  dd r;
+  quick_two_sum(s, t, r.hi, r.lo);
+  return r;
+}
+
+// The w stencil weights of one dimension from the kernel's per-offset
+// polynomials (coefficient k of offset t at coef[k * stride + t], df64).
+// The kernel is even, so offset w-1-t at v is offset t at -v: with
+// P_t(v) = E_t(v^2) + v O_t(v^2), weights t and w-1-t are E_t +- v O_t, and
+// only the first ceil(w/2) polynomials are evaluated, in v^2 (half the
+// Horner steps of evaluating all w).
+template <int W>
+__device__ __forceinline__ void dd_stencil_weights(const float2* coef, int stride, int nc, dd v, dd* w) {
+  constexpr int WH = (W + 1) / 2;
+  const dd v2 = dd_mul(v, v);
+  const int ke = (nc - 1) & ~1, ko = (nc - 2) | 1;  // highest even / odd power present
+  dd e[WH], o[WH];
+#pragma unroll
+  for (int t = 0; t < WH; ++t) {
+    e[t] = dd{coef[ke * stride + t].x, coef[ke * stride + t].y};
+    o[t] = dd{coef[ko * stride + t].x, coef[ko * stride + t].y};
+  }
+  for (int k = ke - 2; k >= 0; k -= 2) {
+#pragma unroll
+    for (int t = 0; t < WH; ++t) e[t] = dd_horner(e[t], v2, coef[k * stride + t]);
+  }
+  for (int k = ko - 2; k >= 1; k -= 2) {
+#pragma unroll
+    for (int t = 0; t < WH; ++t) o[t] = dd_horner(o[t], v2, coef[k * stride + t]);
+  }
+#pragma unroll
+  for (int t = 0; t < WH; ++t) {
+    const dd vo = dd_mul(v, o[t]);
+    w[t] = dd_add(e[t], vo);
+    if (W - 1 - t != t) w[W - 1 - t] = dd_sub(e[t], vo);
+  }
+}
+
 // ---- conversions (integer bit manipulation) ----
 
 // float with sign bit s, unbiased exponent e and a significand m whose leading

@@ -213,20 +213,6 @@ __global__ void gather_q_dd_kernel(const double* __restrict__ q, const int* __re
   q_s[k] = make_float2(v.hi, v.lo);
 }
 
-// acc * v + c with one renormalisation
-__device__ __forceinline__ dd horner_dd(dd acc, dd v, float2 c) {
-  const float p = __fmul_rn(acc.hi, v.hi);
-  float e = __fmaf_rn(acc.hi, v.hi, -p);
-  e = __fmaf_rn(acc.hi, v.lo, e);
-  e = __fmaf_rn(acc.lo, v.hi, e);
-  float s, t;
-  two_sum(p, c.x, s, t);
-  t = __fadd_rn(t, __fadd_rn(e, c.y));
-  dd r;
-  quick_two_sum(s, t, r.hi, r.lo);
-  return r;
-}
-
 // Stencil origin of a df64 patch coordinate u (see dd_stencil of the
 // interpolation): i0 = floor(u - W/2) + 1 and v = u - i0 - (W-1)/2.
 template <int W>
@@ -297,20 +283,10 @@ __global__ void __launch_bounds__(kSubDDThreads) spread_sub_dd_kernel(const __gr
       if (ok) {
         float2* out = wb + lane * WS;
         dd w[W];
-#pragma unroll
-        for (int t = 0; t < W; ++t) w[t] = dd{coef[(nc - 1) * W + t].x, coef[(nc - 1) * W + t].y};
-        for (int k = nc - 2; k >= 0; --k) {
-#pragma unroll
-          for (int t = 0; t < W; ++t) w[t] = horner_dd(w[t], vx, coef[k * W + t]);
-        }
+        dd_stencil_weights<W>(coef, W, nc, vx, w);
 #pragma unroll
         for (int t = 0; t < W; ++t) out[t] = make_float2(w[t].hi, w[t].lo);
-#pragma unroll
-        for (int t = 0; t < W; ++t) w[t] = dd{coef[(nc - 1) * W + t].x, coef[(nc - 1) * W + t].y};
-        for (int k = nc - 2; k >= 0; --k) {
-#pragma unroll
-          for (int t = 0; t < W; ++t) w[t] = horner_dd(w[t], vy, coef[k * W + t]);
-        }
+        dd_stencil_weights<W>(coef, W, nc, vy, w);
         const dd qd = dd{q.x, q.y};
 #pragma unroll
         for (int t = 0; t < W; ++t) {
@@ -338,11 +314,17 @@ __global__ void __launch_bounds__(kSubDDThreads) spread_sub_dd_kernel(const __gr
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
         if (cell[p] < 0) continue;
+        // cur += qwy * wx: the product's high part joins the sum through
+        // two-sum, its error terms and the sum's rounding go to the
+        // correction word (renormalised once, at the flush)
         const float2 wx = wrow[wxo[p]], qwy = wrow[wyo[p]];
-        const dd prod = dd_mul(dd{qwy.x, qwy.y}, dd{wx.x, wx.y});
+        const float ph = __fmul_rn(qwy.x, wx.x);
+        float pe = __fmaf_rn(qwy.x, wx.x, -ph);
+        pe = __fmaf_rn(qwy.x, wx.y, pe);
+        pe = __fmaf_rn(qwy.y, wx.x, pe);
         float s, t;
-        two_sum(cur[p].x, prod.hi, s, t);
-        cur[p].y = __fadd_rn(cur[p].y, __fadd_rn(t, prod.lo));
+        two_sum(cur[p].x, ph, s, t);
+        cur[p].y = __fadd_rn(cur[p].y, __fadd_rn(t, pe));
         cur[p].x = s;
       }
 #pragma unroll

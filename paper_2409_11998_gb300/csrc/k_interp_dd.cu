@@ -1,10 +1,10 @@
 // Type-2 interpolation of the FP64 plans in double-float arithmetic (Sec. 3,
 // Step 4): u(x) = sum over both history grids of the w x w stencil weights
 // times the grid values, which the df64 FFT chain left as (hi, lo) pairs.
-// The stencil weights are the plan's per-offset polynomials evaluated by
-// Horner's rule in df64 (coefficients split from the FP64 fit); products are
-// accumulated with error-free transforms and the three outputs are converted
-// to double once per target.
+// The stencil weights are the plan's per-offset polynomials (coefficients
+// split from the FP64 fit) evaluated in df64 through the kernel's symmetry
+// (dd_stencil_weights); products are accumulated with error-free transforms
+// and the three outputs are converted to double once per target.
 #include <cmath>
 
 #include "df64.cuh"
@@ -13,20 +13,6 @@
 namespace lpg {
 
 namespace {
-
-// acc * v + c with one renormalisation
-__device__ __forceinline__ dd dd_horner_step(dd acc, dd v, dd c) {
-  const float p = __fmul_rn(acc.hi, v.hi);
-  float e = __fmaf_rn(acc.hi, v.hi, -p);
-  e = __fmaf_rn(acc.hi, v.lo, e);
-  e = __fmaf_rn(acc.lo, v.hi, e);
-  float s, t;
-  two_sum(p, c.hi, s, t);
-  t = __fadd_rn(t, __fadd_rn(e, c.lo));
-  dd r;
-  quick_two_sum(s, t, r.hi, r.lo);
-  return r;
-}
 
 // Stencil origin i0 = floor(u - W/2) + 1 of a df64 grid coordinate, and the
 // offset v = u - i0 - (W-1)/2 in [-1/2, 1/2).
@@ -39,23 +25,6 @@ __device__ __forceinline__ bool dd_stencil(dd u, int g, int& i0, dd& v) {
   i0 = (int)f + 1;
   v = dd_add(u, dd{-((float)i0 + 0.5f * (W - 1)), 0.f});
   return i0 >= 0 && i0 + W <= g;
-}
-
-template <int W>
-__device__ __forceinline__ void dd_weights(const InterpDDArgs& a, dd v, dd* w) {
-  const int nc = a.nc;
-#pragma unroll
-  for (int t = 0; t < W; ++t) {
-    const float2 c = a.coef[nc - 1][t];
-    w[t] = dd{c.x, c.y};
-  }
-  for (int k = nc - 2; k >= 0; --k) {
-#pragma unroll
-    for (int t = 0; t < W; ++t) {
-      const float2 c = a.coef[k][t];
-      w[t] = dd_horner_step(w[t], v, dd{c.x, c.y});
-    }
-  }
 }
 
 template <int W>
@@ -76,8 +45,8 @@ __global__ void __launch_bounds__(128) interp_dd_kernel(const __grid_constant__ 
       continue;
     }
     dd wx[W], wy[W];
-    dd_weights<W>(a, vx, wx);
-    dd_weights<W>(a, vy, wy);
+    dd_stencil_weights<W>(&a.coef[0][0], kMaxW, a.nc, vx, wx);
+    dd_stencil_weights<W>(&a.coef[0][0], kMaxW, a.nc, vy, wy);
     // rows and channels stay rolled (wy spills to L1-resident local memory):
     // unrolling all w^2 C products overflows the instruction cache
 #pragma unroll 1
