@@ -52,6 +52,9 @@ def lib():
         _lib.oracle_smooth_charge.argtypes = [i64, vp, vp, i64, vp, d, vp]
         _lib.oracle_smooth_dipole.argtypes = [i64, vp, vp, vp, i64, vp, d, vp]
         _lib.oracle_gl_nodes.argtypes = [i32, vp]
+        _lib.oracle_gl_weights.argtypes = [i32, vp, vp]
+        _lib.oracle_local_dyadic.restype = i32
+        _lib.oracle_local_dyadic.argtypes = [i32, i32, vp, vp, vp, i64, vp, d, i32, d, i32, i32, vp, vp]
         _lib.oracle_local.restype = i32
         _lib.oracle_local.argtypes = [i32, i32, vp, vp, vp, i64, vp, vp, d, i32, d, vp, vp, vp, vp]
         _lib.oracle_frame.argtypes = [i32, i32, vp, vp, vp, i32, d, vp]
@@ -118,6 +121,30 @@ def local(bnd, sigma, mu, tgt_xy, jet, delta, order=5, on_tol=1e-12):
                             _p(jet), float(delta), int(order), float(on_tol), _p(VL), _p(SL),
                             _p(DL), _p(info))
     return VL, SL, DL, info, st
+
+
+def local_dyadic(bnd, sigma, mu, tgt_xy, delta, levels, order=5, on_tol=1e-12, m0=2):
+    """Local layer potentials with `levels` steps of dyadic refinement
+    (Sec. 4.4): the expansions at delta / 4^levels plus direct sums of the
+    difference kernels on panels split into m0 2^(j-1) intervals at level j.
+    Returns (SL, DL); either is None when its density is None."""
+    bxy = _c(bnd["xy"])
+    tgt_xy = _c(tgt_xy)
+    nt = len(tgt_xy)
+    sigma, mu = _c(sigma), _c(mu)
+    SL = np.zeros(nt) if sigma is not None else None
+    DL = np.zeros(nt) if mu is not None else None
+    lib().oracle_local_dyadic(int(bnd["n_panels"]), int(bnd["order"]), _p(bxy), _p(sigma), _p(mu), nt,
+                              _p(tgt_xy), float(delta), int(order), float(on_tol), int(levels), int(m0),
+                              _p(SL), _p(DL))
+    return SL, DL
+
+
+def gl_weights(p):
+    x = gl_nodes(p)
+    w = np.zeros(p)
+    lib().oracle_gl_weights(int(p), _p(x), _p(w))
+    return w
 
 
 def frame(bnd, sigma, mu, panel, t):

@@ -152,6 +152,21 @@ void gl_nodes(int p, double* x) {
   }
 }
 
+// Gauss-Legendre weights for the abscissae x[0..p-1]: 2 / ((1 - x^2) P_p'(x)^2).
+void gl_weights(int p, const double* x, double* w) {
+  for (int i = 0; i < p; ++i) {
+    const double z = x[i];
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= p; ++k) {
+      double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    const double dp = p * (z * p1 - p0) / (z * z - 1.0);
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
 struct Panels {
   int n_panels = 0, p = 0;
   const double* xy = nullptr;   // [n_panels*p][2]
@@ -412,6 +427,7 @@ void oracle_smooth_dipole(int64_t ns, const double* sxy, const double* nrm, cons
 }
 
 void oracle_gl_nodes(int p, double* x) { gl_nodes(p, x); }
+void oracle_gl_weights(int p, const double* x, double* w) { gl_weights(p, x, w); }
 
 // Expansion order p (3, 4 or 5): terms through delta^{(p-1)/2} are kept, so
 // the truncation error is O(delta^{p/2}) (Sec. 4; Sec. 6.1 uses p = 4, 5 and
@@ -520,6 +536,80 @@ int oracle_local(int n_panels, int p, const double* bxy, const double* sigma, co
     if (DL) DL[i] = dl;
   }
   return status;
+}
+
+// Dyadic refinement of the local layer potentials (Sec. 4.4).  With
+// delta_j = delta / 4^j (j = 0..J):
+//   S_L[delta] = S_L[delta_J] + sum_{j=1..J} int_Gamma (G_H[delta_j] - G_H[delta_{j-1}]) sigma ds
+//   D_L[delta] = D_L[delta_J] + sum_{j=1..J} int_Gamma d/dnu (G_H[delta_j] - G_H[delta_{j-1}]) mu ds
+// (S_L[delta] = S - S_H[delta] for every delta; G_H[delta_j] - G_H[delta_{j-1}]
+// is the smooth difference kernel (E1(4^{j-2} r) - E1(4^{j-1} r)) / (4 pi),
+// r = |x - x'|^2 / delta).  S_L[delta_J], D_L[delta_J] are the asymptotic
+// expansions of order `order`; each difference integral is a direct sum over
+// every panel split into m0 2^{j-1} equal parameter intervals of p
+// Gauss-Legendre nodes, with the panel's Lagrange interpolant giving the
+// position, |Gamma'|, the outward normal and sigma, mu at each node.
+// Outputs SL, DL (either may be NULL).
+int oracle_local_dyadic(int n_panels, int p, const double* bxy, const double* sigma, const double* mu,
+                        int64_t nt, const double* txy, double delta, int order, double on_tol, int J,
+                        int m0, double* SL, double* DL) {
+  const double delta_J = delta / std::pow(4.0, J);
+  int st = oracle_local(n_panels, p, bxy, sigma, mu, nt, txy, nullptr, delta_J, order, on_tol, nullptr, SL,
+                        DL, nullptr);
+  if (J <= 0) return st;
+  std::vector<double> tau(p), wgl(p);
+  gl_nodes(p, tau.data());
+  gl_weights(p, tau.data(), wgl.data());
+  for (int j = 1; j <= J; ++j) {
+    const double d_new = delta / std::pow(4.0, j), d_old = delta / std::pow(4.0, j - 1);
+    const int m = m0 << (j - 1);
+    // quadrature nodes of this level: position, outward normal, weight, densities
+    const int64_t nq = (int64_t)n_panels * m * p;
+    std::vector<double> qx(nq), qy(nq), qnx(nq), qny(nq), qw(nq), qs(nq), qm(nq);
+    for (int ip = 0; ip < n_panels; ++ip) {
+      const double* base = bxy + (size_t)ip * p * 2;
+      for (int k = 0; k < m; ++k)
+        for (int i = 0; i < p; ++i) {
+          const double t = -1.0 + (2.0 * k + 1.0 + tau[i]) / m;
+          double cx[2], cy[2];
+          lagrange_taylor(tau.data(), p, base, 2, t, 1, cx);
+          lagrange_taylor(tau.data(), p, base + 1, 2, t, 1, cy);
+          const double sp = std::hypot(cx[1], cy[1]);
+          const int64_t q = ((int64_t)ip * m + k) * p + i;
+          qx[q] = cx[0];
+          qy[q] = cy[0];
+          qnx[q] = cy[1] / sp;  // outward normal of a counter-clockwise curve
+          qny[q] = -cx[1] / sp;
+          qw[q] = sp * wgl[i] / m;
+          double v[1];
+          if (sigma) {
+            lagrange_taylor(tau.data(), p, sigma + (size_t)ip * p, 1, t, 0, v);
+            qs[q] = v[0];
+          }
+          if (mu) {
+            lagrange_taylor(tau.data(), p, mu + (size_t)ip * p, 1, t, 0, v);
+            qm[q] = v[0];
+          }
+        }
+    }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < nt; ++i) {
+      const double x = txy[2 * i], y = txy[2 * i + 1];
+      double s_acc = 0.0, d_acc = 0.0;
+      for (int64_t q = 0; q < nq; ++q) {
+        const double dx = x - qx[q], dy = y - qy[q];
+        const double r2 = dx * dx + dy * dy;
+        if (sigma) s_acc += (green_smooth(r2, d_new) - green_smooth(r2, d_old)) * qs[q] * qw[q];
+        if (mu)
+          d_acc += (green_smooth_dipole(dx, dy, qnx[q], qny[q], d_new) -
+                    green_smooth_dipole(dx, dy, qnx[q], qny[q], d_old)) *
+                   qm[q] * qw[q];
+      }
+      if (SL && sigma) SL[i] += s_acc;
+      if (DL && mu) DL[i] += d_acc;
+    }
+  }
+  return st;
 }
 
 // Frame quantities at a given foot (for tests): out = {kappa, g3, g4, s0, s1,
