@@ -60,7 +60,9 @@ typedef enum {
   LP_ERR_NOMEM = 3,          /* device allocation failed */
   LP_ERR_CUDA = 4,           /* a CUDA runtime or cuFFT call failed */
   LP_ERR_UNSUPPORTED = 5,    /* V requested at an exterior target within 12 sqrt(delta_1)
-                                of the boundary, where Sec. 4 gives no expansion */
+                                of the boundary, where Sec. 4 gives no expansion; or more
+                                than 32 panels near one target for dyadic refinement;
+                                or a refined plan passed to lp_batch_execute */
   LP_ERR_STATE = 6           /* call order violated (e.g. execute before lp_volume) */
 } lp_status;
 
@@ -85,6 +87,15 @@ typedef struct {
   const double* bnd_w;      /* [n_panels*panel_order] arc-length quadrature weights */
   const double* bnd_normal; /* [n_panels*panel_order][2] outward unit normals */
   void* stream;         /* cudaStream_t for all work of the plan */
+  int refine_levels;    /* dyadic refinement of the local layer potentials
+                           (Sec. 4.4): J in 0..6.  0: S_L, D_L from the
+                           expansions at delta.  J > 0: expansions at
+                           delta/4^J plus direct sums of the difference kernels
+                           G_H[delta/4^j] - G_H[delta/4^(j-1)], j = 1..J, over
+                           the panels split into 2^j Gauss-Legendre intervals;
+                           the expansion error falls by 4^(order/2) per level.
+                           V_L keeps delta.  Plans with J > 0 are not accepted
+                           by lp_batch_execute. */
 } lp_domain;
 
 /* Create a plan: chooses the near/far-history grids (Sec. 3: delta_2 =
@@ -184,7 +195,7 @@ lp_status lp_destroy(lp_plan_t plan);
 const char* lp_status_string(lp_status status);
 
 /* Plan parameters, for diagnostics and benchmarks:
- * out[0..22] = {delta_1, delta_2, kernel width w, beta, g_NH, K_NH, P_NH, g_FH, K_FH,
+ * out[0..25] = {delta_1, delta_2, kernel width w, beta, g_NH, K_NH, P_NH, g_FH, K_FH,
  *               P_FH, L_FH, band 12 sqrt(delta_1), node-gap margin, device bytes,
  *               precision, order, kernels launched by this plan so far,
  *               max error of the kernel's polynomial form, its coefficient count,
@@ -192,16 +203,19 @@ const char* lp_status_string(lp_status status);
  *               the library's own FFT kernels (for FP64 plans in double-float
  *               arithmetic, with the double-float interpolation), 0 for cuFFT,
  *               1 if volume sources are spread through bins, bin side in
- *               near-history cells}.  out must hold 23 doubles. */
+ *               near-history cells, dyadic refinement levels, largest error
+ *               of the refinement's kernel tables, refinement subnodes}.
+ *               out must hold 26 doubles. */
 lp_status lp_plan_info(lp_plan_t plan, double* out);
 
 /* Per-stage device times of the last lp_execute in milliseconds (CUDA events
- * on the plan's stream; valid after lp_sync): out[0..9] = {spread, forward
+ * on the plan's stream; valid after lp_sync): out[0..10] = {spread, forward
  * FFT, multiplier, inverse FFT, interpolation, local, total, copies, grid
- * zeroing, spread of the volume sources alone (part of out[0])}.  With the
+ * zeroing, spread of the volume sources alone (part of out[0]), difference
+ * sums of the dyadic refinement (0 without refinement)}.  With the
  * double-float transforms, "forward FFT" is the row transforms, "multiplier"
  * the fused column pass (forward transform, multiplier, inverse transform)
- * and "inverse FFT" the inverse row transforms.  out must hold 10 floats. */
+ * and "inverse FFT" the inverse row transforms.  out must hold 11 floats. */
 lp_status lp_stage_times(lp_plan_t plan, float* out);
 
 #ifdef __cplusplus

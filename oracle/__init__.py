@@ -170,9 +170,11 @@ def on_tolerance(problem):
     return 1e-12 * side
 
 
-def evaluate(problem, targets=None, order=5, want=("V", "S", "D")):
+def evaluate(problem, targets=None, order=5, want=("V", "S", "D"), refine_levels=0):
     """V, S, D at the problem's targets (or at the given subset of target
-    indices).  Returns a dict with totals and their smooth/local parts."""
+    indices).  Returns a dict with totals and their smooth/local parts.
+    With refine_levels > 0 the local parts of S and D are the dyadically
+    refined ones (Sec. 4.4); V keeps its plain local part."""
     delta = problem["delta"]
     idx = np.arange(len(problem["tgt_xy"])) if targets is None else np.asarray(targets)
     txy = problem["tgt_xy"][idx]
@@ -189,6 +191,9 @@ def evaluate(problem, targets=None, order=5, want=("V", "S", "D")):
     if mu is not None:
         out["DH"] = smooth_dipole(bnd["xy"], bnd["normal"], mu * bnd["w"], txy, delta)
     VL, SL, DL, info, st = local(bnd, sigma, mu, txy, jet, delta, order, on_tolerance(problem))
+    if refine_levels > 0 and (sigma is not None or mu is not None):
+        SL, DL = local_dyadic(bnd, sigma, mu, txy, delta, refine_levels, order=order,
+                              on_tol=on_tolerance(problem))
     if "V" in want:
         out["VL"] = VL
         out["V"] = out["VH"] + VL

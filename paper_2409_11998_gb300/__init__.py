@@ -40,7 +40,8 @@ class lp_domain(ctypes.Structure):
                 ("box_lo", ctypes.c_double * 2), ("box_hi", ctypes.c_double * 2),
                 ("n_panels", ctypes.c_int64), ("panel_order", ctypes.c_int),
                 ("bnd_xy", ctypes.c_void_p), ("bnd_w", ctypes.c_void_p),
-                ("bnd_normal", ctypes.c_void_p), ("stream", ctypes.c_void_p)]
+                ("bnd_normal", ctypes.c_void_p), ("stream", ctypes.c_void_p),
+                ("refine_levels", ctypes.c_int)]
 
 
 _LIB = None
@@ -105,7 +106,7 @@ def _ptr(a):
 
 
 def lp_plan(box_lo, box_hi, delta, tol, *, precision=LP_FP64, order=5, n_panels=0, panel_order=16,
-            bnd_xy=None, bnd_w=None, bnd_normal=None, stream=0):
+            bnd_xy=None, bnd_w=None, bnd_normal=None, stream=0, refine_levels=0):
     dom = lp_domain()
     dom.precision = int(precision)
     dom.order = int(order)
@@ -117,6 +118,7 @@ def lp_plan(box_lo, box_hi, delta, tol, *, precision=LP_FP64, order=5, n_panels=
     dom.bnd_w = _ptr(bnd_w)
     dom.bnd_normal = _ptr(bnd_normal)
     dom.stream = int(stream) if stream else None
+    dom.refine_levels = int(refine_levels)
     h = ctypes.c_void_p()
     _check(_lib().lp_plan(ctypes.byref(dom), float(delta), float(tol), ctypes.byref(h)), "lp_plan")
     return h
@@ -192,19 +194,20 @@ def lp_destroy(plan):
 
 
 def lp_plan_info(plan):
-    out = np.zeros(23)
+    out = np.zeros(26)
     _check(_lib().lp_plan_info(plan, out.ctypes.data), "lp_plan_info")
     keys = ["delta1", "delta2", "w", "beta", "g_nh", "K_nh", "P_nh", "g_fh", "K_fh", "P_fh", "L_fh",
             "band", "margin", "device_bytes", "precision", "order", "launches", "es_fit_err", "es_nc",
-            "sigma_eff", "own_fft", "binned", "bin_cells"]
+            "sigma_eff", "own_fft", "binned", "bin_cells", "refine_levels", "refine_table_err",
+            "refine_subnodes"]
     return dict(zip(keys, out.tolist()))
 
 
 def lp_stage_times(plan):
-    out = np.zeros(10, dtype=np.float32)
+    out = np.zeros(11, dtype=np.float32)
     _check(_lib().lp_stage_times(plan, out.ctypes.data), "lp_stage_times")
     keys = ["spread", "fft_fwd", "multiplier", "fft_inv", "interp", "local", "total", "copies", "zero",
-            "spread_volume"]
+            "spread_volume", "refine"]
     return dict(zip(keys, out.tolist()))
 
 
@@ -214,7 +217,7 @@ class Evaluator:
     ``host=True``, in which case the C ABI receives host pointers."""
 
     def __init__(self, problem, precision=None, order=5, tol=None, device="cuda", host=False,
-                 stream=None):
+                 stream=None, refine_levels=0):
         import torch
         self.torch = torch
         self.host = host
@@ -240,7 +243,8 @@ class Evaluator:
             kw = dict(n_panels=b["n_panels"], panel_order=b["order"], bnd_xy=dev(b["xy"]),
                       bnd_w=dev(b["w"]), bnd_normal=dev(b["normal"]))
         self.plan = lp_plan(problem["box_lo"], problem["box_hi"], problem["delta"], self.tol,
-                            precision=self.precision, order=order, stream=self.stream, **kw)
+                            precision=self.precision, order=order, stream=self.stream,
+                            refine_levels=refine_levels, **kw)
         self.problem = problem
 
     def bind(self, src_xy=None, src_w=None, src_f=None, sigma=None, mu=None):

@@ -159,7 +159,7 @@ __device__ __forceinline__ double far_volume(const LocalArgs& a, const double* J
 template <typename T>
 __device__ void local_near_one(const LocalArgs& a, int64_t i, int best) {
   const double x = a.txy[2 * i], y = a.txy[2 * i + 1];
-  const T dl = (T)a.delta;
+  const T dl = (T)a.delta_sd;  // S and D expansions (V uses a.delta)
   const double* J = a.jet ? a.jet + 6 * i : nullptr;
   T vl = 0, sl = 0, dlv = 0;
   bool far = false;
@@ -281,15 +281,24 @@ __device__ void local_near_one(const LocalArgs& a, int64_t i, int best) {
         const T fe = Jt[1] * Nx + Jt[2] * Ny;
         const T fxx = Jt[3] * Tx * Tx + T(2.0) * Jt[4] * Tx * Ty + Jt[5] * Ty * Ty;
         const T fee = Jt[3] * Nx * Nx + T(2.0) * Jt[4] * Nx * Ny + Jt[5] * Ny * Ny;
-        const T Ef = erf(T(0.5) * c);
-        T v = T(0.25) * dl * (T(2.0) * Ef + T(2.0) * c * Ex - c2 * Cc + T(2.0)) * f;
-        if (a.order >= 4) v += d15 * ((T(4.0) - T(2.0) * c2) * Ex + c3 * Cc) * (T(2.0) * fe - kap * f) / T(12.0);
+        // V keeps delta: the c-dependent factors again when refinement
+        // evaluates S and D at a smaller delta
+        const bool same = a.delta_sd == a.delta;
+        const T dv = (T)a.delta;
+        const T cv = same ? c : r / sqrt(dv);
+        const T d15v = same ? d15 : dv * sqrt(dv), d2v = dv * dv;
+        const T Exv = same ? Ex : exp(-T(0.25) * cv * cv) * T(0.56418958354775628695);
+        const T Ccv = same ? Cc : erfc(T(0.5) * cv);
+        const T c2v = cv * cv, c3v = c2v * cv;
+        const T Ef = erf(T(0.5) * cv);
+        T v = T(0.25) * dv * (T(2.0) * Ef + T(2.0) * cv * Exv - c2v * Ccv + T(2.0)) * f;
+        if (a.order >= 4) v += d15v * ((T(4.0) - T(2.0) * c2v) * Exv + c3v * Ccv) * (T(2.0) * fe - kap * f) / T(12.0);
         if (a.order >= 5) {
-          const T c4 = c2 * c2;
-          v += d2 / T(48.0) *
-               (Cc * (T(4.0) * c4 * kap * fe - T(3.0) * (c4 + T(4.0)) * fee + (c4 - T(12.0)) * fxx -
+          const T c4 = c2v * c2v;
+          v += d2v / T(48.0) *
+               (Ccv * (T(4.0) * c4 * kap * fe - T(3.0) * (c4 + T(4.0)) * fee + (c4 - T(12.0)) * fxx -
                       T(3.0) * c4 * kap * kap * f) +
-                T(2.0) * c * (c2 - T(2.0)) * Ex * (-T(4.0) * kap * fe + T(3.0) * fee - fxx + T(3.0) * kap * kap * f) +
+                T(2.0) * cv * (c2v - T(2.0)) * Exv * (-T(4.0) * kap * fe + T(3.0) * fee - fxx + T(3.0) * kap * kap * f) +
                 T(24.0) * (fxx + fee));
         }
         vl = v;
@@ -445,6 +454,7 @@ LocalArgs make_local_args(const Plan& P, int64_t nt, const double* txy, const do
   a.margin = P.margin;
   a.band = P.band;
   a.delta = P.delta1;
+  a.delta_sd = P.dy_levels > 0 ? P.delta1 / std::pow(4.0, P.dy_levels) : P.delta1;
   a.on_tol = P.on_tol;
   a.order = P.order;
   a.status = P.d_status;

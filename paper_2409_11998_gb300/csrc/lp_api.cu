@@ -147,7 +147,9 @@ void destroy_plan(Plan& P) {
                   P.d_sigma_ref, P.d_mu, P.d_mu_coef, P.d_mu_ref, P.d_bq, P.d_qsum, P.d_stage,
                   P.d_out, P.d_status, P.d_near, P.d_near_count, P.d_cell_xy32,
                   P.d_geo_coef32, P.d_keys, P.d_counts, P.d_cursor, P.d_vrel_s, P.d_vperm, P.d_vq_s,
-                  P.d_vstart, P.d_sigma_coef32, P.d_mu_coef32, P.d_vrel_dd, P.d_vq_dd};
+                  P.d_vstart, P.d_sigma_coef32, P.d_mu_coef32, P.d_vrel_dd, P.d_vq_dd,
+                  P.d_dy_tab, P.d_dy_rel, P.d_dy_nw, P.d_dy_sig, P.d_dy_mu,
+                  P.d_dy_rad, P.d_dy_wgl, P.d_dy_cell_start, P.d_dy_cell_panel};
   for (void* b : bufs) dfree(b);
   if (P.h_status) cudaFreeHost(P.h_status);
   for (auto& e : P.ev)
@@ -507,6 +509,7 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
         !std::isfinite(dom->box_hi[d]))
       return LP_ERR_ARG;
   if (dom->n_panels < 0) return LP_ERR_ARG;
+  if (dom->refine_levels < 0 || dom->refine_levels > kMaxDyLevels) return LP_ERR_ARG;
   if (dom->n_panels > 0) {
     if (dom->panel_order < 2 || dom->panel_order > kMaxPanelOrder) return LP_ERR_ARG;
     if (!dom->bnd_xy || !dom->bnd_w) return LP_ERR_ARG;
@@ -585,6 +588,7 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
     for (double v : hw) finite &= std::isfinite(v);
     if (!finite) st = LP_ERR_ARG;
     if (st == LP_OK) st = build_boundary(P, hxy.data(), hw.data(), hn.data());
+    if (st == LP_OK) st = setup_dyadic(P, dom->refine_levels);
   }
   if (st == LP_OK) st = setup_bins(P);
   if (st == LP_OK) st = setup_fft_chain(P);
@@ -677,6 +681,7 @@ static lp_status bind_layer(lp_plan_t h, const double* dens, int kind) {
   cudaMemcpyAsync(dst, d, P.nb * sizeof(double), cudaMemcpyDeviceToDevice, P.stream);
   launch_panel_coef(P, dst, 1, 1, kind == 0 ? P.d_sigma_coef : P.d_mu_coef,
                     kind == 0 ? P.d_sigma_ref : P.d_mu_ref, P.stream);
+  if (P.dy_levels > 0) launch_dyadic_dens(P, kind, P.stream);
   // single-precision copy for the local expansions (both precisions)
   launch_to_float(kind == 0 ? P.d_sigma_coef : P.d_mu_coef, kind == 0 ? P.d_sigma_coef32 : P.d_mu_coef32,
                   P.n_panels * P.p, P.stream);
@@ -809,6 +814,8 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
   }
   cudaEventRecord(P.ev[7], s);
   launch_local(P, nt, dt, dj, dout[0], dout[1], dout[2], s);
+  cudaEventRecord(P.ev[11], s);
+  launch_dyadic(P, nt, dt, dout[1], dout[2], P.d_near, P.d_near_count, s);
   cudaEventRecord(P.ev[8], s);
   for (int c = 0; c < 3; ++c)
     if (host_out[c]) cudaMemcpyAsync(outs[c], dout[c], nt * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -891,6 +898,8 @@ lp_status lp_execute_noalloc(lp_plan_t h, int64_t nt, const double* txy, const d
   launch_interp(P, nt, txy, V, S, D, s);
   cudaEventRecord(P.ev[7], s);
   launch_local_list(P, nt, txy, wv ? jet : nullptr, V, S, D, list, count, s);
+  cudaEventRecord(P.ev[11], s);
+  launch_dyadic(P, nt, txy, S, D, list, count, s);
   cudaEventRecord(P.ev[8], s);
   cudaEventRecord(P.ev[9], s);
   return status_from_cuda();
@@ -919,11 +928,12 @@ lp_status lp_destroy(lp_plan_t h) {
 lp_status lp_plan_info(lp_plan_t h, double* out) {
   if (!h || !out) return LP_ERR_ARG;
   const Plan& P = h->P;
-  double v[23] = {P.delta1, P.delta2, (double)P.ker.w, P.ker.beta, (double)P.lv[0].g, (double)P.lv[0].K,
+  double v[26] = {P.delta1, P.delta2, (double)P.ker.w, P.ker.beta, (double)P.lv[0].g, (double)P.lv[0].K,
                   P.lv[0].P, (double)P.lv[1].g, (double)P.lv[1].K, P.lv[1].P, P.lv[1].L, P.band,
                   P.margin, (double)P.device_bytes, (double)P.precision, (double)P.order,
                   (double)P.launches, P.es_fit_err, (double)P.es.nc, P.sigma_eff,
-                  P.own_fft ? 1.0 : 0.0, P.binned ? 1.0 : 0.0, (double)P.bin_cells};
+                  P.own_fft ? 1.0 : 0.0, P.binned ? 1.0 : 0.0, (double)P.bin_cells,
+                  (double)P.dy_levels, P.dy_err, (double)P.dy_nq};
   std::memcpy(out, v, sizeof(v));
   return LP_OK;
 }
@@ -932,7 +942,7 @@ lp_status lp_stage_times(lp_plan_t h, float* out) {
   if (!h || !out) return LP_ERR_ARG;
   Plan& P = h->P;
   // events: 0 start, 1 staged, 2 zeroed, 10 volume spread, 3 spread, 4 fwd,
-  // 5 mult, 6 inv, 7 interp, 8 local, 9 copies
+  // 5 mult, 6 inv, 7 interp, 11 local, 8 refinement sums, 9 copies
   auto el = [&](int a, int b) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, P.ev[a], P.ev[b]) != cudaSuccess) {
@@ -946,11 +956,12 @@ lp_status lp_stage_times(lp_plan_t h, float* out) {
   out[2] = el(4, 5);
   out[3] = el(5, 6);
   out[4] = el(6, 7);
-  out[5] = el(7, 8);
+  out[5] = el(7, 11);
   out[6] = el(0, 9);
   out[7] = el(0, 1) + el(8, 9);
   out[8] = el(1, 2);
   out[9] = el(2, 10);
+  out[10] = el(11, 8);
   return LP_OK;
 }
 

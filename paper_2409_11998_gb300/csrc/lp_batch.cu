@@ -106,6 +106,7 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
     if (!plans[i]) return LP_ERR_ARG;
     const Plan& P = plans[i]->P;
     if (P.precision != prec || P.ker.w != w) return LP_ERR_ARG;  // one kernel shape per wave
+    if (P.dy_levels > 0) return LP_ERR_UNSUPPORTED;              // refinement: lp_execute only
     for (int j = 0; j < i; ++j)
       if (plans[j] == plans[i]) return LP_ERR_ARG;  // a plan's grids serve one problem
     if (n_t[i] < 0 || n_t[i] > (int64_t)INT32_MAX) return LP_ERR_ARG;

@@ -24,8 +24,13 @@ constexpr int kSubDDThreads = 128;  // threads per CTA of the binned df64 spread
 // point-parallel spread).
 constexpr int sub_ncw(int w) { return w + 3; }
 constexpr int kMaxPanelOrder = 32;  // Gauss-Legendre nodes per boundary panel
-constexpr int kNumEvents = 11;
+constexpr int kNumEvents = 12;
 constexpr int kFftThreads = 256;    // threads per CTA of the df64 FFT kernels
+constexpr int kMaxDyLevels = 6;     // dyadic refinement levels of the local layer potentials
+constexpr int kDyPieces = 144;      // unit pieces of the difference-kernel tables, x in [0, 144)
+constexpr int kDyMaxDeg = 15;       // highest polynomial degree of a table piece
+constexpr int kDyTabVec = 5;        // float4 per table piece: c0..c3 as df64 pairs, c4..c15 as floats
+constexpr int kDyThreads = 256;     // threads per block of the refinement sums
 constexpr int kMaxFftStages = 24;   // radix stages of one df64 transform
 
 // Device status bits (OR-ed by kernels, read by lp_sync).
@@ -238,7 +243,35 @@ struct LocalArgs {
   const float* sig_coef32;   // FP32 copies of sig_coef / mu_coef (FP32 plans)
   const float* mu_coef32;
   double margin, band, delta, on_tol;
+  double delta_sd;  // delta of the S and D expansions (delta / 4^J with dyadic refinement)
   int order;
+  unsigned* status;
+};
+
+// Dyadic refinement sums over the band targets (k_dyadic.cu).
+struct DyadicArgs {
+  const double* txy;
+  double* out_s;
+  double* out_d;
+  const float2* sig_w;   // sigma * weight at the subnodes (df64), or null
+  const float2* mu;      // mu at the subnodes (df64), or null
+  const float4* rel;     // subnode offset from its panel's reference node (df64 x, y)
+  const float4* nw;      // outward normal times weight (df64 x, y)
+  const float4* tab;     // piecewise polynomials of F, then H (kDyTabVec float4 per piece)
+  int levels, p;
+  int64_t q_off[kMaxDyLevels];  // first subnode of each level
+  const double* geo_ref;
+  const float* panel_rad;  // panel radius about its reference node
+  // panels hashed by their reference node into cells of side >= range1 +
+  // the largest panel radius: every panel within range1 of a target lies in
+  // the 3x3 cells around it, each panel in exactly one cell
+  double hx0, hy0;
+  float inv_hh;           // 1 / cell side
+  int hnx, hny;
+  const int* cell_start;
+  const int* cell_panel;
+  float range1f;          // 12 sqrt(delta): the level-1 range
+  float2 inv_delta, inv_4pi, dcoef;  // 1/delta, 1/(4 pi), 1/(2 pi delta), df64
   unsigned* status;
 };
 
@@ -255,6 +288,23 @@ struct Plan {
   EsPoly<double> es{};
   EsPoly<float> es32{};
   float2 es_dd[kMaxNC][kMaxW] = {};  // es as df64 (hi, lo) pairs
+  // dyadic refinement (k_dyadic.cu): levels J, difference-kernel tables,
+  // subnodes of every level (offsets, normal x weight, densities)
+  int dy_levels = 0, dy_deg_f = 0, dy_deg_h = 0;  // levels; fitted table degrees
+  double dy_err = 0;
+  int64_t dy_q_off[kMaxDyLevels] = {};
+  int64_t dy_nq = 0;
+  float4* d_dy_tab = nullptr;
+  float4* d_dy_rel = nullptr;
+  float4* d_dy_nw = nullptr;
+  float2* d_dy_sig = nullptr;
+  float2* d_dy_mu = nullptr;
+  float* d_dy_rad = nullptr;
+  double* d_dy_wgl = nullptr;
+  double dy_hx0 = 0, dy_hy0 = 0, dy_hh = 0;
+  int dy_hnx = 0, dy_hny = 0;
+  int* d_dy_cell_start = nullptr;
+  int* d_dy_cell_panel = nullptr;
   bool own_fft = false;              // transforms run in this library's FFT chain (df64 for FP64 plans,
                                      // with the df64 interpolation), not cuFFT
   double es_fit_err = 0;
@@ -393,6 +443,10 @@ void launch_fft_rows_inv(const FftRowArgs& a, int nchan, bool f64, cudaStream_t 
 void launch_fft_cols(const FftColArgs& a, int njobs, bool f64, cudaStream_t s);
 void launch_split_table(const double* src, float2* dst, int64_t n, cudaStream_t s);
 void launch_interp_dd(const InterpDDArgs& a, int w, cudaStream_t s);
+lp_status setup_dyadic(Plan& P, int levels);
+void launch_dyadic_dens(const Plan& P, int kind, cudaStream_t s);
+void launch_dyadic(const Plan& P, int64_t nt, const double* txy, double* S, double* D, const int2* list,
+                   const int* count, cudaStream_t s);
 // pipeline pieces shared by lp_execute and lp_batch_execute (lp_api.cu)
 void spread_volume_binned(const Plan& P, int l, cudaStream_t s);
 void history_transforms(const Plan& P, bool wv, bool ws, bool wd, cudaStream_t s, bool events);

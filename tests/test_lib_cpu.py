@@ -72,6 +72,11 @@ def test_invalid_arguments_rejected_without_device(lib):
     dom.n_panels = 4
     dom.panel_order = 1
     assert L.lp_plan(ctypes.byref(dom), 1e-3, 1e-9, ctypes.byref(h)) == 1
+    dom.n_panels = 0
+    for levels in (-1, 7):  # dyadic refinement takes 0..6 levels
+        dom.refine_levels = levels
+        assert L.lp_plan(ctypes.byref(dom), 1e-3, 1e-9, ctypes.byref(h)) == 1
+    dom.refine_levels = 0
     for fn in (L.lp_sync, L.lp_destroy):
         assert fn(None) == 1
     assert L.lp_volume(None, 0, None, None, None) == 1
