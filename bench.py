@@ -50,7 +50,16 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline, fp32 and serving lines")
     ap.add_argument("--batch-size", type=int, default=256, help="problems per wave (--workload batch)")
     ap.add_argument("--serve-seconds", type=float, default=8.0, help="seconds per arrival rate (--workload serve)")
-    return ap.parse_args()
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
+                    help="plan precision of the timed line (fp64: tol 1e-9; fp32: tol 1e-5)")
+    ap.add_argument("--refine-levels", type=int, default=0,
+                    help="dyadic refinement levels of the local layer potentials (starfish/disk/square)")
+    args = ap.parse_args()
+    if args.refine_levels and args.workload in ("batch", "serve"):
+        ap.error("--refine-levels applies to the single-problem workloads (batched waves take unrefined plans)")
+    if not 0 <= args.refine_levels <= 6:
+        ap.error("--refine-levels takes 0..6")
+    return args
 
 
 def make_problem(name):
@@ -178,7 +187,9 @@ def run_lp(args, rank, world, local_rank):
     txy, jet = T(prob["tgt_xy"]), T(prob["tgt_jet"])
     outs = output_buffers(prob, nt, lambda: torch.empty(nt, dtype=torch.float64, device=dev))
     stream = torch.cuda.Stream(device=dev)
-    ev = lp.Evaluator(prob, precision="fp64", stream=stream.cuda_stream)
+    fp64 = args.precision == "fp64"
+    ev = lp.Evaluator(prob, precision=args.precision, tol=1e-9 if fp64 else 1e-5, stream=stream.cuda_stream,
+                      refine_levels=args.refine_levels)
     plan = ev.plan
 
     def step():
@@ -222,18 +233,17 @@ def run_lp(args, rank, world, local_rank):
     info = lp.lp_plan_info(plan)
     st = {k: statistics.mean(s[k] for s in stages) for k in stages[0]}
 
-    roof = roofline(info, st, nv, nb, nt, precision="fp64", n_out=sum(o is not None for o in outs),
+    roof = roofline(info, st, nv, nb, nt, precision=args.precision, n_out=sum(o is not None for o in outs),
                     workload=args.workload)
 
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "df64+f64" if (info.get("own_fft") and info.get("precision") == 0) else "f64",
-           "dtype_detail": ("volume spread, transforms, multiplier and interpolation in double-float "
-                            "(FP32 pairs, ~48-bit); boundary spread, local expansions and outputs in FP64")
-           if (info.get("own_fft") and info.get("precision") == 0) else "FP64 throughout",
+           "dtype": dtype_of(info),
+           "dtype_detail": dtype_detail(info),
            "data": "synthetic (seeded generators; no dataset)",
-           "config": {**describe(prob), "parallelism": "replicas" if world > 1 else "single",
+           "config": {**describe(prob), **refine_desc(args), "tol": ev.tol,
+                      "parallelism": "replicas" if world > 1 else "single",
                       "l2": "flushed by a 512 MiB write between timed steps, outside the step events",
                       "timing": "CUDA events on the plan stream around each step",
                       "grids": {"g_nh": int(info["g_nh"]), "g_fh": int(info["g_fh"]), "w": int(info["w"])}},
@@ -242,16 +252,17 @@ def run_lp(args, rank, world, local_rank):
            "clocks": clocks}
 
     if rank == 0 and not args.no_extras:
-        res["parity"] = parity_sample(prob, outs)
+        res["parity"] = parity_sample(prob, outs, refine_levels=args.refine_levels)
         res["e2e"] = run_e2e(args, prob, dev, ev, points)
-        res["fp32_same_workload"] = run_fp32(args, prob, dev, stream, points)
+        if fp64:
+            res["fp32_same_workload"] = run_fp32(args, prob, dev, stream, points)
         if args.workload == "starfish":
             from workloads import configs as _cfg
             small_pool = _cfg.serving_pool(n_meshes=6, t_min=10_000, t_max=300_000, seed=5300)
             res["served"] = run_serve(args, rank, world, local_rank, pool=small_pool, rates=(100, 400),
                                       seconds=3.0)
         if world == 1:
-            res["cpu_baseline"] = cpu_baseline(prob, budget_s=15.0)
+            res["cpu_baseline"] = cpu_baseline(prob, budget_s=15.0, refine_levels=args.refine_levels)
     ev.close()
     return res
 
@@ -351,11 +362,30 @@ def wanted(prob):
     return tuple(k for k, o in zip("VSD", output_buffers(prob, 0, lambda: 1)) if o is not None)
 
 
-def parity_sample(prob, outs, n=48):
+def dtype_of(info):
+    if info.get("precision") == 1:
+        return "f32 (FP64 zero mode)"
+    return "df64+f64" if info.get("own_fft") else "f64"
+
+
+def dtype_detail(info):
+    if info.get("precision") == 1:
+        return "FP32 arithmetic with FP64 foot search and outputs; tolerance 1e-5"
+    if info.get("own_fft"):
+        return ("volume spread, transforms, multiplier and interpolation in double-float (FP32 pairs, "
+                "~48-bit); boundary spread, local expansions and outputs in FP64")
+    return "FP64 throughout"
+
+
+def refine_desc(args):
+    return {"refine_levels": args.refine_levels} if args.refine_levels else {}
+
+
+def parity_sample(prob, outs, n=48, refine_levels=0):
     import numpy as np
     import oracle
     idx = np.random.default_rng(11).choice(len(prob["tgt_xy"]), n, replace=False)
-    ref = oracle.evaluate(prob, targets=idx, want=wanted(prob))
+    ref = oracle.evaluate(prob, targets=idx, want=wanted(prob), refine_levels=refine_levels)
     r = {}
     for k, o in zip("VSD", outs):
         if o is None:
@@ -390,19 +420,22 @@ def run_e2e(args, prob, dev, ev, points):
         lp.lp_execute(plan, nt, h["tgt_xy"], h["tgt_jet"], houts[0], houts[1], houts[2])
         lp.lp_sync(plan)
 
-    for _ in range(2):
+    for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
-    n = max(3, args.steps // 2)
-    t0 = time.perf_counter()
+    n = max(5, args.steps)
+    times = []
     for _ in range(n):
-        step()
-    torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / n
+        t0 = time.perf_counter()
+        step()                              # ends in lp_sync: the outputs are in host memory
+        times.append(time.perf_counter() - t0)
+    dt = statistics.median(times)
     h2d = sum(h[k].numel() * 8 for k in h)
     d2h = sum(o is not None for o in houts) * nt * 8
     return {"value": points / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3, "steps": n,
+            "statistic": "median host wall time per step (each step ends in lp_sync)",
+            "mean_ms_per_step": statistics.mean(times) * 1e3,
             "api": "lp_volume/lp_single_layer/lp_double_layer/lp_execute/lp_sync on pinned host buffers"}
 
 
@@ -412,7 +445,7 @@ def run_fp32(args, prob, dev, stream, points):
     import oracle
     import paper_2409_11998_gb300 as lp
     T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
-    ev = lp.Evaluator(prob, precision="fp32", tol=1e-5, stream=stream.cuda_stream)
+    ev = lp.Evaluator(prob, precision="fp32", tol=1e-5, stream=stream.cuda_stream, refine_levels=args.refine_levels)
     nv, nt = len(prob["src_w"]), len(prob["tgt_xy"])
     sxy, sw, sf, txy, jet = (T(prob[k]) for k in ("src_xy", "src_w", "src_f", "tgt_xy", "tgt_jet"))
     sig, mu = layer_densities(prob, T)
@@ -439,7 +472,7 @@ def run_fp32(args, prob, dev, stream, points):
         lp.lp_sync(plan)
         ms.append(a.elapsed_time(b))
     st = lp.lp_stage_times(plan)
-    par = parity_sample(prob, outs)
+    par = parity_sample(prob, outs, refine_levels=args.refine_levels)
     info = lp.lp_plan_info(plan)
     roof = roofline(info, st, nv, len(prob["bnd"]["w"]), nt, precision="fp32",
                     n_out=sum(o is not None for o in outs), workload=args.workload)
@@ -449,7 +482,7 @@ def run_fp32(args, prob, dev, stream, points):
             "stages_ms": {k: round(v, 4) for k, v in st.items()}, "parity": par, "roofline": roof}
 
 
-def cpu_baseline(prob, budget_s=15.0):
+def cpu_baseline(prob, budget_s=15.0, refine_levels=0):
     """The oracle as it stands, on the host cores, on a bounded sample of
     targets; extrapolated to the workload's points/s."""
     import numpy as np
@@ -462,7 +495,7 @@ def cpu_baseline(prob, budget_s=15.0):
     while True:
         idx = rng.choice(nt, n, replace=False)
         t0 = time.perf_counter()
-        oracle.evaluate(prob, targets=idx)
+        oracle.evaluate(prob, targets=idx, refine_levels=refine_levels)
         dt = time.perf_counter() - t0
         if dt > budget_s / 4 or n >= nt:
             break
@@ -604,16 +637,16 @@ def run_reference(args, rank, world):
     per_step = max(0.3, 120.0 / (args.steps + args.warmup))
     n = 16
     t0 = time.perf_counter()
-    oracle.evaluate(prob, targets=rng.choice(nt, n, replace=False))
+    oracle.evaluate(prob, targets=rng.choice(nt, n, replace=False), refine_levels=args.refine_levels)
     per_target = (time.perf_counter() - t0) / n
     n = int(min(nt, max(8, per_step / max(per_target, 1e-9))))
     for _ in range(args.warmup):
-        oracle.evaluate(prob, targets=rng.choice(nt, n, replace=False))
+        oracle.evaluate(prob, targets=rng.choice(nt, n, replace=False), refine_levels=args.refine_levels)
     times = []
     for _ in range(args.steps):
         idx = rng.choice(nt, n, replace=False)
         t0 = time.perf_counter()
-        oracle.evaluate(prob, targets=idx)
+        oracle.evaluate(prob, targets=idx, refine_levels=args.refine_levels)
         times.append(time.perf_counter() - t0)
     dt = statistics.mean(times)
     t_full = dt / n * nt
@@ -622,7 +655,7 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded generators; no dataset)",
-            "config": {**describe(prob), "parallelism": "host cores (OpenMP over targets)"},
+            "config": {**describe(prob), **refine_desc(args), "parallelism": "host cores (OpenMP over targets)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
                              "kind": "oracle",
                              "sample": f"{n} random targets per step (all {len(prob['src_w'])} sources "

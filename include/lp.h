@@ -60,13 +60,16 @@ typedef enum {
   LP_ERR_NOMEM = 3,          /* device allocation failed */
   LP_ERR_CUDA = 4,           /* a CUDA runtime or cuFFT call failed */
   LP_ERR_UNSUPPORTED = 5,    /* V requested at an exterior target within 12 sqrt(delta_1)
-                                of the boundary, where Sec. 4 gives no expansion; or more
-                                than 32 panels near one target for dyadic refinement;
-                                or a refined plan passed to lp_batch_execute */
+                                of the boundary, where Sec. 4 gives no expansion; or a
+                                refined plan passed to lp_batch_execute */
   LP_ERR_STATE = 6           /* call order violated (e.g. execute before lp_volume) */
 } lp_status;
 
 enum { LP_FP64 = 0, LP_FP32 = 1 };
+
+/* lp_domain.refine_levels: choose the number of refinement levels from the
+ * plan's tolerance and expansion order (Sec. 4.4). */
+#define LP_REFINE_AUTO (-1)
 
 typedef struct {
   int precision;        /* LP_FP64: tolerances down to ~1e-12.  The volume spread,
@@ -88,14 +91,17 @@ typedef struct {
   const double* bnd_normal; /* [n_panels*panel_order][2] outward unit normals */
   void* stream;         /* cudaStream_t for all work of the plan */
   int refine_levels;    /* dyadic refinement of the local layer potentials
-                           (Sec. 4.4): J in 0..6.  0: S_L, D_L from the
-                           expansions at delta.  J > 0: expansions at
-                           delta/4^J plus direct sums of the difference kernels
-                           G_H[delta/4^j] - G_H[delta/4^(j-1)], j = 1..J, over
-                           the panels split into 2^j Gauss-Legendre intervals;
-                           the expansion error falls by 4^(order/2) per level.
-                           V_L keeps delta.  Plans with J > 0 are not accepted
-                           by lp_batch_execute. */
+                           (Sec. 4.4): J in 0..6, or LP_REFINE_AUTO.  0: S_L,
+                           D_L from the expansions at delta.  J > 0: expansions
+                           at delta/4^J plus direct sums of the difference
+                           kernels G_H[delta/4^j] - G_H[delta/4^(j-1)],
+                           j = 1..J, over the panels split into 2^j
+                           Gauss-Legendre intervals; the expansion error falls
+                           by 4^(order/2) per level.  LP_REFINE_AUTO: the
+                           smallest J with (delta/4^J)^(order/2) <= tol (the
+                           selection rule of Sec. 4.4), at most 6.  V_L keeps
+                           delta.  Plans with J > 0 are not accepted by
+                           lp_batch_execute. */
 } lp_domain;
 
 /* Create a plan: chooses the near/far-history grids (Sec. 3: delta_2 =

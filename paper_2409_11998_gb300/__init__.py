@@ -21,6 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "liblp.so")
 
 LP_FP64, LP_FP32 = 0, 1
+LP_REFINE_AUTO = -1  # refine_levels: levels from tol and order (Sec. 4.4)
 STATUS = {0: "LP_OK", 1: "LP_ERR_ARG", 2: "LP_ERR_OUT_OF_BOX", 3: "LP_ERR_NOMEM",
           4: "LP_ERR_CUDA", 5: "LP_ERR_UNSUPPORTED", 6: "LP_ERR_STATE"}
 EXPORTS = ("lp_plan", "lp_volume", "lp_single_layer", "lp_double_layer", "lp_execute", "lp_sync",
@@ -118,7 +119,7 @@ def lp_plan(box_lo, box_hi, delta, tol, *, precision=LP_FP64, order=5, n_panels=
     dom.bnd_w = _ptr(bnd_w)
     dom.bnd_normal = _ptr(bnd_normal)
     dom.stream = int(stream) if stream else None
-    dom.refine_levels = int(refine_levels)
+    dom.refine_levels = LP_REFINE_AUTO if refine_levels == "auto" else int(refine_levels)
     h = ctypes.c_void_p()
     _check(_lib().lp_plan(ctypes.byref(dom), float(delta), float(tol), ctypes.byref(h)), "lp_plan")
     return h

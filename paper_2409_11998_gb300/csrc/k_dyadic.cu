@@ -226,8 +226,11 @@ __device__ __forceinline__ void level_sums(const DyadicArgs& a, const float4* __
     const V xv = A::mul(A::dot2(dx, dx, dy, dy), xs);
     const float xh = A::hi(xv);
     if (!(xh < (float)kDyPieces)) continue;
-    const int k = min(max((int)xh, 0), kDyPieces - 1);
-    const V s = A::sub(xv, A::make((float)k + 0.5f, 0.f));
+    // floor(xh) for 0 <= xh < 2^22 without conversion instructions: adding
+    // 2^23 rounded down leaves floor(xh) in the low mantissa bits
+    const float fl = __fadd_rd(fmaxf(xh, 0.f), 8388608.f);
+    const int k = __float_as_int(fl) - 0x4B000000;
+    const V s = A::sub(xv, A::make(__fsub_rn(fl, 8388608.f) + 0.5f, 0.f));
     if (a.sig_w) {
       const float2 sw = __ldg(a.sig_w + q);
       A::fma(s_acc, A::poly(tab + k * kDyTabVec, s), A::make(sw.x, sw.y));
@@ -247,7 +250,7 @@ __device__ __forceinline__ void level_sums(const DyadicArgs& a, const float4* __
 // the 3x3 hash cells around the target (each lane one panel: how many levels
 // reach the target), then the warp walks the surviving panels together.
 template <class A>
-__global__ void __launch_bounds__(kDyThreads) dyadic_kernel(const __grid_constant__ DyadicArgs a,
+__global__ void __launch_bounds__(kDyThreads, 4) dyadic_kernel(const __grid_constant__ DyadicArgs a,
                                                             const int2* __restrict__ list,
                                                             const int* __restrict__ count) {
   using V = typename A::V;
@@ -259,11 +262,12 @@ __global__ void __launch_bounds__(kDyThreads) dyadic_kernel(const __grid_constan
   const int warps = gridDim.x * (blockDim.x >> 5);
   for (int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); idx < n_near; idx += warps) {
     const int64_t i = list[idx].x;
-    const double x = a.txy[2 * i], y = a.txy[2 * i + 1];
+    // the target as df64 (integer conversion): FP64 runs at 1/58 of the FP32
+    // rate on this part, so the per-target work avoids it
+    const dd X = dd_from_double(a.txy[2 * i]), Y = dd_from_double(a.txy[2 * i + 1]);
     // cell index in single precision (the cells carry a relative slack of
-    // 1e-4 for this), clamped before the integer conversion; FP64 runs at
-    // 1/58 of the FP32 rate, so the per-target work avoids it
-    const float ux = dd_from_double(x - a.hx0).hi * a.inv_hh, uy = dd_from_double(y - a.hy0).hi * a.inv_hh;
+    // 1e-4 for this), clamped before the integer conversion
+    const float ux = (X.hi - a.hx0) * a.inv_hh, uy = (Y.hi - a.hy0) * a.inv_hh;
     const int cx = (int)fminf(fmaxf(floorf(ux), -2.f), (float)a.hnx + 1.f);
     const int cy = (int)fminf(fmaxf(floorf(uy), -2.f), (float)a.hny + 1.f);
     typename A::Acc s_acc = A::zero(), d_acc = A::zero();
@@ -277,8 +281,9 @@ __global__ void __launch_bounds__(kDyThreads) dyadic_kernel(const __grid_constan
         dd tdx = dd{0.f, 0.f}, tdy = dd{0.f, 0.f};
         if (k < k1) {
           ip = a.cell_panel[k];
-          tdx = dd_from_double(x - a.geo_ref[2 * ip]);
-          tdy = dd_from_double(y - a.geo_ref[2 * ip + 1]);
+          const float4 r = __ldg(a.ref_dd + ip);
+          tdx = dd_sub(X, dd{r.x, r.y});
+          tdy = dd_sub(Y, dd{r.z, r.w});
           const float d = sqrtf(tdx.hi * tdx.hi + tdy.hi * tdy.hi) - a.panel_rad[ip];
           for (int j = 1; j <= a.levels; ++j) {
             if (d > a.range1f * pow2f(1 - j) * 1.0001f) break;  // ranges shrink with j
@@ -464,6 +469,7 @@ lp_status setup_dyadic(Plan& P, int levels) {
   // per-panel radius about the reference node (for the range test)
   std::vector<double> hxy(P.nb * 2), href(P.n_panels * 2), rad(P.n_panels, 0.0);
   std::vector<float> radf(P.n_panels);
+  std::vector<float4> refdd(P.n_panels);
   cudaMemcpy(hxy.data(), P.d_bxy, hxy.size() * sizeof(double), cudaMemcpyDeviceToHost);
   cudaMemcpy(href.data(), P.d_geo_ref, href.size() * sizeof(double), cudaMemcpyDeviceToHost);
   for (int64_t ip = 0; ip < P.n_panels; ++ip) {
@@ -473,6 +479,8 @@ lp_status setup_dyadic(Plan& P, int levels) {
     }
     rad[ip] *= 1.05;  // the interpolant between nodes bulges slightly
     radf[ip] = (float)rad[ip];
+    const float rx = (float)href[2 * ip], ry = (float)href[2 * ip + 1];
+    refdd[ip] = make_float4(rx, (float)(href[2 * ip] - rx), ry, (float)(href[2 * ip + 1] - ry));
   }
   // panel hash: reference nodes into cells of side >= range1 + max radius
   {
@@ -526,9 +534,11 @@ lp_status setup_dyadic(Plan& P, int levels) {
       !dalloc_((void**)&P.d_dy_sig, total * sizeof(float2)) ||
       !dalloc_((void**)&P.d_dy_mu, total * sizeof(float2)) ||
       !dalloc_((void**)&P.d_dy_rad, P.n_panels * sizeof(float)) ||
+      !dalloc_((void**)&P.d_dy_ref, P.n_panels * sizeof(float4)) ||
       !dalloc_((void**)&P.d_dy_wgl, P.p * sizeof(double)))
     return LP_ERR_NOMEM;
   cudaMemcpy(P.d_dy_rad, radf.data(), radf.size() * sizeof(float), cudaMemcpyHostToDevice);
+  cudaMemcpy(P.d_dy_ref, refdd.data(), refdd.size() * sizeof(float4), cudaMemcpyHostToDevice);
   cudaMemcpy(P.d_dy_wgl, wgl.data(), wgl.size() * sizeof(double), cudaMemcpyHostToDevice);
   for (int j = 1; j <= levels; ++j) {
     const int m = 1 << j;
@@ -568,11 +578,11 @@ void launch_dyadic(const Plan& P, int64_t nt, const double* txy, double* S, doub
   a.tab = P.d_dy_tab;
   a.levels = P.dy_levels;
   for (int j = 0; j < P.dy_levels; ++j) a.q_off[j] = P.dy_q_off[j];
-  a.geo_ref = P.d_geo_ref;
+  a.ref_dd = P.d_dy_ref;
   a.panel_rad = P.d_dy_rad;
   a.p = P.p;
-  a.hx0 = P.dy_hx0;
-  a.hy0 = P.dy_hy0;
+  a.hx0 = (float)P.dy_hx0;
+  a.hy0 = (float)P.dy_hy0;
   a.inv_hh = (float)(1.0 / P.dy_hh);
   a.hnx = P.dy_hnx;
   a.hny = P.dy_hny;

@@ -85,11 +85,11 @@ void dfree(void* p) {
 
 // Device view of a caller array: used in place when it is device memory,
 // otherwise copied into plan-owned staging at byte offset *off.
-const double* device_view(Plan& P, const double* src, size_t count, size_t* off) {
+const double* device_view(Plan& P, const double* src, size_t count, size_t* off, cudaStream_t s) {
   if (!src || count == 0) return src;
   if (is_device_ptr(src)) return src;
   double* dst = (double*)((char*)P.d_stage + *off);
-  cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyHostToDevice, P.stream);
+  cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyHostToDevice, s);
   *off += ((count * sizeof(double) + 255) / 256) * 256;
   return dst;
 }
@@ -130,6 +130,7 @@ lp_status make_fft_plans(Plan& P, GridLevel& G) {
 }
 
 void destroy_plan(Plan& P) {
+  if (P.copy_stream) cudaStreamSynchronize(P.copy_stream);
   if (P.stream) cudaStreamSynchronize(P.stream);
   for (auto& G : P.lv) {
     for (auto& c : G.chan) dfree(c);
@@ -149,11 +150,14 @@ void destroy_plan(Plan& P) {
                   P.d_geo_coef32, P.d_keys, P.d_counts, P.d_cursor, P.d_vrel_s, P.d_vperm, P.d_vq_s,
                   P.d_vstart, P.d_sigma_coef32, P.d_mu_coef32, P.d_vrel_dd, P.d_vq_dd,
                   P.d_dy_tab, P.d_dy_rel, P.d_dy_nw, P.d_dy_sig, P.d_dy_mu,
-                  P.d_dy_rad, P.d_dy_wgl, P.d_dy_cell_start, P.d_dy_cell_panel};
+                  P.d_dy_rad, P.d_dy_wgl, P.d_dy_cell_start, P.d_dy_cell_panel, P.d_dy_ref};
   for (void* b : bufs) dfree(b);
   if (P.h_status) cudaFreeHost(P.h_status);
   for (auto& e : P.ev)
     if (e) cudaEventDestroy(e);
+  if (P.ev_in) cudaEventDestroy(P.ev_in);
+  if (P.ev_staged) cudaEventDestroy(P.ev_staged);
+  if (P.copy_stream) cudaStreamDestroy(P.copy_stream);
 }
 
 lp_status status_from_cuda() {
@@ -495,6 +499,16 @@ const char* lp_status_string(lp_status s) {
   return "unknown status";
 }
 
+// Refinement levels of a plan: explicit, or (LP_REFINE_AUTO) the smallest J
+// with (delta/4^J)^(order/2) <= tol, the selection rule of Sec. 4.4 for an
+// expansion whose error is O(delta^(order/2)), capped at kMaxDyLevels.
+static int refine_levels_for(int requested, double delta, double tol, int order) {
+  if (requested != LP_REFINE_AUTO) return requested;
+  int J = 0;
+  while (J < kMaxDyLevels && std::pow(delta / std::pow(4.0, J), 0.5 * order) > tol) ++J;
+  return J;
+}
+
 lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out) {
   if (!dom || !out) return LP_ERR_ARG;
   *out = nullptr;
@@ -509,7 +523,7 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
         !std::isfinite(dom->box_hi[d]))
       return LP_ERR_ARG;
   if (dom->n_panels < 0) return LP_ERR_ARG;
-  if (dom->refine_levels < 0 || dom->refine_levels > kMaxDyLevels) return LP_ERR_ARG;
+  if (dom->refine_levels < LP_REFINE_AUTO || dom->refine_levels > kMaxDyLevels) return LP_ERR_ARG;
   if (dom->n_panels > 0) {
     if (dom->panel_order < 2 || dom->panel_order > kMaxPanelOrder) return LP_ERR_ARG;
     if (!dom->bnd_xy || !dom->bnd_w) return LP_ERR_ARG;
@@ -588,7 +602,7 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
     for (double v : hw) finite &= std::isfinite(v);
     if (!finite) st = LP_ERR_ARG;
     if (st == LP_OK) st = build_boundary(P, hxy.data(), hw.data(), hn.data());
-    if (st == LP_OK) st = setup_dyadic(P, dom->refine_levels);
+    if (st == LP_OK) st = setup_dyadic(P, refine_levels_for(dom->refine_levels, delta, tol, order));
   }
   if (st == LP_OK) st = setup_bins(P);
   if (st == LP_OK) st = setup_fft_chain(P);
@@ -620,9 +634,9 @@ lp_status lp_volume(lp_plan_t h, int64_t n, const double* xy, const double* w, c
     if (!ensure_stage(P, round256(n * 2 * sizeof(double)) + 2 * round256(n * sizeof(double))))
       return LP_ERR_NOMEM;
     size_t off = 0;
-    const double* dxy = device_view(P, xy, n * 2, &off);
-    const double* dw = device_view(P, w, n, &off);
-    const double* df = device_view(P, f, n, &off);
+    const double* dxy = device_view(P, xy, n * 2, &off, P.stream);
+    const double* dw = device_view(P, w, n, &off, P.stream);
+    const double* df = device_view(P, f, n, &off, P.stream);
     cudaMemcpyAsync(P.d_vxy, dxy, n * 2 * sizeof(double), cudaMemcpyDeviceToDevice, P.stream);
     launch_volume_q(P, df, dw, P.d_vq, n, P.stream);
   }
@@ -676,7 +690,7 @@ static lp_status bind_layer(lp_plan_t h, const double* dens, int kind) {
   if (P.nb == 0) return LP_ERR_STATE;
   if (!ensure_stage(P, round256(P.nb * sizeof(double)))) return LP_ERR_NOMEM;
   size_t off = 0;
-  const double* d = device_view(P, dens, P.nb, &off);
+  const double* d = device_view(P, dens, P.nb, &off, P.stream);
   double* dst = kind == 0 ? P.d_sigma : P.d_mu;
   cudaMemcpyAsync(dst, d, P.nb * sizeof(double), cudaMemcpyDeviceToDevice, P.stream);
   launch_panel_coef(P, dst, 1, 1, kind == 0 ? P.d_sigma_coef : P.d_mu_coef,
@@ -737,9 +751,27 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
   }
   if (!P.d_near_count && !dalloc(P, (void**)&P.d_near_count, sizeof(int))) return LP_ERR_NOMEM;
   cudaEventRecord(P.ev[0], s);
+  // Host targets and jets are copied on the plan's copy stream, overlapping
+  // the spreads and transforms; the staging buffer is free once the work
+  // already queued on the plan's stream has run, and the interpolation
+  // waits for the copies.
+  const bool host_in = !is_device_ptr(txy) || (wv && !is_device_ptr(jet));
+  cudaStream_t cs = s;
+  if (host_in) {
+    if (!P.copy_stream) {
+      if (cudaStreamCreateWithFlags(&P.copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&P.ev_in, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&P.ev_staged, cudaEventDisableTiming) != cudaSuccess)
+        return LP_ERR_CUDA;
+    }
+    cudaEventRecord(P.ev_in, s);
+    cudaStreamWaitEvent(P.copy_stream, P.ev_in, 0);
+    cs = P.copy_stream;
+  }
   size_t off = 0;
-  const double* dt = device_view(P, txy, nt * 2, &off);
-  const double* dj = wv ? device_view(P, jet, nt * 6, &off) : nullptr;
+  const double* dt = device_view(P, txy, nt * 2, &off, cs);
+  const double* dj = wv ? device_view(P, jet, nt * 6, &off, cs) : nullptr;
+  if (host_in) cudaEventRecord(P.ev_staged, cs);
   double* dout[3];
   for (int c = 0; c < 3; ++c) dout[c] = host_out[c] ? P.d_out + c * nt : outs[c];
   cudaEventRecord(P.ev[1], s);
@@ -790,6 +822,7 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
   cudaEventRecord(P.ev[3], s);
   if (P.own_fft) {
     history_transforms(P, wv, ws, wd, s, true);
+    if (host_in) cudaStreamWaitEvent(s, P.ev_staged, 0);
     history_interp(P, nt, dt, dout, s);
   } else {
     for (int l = 0; l < 2; ++l) {
@@ -810,6 +843,7 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
       if (wd) fft_inverse(P, l, 2);
     }
     cudaEventRecord(P.ev[6], s);
+    if (host_in) cudaStreamWaitEvent(s, P.ev_staged, 0);
     launch_interp(P, nt, dt, dout[0], dout[1], dout[2], s);
   }
   cudaEventRecord(P.ev[7], s);

@@ -260,12 +260,12 @@ struct DyadicArgs {
   const float4* tab;     // piecewise polynomials of F, then H (kDyTabVec float4 per piece)
   int levels, p;
   int64_t q_off[kMaxDyLevels];  // first subnode of each level
-  const double* geo_ref;
+  const float4* ref_dd;    // panel reference node (df64 x, y)
   const float* panel_rad;  // panel radius about its reference node
   // panels hashed by their reference node into cells of side >= range1 +
   // the largest panel radius: every panel within range1 of a target lies in
   // the 3x3 cells around it, each panel in exactly one cell
-  double hx0, hy0;
+  float hx0, hy0;         // grid origin (single precision suffices for cells)
   float inv_hh;           // 1 / cell side
   int hnx, hny;
   const int* cell_start;
@@ -300,6 +300,7 @@ struct Plan {
   float2* d_dy_sig = nullptr;
   float2* d_dy_mu = nullptr;
   float* d_dy_rad = nullptr;
+  float4* d_dy_ref = nullptr;
   double* d_dy_wgl = nullptr;
   double dy_hx0 = 0, dy_hy0 = 0, dy_hh = 0;
   int dy_hnx = 0, dy_hny = 0;
@@ -377,6 +378,10 @@ struct Plan {
   unsigned* d_status = nullptr;
   unsigned* h_status = nullptr;  // pinned
   cudaEvent_t ev[kNumEvents] = {};
+  // host targets are staged on a second stream while the spreads and
+  // transforms run (created at the first execute with host inputs)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_staged = nullptr;
   size_t device_bytes = 0;
   mutable long long launches = 0;  // kernels launched by this plan (all calls)
 };

@@ -131,3 +131,18 @@ def test_refined_plan_rejected_by_batch_and_served_by_noalloc(lp):
         lp.lp_batch_execute(b, [ev.plan], [n], [t], [j], [None], o, [None])
     lp.lp_batch_destroy(b)
     ev.close()
+
+
+@pytest.mark.parametrize("order,tol,delta,want", [(3, 1e-8, 4e-3, 5), (5, 1e-9, 8e-6, 0), (3, 1e-9, 8e-6, 2),
+                                                  (3, 1e-12, 4e-3, 6)])
+def test_automatic_levels(lp, order, tol, delta, want):
+    """refine_levels="auto": the smallest J with (delta/4^J)^(order/2) <= tol,
+    at most 6 (the selection rule of Sec. 4.4)."""
+    p = _circle(delta=delta, n_targets=10)
+    ev = lp.Evaluator(p, precision="fp64", tol=tol, order=order, refine_levels="auto")
+    assert ev.info()["refine_levels"] == want
+    J = 0
+    while J < 6 and (delta / 4 ** J) ** (order / 2) > tol:
+        J += 1
+    assert J == want
+    ev.close()

@@ -73,7 +73,7 @@ def test_invalid_arguments_rejected_without_device(lib):
     dom.panel_order = 1
     assert L.lp_plan(ctypes.byref(dom), 1e-3, 1e-9, ctypes.byref(h)) == 1
     dom.n_panels = 0
-    for levels in (-1, 7):  # dyadic refinement takes 0..6 levels
+    for levels in (-2, 7):  # dyadic refinement takes 0..6 levels or LP_REFINE_AUTO (-1)
         dom.refine_levels = levels
         assert L.lp_plan(ctypes.byref(dom), 1e-3, 1e-9, ctypes.byref(h)) == 1
     dom.refine_levels = 0
