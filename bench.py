@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=8.0, help="seconds per arrival rate (--workload serve)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                     help="plan precision of the timed line (fp64: tol 1e-9; fp32: tol 1e-5)")
+    ap.add_argument("--levels", default="auto", choices=["auto", "1", "2"],
+                    help="history levels of every plan (auto: one level when its grid side is <= 1536)")
     ap.add_argument("--refine-levels", type=int, default=0,
                     help="dyadic refinement levels of the local layer potentials (starfish/disk/square)")
     args = ap.parse_args()
@@ -189,7 +191,7 @@ def run_lp(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     fp64 = args.precision == "fp64"
     ev = lp.Evaluator(prob, precision=args.precision, tol=1e-9 if fp64 else 1e-5, stream=stream.cuda_stream,
-                      refine_levels=args.refine_levels)
+                      refine_levels=args.refine_levels, levels=levels_arg(args))
     plan = ev.plan
 
     def step():
@@ -242,7 +244,7 @@ def run_lp(args, rank, world, local_rank):
            "dtype": dtype_of(info),
            "dtype_detail": dtype_detail(info),
            "data": "synthetic (seeded generators; no dataset)",
-           "config": {**describe(prob), **refine_desc(args), "tol": ev.tol,
+           "config": {**describe(prob), **refine_desc(args), "tol": ev.tol, "levels": int(info["levels"]),
                       "parallelism": "replicas" if world > 1 else "single",
                       "l2": "flushed by a 512 MiB write between timed steps, outside the step events",
                       "timing": "CUDA events on the plan stream around each step",
@@ -377,6 +379,10 @@ def dtype_detail(info):
     return "FP64 throughout"
 
 
+def levels_arg(args):
+    return "auto" if args.levels == "auto" else int(args.levels)
+
+
 def refine_desc(args):
     return {"refine_levels": args.refine_levels} if args.refine_levels else {}
 
@@ -445,7 +451,8 @@ def run_fp32(args, prob, dev, stream, points):
     import oracle
     import paper_2409_11998_gb300 as lp
     T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
-    ev = lp.Evaluator(prob, precision="fp32", tol=1e-5, stream=stream.cuda_stream, refine_levels=args.refine_levels)
+    ev = lp.Evaluator(prob, precision="fp32", tol=1e-5, stream=stream.cuda_stream, refine_levels=args.refine_levels,
+                      levels=levels_arg(args))
     nv, nt = len(prob["src_w"]), len(prob["tgt_xy"])
     sxy, sw, sf, txy, jet = (T(prob[k]) for k in ("src_xy", "src_w", "src_f", "tgt_xy", "tgt_jet"))
     sig, mu = layer_densities(prob, T)
@@ -526,7 +533,8 @@ def run_batch(args, rank, world, local_rank):
     out = {}
     stream = torch.cuda.Stream(device=dev)
     for prec, tol in (("fp64", 1e-9), ("fp32", 1e-5)):
-        evs = [lp.Evaluator(p, precision=prec, tol=tol, stream=stream.cuda_stream).bind() for p in probs]
+        evs = [lp.Evaluator(p, precision=prec, tol=tol, stream=stream.cuda_stream, levels=levels_arg(args)).bind()
+               for p in probs]
         T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
         txy = [T(p["tgt_xy"]) for p in probs]
         jet = [T(p["tgt_jet"]) for p in probs]
@@ -570,6 +578,8 @@ def run_batch(args, rank, world, local_rank):
                 errs.append(float(np.linalg.norm(got - ref[k]) / np.linalg.norm(ref[k])))
         res["parity_max_rel_l2_sampled"] = max(errs)
         res["tol"] = tol
+        res["single_level_plans"] = int(sum(e.info()["levels"] == 1 for e in evs))
+        res["dtype"] = dtype_of(evs[0].info())
         out[prec] = res
         lp.lp_batch_destroy(b)
         for e in evs:
@@ -578,10 +588,10 @@ def run_batch(args, rank, world, local_rank):
     return {"metric": METRIC, "value": r64["batched"]["points_per_s"], "unit": UNIT, "n_gpus": world,
             "steps": max(3, args.steps // 5), "warmup": max(args.warmup, 2),
             "ms_per_step": r64["batched"]["ms_per_wave"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generators; no dataset)",
+            "vs_baseline": None, "dtype": r64["dtype"], "data": "synthetic (seeded generators; no dataset)",
             "config": {"workload": f"{len(probs)} star domains r=1+a cos kt, a~U[0.1,0.4], k in 3..9, "
                                    "log-uniform 1k..200k triangles, one wave",
-                       "n_problems": len(probs), "points_per_wave": points,
+                       "n_problems": len(probs), "points_per_wave": points, "levels": args.levels,
                        "triangles_total": int(sum(p["meta"]["n_triangles"] for p in probs))},
             "batch": out}
 
@@ -602,8 +612,8 @@ def run_serve(args, rank, world, local_rank, pool=None, rates=(25, 50, 100, 200)
     out = {"pool": [{"name": p["name"], "triangles": p["meta"]["n_triangles"],
                      "points": len(p["src_w"]) + len(p["bnd"]["w"]) + len(p["tgt_xy"])} for p in pool],
            "rates": {}}
-    srv = serve.Server(pool, precision="fp32", tol=1e-5, n_slots=2, max_wave=32)
-    one = serve.Server(pool64, precision="fp64", tol=1e-9, one_at_a_time=True)
+    srv = serve.Server(pool, precision="fp32", tol=1e-5, n_slots=2, max_wave=32, levels=levels_arg(args))
+    one = serve.Server(pool64, precision="fp64", tol=1e-9, one_at_a_time=True, levels=levels_arg(args))
     srv.prewarm()
     one.prewarm()
     srv.run(serve.poisson_arrivals(20, 1.0, len(pool), seed=1))   # warm-up

@@ -71,6 +71,11 @@ enum { LP_FP64 = 0, LP_FP32 = 1 };
  * plan's tolerance and expansion order (Sec. 4.4). */
 #define LP_REFINE_AUTO (-1)
 
+/* lp_domain.levels: one history level when its grid is small (at most
+ * LP_SINGLE_LEVEL_MAX_GRID points per side), else two. */
+#define LP_LEVELS_AUTO (-1)
+#define LP_SINGLE_LEVEL_MAX_GRID 1536
+
 typedef struct {
   int precision;        /* LP_FP64: tolerances down to ~1e-12.  The volume spread,
                            FFTs, multiplier and interpolation run in double-float
@@ -102,6 +107,17 @@ typedef struct {
                            selection rule of Sec. 4.4), at most 6.  V_L keeps
                            delta.  Plans with J > 0 are not accepted by
                            lp_batch_execute. */
+  int levels;           /* history levels (Sec. 3): 0 or 2 = near history on
+                           [delta_1, delta_2] plus far history from delta_2 =
+                           32 delta_1; 1 = one level, the truncated-kernel
+                           representation of G_H[delta_1] on one grid (the
+                           paper's one-level alternative, delta_2 = delta_1);
+                           LP_LEVELS_AUTO = one level if its grid side is at
+                           most LP_SINGLE_LEVEL_MAX_GRID, else two. */
+  double upsampling;    /* grid upsampling sigma (g >= sigma (2K+1)): 0 = the
+                           default (FP64 1.5, FP32 2), else 1.25 .. 3; the
+                           kernel width follows from tol and sigma (LP_ERR_ARG
+                           when it would exceed 16) */
 } lp_domain;
 
 /* Create a plan: chooses the near/far-history grids (Sec. 3: delta_2 =
@@ -201,7 +217,7 @@ lp_status lp_destroy(lp_plan_t plan);
 const char* lp_status_string(lp_status status);
 
 /* Plan parameters, for diagnostics and benchmarks:
- * out[0..25] = {delta_1, delta_2, kernel width w, beta, g_NH, K_NH, P_NH, g_FH, K_FH,
+ * out[0..27] = {delta_1, delta_2, kernel width w, beta, g_NH, K_NH, P_NH, g_FH, K_FH,
  *               P_FH, L_FH, band 12 sqrt(delta_1), node-gap margin, device bytes,
  *               precision, order, kernels launched by this plan so far,
  *               max error of the kernel's polynomial form, its coefficient count,
@@ -210,8 +226,10 @@ const char* lp_status_string(lp_status status);
  *               arithmetic, with the double-float interpolation), 0 for cuFFT,
  *               1 if volume sources are spread through bins, bin side in
  *               near-history cells, dyadic refinement levels, largest error
- *               of the refinement's kernel tables, refinement subnodes}.
- *               out must hold 26 doubles. */
+ *               of the refinement's kernel tables, refinement subnodes,
+ *               history levels in use (2 or 1), upsampling sigma}; the
+ *               near-history entries are 0 for single-level plans.
+ *               out must hold 28 doubles. */
 lp_status lp_plan_info(lp_plan_t plan, double* out);
 
 /* Per-stage device times of the last lp_execute in milliseconds (CUDA events

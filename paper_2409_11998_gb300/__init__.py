@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblp.so")
 
 LP_FP64, LP_FP32 = 0, 1
 LP_REFINE_AUTO = -1  # refine_levels: levels from tol and order (Sec. 4.4)
+LP_LEVELS_AUTO = -1  # levels: one history level when its grid is small
 STATUS = {0: "LP_OK", 1: "LP_ERR_ARG", 2: "LP_ERR_OUT_OF_BOX", 3: "LP_ERR_NOMEM",
           4: "LP_ERR_CUDA", 5: "LP_ERR_UNSUPPORTED", 6: "LP_ERR_STATE"}
 EXPORTS = ("lp_plan", "lp_volume", "lp_single_layer", "lp_double_layer", "lp_execute", "lp_sync",
@@ -42,7 +43,9 @@ class lp_domain(ctypes.Structure):
                 ("n_panels", ctypes.c_int64), ("panel_order", ctypes.c_int),
                 ("bnd_xy", ctypes.c_void_p), ("bnd_w", ctypes.c_void_p),
                 ("bnd_normal", ctypes.c_void_p), ("stream", ctypes.c_void_p),
-                ("refine_levels", ctypes.c_int)]
+                ("refine_levels", ctypes.c_int),
+                ("levels", ctypes.c_int),
+                ("upsampling", ctypes.c_double)]
 
 
 _LIB = None
@@ -107,7 +110,7 @@ def _ptr(a):
 
 
 def lp_plan(box_lo, box_hi, delta, tol, *, precision=LP_FP64, order=5, n_panels=0, panel_order=16,
-            bnd_xy=None, bnd_w=None, bnd_normal=None, stream=0, refine_levels=0):
+            bnd_xy=None, bnd_w=None, bnd_normal=None, stream=0, refine_levels=0, levels=0, upsampling=0.0):
     dom = lp_domain()
     dom.precision = int(precision)
     dom.order = int(order)
@@ -120,6 +123,8 @@ def lp_plan(box_lo, box_hi, delta, tol, *, precision=LP_FP64, order=5, n_panels=
     dom.bnd_normal = _ptr(bnd_normal)
     dom.stream = int(stream) if stream else None
     dom.refine_levels = LP_REFINE_AUTO if refine_levels == "auto" else int(refine_levels)
+    dom.levels = LP_LEVELS_AUTO if levels == "auto" else int(levels)
+    dom.upsampling = float(upsampling)
     h = ctypes.c_void_p()
     _check(_lib().lp_plan(ctypes.byref(dom), float(delta), float(tol), ctypes.byref(h)), "lp_plan")
     return h
@@ -195,12 +200,12 @@ def lp_destroy(plan):
 
 
 def lp_plan_info(plan):
-    out = np.zeros(26)
+    out = np.zeros(28)
     _check(_lib().lp_plan_info(plan, out.ctypes.data), "lp_plan_info")
     keys = ["delta1", "delta2", "w", "beta", "g_nh", "K_nh", "P_nh", "g_fh", "K_fh", "P_fh", "L_fh",
             "band", "margin", "device_bytes", "precision", "order", "launches", "es_fit_err", "es_nc",
             "sigma_eff", "own_fft", "binned", "bin_cells", "refine_levels", "refine_table_err",
-            "refine_subnodes"]
+            "refine_subnodes", "levels", "sigma"]
     return dict(zip(keys, out.tolist()))
 
 
@@ -218,7 +223,7 @@ class Evaluator:
     ``host=True``, in which case the C ABI receives host pointers."""
 
     def __init__(self, problem, precision=None, order=5, tol=None, device="cuda", host=False,
-                 stream=None, refine_levels=0):
+                 stream=None, refine_levels=0, levels=0, upsampling=0.0):
         import torch
         self.torch = torch
         self.host = host
@@ -245,7 +250,7 @@ class Evaluator:
                       bnd_w=dev(b["w"]), bnd_normal=dev(b["normal"]))
         self.plan = lp_plan(problem["box_lo"], problem["box_hi"], problem["delta"], self.tol,
                             precision=self.precision, order=order, stream=self.stream,
-                            refine_levels=refine_levels, **kw)
+                            refine_levels=refine_levels, levels=levels, upsampling=upsampling, **kw)
         self.problem = problem
 
     def bind(self, src_xy=None, src_w=None, src_f=None, sigma=None, mu=None):

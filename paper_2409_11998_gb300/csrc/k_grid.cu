@@ -131,7 +131,7 @@ __device__ __forceinline__ void interp_target(const InterpArgs<T>& a, int64_t i)
     acc[1] = a.zero_factor * a.qsum[1];
   }
   bool bad = false;
-  for (int l = 0; l < 2; ++l) {
+  for (int l = a.l0; l < 2; ++l) {
     const GridDev gd = a.gd[l];
     double ux = (a.txy[2 * i] - gd.x0) * gd.inv_h;
     double uy = (a.txy[2 * i + 1] - gd.y0) * gd.inv_h;
@@ -311,7 +311,8 @@ InterpArgs<T> make_interp_args(const Plan& P, int64_t nt, const double* txy, dou
     a.gd[l] = grid_dev(P.lv[l]);
     for (int c = 0; c < 3; ++c) a.grid[l][c] = a.out[c] ? P.lv[l].chan[c] : nullptr;
   }
-  a.zero_factor = P.lv[0].zero_mode + P.lv[1].zero_mode;
+  a.zero_factor = P.lv[0].zero_mode + P.lv[1].zero_mode;  // 0 for an unused level
+  a.l0 = P.l0;
   // FP32 path: the zero mode was removed from the FP32 tables
   a.qsum = sizeof(T) == 8 ? nullptr : P.d_qsum;
   if constexpr (sizeof(T) == 8) a.es = P.es; else a.es = P.es32;

@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(128) interp_dd_kernel(const __grid_constant__ 
   const dd X = dd_from_double(a.txy[2 * i]), Y = dd_from_double(a.txy[2 * i + 1]);
   dd_acc acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   bool bad = false;
-  for (int l = 0; l < 2; ++l) {
+  for (int l = a.l0; l < 2; ++l) {
     const InterpDDLevel& L = a.lv[l];
     const dd ux = dd_mul(dd_sub(X, dd{L.x0.x, L.x0.y}), dd{L.inv_h.x, L.inv_h.y});
     const dd uy = dd_mul(dd_sub(Y, dd{L.y0.x, L.y0.y}), dd{L.inv_h.x, L.inv_h.y});

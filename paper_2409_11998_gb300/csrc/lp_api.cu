@@ -241,7 +241,7 @@ namespace lpg {
 // shared memory).  FP32 plans whose kernel fit needs more coefficients than
 // the binned kernel holds keep the point-parallel spread.
 lp_status setup_bins(Plan& P) {
-  const GridLevel& N = P.lv[0];
+  const GridLevel& N = P.lv[P.l0];
   const int w = P.ker.w;
   const bool f64 = P.precision == LP_FP64;
   if (w < 4 || (!f64 && (w > 10 || P.es32.nc > sub_ncw(w)))) return LP_OK;
@@ -255,7 +255,7 @@ lp_status setup_bins(Plan& P) {
   // shared-memory wavefronts for the w^2 stencil cells taken 32 at a time
   // (4-byte cells: 32 banks per warp; 8-byte cells: 16 per half warp).
   const int banks = f64 ? 16 : 32, group = f64 ? 16 : 32;
-  for (int l = 0; l < 2; ++l) {
+  for (int l = P.l0; l < 2; ++l) {
     const double cells = P.bin_cells * N.h / P.lv[l].h;
     const int m0 = (int)std::ceil(cells) + w + 3;
     int best = m0, best_wf = 1 << 30;
@@ -361,7 +361,7 @@ float2 split_host(double x) {
 lp_status setup_fft_chain(Plan& P) {
   const size_t limit = 220 * 1024;
   const bool f64 = P.precision == LP_FP64;
-  for (int l = 0; l < 2; ++l) {
+  for (int l = P.l0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
     G.full = fft_shape(G.g);
     G.half = fft_shape(G.g / 2);
@@ -369,7 +369,7 @@ lp_status setup_fft_chain(Plan& P) {
     if (fft_cols_smem(G.g, f64) > limit || fft_rows_smem(G.g, f64) > limit) return LP_OK;
   }
   if (!fft_dd_configure()) return LP_ERR_CUDA;
-  for (int l = 0; l < 2; ++l) {
+  for (int l = P.l0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
     G.kp = (G.K + 2) & ~1;
     const size_t spec_bytes = (size_t)G.g * G.kp * (f64 ? sizeof(float4) : sizeof(float2));
@@ -422,12 +422,12 @@ void history_transforms(const Plan& P, bool wv, bool ws, bool wd, cudaStream_t s
     a.row_hi = G.row_hi;
     return a;
   };
-  for (int l = 0; l < 2; ++l) {
+  for (int l = P.l0; l < 2; ++l) {
     launch_fft_rows_fwd(row_args(P.lv[l], fch, nf), nf, f64, s);
     ++P.launches;
   }
   if (events) cudaEventRecord(P.ev[4], s);
-  for (int l = 0; l < 2; ++l) {
+  for (int l = P.l0; l < 2; ++l) {
     const GridLevel& G = P.lv[l];
     FftColArgs a{};
     a.full = G.full;
@@ -446,7 +446,7 @@ void history_transforms(const Plan& P, bool wv, bool ws, bool wd, cudaStream_t s
     ++P.launches;
   }
   if (events) cudaEventRecord(P.ev[5], s);
-  for (int l = 0; l < 2; ++l) {
+  for (int l = P.l0; l < 2; ++l) {
     launch_fft_rows_inv(row_args(P.lv[l], ich, ni), ni, f64, s);
     ++P.launches;
   }
@@ -463,7 +463,8 @@ void history_interp(const Plan& P, int64_t nt, const double* txy, double* const*
   InterpDDArgs a{};
   a.txy = txy;
   a.n = nt;
-  for (int l = 0; l < 2; ++l) {
+  a.l0 = P.l0;
+  for (int l = P.l0; l < 2; ++l) {
     const GridLevel& G = P.lv[l];
     InterpDDLevel& L = a.lv[l];
     for (int c = 0; c < 3; ++c) L.grid[c] = G.chan[c];
@@ -524,6 +525,8 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
       return LP_ERR_ARG;
   if (dom->n_panels < 0) return LP_ERR_ARG;
   if (dom->refine_levels < LP_REFINE_AUTO || dom->refine_levels > kMaxDyLevels) return LP_ERR_ARG;
+  if (dom->levels < LP_LEVELS_AUTO || dom->levels > 2) return LP_ERR_ARG;
+  if (dom->upsampling != 0.0 && !(dom->upsampling >= 1.25 && dom->upsampling <= 3.0)) return LP_ERR_ARG;
   if (dom->n_panels > 0) {
     if (dom->panel_order < 2 || dom->panel_order > kMaxPanelOrder) return LP_ERR_ARG;
     if (!dom->bnd_xy || !dom->bnd_w) return LP_ERR_ARG;
@@ -535,7 +538,8 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
   P.precision = dom->precision;
   P.order = order;
   P.delta1 = delta;
-  P.delta2 = 32.0 * delta;
+  P.l0 = dom->levels == 1 ? 1 : 0;
+  P.delta2 = P.l0 ? delta : 32.0 * delta;
   P.tol = tol;
   for (int d = 0; d < 2; ++d) {
     P.box_lo[d] = dom->box_lo[d];
@@ -551,17 +555,40 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
   // lobed problems reached 1.2e-9 at w 11, so FP64 takes w = ceil(-log10 tol)
   // + 3 (12 at 1e-9); FP32 takes + 2 (7 at 1e-5) for margin against
   // single-precision rounding.
-  P.sigma = P.precision == LP_FP64 ? 1.5 : 2.0;
-  int w = (int)std::ceil(-std::log10(tol)) + (P.precision == LP_FP64 ? 3 : 2);
+  // Other upsampling factors (1.25 .. 3) take the width at which the ES
+  // kernel's aliasing error e^{-pi w sqrt(1 - 1/sigma)} reaches tol, plus one.
+  const double sigma_default = P.precision == LP_FP64 ? 1.5 : 2.0;
+  P.sigma = dom->upsampling > 0.0 ? dom->upsampling : sigma_default;
+  int w;
+  if (P.sigma == sigma_default) {
+    w = (int)std::ceil(-std::log10(tol)) + (P.precision == LP_FP64 ? 3 : 2);
+  } else {
+    w = (int)std::ceil(std::log(1.0 / tol) / (3.14159265358979323846 * std::sqrt(1.0 - 1.0 / P.sigma))) + 1;
+    if (w > kMaxW) {
+      delete h;
+      return LP_ERR_ARG;  // tolerance out of reach at this upsampling
+    }
+  }
   w = std::min(std::max(w, 4), kMaxW);
   P.ker.w = w;
   P.ker.beta = 2.30 * w;  // refined by choose_levels for the realised sigma
   P.ker.half_w = 0.5 * w;
+  if (dom->levels == LP_LEVELS_AUTO) {
+    // one level when its grid is small: the launch chain of the second level
+    // then costs more than the larger single grid (measured on GB300)
+    Plan Q = P;
+    Q.l0 = 1;
+    Q.delta2 = delta;
+    if (choose_levels(Q) == LP_OK && Q.lv[1].g <= LP_SINGLE_LEVEL_MAX_GRID) {
+      P.l0 = 1;
+      P.delta2 = delta;
+    }
+  }
   lp_status st = choose_levels(P);
   if (st == LP_OK) st = build_tables(P);
   if (st == LP_OK) st = fit_kernel_poly(P);
   const size_t rs = P.precision == LP_FP64 ? sizeof(double) : sizeof(float);
-  for (int l = 0; l < 2 && st == LP_OK; ++l) {
+  for (int l = P.l0; l < 2 && st == LP_OK; ++l) {
     GridLevel& G = P.lv[l];
     G.chan_bytes = (size_t)G.g * G.pitch * rs;
     for (int c = 0; c < 4 && st == LP_OK; ++c)
@@ -779,7 +806,7 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
   // Steps 2-3: spread every requested channel onto both history grids:
   // volume nodes through the bins (FP32 plans) or point-parallel with global
   // atomics; boundary nodes point-parallel.
-  for (int l = 0; l < 2; ++l) {
+  for (int l = P.l0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
     if (wv) cudaMemsetAsync(G.chan[0], 0, G.chan_bytes, s);
     if (ws) cudaMemsetAsync(G.chan[1], 0, G.chan_bytes, s);
@@ -789,7 +816,7 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
     }
   }
   cudaEventRecord(P.ev[2], s);
-  for (int l = 0; l < 2; ++l) {
+  for (int l = P.l0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
     if (wv && P.nv > 0) {
       if (P.binned) {
@@ -802,7 +829,7 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
     }
   }
   cudaEventRecord(P.ev[10], s);
-  for (int l = 0; l < 2; ++l) {
+  for (int l = P.l0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
     const double* bq[3];
     void* bg[3];
@@ -825,7 +852,7 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
     if (host_in) cudaStreamWaitEvent(s, P.ev_staged, 0);
     history_interp(P, nt, dt, dout, s);
   } else {
-    for (int l = 0; l < 2; ++l) {
+    for (int l = P.l0; l < 2; ++l) {
       if (wv) fft_forward(P, l, 0);
       if (ws) fft_forward(P, l, 1);
       if (wd) {
@@ -835,9 +862,9 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
     }
     cudaEventRecord(P.ev[4], s);
     // Step 4: deconvolved multiplier (in place; D written to channel 2)
-    for (int l = 0; l < 2; ++l) launch_multiplier(P, l, wv, ws, wd, s);
+    for (int l = P.l0; l < 2; ++l) launch_multiplier(P, l, wv, ws, wd, s);
     cudaEventRecord(P.ev[5], s);
-    for (int l = 0; l < 2; ++l) {
+    for (int l = P.l0; l < 2; ++l) {
       if (wv) fft_inverse(P, l, 0);
       if (ws) fft_inverse(P, l, 1);
       if (wd) fft_inverse(P, l, 2);
@@ -878,7 +905,7 @@ lp_status lp_execute_noalloc(lp_plan_t h, int64_t nt, const double* txy, const d
   cudaStream_t s = P.stream;
   cudaEventRecord(P.ev[0], s);
   cudaEventRecord(P.ev[1], s);
-  for (int l = 0; l < 2; ++l) {
+  for (int l = P.l0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
     if (wv) cudaMemsetAsync(G.chan[0], 0, G.chan_bytes, s);
     if (ws) cudaMemsetAsync(G.chan[1], 0, G.chan_bytes, s);
@@ -888,7 +915,7 @@ lp_status lp_execute_noalloc(lp_plan_t h, int64_t nt, const double* txy, const d
     }
   }
   cudaEventRecord(P.ev[2], s);
-  for (int l = 0; l < 2; ++l) {
+  for (int l = P.l0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
     if (wv && P.nv > 0) {
       const double* q[1] = {P.d_vq};
@@ -897,7 +924,7 @@ lp_status lp_execute_noalloc(lp_plan_t h, int64_t nt, const double* txy, const d
     }
   }
   cudaEventRecord(P.ev[10], s);
-  for (int l = 0; l < 2; ++l) {
+  for (int l = P.l0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
     const double* bq[3];
     void* bg[3];
@@ -915,15 +942,15 @@ lp_status lp_execute_noalloc(lp_plan_t h, int64_t nt, const double* txy, const d
     if (nq) launch_spread(P, l, P.d_bxy, bq, nq, bg, P.nb, s);
   }
   cudaEventRecord(P.ev[3], s);
-  for (int l = 0; l < 2; ++l) {
+  for (int l = P.l0; l < 2; ++l) {
     const int chans[4] = {wv ? 0 : -1, ws ? 1 : -1, wd ? 2 : -1, wd ? 3 : -1};
     for (int c : chans)
       if (c >= 0) fft_forward(P, l, c);
   }
   cudaEventRecord(P.ev[4], s);
-  for (int l = 0; l < 2; ++l) launch_multiplier(P, l, wv, ws, wd, s);
+  for (int l = P.l0; l < 2; ++l) launch_multiplier(P, l, wv, ws, wd, s);
   cudaEventRecord(P.ev[5], s);
-  for (int l = 0; l < 2; ++l) {
+  for (int l = P.l0; l < 2; ++l) {
     const int chans[3] = {wv ? 0 : -1, ws ? 1 : -1, wd ? 2 : -1};
     for (int c : chans)
       if (c >= 0) fft_inverse(P, l, c);
@@ -962,12 +989,12 @@ lp_status lp_destroy(lp_plan_t h) {
 lp_status lp_plan_info(lp_plan_t h, double* out) {
   if (!h || !out) return LP_ERR_ARG;
   const Plan& P = h->P;
-  double v[26] = {P.delta1, P.delta2, (double)P.ker.w, P.ker.beta, (double)P.lv[0].g, (double)P.lv[0].K,
+  double v[28] = {P.delta1, P.delta2, (double)P.ker.w, P.ker.beta, (double)P.lv[0].g, (double)P.lv[0].K,
                   P.lv[0].P, (double)P.lv[1].g, (double)P.lv[1].K, P.lv[1].P, P.lv[1].L, P.band,
                   P.margin, (double)P.device_bytes, (double)P.precision, (double)P.order,
                   (double)P.launches, P.es_fit_err, (double)P.es.nc, P.sigma_eff,
                   P.own_fft ? 1.0 : 0.0, P.binned ? 1.0 : 0.0, (double)P.bin_cells,
-                  (double)P.dy_levels, P.dy_err, (double)P.dy_nq};
+                  (double)P.dy_levels, P.dy_err, (double)P.dy_nq, (double)(2 - P.l0), P.sigma};
   std::memcpy(out, v, sizeof(v));
   return LP_OK;
 }

@@ -143,7 +143,7 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
     const bool wv = V && V[i], ws = S && S[i], wd = D && D[i];
     const int64_t nt = n_t[i];
     if (nt == 0 || (!wv && !ws && !wd)) continue;
-    for (int l = 0; l < 2; ++l) {
+    for (int l = P.l0; l < 2; ++l) {
       const GridLevel& G = P.lv[l];
       const bool need[4] = {wv, ws, wd, wd};
       for (int c = 0; c < 4; ++c) {
@@ -245,7 +245,7 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
   for (int i = 0; i < n; ++i) {
     const Plan& P = plans[i]->P;
     if (n_t[i] > 0 && V && V[i] && P.binned && P.nv > 0)
-      for (int l = 0; l < 2; ++l) spread_volume_binned(P, l, s);
+      for (int l = P.l0; l < 2; ++l) spread_volume_binned(P, l, s);
   }
   cudaEventRecord(b->ev[2], s);
   // each plan's transforms on the batch stream: the whole FFT chain for plans
@@ -258,7 +258,7 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
       history_transforms(P, wv, ws, wd, s, false);
       continue;
     }
-    for (int l = 0; l < 2; ++l) {
+    for (int l = P.l0; l < 2; ++l) {
       const GridLevel& G = P.lv[l];
       cufftSetStream(G.row_fwd, s);
       cufftSetStream(G.col, s);
@@ -277,7 +277,7 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
     const Plan& P = plans[i]->P;
     const bool wv = V && V[i], ws = S && S[i], wd = D && D[i];
     if (n_t[i] == 0 || (!wv && !ws && !wd) || P.own_fft) continue;
-    for (int l = 0; l < 2; ++l) {
+    for (int l = P.l0; l < 2; ++l) {
       const GridLevel& G = P.lv[l];
       cufftSetStream(G.row_inv, s);
       if (wv) fft_inverse(P, l, 0);

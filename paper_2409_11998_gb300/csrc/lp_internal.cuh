@@ -122,6 +122,7 @@ struct InterpArgs {
   GridDev gd[2];
   const double* qsum;      // FP64 strength sums of V and S (FP32 path), or null
   double zero_factor;      // sum over levels of (dk/2pi)^2 M(0)
+  int l0;                  // first level in use (1 for single-level plans)
   double* out[3];
   unsigned* status;
   EsPoly<T> es;
@@ -212,6 +213,7 @@ struct InterpDDArgs {
   const double* txy;
   int64_t n;
   InterpDDLevel lv[2];
+  int l0;                  // first level in use (1 for single-level plans)
   double* out[3];
   unsigned* status;
   int nc;
@@ -279,6 +281,10 @@ struct Plan {
   int precision = LP_FP64;
   int order = 5;
   double delta1 = 0, delta2 = 0, tol = 0;
+  // history levels: two (near history at delta_1..delta_2, far history from
+  // delta_2), or one (l0 = 1: the far-history level alone with delta_2 =
+  // delta_1, so the near-history multiplier would vanish identically)
+  int l0 = 0;
   double box_lo[2] = {0, 0}, box_hi[2] = {0, 0};
   double side = 0;        // max box extent
   double sigma = 2.0;     // target upsampling of the history grids (g >= sigma (2K+1))

@@ -77,7 +77,7 @@ lp_status choose_levels(Plan& P) {
   // Reach of the Gaussian tails beyond which the history kernels are below
   // eps: e^{-R^2 / (4 delta_2)} = eps.
   const double R = std::sqrt(4.0 * P.delta2 * std::log(1.0 / eps));
-  for (int l = 0; l < 2; ++l) {
+  for (int l = P.l0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
     G.kind = l;
     G.R = R;
@@ -112,7 +112,8 @@ lp_status choose_levels(Plan& P) {
   // ES shape parameter for the realised upsampling (the smaller of the two
   // levels): beta = 0.97 pi (1 - 1/(2 sigma)) w, the exponential-of-semicircle
   // choice of Barnett, Magland and af Klinteberg (SISC 2019).
-  P.sigma_eff = std::min(P.lv[0].g / (2.0 * P.lv[0].K + 1.0), P.lv[1].g / (2.0 * P.lv[1].K + 1.0));
+  P.sigma_eff = P.lv[1].g / (2.0 * P.lv[1].K + 1.0);
+  if (P.l0 == 0) P.sigma_eff = std::min(P.sigma_eff, P.lv[0].g / (2.0 * P.lv[0].K + 1.0));
   P.ker.beta = 0.97 * kPi * (1.0 - 0.5 / P.sigma_eff) * P.ker.w;
   return LP_OK;
 }
@@ -123,7 +124,7 @@ lp_status build_tables(Plan& P) {
   const int nq = 4 * w + 8;
   std::vector<double> qx(nq), qw(nq);
   gauss_legendre(nq, qx.data(), qw.data());
-  for (int l = 0; l < 2; ++l) {
+  for (int l = P.l0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
     const int K = G.K;
     std::vector<double> ph(K + 1);

@@ -83,12 +83,13 @@ class _PlanInst:
 
 class Server:
     def __init__(self, pool, precision="fp32", tol=1e-5, n_slots=2, max_wave=32,
-                 mem_budget=64 << 30, one_at_a_time=False, keep_outputs=False, device="cuda"):
+                 mem_budget=64 << 30, one_at_a_time=False, keep_outputs=False, device="cuda", levels="auto"):
         import torch
         self.torch = torch
         self.device = device
         self.prec = LP_FP32 if precision == "fp32" else LP_FP64
         self.tol = tol
+        self.levels = levels              # history levels of every plan (lp_domain.levels)
         self.one = one_at_a_time
         self.max_wave = 1 if one_at_a_time else max_wave
         self.keep = keep_outputs
@@ -112,7 +113,7 @@ class Server:
         b = p["bnd"]
         h = lp_plan(p["box_lo"], p["box_hi"], p["delta"], self.tol, precision=self.prec,
                     n_panels=b["n_panels"], panel_order=b["order"], bnd_xy=m.bxy, bnd_w=m.bw,
-                    bnd_normal=m.bn, stream=self.slots[slot]["stream"].cuda_stream)
+                    bnd_normal=m.bn, stream=self.slots[slot]["stream"].cuda_stream, levels=self.levels)
         inst = _PlanInst(h, int(lp_plan_info(h)["device_bytes"]))
         self.pools[(slot, mid)].append(inst)
         self.resident += inst.bytes

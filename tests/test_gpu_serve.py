@@ -31,7 +31,7 @@ def test_results_same_alone_and_in_the_mix(lp):
     waves_with_many = srv.created > len(pool) * 2  # extra plans were needed for repeated meshes
     for r in reqs:
         p = pool[r.mesh]
-        ev = lp.Evaluator(p, precision="fp32", tol=1e-5).bind(src_f=p["src_f"] * r.scale,
+        ev = lp.Evaluator(p, precision="fp32", tol=1e-5, levels=srv.levels).bind(src_f=p["src_f"] * r.scale,
                                                              sigma=p["sigma"] * r.scale,
                                                              mu=p["mu"] * r.scale)
         alone = ev.evaluate(tgt_jet=p["tgt_jet"] * r.scale)

@@ -77,6 +77,12 @@ def test_invalid_arguments_rejected_without_device(lib):
         dom.refine_levels = levels
         assert L.lp_plan(ctypes.byref(dom), 1e-3, 1e-9, ctypes.byref(h)) == 1
     dom.refine_levels = 0
+    for levels, ups in ((3, 0.0), (-2, 0.0), (0, 1.1), (0, 4.0)):  # -1..2 levels; sigma 0 or 1.25..3
+        dom.levels, dom.upsampling = levels, ups
+        assert L.lp_plan(ctypes.byref(dom), 1e-3, 1e-9, ctypes.byref(h)) == 1
+    dom.levels, dom.upsampling = 0, 1.25   # sigma 1.25 needs w = 21 at 1e-12 (> 16)
+    assert L.lp_plan(ctypes.byref(dom), 1e-3, 1e-12, ctypes.byref(h)) == 1
+    dom.upsampling = 0.0
     for fn in (L.lp_sync, L.lp_destroy):
         assert fn(None) == 1
     assert L.lp_volume(None, 0, None, None, None) == 1
