@@ -206,3 +206,35 @@ def evaluate(problem, targets=None, order=5, want=("V", "S", "D"), refine_levels
     out["info"] = info
     out["status"] = st
     return out
+
+
+def dirichlet_matrix(bnd, delta, order=5, on_tol=1e-12, refine_levels=0):
+    """The discrete operator of the interior Dirichlet equation (Sec. 5,
+    eq. dir_inteq) at the boundary nodes: A = -I/2 + D, with column j the
+    double layer of the unit nodal density e_j evaluated at every boundary
+    node (on-surface targets): smooth part by direct sums, local part by the
+    on-surface expansions (with dyadic refinement when refine_levels > 0).
+    Dense, built column by column -- for small boundaries only."""
+    xy, nrm, w = bnd["xy"], bnd["normal"], bnd["w"]
+    nb = len(xy)
+    A = np.empty((nb, nb))
+    for j in range(nb):
+        e = np.zeros(nb)
+        e[j] = 1.0
+        DH = smooth_dipole(xy, nrm, e * w, xy, delta)
+        if refine_levels > 0:
+            _, DL = local_dyadic(bnd, None, e, xy, delta, refine_levels, order=order, on_tol=on_tol)
+        else:
+            _, _, DL, _, _ = local(bnd, None, e, xy, None, delta, order, on_tol)
+        A[:, j] = DH + DL
+    A[np.diag_indices(nb)] -= 0.5
+    return A
+
+
+def solve_dirichlet(bnd, g, delta, order=5, on_tol=1e-12, v_boundary=None, refine_levels=0):
+    """mu solving -mu/2 + D[mu] = g - V[f] at the boundary nodes (Sec. 5,
+    eq. dir_inteq) by a dense direct solve of dirichlet_matrix; v_boundary is
+    V[f] at the boundary nodes (None: f = 0)."""
+    A = dirichlet_matrix(bnd, delta, order, on_tol, refine_levels)
+    rhs = np.asarray(g, dtype=np.float64) - (0.0 if v_boundary is None else np.asarray(v_boundary))
+    return np.linalg.solve(A, rhs)
