@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lp", choices=["lp", "reference"])
-    ap.add_argument("--workload", default="starfish", choices=["starfish", "disk", "square", "batch", "serve"])
+    ap.add_argument("--workload", default="starfish",
+                    choices=["starfish", "disk", "square", "batch", "serve", "solve"])
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline, fp32 and serving lines")
     ap.add_argument("--batch-size", type=int, default=256, help="problems per wave (--workload batch)")
     ap.add_argument("--serve-seconds", type=float, default=8.0, help="seconds per arrival rate (--workload serve)")
@@ -596,6 +597,56 @@ def run_batch(args, rank, world, local_rank):
             "batch": out}
 
 
+# ---------------------------------------------------------------- Dirichlet solve
+def run_solve(args, rank, world, local_rank):
+    """Interior Dirichlet problem on the starfish (Sec. 5): GMRES on
+    -mu/2 + D[mu] = g - V[f] at the 16k boundary nodes, D applied by the
+    evaluator; one step = one solve to 1e-10 (FP64) from mu = 0."""
+    import numpy as np
+    import torch
+    import paper_2409_11998_gb300 as lp
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    prob = make_problem("starfish")
+    nv, nb = len(prob["src_w"]), len(prob["bnd"]["w"])
+    fp64 = args.precision == "fp64"
+    tol = 1e-10 if fp64 else 2e-4   # FP32 D stalls GMRES near 1e-4
+    stream = torch.cuda.Stream(device=dev)
+    ev = lp.Evaluator(prob, precision=args.precision, tol=1e-9 if fp64 else 1e-5, stream=stream.cuda_stream,
+                      refine_levels=args.refine_levels, levels=levels_arg(args)).bind()
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    g, jb = T(prob["dirichlet_g"]), T(prob["bnd_jet"])
+    mu = torch.empty(nb, dtype=torch.float64, device=dev)
+    launches0 = None
+    for k in range(max(args.warmup, 3) + args.steps):
+        if k == max(args.warmup, 3):
+            torch.cuda.synchronize()
+            launches0 = lp.lp_plan_info(ev.plan)["launches"]
+            times, its, res = [], [], []
+        t0 = time.perf_counter()
+        it, r = lp.lp_solve_dirichlet(ev.plan, g, mu, f_jet_b=jb, tol=tol, max_iter=300, restart=40)
+        dt = time.perf_counter() - t0      # the call synchronises the plan stream
+        if launches0 is not None:
+            times.append(dt)
+            its.append(it)
+            res.append(r)
+    launches = lp.lp_plan_info(ev.plan)["launches"] - launches0
+    ms = statistics.mean(times) * 1e3
+    info = ev.info()
+    ev.close()
+    return {"metric": METRIC, "value": (nv + nb) / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype_of(info),
+            "data": "synthetic (seeded generators; no dataset)",
+            "config": {"workload": "interior Dirichlet solve on the starfish (1.2M volume nodes, 1024x16 "
+                                   "boundary nodes): GMRES(40) from mu = 0 to a relative residual "
+                                   f"{tol:g}, g = cos x + sin 2y", **refine_desc(args),
+                       "levels": int(info["levels"]), "timing": "host wall time per solve (synchronising)"},
+            "solve": {"iterations": its[-1], "residual": res[-1], "ms_per_iteration": ms / max(its[-1], 1),
+                      "boundary_nodes": nb},
+            "gpu_launches": int(launches)}
+
+
 # ---------------------------------------------------------------- serving (config 5)
 def run_serve(args, rank, world, local_rank, pool=None, rates=(25, 50, 100, 200), seconds=None):
     """Poisson arrivals of V+S+D requests over a resident mesh pool (10k..5M
@@ -710,6 +761,8 @@ def main():
         res = run_reference(args, rank, world)
     elif args.workload == "batch":
         res = run_batch(args, rank, world, local)
+    elif args.workload == "solve":
+        res = run_solve(args, rank, world, local)
     elif args.workload == "serve":
         sv = run_serve(args, rank, world, local)
         top = sv["rates"][max(sv["rates"], key=float)]

@@ -176,8 +176,8 @@ lp_status lp_execute(lp_plan_t plan, int64_t n_t, const double* t_xy, const doub
 lp_status lp_execute_noalloc(lp_plan_t plan, int64_t n_t, const double* t_xy, const double* f_jet,
                              double* V, double* S, double* D);
 
-/* Batched evaluation of a wave of independent problems (SURVEY configs 4/5:
- * uneven problems in one launch per kernel per wave).  A batch owns only the
+/* Batched evaluation of a wave of independent problems (many uneven
+ * problems, one launch per kernel per wave).  A batch owns only the
  * wave's argument records and candidate list; the member plans are ordinary
  * plans (each bound with lp_volume / lp_single_layer / lp_double_layer on a
  * stream the batch stream is ordered after, e.g. the same stream).
@@ -206,6 +206,29 @@ lp_status lp_batch_execute(lp_batch_t batch, int n, const lp_plan_t* plans, cons
 lp_status lp_batch_sync(lp_batch_t batch);
 lp_status lp_batch_stage_times(lp_batch_t batch, float* out);
 lp_status lp_batch_destroy(lp_batch_t batch);
+
+/* Interior Dirichlet problem (Sec. 5): with u = V[f] + D[mu] in the domain,
+ * solve -mu/2 + D[mu] = g - V[f] at the plan's boundary nodes
+ * (eq. dir_inteq) by restarted GMRES, D applied by this library's evaluator at
+ * the boundary nodes (on-surface targets; refined when the plan refines).
+ *   g:        [n_b] boundary values at the nodes given to lp_plan
+ *             (host or device).
+ *   f_jet_b:  [n_b][6] f-jet at the boundary nodes, or NULL for f = 0; with it
+ *             the sources bound by lp_volume give V[f] at the nodes.
+ *   mu:       [n_b] out, the density (host or device).
+ *   tol:      relative residual |b - A mu| / |b| to reach.
+ *   max_iter: total GMRES iterations (each one D evaluation); restart: Krylov
+ *             dimension per cycle, 1..64 (0: 30).
+ *   iterations, residual: out (host; may be NULL): iterations taken and the
+ *             true relative residual of the returned mu (one more D
+ *             evaluation), which the caller compares with tol.
+ * On return the plan's double-layer density is mu (lp_execute then gives
+ * D[mu] anywhere).  LP_ERR_STATE if the plan has no boundary, or f_jet_b is
+ * given without lp_volume.  Synchronises the plan's stream.  FP32 plans
+ * stall near 1e-4 on large boundaries (single-precision D, summed with
+ * atomics in varying order). */
+lp_status lp_solve_dirichlet(lp_plan_t plan, const double* g, const double* f_jet_b, double* mu, double tol,
+                             int max_iter, int restart, int* iterations, double* residual);
 
 /* Wait for the plan's stream; return and clear the device status word. */
 lp_status lp_sync(lp_plan_t plan);

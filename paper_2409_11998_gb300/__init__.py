@@ -28,7 +28,7 @@ STATUS = {0: "LP_OK", 1: "LP_ERR_ARG", 2: "LP_ERR_OUT_OF_BOX", 3: "LP_ERR_NOMEM"
 EXPORTS = ("lp_plan", "lp_volume", "lp_single_layer", "lp_double_layer", "lp_execute", "lp_sync",
            "lp_destroy", "lp_status_string", "lp_plan_info", "lp_stage_times", "lp_execute_noalloc",
            "lp_batch_create", "lp_batch_execute", "lp_batch_sync", "lp_batch_stage_times",
-           "lp_batch_destroy")
+           "lp_batch_destroy", "lp_solve_dirichlet")
 
 
 class LpError(RuntimeError):
@@ -75,6 +75,7 @@ def _lib():
         L.lp_status_string.restype = ctypes.c_char_p
         L.lp_plan_info.argtypes = [vp, vp]
         L.lp_stage_times.argtypes = [vp, vp]
+        L.lp_solve_dirichlet.argtypes = [vp, vp, vp, vp, d, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(d)]
         for name in EXPORTS:
             if name != "lp_status_string":
                 getattr(L, name).restype = i32
@@ -152,6 +153,17 @@ def lp_execute_noalloc(plan, n_t, t_xy, f_jet, V=None, S=None, D=None):
     (see include/lp.h)."""
     _check(_lib().lp_execute_noalloc(plan, int(n_t), _ptr(t_xy), _ptr(f_jet), _ptr(V), _ptr(S),
                                      _ptr(D)), "lp_execute_noalloc")
+
+
+def lp_solve_dirichlet(plan, g, mu, f_jet_b=None, tol=1e-10, max_iter=200, restart=30):
+    """-mu/2 + D[mu] = g - V[f] at the plan's boundary nodes (Sec. 5) by GMRES;
+    writes mu, returns (iterations, true relative residual)."""
+    it = ctypes.c_int(0)
+    res = ctypes.c_double(0.0)
+    _check(_lib().lp_solve_dirichlet(plan, _ptr(g), _ptr(f_jet_b), _ptr(mu), ctypes.c_double(tol),
+                                     int(max_iter), int(restart), ctypes.byref(it), ctypes.byref(res)),
+           "lp_solve_dirichlet")
+    return it.value, res.value
 
 
 def lp_batch_create(stream=0):
@@ -290,6 +302,20 @@ class Evaluator:
         if sync:
             lp_sync(self.plan)
         return outs
+
+    def solve_dirichlet(self, g, f_jet_b=None, tol=1e-10, max_iter=200, restart=30):
+        """mu with -mu/2 + D[mu] = g - V[f] at the boundary nodes (Sec. 5);
+        returns (mu, iterations, residual); mu is left bound as the plan's
+        double-layer density."""
+        n = len(self.problem["bnd"]["w"])
+        conv = (lambda a: np.ascontiguousarray(a, dtype=np.float64)) if self.host else \
+            (lambda a: self.torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=self.device))
+        gd = conv(g)
+        fj = None if f_jet_b is None else conv(f_jet_b)
+        mu = np.zeros(n) if self.host else self.torch.empty(n, dtype=self.torch.float64, device=self.device)
+        it, res = lp_solve_dirichlet(self.plan, gd, mu, f_jet_b=fj, tol=tol, max_iter=max_iter, restart=restart)
+        self._mu = mu
+        return mu, it, res
 
     def info(self):
         return lp_plan_info(self.plan)

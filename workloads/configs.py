@@ -103,7 +103,12 @@ def starfish(seed=2000, n_interior=53700, n_boundary_vertices=930, n_panels=1024
     jet = field.jet(xy)
     meta = {"n_triangles": int(len(mesh["T"])), "n_vertices": int(len(mesh["P"])),
             "curve": "starfish r=1+0.3cos5t", **mesh["stats"]}
-    return _finish("starfish", precision, tol, xy, w, f, bnd, sigma, mu, xy, jet, meta)
+    out = _finish("starfish", precision, tol, xy, w, f, bnd, sigma, mu, xy, jet, meta)
+    # interior Dirichlet data: g = cos x + sin 2y on the boundary, and the
+    # f-jet at the boundary nodes (for V[f] there)
+    out["dirichlet_g"] = np.cos(bnd["xy"][:, 0]) + np.sin(2 * bnd["xy"][:, 1])
+    out["bnd_jet"] = np.ascontiguousarray(field.jet(bnd["xy"]), dtype=np.float64)
+    return out
 
 
 def square(seed=3000, n=1000, jitter=0.3, panels_per_side=64, order=16, precision="fp32",
