@@ -55,6 +55,8 @@ def parse():
                     help="plan precision of the timed line (fp64: tol 1e-9; fp32: tol 1e-5)")
     ap.add_argument("--levels", default="auto", choices=["auto", "1", "2"],
                     help="history levels of every plan (auto: one level when its grid side is <= 1536)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="plans time three bin sides on their sources at the first lp_volume")
     ap.add_argument("--refine-levels", type=int, default=0,
                     help="dyadic refinement levels of the local layer potentials (starfish/disk/square)")
     args = ap.parse_args()
@@ -192,7 +194,7 @@ def run_lp(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     fp64 = args.precision == "fp64"
     ev = lp.Evaluator(prob, precision=args.precision, tol=1e-9 if fp64 else 1e-5, stream=stream.cuda_stream,
-                      refine_levels=args.refine_levels, levels=levels_arg(args))
+                      refine_levels=args.refine_levels, levels=levels_arg(args), autotune=args.autotune)
     plan = ev.plan
 
     def step():
@@ -534,8 +536,8 @@ def run_batch(args, rank, world, local_rank):
     out = {}
     stream = torch.cuda.Stream(device=dev)
     for prec, tol in (("fp64", 1e-9), ("fp32", 1e-5)):
-        evs = [lp.Evaluator(p, precision=prec, tol=tol, stream=stream.cuda_stream, levels=levels_arg(args)).bind()
-               for p in probs]
+        evs = [lp.Evaluator(p, precision=prec, tol=tol, stream=stream.cuda_stream, levels=levels_arg(args),
+                            autotune=args.autotune).bind() for p in probs]
         T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
         txy = [T(p["tgt_xy"]) for p in probs]
         jet = [T(p["tgt_jet"]) for p in probs]
@@ -580,6 +582,8 @@ def run_batch(args, rank, world, local_rank):
         res["parity_max_rel_l2_sampled"] = max(errs)
         res["tol"] = tol
         res["single_level_plans"] = int(sum(e.info()["levels"] == 1 for e in evs))
+        res["bin_sides"] = {str(c): int(sum(e.info()["bin_cells"] == c for e in evs))
+                            for c in sorted(set(int(e.info()["bin_cells"]) for e in evs))}
         res["dtype"] = dtype_of(evs[0].info())
         out[prec] = res
         lp.lp_batch_destroy(b)
@@ -593,6 +597,7 @@ def run_batch(args, rank, world, local_rank):
             "config": {"workload": f"{len(probs)} star domains r=1+a cos kt, a~U[0.1,0.4], k in 3..9, "
                                    "log-uniform 1k..200k triangles, one wave",
                        "n_problems": len(probs), "points_per_wave": points, "levels": args.levels,
+                       "autotune": bool(args.autotune),
                        "triangles_total": int(sum(p["meta"]["n_triangles"] for p in probs))},
             "batch": out}
 

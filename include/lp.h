@@ -118,6 +118,11 @@ typedef struct {
                            default (FP64 1.5, FP32 2), else 1.25 .. 3; the
                            kernel width follows from tol and sigma (LP_ERR_ARG
                            when it would exceed 16) */
+  int autotune;         /* nonzero: the first lp_volume that binds sources
+                           times the binned volume spread for three bin sides
+                           (FP64 16/24/32, FP32 16/32/48 near-history cells)
+                           on those sources and keeps the fastest (it
+                           synchronises the plan's stream once) */
 } lp_domain;
 
 /* Create a plan: chooses the near/far-history grids (Sec. 3: delta_2 =
@@ -240,7 +245,7 @@ lp_status lp_destroy(lp_plan_t plan);
 const char* lp_status_string(lp_status status);
 
 /* Plan parameters, for diagnostics and benchmarks:
- * out[0..27] = {delta_1, delta_2, kernel width w, beta, g_NH, K_NH, P_NH, g_FH, K_FH,
+ * out[0..30] = {delta_1, delta_2, kernel width w, beta, g_NH, K_NH, P_NH, g_FH, K_FH,
  *               P_FH, L_FH, band 12 sqrt(delta_1), node-gap margin, device bytes,
  *               precision, order, kernels launched by this plan so far,
  *               max error of the kernel's polynomial form, its coefficient count,
@@ -250,9 +255,11 @@ const char* lp_status_string(lp_status status);
  *               1 if volume sources are spread through bins, bin side in
  *               near-history cells, dyadic refinement levels, largest error
  *               of the refinement's kernel tables, refinement subnodes,
- *               history levels in use (2 or 1), upsampling sigma}; the
+ *               history levels in use (2 or 1), upsampling sigma, and the
+ *               autotuner's spread times in ms of its three bin sides
+ *               (0 if it has not run, -1 for a side that does not fit)}; the
  *               near-history entries are 0 for single-level plans.
- *               out must hold 28 doubles. */
+ *               out must hold 31 doubles. */
 lp_status lp_plan_info(lp_plan_t plan, double* out);
 
 /* Per-stage device times of the last lp_execute in milliseconds (CUDA events

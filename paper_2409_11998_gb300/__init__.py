@@ -45,7 +45,8 @@ class lp_domain(ctypes.Structure):
                 ("bnd_normal", ctypes.c_void_p), ("stream", ctypes.c_void_p),
                 ("refine_levels", ctypes.c_int),
                 ("levels", ctypes.c_int),
-                ("upsampling", ctypes.c_double)]
+                ("upsampling", ctypes.c_double),
+                ("autotune", ctypes.c_int)]
 
 
 _LIB = None
@@ -111,7 +112,8 @@ def _ptr(a):
 
 
 def lp_plan(box_lo, box_hi, delta, tol, *, precision=LP_FP64, order=5, n_panels=0, panel_order=16,
-            bnd_xy=None, bnd_w=None, bnd_normal=None, stream=0, refine_levels=0, levels=0, upsampling=0.0):
+            bnd_xy=None, bnd_w=None, bnd_normal=None, stream=0, refine_levels=0, levels=0, upsampling=0.0,
+            autotune=False):
     dom = lp_domain()
     dom.precision = int(precision)
     dom.order = int(order)
@@ -126,6 +128,7 @@ def lp_plan(box_lo, box_hi, delta, tol, *, precision=LP_FP64, order=5, n_panels=
     dom.refine_levels = LP_REFINE_AUTO if refine_levels == "auto" else int(refine_levels)
     dom.levels = LP_LEVELS_AUTO if levels == "auto" else int(levels)
     dom.upsampling = float(upsampling)
+    dom.autotune = 1 if autotune else 0
     h = ctypes.c_void_p()
     _check(_lib().lp_plan(ctypes.byref(dom), float(delta), float(tol), ctypes.byref(h)), "lp_plan")
     return h
@@ -212,12 +215,12 @@ def lp_destroy(plan):
 
 
 def lp_plan_info(plan):
-    out = np.zeros(28)
+    out = np.zeros(31)
     _check(_lib().lp_plan_info(plan, out.ctypes.data), "lp_plan_info")
     keys = ["delta1", "delta2", "w", "beta", "g_nh", "K_nh", "P_nh", "g_fh", "K_fh", "P_fh", "L_fh",
             "band", "margin", "device_bytes", "precision", "order", "launches", "es_fit_err", "es_nc",
             "sigma_eff", "own_fft", "binned", "bin_cells", "refine_levels", "refine_table_err",
-            "refine_subnodes", "levels", "sigma"]
+            "refine_subnodes", "levels", "sigma", "tune_ms_0", "tune_ms_1", "tune_ms_2"]
     return dict(zip(keys, out.tolist()))
 
 
@@ -235,7 +238,7 @@ class Evaluator:
     ``host=True``, in which case the C ABI receives host pointers."""
 
     def __init__(self, problem, precision=None, order=5, tol=None, device="cuda", host=False,
-                 stream=None, refine_levels=0, levels=0, upsampling=0.0):
+                 stream=None, refine_levels=0, levels=0, upsampling=0.0, autotune=False):
         import torch
         self.torch = torch
         self.host = host
@@ -262,7 +265,8 @@ class Evaluator:
                       bnd_w=dev(b["w"]), bnd_normal=dev(b["normal"]))
         self.plan = lp_plan(problem["box_lo"], problem["box_hi"], problem["delta"], self.tol,
                             precision=self.precision, order=order, stream=self.stream,
-                            refine_levels=refine_levels, levels=levels, upsampling=upsampling, **kw)
+                            refine_levels=refine_levels, levels=levels, upsampling=upsampling,
+                            autotune=autotune, **kw)
         self.problem = problem
 
     def bind(self, src_xy=None, src_w=None, src_f=None, sigma=None, mu=None):

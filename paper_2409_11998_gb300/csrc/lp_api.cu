@@ -240,24 +240,26 @@ namespace lpg {
 // (32 for FP32 plans; 24 for FP64 plans, whose df64 patches take twice the
 // shared memory).  FP32 plans whose kernel fit needs more coefficients than
 // the binned kernel holds keep the point-parallel spread.
-lp_status setup_bins(Plan& P) {
+// Bin geometry for bins of `cells` near-history cells (first level in use):
+// origin, count, and per level the patch side -- the bin, the stencil halo
+// and a cell of rounding slack; among the next 16 sizes, the one whose row
+// pitch gives the fewest shared-memory wavefronts for the w^2 stencil cells
+// taken 32 at a time (4-byte cells: 32 banks per warp; 8-byte cells: 16 per
+// half warp).  False if a patch would not fit in shared memory.
+static bool configure_bins(Plan& P, int cells) {
   const GridLevel& N = P.lv[P.l0];
   const int w = P.ker.w;
   const bool f64 = P.precision == LP_FP64;
-  if (w < 4 || (!f64 && (w > 10 || P.es32.nc > sub_ncw(w)))) return LP_OK;
-  P.bin_cells = f64 ? 24 : kTile;
-  P.bins.x0 = N.x0;
-  P.bins.y0 = N.y0;
-  P.bins.inv_bt = 1.0 / (P.bin_cells * N.h);
-  P.bins.nbx = P.bins.nby = (N.g + P.bin_cells - 1) / P.bin_cells;
-  // Patch side per level: the bin, the stencil halo and a cell of rounding
-  // slack; among the next 16 sizes, the one whose row pitch gives the fewest
-  // shared-memory wavefronts for the w^2 stencil cells taken 32 at a time
-  // (4-byte cells: 32 banks per warp; 8-byte cells: 16 per half warp).
+  BinGeom bins;
+  bins.x0 = N.x0;
+  bins.y0 = N.y0;
+  bins.inv_bt = 1.0 / (cells * N.h);
+  bins.nbx = bins.nby = (N.g + cells - 1) / cells;
+  int M[2] = {0, 0};
   const int banks = f64 ? 16 : 32, group = f64 ? 16 : 32;
   for (int l = P.l0; l < 2; ++l) {
-    const double cells = P.bin_cells * N.h / P.lv[l].h;
-    const int m0 = (int)std::ceil(cells) + w + 3;
+    const double c = cells * N.h / P.lv[l].h;
+    const int m0 = (int)std::ceil(c) + w + 3;
     int best = m0, best_wf = 1 << 30;
     for (int m = m0; m < m0 + 16; ++m) {
       int wf = 0;
@@ -272,13 +274,32 @@ lp_status setup_bins(Plan& P) {
         best = m;
       }
     }
-    P.sub_M[l] = best;
+    M[l] = best;
     const size_t smem = f64 ? spread_sub_dd_smem(best, w)
                             : (size_t)(((sub_ncw(w) * w + 3) & ~3) + (kSubThreads / 32) * best * best) * sizeof(float);
-    if (smem > 200 * 1024) return LP_OK;
+    if (smem > 200 * 1024) return false;
   }
+  P.bin_cells = cells;
+  P.bins = bins;
+  P.sub_M[0] = M[0];
+  P.sub_M[1] = M[1];
+  return true;
+}
+
+// Bins of the binned volume spread: squares of bin_cells near-history cells
+// (32 for FP32 plans; 24 for FP64 plans, whose df64 patches take twice the
+// shared memory; plans created with autotune time kBinCandidates at the first
+// lp_volume).  FP32 plans whose kernel fit needs more coefficients than the
+// binned kernel holds keep the point-parallel spread.
+lp_status setup_bins(Plan& P) {
+  const int w = P.ker.w;
+  const bool f64 = P.precision == LP_FP64;
+  if (w < 4 || (!f64 && (w > 10 || P.es32.nc > sub_ncw(w)))) return LP_OK;
+  if (!configure_bins(P, f64 ? 24 : kTile)) return LP_OK;
   if (!(f64 ? spread_sub_dd_configure(w) : spread_sub_configure(w))) return LP_ERR_CUDA;
-  const size_t nbins = (size_t)P.bins.nbx * P.bins.nby + 1;
+  // bin bookkeeping sized for the smallest candidate bin
+  const int nb_max = (P.lv[P.l0].g + kBinCandidates[f64][0] - 1) / kBinCandidates[f64][0];
+  const size_t nbins = (size_t)nb_max * nb_max + 1;
   if (!dalloc(P, (void**)&P.d_counts, nbins * sizeof(int)) ||
       !dalloc(P, (void**)&P.d_cursor, nbins * sizeof(int)) ||
       !dalloc(P, (void**)&P.d_vstart, (nbins + 1) * sizeof(int)))
@@ -538,6 +559,7 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
   P.precision = dom->precision;
   P.order = order;
   P.delta1 = delta;
+  P.autotune = dom->autotune != 0;
   P.l0 = dom->levels == 1 ? 1 : 0;
   P.delta2 = P.l0 ? delta : 32.0 * delta;
   P.tol = tol;
@@ -643,6 +665,59 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
   return LP_OK;
 }
 
+// Counting sort of the bound volume nodes into the current bins.
+static void bin_volume(Plan& P, int64_t n) {
+  if (P.precision == LP_FP64) {
+    launch_bin_sort_dd(P.d_vxy, n, P.bins, P.d_keys, P.d_counts, P.d_cursor, P.d_vstart, P.d_vrel_dd, P.d_vperm,
+                       P.d_status, P.stream);
+    launch_gather_q_dd(P.d_vq, P.d_vperm, n, P.d_vq_dd, P.stream);
+  } else {
+    launch_bin_sort(P.d_vxy, n, P.bins, P.d_keys, P.d_counts, P.d_cursor, P.d_vstart, P.d_vrel_s, P.d_vperm,
+                    P.d_status, P.stream);
+    launch_gather_q(P.d_vq, n, 1, P.d_vperm, n, P.d_vq_s, P.stream);
+  }
+  P.launches += 4;
+}
+
+// Autotuner of the bin side: for each candidate, bin the bound volume nodes
+// and time the binned spread of both levels (median of three after one
+// warm-up, CUDA events on the plan's stream; the grids are scratch until
+// lp_execute zeroes them); keep the fastest and bin with it.
+static lp_status tune_bins(Plan& P, int64_t n) {
+  const int f64 = P.precision == LP_FP64 ? 1 : 0;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LP_ERR_CUDA;
+  const int base = P.bin_cells;
+  int best = base;
+  float best_ms = 1e30f;
+  for (int c = 0; c < 3; ++c) {
+    const int cells = kBinCandidates[f64][c];
+    P.tune_ms[c] = -1.f;
+    if (!configure_bins(P, cells)) continue;
+    bin_volume(P, n);
+    float t[3];
+    for (int r = 0; r < 4; ++r) {
+      cudaEventRecord(e0, P.stream);
+      for (int l = P.l0; l < 2; ++l) spread_volume_binned(P, l, P.stream);
+      cudaEventRecord(e1, P.stream);
+      cudaEventSynchronize(e1);
+      if (r > 0) cudaEventElapsedTime(&t[r - 1], e0, e1);
+    }
+    std::sort(t, t + 3);
+    P.tune_ms[c] = t[1];
+    if (t[1] < best_ms) {
+      best_ms = t[1];
+      best = cells;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!configure_bins(P, best)) configure_bins(P, base);
+  bin_volume(P, n);
+  P.tuned = true;
+  return status_from_cuda();
+}
+
 lp_status lp_volume(lp_plan_t h, int64_t n, const double* xy, const double* w, const double* f) {
   if (!h || n < 0) return LP_ERR_ARG;
   if (n > 0 && (!xy || !w || !f)) return LP_ERR_ARG;
@@ -695,16 +770,11 @@ lp_status lp_volume(lp_plan_t h, int64_t n, const double* xy, const double* w, c
         P.vsort_cap = n;
       }
     }
-    if (f64) {
-      launch_bin_sort_dd(P.d_vxy, n, P.bins, P.d_keys, P.d_counts, P.d_cursor, P.d_vstart, P.d_vrel_dd,
-                         P.d_vperm, P.d_status, P.stream);
-      launch_gather_q_dd(P.d_vq, P.d_vperm, n, P.d_vq_dd, P.stream);
-    } else {
-      launch_bin_sort(P.d_vxy, n, P.bins, P.d_keys, P.d_counts, P.d_cursor, P.d_vstart, P.d_vrel_s, P.d_vperm,
-                      P.d_status, P.stream);
-      launch_gather_q(P.d_vq, n, 1, P.d_vperm, n, P.d_vq_s, P.stream);
+    bin_volume(P, n);
+    if (P.autotune && !P.tuned) {
+      const lp_status st = tune_bins(P, n);
+      if (st != LP_OK) return st;
     }
-    P.launches += 4;
   }
   launch_sum(P, P.d_vq, n, P.d_qsum, P.stream);
   P.have_volume = true;
@@ -989,12 +1059,13 @@ lp_status lp_destroy(lp_plan_t h) {
 lp_status lp_plan_info(lp_plan_t h, double* out) {
   if (!h || !out) return LP_ERR_ARG;
   const Plan& P = h->P;
-  double v[28] = {P.delta1, P.delta2, (double)P.ker.w, P.ker.beta, (double)P.lv[0].g, (double)P.lv[0].K,
+  double v[31] = {P.delta1, P.delta2, (double)P.ker.w, P.ker.beta, (double)P.lv[0].g, (double)P.lv[0].K,
                   P.lv[0].P, (double)P.lv[1].g, (double)P.lv[1].K, P.lv[1].P, P.lv[1].L, P.band,
                   P.margin, (double)P.device_bytes, (double)P.precision, (double)P.order,
                   (double)P.launches, P.es_fit_err, (double)P.es.nc, P.sigma_eff,
                   P.own_fft ? 1.0 : 0.0, P.binned ? 1.0 : 0.0, (double)P.bin_cells,
-                  (double)P.dy_levels, P.dy_err, (double)P.dy_nq, (double)(2 - P.l0), P.sigma};
+                  (double)P.dy_levels, P.dy_err, (double)P.dy_nq, (double)(2 - P.l0), P.sigma,
+                  (double)P.tune_ms[0], (double)P.tune_ms[1], (double)P.tune_ms[2]};
   std::memcpy(out, v, sizeof(v));
   return LP_OK;
 }

@@ -17,6 +17,8 @@ constexpr int kMaxNC = 20;          // coefficients per piece of the kernel poly
 constexpr int kBatchThreads = 128;  // threads per block (and items per work entry) of batched launches
 constexpr int kZeroChunk = 4096;    // 16-byte words cleared per work entry of the batched zeroing
 constexpr int kTile = 32;           // bin side (near-history cells) of the binned spread
+// bin sides the autotuner times, [FP64 plan][candidate], smallest first
+constexpr int kBinCandidates[2][3] = {{16, 32, 48}, {16, 24, 32}};
 constexpr int kSubThreads = 256;    // threads per CTA of the binned spread
 constexpr int kSubDDThreads = 128;  // threads per CTA of the binned df64 spread (FP64 plans)
 // Coefficient count of the binned spread's weight polynomials for width w
@@ -352,6 +354,9 @@ struct Plan {
   int* d_vstart = nullptr;         // [nbins + 2]
   bool binned = false;             // volume spread through the bins
   int bin_cells = kTile;           // bin side in near-history cells (FP32 32, FP64 24)
+  bool autotune = false;           // time the bin candidates at the first lp_volume
+  bool tuned = false;
+  float tune_ms[3] = {0, 0, 0};    // spread time of each candidate (both levels)
   float4* d_vrel_dd = nullptr;     // FP64 plans: offsets from the bin corner, df64
   float2* d_vq_dd = nullptr;       // FP64 plans: strengths in bin order, df64
   size_t key_cap = 0;
