@@ -181,6 +181,19 @@ lp_status lp_execute(lp_plan_t plan, int64_t n_t, const double* t_xy, const doub
 lp_status lp_execute_noalloc(lp_plan_t plan, int64_t n_t, const double* t_xy, const double* f_jet,
                              double* V, double* S, double* D);
 
+/* lp_execute replayed from a CUDA graph (same arguments and results): the
+ * first call for an argument signature -- the pointers, n_t, the bound
+ * source count, and no reallocation or bin change in the plan since --
+ * runs lp_execute and captures the same call into a graph; later calls with
+ * that signature launch the graph (one launch for the whole chain).  Bound
+ * densities and sources may change between calls (their buffers are
+ * reused).  Device pointers only (LP_ERR_ARG otherwise).  Plans whose
+ * transforms run on cuFFT run lp_execute directly.  The replay is ordered
+ * after the work already queued on the plan's stream, and later work on
+ * that stream after the replay. */
+lp_status lp_execute_graph(lp_plan_t plan, int64_t n_t, const double* t_xy, const double* f_jet, double* V,
+                           double* S, double* D);
+
 /* Batched evaluation of a wave of independent problems (many uneven
  * problems, one launch per kernel per wave).  A batch owns only the
  * wave's argument records and candidate list; the member plans are ordinary

@@ -28,7 +28,7 @@ STATUS = {0: "LP_OK", 1: "LP_ERR_ARG", 2: "LP_ERR_OUT_OF_BOX", 3: "LP_ERR_NOMEM"
 EXPORTS = ("lp_plan", "lp_volume", "lp_single_layer", "lp_double_layer", "lp_execute", "lp_sync",
            "lp_destroy", "lp_status_string", "lp_plan_info", "lp_stage_times", "lp_execute_noalloc",
            "lp_batch_create", "lp_batch_execute", "lp_batch_sync", "lp_batch_stage_times",
-           "lp_batch_destroy", "lp_solve_dirichlet")
+           "lp_batch_destroy", "lp_solve_dirichlet", "lp_execute_graph")
 
 
 class LpError(RuntimeError):
@@ -65,6 +65,7 @@ def _lib():
         L.lp_double_layer.argtypes = [vp, vp]
         L.lp_execute.argtypes = [vp, i64, vp, vp, vp, vp, vp]
         L.lp_execute_noalloc.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+        L.lp_execute_graph.argtypes = [vp, i64, vp, vp, vp, vp, vp]
         L.lp_batch_create.argtypes = [vp, ctypes.POINTER(vp)]
         L.lp_batch_execute.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp]
         L.lp_batch_sync.argtypes = [vp]
@@ -156,6 +157,13 @@ def lp_execute_noalloc(plan, n_t, t_xy, f_jet, V=None, S=None, D=None):
     (see include/lp.h)."""
     _check(_lib().lp_execute_noalloc(plan, int(n_t), _ptr(t_xy), _ptr(f_jet), _ptr(V), _ptr(S),
                                      _ptr(D)), "lp_execute_noalloc")
+
+
+def lp_execute_graph(plan, n_t, t_xy, f_jet, V, S, D):
+    """lp_execute replayed from a CUDA graph after the first call with these
+    arguments (device buffers only)."""
+    _check(_lib().lp_execute_graph(plan, int(n_t), _ptr(t_xy), _ptr(f_jet), _ptr(V), _ptr(S), _ptr(D)),
+           "lp_execute_graph")
 
 
 def lp_solve_dirichlet(plan, g, mu, f_jet_b=None, tol=1e-10, max_iter=200, restart=30):
@@ -288,8 +296,32 @@ class Evaluator:
             lp_double_layer(self.plan, self._mu)
         return self
 
-    def evaluate(self, tgt_xy=None, tgt_jet=None, want=("V", "S", "D"), sync=True):
+    def evaluate(self, tgt_xy=None, tgt_jet=None, want=("V", "S", "D"), sync=True, graph=False):
+        """V, S, D at the targets (default: the problem's).  graph=True goes
+        through lp_execute_graph with device buffers kept by the evaluator
+        (the problem's targets, or the given device tensors), so repeated
+        calls replay one CUDA graph; the returned outputs are those buffers."""
         p = self.problem
+        if graph:
+            if self.host:
+                raise ValueError("graph replay needs device buffers")
+            torch = self.torch
+            if tgt_xy is None:
+                if getattr(self, "_graph_tgt", None) is None:
+                    self._graph_tgt = (torch.as_tensor(np.ascontiguousarray(p["tgt_xy"]), device=self.device),
+                                       torch.as_tensor(np.ascontiguousarray(p["tgt_jet"]), device=self.device))
+                t, j = self._graph_tgt
+            else:
+                t, j = tgt_xy, tgt_jet
+            n = len(t)
+            key = (n, tuple(want))
+            if getattr(self, "_graph_outs", None) is None or self._graph_outs[0] != key:
+                self._graph_outs = (key, {k: torch.empty(n, dtype=torch.float64, device=self.device) for k in want})
+            outs = self._graph_outs[1]
+            lp_execute_graph(self.plan, n, t, j if "V" in want else None, outs.get("V"), outs.get("S"), outs.get("D"))
+            if sync:
+                lp_sync(self.plan)
+            return outs
         txy = p["tgt_xy"] if tgt_xy is None else tgt_xy
         jet = p["tgt_jet"] if tgt_jet is None else tgt_jet
         n = len(txy)

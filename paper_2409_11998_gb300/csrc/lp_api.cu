@@ -75,12 +75,23 @@ bool dalloc(Plan& P, void** ptr, size_t bytes) {
     *ptr = nullptr;
     return false;
   }
+  ++P.gen;
   P.device_bytes += bytes;
   return true;
 }
 
 void dfree(void* p) {
   if (p) cudaFree(p);
+}
+
+// Stage timing event k on stream s; while lp_execute is captured into a
+// graph the record becomes a graph node (external record), so the replayed
+// graph still times its stages.
+void record_stage(const Plan& P, int k, cudaStream_t s) {
+  if (P.capturing)
+    cudaEventRecordWithFlags(P.ev[k], s, cudaEventRecordExternal);
+  else
+    cudaEventRecord(P.ev[k], s);
 }
 
 // Device view of a caller array: used in place when it is device memory,
@@ -130,6 +141,7 @@ lp_status make_fft_plans(Plan& P, GridLevel& G) {
 }
 
 void destroy_plan(Plan& P) {
+  if (P.graph_stream) cudaStreamSynchronize(P.graph_stream);
   if (P.copy_stream) cudaStreamSynchronize(P.copy_stream);
   if (P.stream) cudaStreamSynchronize(P.stream);
   for (auto& G : P.lv) {
@@ -155,6 +167,10 @@ void destroy_plan(Plan& P) {
   if (P.h_status) cudaFreeHost(P.h_status);
   for (auto& e : P.ev)
     if (e) cudaEventDestroy(e);
+  if (P.graph_exec) cudaGraphExecDestroy(P.graph_exec);
+  if (P.ev_g0) cudaEventDestroy(P.ev_g0);
+  if (P.ev_g1) cudaEventDestroy(P.ev_g1);
+  if (P.graph_stream) cudaStreamDestroy(P.graph_stream);
   if (P.ev_in) cudaEventDestroy(P.ev_in);
   if (P.ev_staged) cudaEventDestroy(P.ev_staged);
   if (P.copy_stream) cudaStreamDestroy(P.copy_stream);
@@ -280,6 +296,7 @@ static bool configure_bins(Plan& P, int cells) {
     if (smem > 200 * 1024) return false;
   }
   P.bin_cells = cells;
+  ++P.gen;
   P.bins = bins;
   P.sub_M[0] = M[0];
   P.sub_M[1] = M[1];
@@ -447,7 +464,7 @@ void history_transforms(const Plan& P, bool wv, bool ws, bool wd, cudaStream_t s
     launch_fft_rows_fwd(row_args(P.lv[l], fch, nf), nf, f64, s);
     ++P.launches;
   }
-  if (events) cudaEventRecord(P.ev[4], s);
+  if (events) record_stage(P, 4, s);
   for (int l = P.l0; l < 2; ++l) {
     const GridLevel& G = P.lv[l];
     FftColArgs a{};
@@ -466,12 +483,12 @@ void history_transforms(const Plan& P, bool wv, bool ws, bool wd, cudaStream_t s
     launch_fft_cols(a, nj, f64, s);
     ++P.launches;
   }
-  if (events) cudaEventRecord(P.ev[5], s);
+  if (events) record_stage(P, 5, s);
   for (int l = P.l0; l < 2; ++l) {
     launch_fft_rows_inv(row_args(P.lv[l], ich, ni), ni, f64, s);
     ++P.launches;
   }
-  if (events) cudaEventRecord(P.ev[6], s);
+  if (events) record_stage(P, 6, s);
 }
 
 // Step 4 after the FFT chain: interpolation from the chain's grids (df64
@@ -847,7 +864,7 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
     P.near_cap = nt;
   }
   if (!P.d_near_count && !dalloc(P, (void**)&P.d_near_count, sizeof(int))) return LP_ERR_NOMEM;
-  cudaEventRecord(P.ev[0], s);
+  record_stage(P, 0, s);
   // Host targets and jets are copied on the plan's copy stream, overlapping
   // the spreads and transforms; the staging buffer is free once the work
   // already queued on the plan's stream has run, and the interpolation
@@ -871,7 +888,7 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
   if (host_in) cudaEventRecord(P.ev_staged, cs);
   double* dout[3];
   for (int c = 0; c < 3; ++c) dout[c] = host_out[c] ? P.d_out + c * nt : outs[c];
-  cudaEventRecord(P.ev[1], s);
+  record_stage(P, 1, s);
 
   // Steps 2-3: spread every requested channel onto both history grids:
   // volume nodes through the bins (FP32 plans) or point-parallel with global
@@ -885,7 +902,7 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
       cudaMemsetAsync(G.chan[3], 0, G.chan_bytes, s);
     }
   }
-  cudaEventRecord(P.ev[2], s);
+  record_stage(P, 2, s);
   for (int l = P.l0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
     if (wv && P.nv > 0) {
@@ -898,7 +915,7 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
       }
     }
   }
-  cudaEventRecord(P.ev[10], s);
+  record_stage(P, 10, s);
   for (int l = P.l0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
     const double* bq[3];
@@ -916,7 +933,7 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
     }
     if (nq) launch_spread(P, l, P.d_bxy, bq, nq, bg, P.nb, s);
   }
-  cudaEventRecord(P.ev[3], s);
+  record_stage(P, 3, s);
   if (P.own_fft) {
     history_transforms(P, wv, ws, wd, s, true);
     if (host_in) cudaStreamWaitEvent(s, P.ev_staged, 0);
@@ -930,27 +947,103 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
         fft_forward(P, l, 3);
       }
     }
-    cudaEventRecord(P.ev[4], s);
+    record_stage(P, 4, s);
     // Step 4: deconvolved multiplier (in place; D written to channel 2)
     for (int l = P.l0; l < 2; ++l) launch_multiplier(P, l, wv, ws, wd, s);
-    cudaEventRecord(P.ev[5], s);
+    record_stage(P, 5, s);
     for (int l = P.l0; l < 2; ++l) {
       if (wv) fft_inverse(P, l, 0);
       if (ws) fft_inverse(P, l, 1);
       if (wd) fft_inverse(P, l, 2);
     }
-    cudaEventRecord(P.ev[6], s);
+    record_stage(P, 6, s);
     if (host_in) cudaStreamWaitEvent(s, P.ev_staged, 0);
     launch_interp(P, nt, dt, dout[0], dout[1], dout[2], s);
   }
-  cudaEventRecord(P.ev[7], s);
+  record_stage(P, 7, s);
   launch_local(P, nt, dt, dj, dout[0], dout[1], dout[2], s);
-  cudaEventRecord(P.ev[11], s);
+  record_stage(P, 11, s);
   launch_dyadic(P, nt, dt, dout[1], dout[2], P.d_near, P.d_near_count, s);
-  cudaEventRecord(P.ev[8], s);
+  record_stage(P, 8, s);
   for (int c = 0; c < 3; ++c)
     if (host_out[c]) cudaMemcpyAsync(outs[c], dout[c], nt * sizeof(double), cudaMemcpyDeviceToHost, s);
-  cudaEventRecord(P.ev[9], s);
+  record_stage(P, 9, s);
+  return status_from_cuda();
+}
+
+// lp_execute replayed from a CUDA graph.  A miss (new pointers, target
+// count, source count, or any reallocation or bin change since the capture)
+// runs lp_execute directly -- which also grows every buffer to its final
+// capacity -- and then captures a second lp_execute, issued on the plan's
+// graph stream, into an executable graph.  Each call (hit or miss) orders
+// the graph stream after the work already on the plan's stream and the
+// plan's stream after the replay, so plans on the legacy default stream work.
+lp_status lp_execute_graph(lp_plan_t h, int64_t nt, const double* txy, const double* jet, double* V, double* S,
+                           double* D) {
+  if (!h || nt < 0 || nt > (int64_t)INT32_MAX) return LP_ERR_ARG;
+  Plan& P = h->P;
+  const void* key[5] = {txy, V ? jet : nullptr, V, S, D};
+  for (const void* b : key)
+    if (b && !is_device_ptr(b)) return LP_ERR_ARG;  // device memory only: no staging copies in a graph
+  if (!P.own_fft || nt == 0 || (!V && !S && !D)) return lp_execute(h, nt, txy, jet, V, S, D);
+  if (!P.graph_stream) {
+    if (cudaStreamCreateWithFlags(&P.graph_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&P.ev_g0, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&P.ev_g1, cudaEventDisableTiming) != cudaSuccess)
+      return LP_ERR_CUDA;
+  }
+  bool hit = P.graph_exec && P.graph_nt == nt && P.graph_nv == P.nv && P.graph_gen == P.gen;
+  for (int i = 0; i < 5 && hit; ++i) hit = P.graph_key[i] == key[i];
+  if (!hit) {
+    lp_status st = lp_execute(h, nt, txy, jet, V, S, D);  // this call's result; sizes every buffer
+    if (st != LP_OK) return st;
+    if (P.graph_exec) {
+      cudaGraphExecDestroy(P.graph_exec);
+      P.graph_exec = nullptr;
+    }
+    const unsigned long long gen0 = P.gen;
+    const long long launches0 = P.launches;
+    cudaStream_t user = P.stream;
+    P.stream = P.graph_stream;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(P.graph_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      P.stream = user;
+      return LP_ERR_CUDA;
+    }
+    P.capturing = true;
+    st = lp_execute(h, nt, txy, jet, V, S, D);
+    P.capturing = false;
+    const cudaError_t ce = cudaStreamEndCapture(P.graph_stream, &graph);
+    P.stream = user;
+    P.graph_launches = P.launches - launches0;
+    P.launches = launches0;  // captured, not run
+    if (st != LP_OK || ce != cudaSuccess || P.gen != gen0) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return st != LP_OK ? st : LP_ERR_CUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&P.graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      P.graph_exec = nullptr;
+      cudaGetLastError();
+      return LP_ERR_CUDA;
+    }
+    P.graph_nt = nt;
+    P.graph_nv = P.nv;
+    P.graph_gen = P.gen;
+    for (int i = 0; i < 5; ++i) P.graph_key[i] = key[i];
+    return LP_OK;
+  }
+  cudaEventRecord(P.ev_g0, P.stream);
+  cudaStreamWaitEvent(P.graph_stream, P.ev_g0, 0);
+  if (cudaGraphLaunch(P.graph_exec, P.graph_stream) != cudaSuccess) {
+    cudaGetLastError();
+    return LP_ERR_CUDA;
+  }
+  cudaEventRecord(P.ev_g1, P.graph_stream);
+  cudaStreamWaitEvent(P.stream, P.ev_g1, 0);
+  P.launches += P.graph_launches;
   return status_from_cuda();
 }
 
@@ -973,8 +1066,8 @@ lp_status lp_execute_noalloc(lp_plan_t h, int64_t nt, const double* txy, const d
   int2* list = (int2*)scratch;
   int* count = (int*)((char*)scratch + kNoAllocListBytes);
   cudaStream_t s = P.stream;
-  cudaEventRecord(P.ev[0], s);
-  cudaEventRecord(P.ev[1], s);
+  record_stage(P, 0, s);
+  record_stage(P, 1, s);
   for (int l = P.l0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
     if (wv) cudaMemsetAsync(G.chan[0], 0, G.chan_bytes, s);
@@ -984,7 +1077,7 @@ lp_status lp_execute_noalloc(lp_plan_t h, int64_t nt, const double* txy, const d
       cudaMemsetAsync(G.chan[3], 0, G.chan_bytes, s);
     }
   }
-  cudaEventRecord(P.ev[2], s);
+  record_stage(P, 2, s);
   for (int l = P.l0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
     if (wv && P.nv > 0) {
@@ -993,7 +1086,7 @@ lp_status lp_execute_noalloc(lp_plan_t h, int64_t nt, const double* txy, const d
       launch_spread(P, l, P.d_vxy, q, 1, g, P.nv, s);
     }
   }
-  cudaEventRecord(P.ev[10], s);
+  record_stage(P, 10, s);
   for (int l = P.l0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
     const double* bq[3];
@@ -1011,28 +1104,28 @@ lp_status lp_execute_noalloc(lp_plan_t h, int64_t nt, const double* txy, const d
     }
     if (nq) launch_spread(P, l, P.d_bxy, bq, nq, bg, P.nb, s);
   }
-  cudaEventRecord(P.ev[3], s);
+  record_stage(P, 3, s);
   for (int l = P.l0; l < 2; ++l) {
     const int chans[4] = {wv ? 0 : -1, ws ? 1 : -1, wd ? 2 : -1, wd ? 3 : -1};
     for (int c : chans)
       if (c >= 0) fft_forward(P, l, c);
   }
-  cudaEventRecord(P.ev[4], s);
+  record_stage(P, 4, s);
   for (int l = P.l0; l < 2; ++l) launch_multiplier(P, l, wv, ws, wd, s);
-  cudaEventRecord(P.ev[5], s);
+  record_stage(P, 5, s);
   for (int l = P.l0; l < 2; ++l) {
     const int chans[3] = {wv ? 0 : -1, ws ? 1 : -1, wd ? 2 : -1};
     for (int c : chans)
       if (c >= 0) fft_inverse(P, l, c);
   }
-  cudaEventRecord(P.ev[6], s);
+  record_stage(P, 6, s);
   launch_interp(P, nt, txy, V, S, D, s);
-  cudaEventRecord(P.ev[7], s);
+  record_stage(P, 7, s);
   launch_local_list(P, nt, txy, wv ? jet : nullptr, V, S, D, list, count, s);
-  cudaEventRecord(P.ev[11], s);
+  record_stage(P, 11, s);
   launch_dyadic(P, nt, txy, S, D, list, count, s);
-  cudaEventRecord(P.ev[8], s);
-  cudaEventRecord(P.ev[9], s);
+  record_stage(P, 8, s);
+  record_stage(P, 9, s);
   return status_from_cuda();
 }
 

@@ -393,6 +393,17 @@ struct Plan {
   // transforms run (created at the first execute with host inputs)
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_staged = nullptr;
+  // graph replay of lp_execute (lp_execute_graph): one cached executable
+  // graph per argument signature, captured on graph_stream
+  unsigned long long gen = 0;      // bumped by every allocation or bin change
+  cudaStream_t graph_stream = nullptr;
+  cudaEvent_t ev_g0 = nullptr, ev_g1 = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  const void* graph_key[5] = {};
+  int64_t graph_nt = -1, graph_nv = -1;
+  unsigned long long graph_gen = 0;
+  long long graph_launches = 0;
+  bool capturing = false;          // lp_execute is being captured into a graph
   size_t device_bytes = 0;
   mutable long long launches = 0;  // kernels launched by this plan (all calls)
 };
