@@ -239,6 +239,7 @@ struct LocalArgs {
   const double* mu_coef;
   const double* mu_ref;
   double hx0, hy0, hh;
+  float hh32, inv_hh32, band32, margin32;  // single-precision copies for the classification
   int hnx, hny;
   const int* cell_start;
   const int* cell_node;
