@@ -59,6 +59,7 @@ struct DD {
     return cdd{dd_mul(a.re, c), dd_mul(a.im, c)};
   }
   __device__ static V tw(const float4* t, int k) { return cdd_load(t + k); }
+  __device__ static void store_tw(S* p, float4 v) { *p = v; }
   __device__ static V mul(V a, V t) { return cdd_mul(a, t); }
   __device__ static V mul_conj(V a, V t) { return cdd_mul_conj(a, t); }
 };
@@ -80,6 +81,7 @@ struct F32 {
     const float4 v = t[k];
     return make_float2(v.x, v.z);
   }
+  __device__ static void store_tw(S* p, float4 v) { *p = make_float2(v.x, v.z); }
   __device__ static V mul(V a, V t) { return make_float2(a.x * t.x - a.y * t.y, a.x * t.y + a.y * t.x); }
   __device__ static V mul_conj(V a, V t) { return make_float2(a.x * t.x + a.y * t.y, a.y * t.x - a.x * t.y); }
 };
@@ -111,9 +113,31 @@ __device__ __forceinline__ void dft_small(typename A::V* v, bool inv) {
   }
 }
 
-template <class A, int R>
+// Twiddles e^{-2 pi i m / N} of a length-N transform: from a shared-memory
+// table of the N values, or from the global df64 table of length g at
+// stride tws = g / N.
+template <class A>
+struct SmemTw {
+  const typename A::S* t;
+  __device__ typename A::V operator()(int m) const { return A::load(t + m); }
+};
+template <class A>
+struct GlobTw {
+  const float4* __restrict__ t;
+  int tws;
+  __device__ typename A::V operator()(int m) const { return A::tw(t, m * tws); }
+};
+
+// the N twiddles of a length-N transform into shared memory (the caller
+// synchronises before use)
+template <class A>
+__device__ __forceinline__ void load_twiddles(typename A::S* dst, const float4* __restrict__ tw, int N, int tws) {
+  for (int m = threadIdx.x; m < N; m += blockDim.x) A::store_tw(dst + m, __ldg(tw + (size_t)m * tws));
+}
+
+template <class A, int R, class TW>
 __device__ __forceinline__ void stockham_butterfly(const typename A::S* in, typename A::S* out, int j, int N,
-                                                   int Ns, const float4* __restrict__ tw, int tws, bool inv) {
+                                                   int Ns, const TW& tw, bool inv) {
   using V = typename A::V;
   const int stride = N / R;
   V v[R];
@@ -121,10 +145,10 @@ __device__ __forceinline__ void stockham_butterfly(const typename A::S* in, type
   for (int r = 0; r < R; ++r) v[r] = A::load(in + j + r * stride);
   const int k = j % Ns;
   if (k != 0) {
-    const int step = (N / (Ns * R)) * tws;
+    const int step = N / (Ns * R);
 #pragma unroll
     for (int r = 1; r < R; ++r) {
-      const V t = A::tw(tw, k * r * step);
+      const V t = tw(k * r * step);
       v[r] = inv ? A::mul_conj(v[r], t) : A::mul(v[r], t);
     }
   }
@@ -137,20 +161,20 @@ __device__ __forceinline__ void stockham_butterfly(const typename A::S* in, type
 // Transform of length N held in a (scratch b); returns the buffer holding
 // the result.  All threads of the CTA take part; the caller synchronises
 // before (data in a) and the function synchronises after every stage.
-template <class A>
-__device__ typename A::S* fft_smem(typename A::S* a, typename A::S* b, const FftShape& sh,
-                                   const float4* __restrict__ tw, int tws, bool inv) {
+template <class A, class TW>
+__device__ typename A::S* fft_smem(typename A::S* a, typename A::S* b, const FftShape& sh, const TW& tw,
+                                   bool inv) {
   const int N = sh.n;
   int Ns = 1;
   for (int s = 0; s < sh.nst; ++s) {
     const int R = sh.radix[s];
     const int nb = N / R;
     if (R == 4) {
-      for (int j = threadIdx.x; j < nb; j += blockDim.x) stockham_butterfly<A, 4>(a, b, j, N, Ns, tw, tws, inv);
+      for (int j = threadIdx.x; j < nb; j += blockDim.x) stockham_butterfly<A, 4>(a, b, j, N, Ns, tw, inv);
     } else if (R == 2) {
-      for (int j = threadIdx.x; j < nb; j += blockDim.x) stockham_butterfly<A, 2>(a, b, j, N, Ns, tw, tws, inv);
+      for (int j = threadIdx.x; j < nb; j += blockDim.x) stockham_butterfly<A, 2>(a, b, j, N, Ns, tw, inv);
     } else {
-      for (int j = threadIdx.x; j < nb; j += blockDim.x) stockham_butterfly<A, 3>(a, b, j, N, Ns, tw, tws, inv);
+      for (int j = threadIdx.x; j < nb; j += blockDim.x) stockham_butterfly<A, 3>(a, b, j, N, Ns, tw, inv);
     }
     __syncthreads();
     typename A::S* t = a;
@@ -159,6 +183,86 @@ __device__ typename A::S* fft_smem(typename A::S* a, typename A::S* b, const Fft
     Ns *= R;
   }
   return a;
+}
+
+// In-place mixed-radix transforms of one shared-memory buffer (used by the
+// column pass, whose spectrum is only multiplied between the forward and the
+// inverse transform).  Forward: decimation in frequency (Sande-Tukey) over the
+// radices in order; stage s splits blocks of length L into R interleaved
+// sub-blocks of length L/R (butterfly, then twiddles W_L^{t j}), leaving the
+// transform in mixed-radix digit-reversed order (position p holds frequency
+// fft_dif_order[p]).  Inverse: decimation in time over the radices in
+// reverse order (conjugate twiddles, then the conjugate butterfly), taking
+// that order back to natural order.  Unnormalised, like the Stockham form.
+template <class A, int R, class TW>
+__device__ __forceinline__ void dif_stage(typename A::S* x, int N, int L, const TW& tw, int t0, int nt) {
+  using V = typename A::V;
+  const int Lr = L / R, step = N / L;
+  for (int q = t0; q < N / R; q += nt) {
+    const int b = q / Lr, j = q - b * Lr;
+    typename A::S* base = x + b * L + j;
+    V v[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u) v[u] = A::load(base + u * Lr);
+    dft_small<A, R>(v, false);
+    if (j != 0) {
+#pragma unroll
+      for (int t = 1; t < R; ++t) v[t] = A::mul(v[t], tw(t * j * step));
+    }
+#pragma unroll
+    for (int t = 0; t < R; ++t) A::store(base + t * Lr, v[t]);
+  }
+}
+
+template <class A, int R, class TW>
+__device__ __forceinline__ void dit_stage_inv(typename A::S* x, int N, int L, const TW& tw, int t0, int nt) {
+  using V = typename A::V;
+  const int Lr = L / R, step = N / L;
+  for (int q = t0; q < N / R; q += nt) {
+    const int b = q / Lr, j = q - b * Lr;
+    typename A::S* base = x + b * L + j;
+    V v[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) v[t] = A::load(base + t * Lr);
+    if (j != 0) {
+#pragma unroll
+      for (int t = 1; t < R; ++t) v[t] = A::mul_conj(v[t], tw(t * j * step));
+    }
+    dft_small<A, R>(v, true);
+#pragma unroll
+    for (int u = 0; u < R; ++u) A::store(base + u * Lr, v[u]);
+  }
+}
+
+// Threads t0, t0 + nt, ... of the CTA transform x; the caller synchronises
+// before (data in x); every stage ends with a CTA-wide barrier, so all
+// thread groups of the CTA must run the same sequence of stages.
+template <class A, class TW>
+__device__ void fft_dif(typename A::S* x, const FftShape& sh, const TW& tw, int t0, int nt) {
+  const int N = sh.n;
+  int L = N;
+  for (int s = 0; s < sh.nst; ++s) {
+    const int R = sh.radix[s];
+    if (R == 4) dif_stage<A, 4>(x, N, L, tw, t0, nt);
+    else if (R == 2) dif_stage<A, 2>(x, N, L, tw, t0, nt);
+    else dif_stage<A, 3>(x, N, L, tw, t0, nt);
+    __syncthreads();
+    L /= R;
+  }
+}
+
+template <class A, class TW>
+__device__ void fft_dit_inv(typename A::S* x, const FftShape& sh, const TW& tw, int t0, int nt) {
+  const int N = sh.n;
+  int L = sh.radix[sh.nst - 1];  // the block length of the last forward stage
+  for (int s = sh.nst - 1; s >= 0; --s) {
+    const int R = sh.radix[s];
+    if (R == 4) dit_stage_inv<A, 4>(x, N, L, tw, t0, nt);
+    else if (R == 2) dit_stage_inv<A, 2>(x, N, L, tw, t0, nt);
+    else dit_stage_inv<A, 3>(x, N, L, tw, t0, nt);
+    __syncthreads();
+    if (s > 0) L *= sh.radix[s - 1];
+  }
 }
 
 // grid row -> complex sequence z_n = x_2n + i x_2n+1
@@ -195,6 +299,16 @@ __device__ __forceinline__ float2 dipole_mode(float2 f1, float2 f2, float m, flo
   return make_float2(m * (kx * f1.y + ky * f2.y), -m * (kx * f1.x + ky * f2.x));
 }
 
+// Twiddles in shared memory (a third buffer) for the single-precision chain:
+// its butterflies are cheap and the per-stage global twiddle loads saturated
+// the L1 pipe.  The double-float chain keeps the global table: a third
+// 16-byte buffer cuts the CTAs per SM (measured slower) and, for columns of
+// the largest grids, exceeds shared memory.
+template <class A>
+constexpr bool kTwSmem = false;
+template <>
+constexpr bool kTwSmem<F32> = true;
+
 // Forward transform of real rows: one CTA per (row, channel).
 template <class A>
 __global__ void __launch_bounds__(kFftThreads) fft_rows_fwd_kernel(const __grid_constant__ FftRowArgs a) {
@@ -208,9 +322,12 @@ __global__ void __launch_bounds__(kFftThreads) fft_rows_fwd_kernel(const __grid_
   const char* src = (const char*)a.grid[c] + (size_t)row * a.pitch * (sizeof(S) / 2);
   S* buf0 = sm;
   S* buf1 = sm + N;
+  S* twt = sm + 2 * N;
+  if (kTwSmem<A>) load_twiddles<A>(twt, a.tw, N, 2);
   for (int n = threadIdx.x; n < N; n += blockDim.x) A::store(buf0 + n, load_pair(src, n, A()));
   __syncthreads();
-  const S* Z = fft_smem<A>(buf0, buf1, a.half, a.tw, 2, false);
+  const S* Z = kTwSmem<A> ? fft_smem<A>(buf0, buf1, a.half, SmemTw<A>{twt}, false)
+                          : fft_smem<A>(buf0, buf1, a.half, GlobTw<A>{a.tw, 2}, false);
   S* dst = (S*)a.spec[c] + (size_t)row * a.kp;
   for (int k = threadIdx.x; k <= a.K; k += blockDim.x) {
     const V zk = A::load(Z + k), zn = A::conj(A::load(Z + (k == 0 ? 0 : N - k)));
@@ -220,63 +337,91 @@ __global__ void __launch_bounds__(kFftThreads) fft_rows_fwd_kernel(const __grid_
   }
 }
 
-// Column pass: one CTA per (kept column m_x, job).  Jobs of kind 0 transform
-// one spectrum and multiply by M; kind 1 (D) transforms two and combines
-// them, parking the first transform in its own (global) column meanwhile so
-// that every job needs only two shared-memory buffers of g values.
-template <class A>
-__global__ void __launch_bounds__(kFftThreads) fft_cols_kernel(const __grid_constant__ FftColArgs a) {
+// Column pass: one CTA per (C adjacent kept columns, job), one shared-memory
+// buffer of g values per column (in-place transforms) and a group of
+// kFftThreads threads per column.  Loads and stores interleave the C columns,
+// so the C values of a spectrum row fill whole 32-byte sectors (the spectrum
+// is stored row by row).  Jobs of kind 0 transform one spectrum and multiply
+// by M; kind 1 (D) transforms two and combines them, parking the first
+// transform (in digit-reversed order) in its own global columns meanwhile.
+// The multiplier is applied in the forward transform's order.
+template <class A, int C>
+__global__ void __launch_bounds__(kFftThreads * C) fft_cols_kernel(const __grid_constant__ FftColArgs a) {
   using V = typename A::V;
   using S = typename A::S;
   extern __shared__ float4 sm_raw[];
   S* sm = (S*)sm_raw;
-  const int g = a.full.n, K = a.K, mx = blockIdx.x;
+  const int g = a.full.n, K = a.K, mx0 = blockIdx.x * C;
+  const int grp = threadIdx.x / kFftThreads, t0 = threadIdx.x % kFftThreads;
+  const int mx = mx0 + grp;  // this group's column
   const FftColJob& job = a.job[blockIdx.y];
-  S* buf0 = sm;
-  S* buf1 = sm + g;
-  auto load_col = [&](const void* spec) {
+  S* x = sm + (size_t)grp * g;
+  S* twt = sm + (size_t)C * g;
+  if (kTwSmem<A>) load_twiddles<A>(twt, a.tw, g, 1);
+  const SmemTw<A> tws{twt};
+  const GlobTw<A> twg{a.tw, 1};
+  // element e of the CTA's C x g block: row e / C, column mx0 + e % C
+  auto load_cols = [&](const void* spec) {
     const S* sp = (const S*)spec;
-    for (int r = threadIdx.x; r < g; r += blockDim.x) {
-      if (r >= a.row_lo && r < a.row_hi)
-        buf0[r] = sp[(size_t)r * a.kp + mx];
+    for (int e = threadIdx.x; e < C * g; e += blockDim.x) {
+      const int r = e / C, c = e - r * C;
+      S* dst = sm + (size_t)c * g + r;
+      if (r >= a.row_lo && r < a.row_hi && mx0 + c < a.kp)
+        *dst = sp[(size_t)r * a.kp + mx0 + c];
       else
-        A::store(buf0 + r, A::zero());
+        A::store(dst, A::zero());
     }
     __syncthreads();
   };
-  S* X;
+  auto forward = [&]() {
+    if (kTwSmem<A>)
+      fft_dif<A>(x, a.full, tws, t0, kFftThreads);
+    else
+      fft_dif<A>(x, a.full, twg, t0, kFftThreads);
+  };
   if (job.kind == 1) {
-    load_col(job.in[0]);
-    const S* F1 = fft_smem<A>(buf0, buf1, a.full, a.tw, 1, false);
-    S* park = (S*)job.out;  // the D1 spectrum column, all g rows
-    for (int r = threadIdx.x; r < g; r += blockDim.x) park[(size_t)r * a.kp + mx] = F1[r];
+    load_cols(job.in[0]);
+    forward();
+    S* park = (S*)job.out;  // the D1 spectrum columns, all g rows
+    for (int e = threadIdx.x; e < C * g; e += blockDim.x) {
+      const int p = e / C, c = e - p * C;
+      if (mx0 + c < a.kp) park[(size_t)p * a.kp + mx0 + c] = sm[(size_t)c * g + p];
+    }
     __syncthreads();
-    load_col(job.in[1]);
-    X = fft_smem<A>(buf0, buf1, a.full, a.tw, 1, false);
-    for (int r = threadIdx.x; r < g; r += blockDim.x) {
+    load_cols(job.in[1]);
+    forward();
+    for (int p = t0; p < g; p += kFftThreads) {
+      const int r = __ldg(a.freq + p);
       const int my = r <= g / 2 ? r : r - g;
       const int amy = my < 0 ? -my : my;
       V o = A::zero();
-      if (amy <= K)
-        o = dipole_mode(A::load(park + (size_t)r * a.kp + mx), A::load(X + r),
+      if (amy <= K && mx <= K)
+        o = dipole_mode(A::load(park + (size_t)p * a.kp + mx), A::load(x + p),
                         mult_value(a.tab, (size_t)amy * (K + 1) + mx, A()), a.dk, mx, my);
-      A::store(X + r, o);
+      A::store(x + p, o);
     }
   } else {
-    load_col(job.in[0]);
-    X = fft_smem<A>(buf0, buf1, a.full, a.tw, 1, false);
-    for (int r = threadIdx.x; r < g; r += blockDim.x) {
+    load_cols(job.in[0]);
+    forward();
+    for (int p = t0; p < g; p += kFftThreads) {
+      const int r = __ldg(a.freq + p);
       const int my = r <= g / 2 ? r : r - g;
       const int amy = my < 0 ? -my : my;
       V o = A::zero();
-      if (amy <= K) o = scale_real(A::load(X + r), mult_value(a.tab, (size_t)amy * (K + 1) + mx, A()));
-      A::store(X + r, o);
+      if (amy <= K && mx <= K) o = scale_real(A::load(x + p), mult_value(a.tab, (size_t)amy * (K + 1) + mx, A()));
+      A::store(x + p, o);
     }
   }
   __syncthreads();
-  const S* Y = fft_smem<A>(X, X == buf0 ? buf1 : buf0, a.full, a.tw, 1, true);
+  if (kTwSmem<A>)
+    fft_dit_inv<A>(x, a.full, tws, t0, kFftThreads);
+  else
+    fft_dit_inv<A>(x, a.full, twg, t0, kFftThreads);
   S* out = (S*)job.out;
-  for (int r = a.row_lo + threadIdx.x; r < a.row_hi; r += blockDim.x) out[(size_t)r * a.kp + mx] = Y[r];
+  for (int e = threadIdx.x; e < C * (a.row_hi - a.row_lo); e += blockDim.x) {
+    const int rr = e / C, c = e - rr * C, r = a.row_lo + rr;
+    if (mx0 + c < a.kp) out[(size_t)r * a.kp + mx0 + c] = sm[(size_t)c * g + r];
+  }
 }
 
 // Inverse transform of rows: one CTA per (row, job); writes the g values of
@@ -292,6 +437,8 @@ __global__ void __launch_bounds__(kFftThreads) fft_rows_inv_kernel(const __grid_
   const S* spec = (const S*)a.spec[c] + (size_t)row * a.kp;
   S* buf0 = sm;
   S* buf1 = sm + N;
+  S* twt = sm + 2 * N;
+  if (kTwSmem<A>) load_twiddles<A>(twt, a.tw, N, 2);
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     V xk = k <= a.K ? A::load(spec + k) : A::zero();
     if (k == 0) xk = A::add(A::half(xk), A::half(A::conj(xk)));  // drop the imaginary part
@@ -301,7 +448,8 @@ __global__ void __launch_bounds__(kFftThreads) fft_rows_inv_kernel(const __grid_
     A::store(buf0 + k, A::add(A::add(xk, xn), A::pi(B)));
   }
   __syncthreads();
-  const S* z = fft_smem<A>(buf0, buf1, a.half, a.tw, 2, true);
+  const S* z = kTwSmem<A> ? fft_smem<A>(buf0, buf1, a.half, SmemTw<A>{twt}, true)
+                          : fft_smem<A>(buf0, buf1, a.half, GlobTw<A>{a.tw, 2}, true);
   char* dst = (char*)a.grid[c] + (size_t)row * a.pitch * (sizeof(S) / 2);
   for (int n = threadIdx.x; n < N; n += blockDim.x) store_pair(dst, n, A::load(z + n), A());
 }
@@ -353,14 +501,48 @@ std::vector<float4> fft_twiddles(int g) {
   return t;
 }
 
-size_t fft_rows_smem(int g, bool f64) { return (size_t)2 * (g / 2) * (f64 ? sizeof(float4) : sizeof(float2)); }
-size_t fft_cols_smem(int g, bool f64) { return (size_t)2 * g * (f64 ? sizeof(float4) : sizeof(float2)); }
+// rows: two buffers of the transform length, and for FP32 the twiddle table
+size_t fft_rows_smem(int g, bool f64) { return f64 ? (size_t)2 * (g / 2) * sizeof(float4) : (size_t)3 * (g / 2) * sizeof(float2); }
+// columns: one buffer per column of a CTA (in-place transforms), and for
+// FP32 the twiddle table
+size_t fft_cols_smem_c(int g, bool f64, int C) {
+  return f64 ? (size_t)C * g * sizeof(float4) : (size_t)(C + 1) * g * sizeof(float2);
+}
+// Columns per CTA: FP64 two when they fit (their 16-byte values then fill
+// whole sectors; measured 0.56 -> 0.54 ms on the starfish), FP32 one (four
+// 1024-thread groups measured slower: 0.30 -> 0.32 ms).
+int fft_cols_per_cta(int g, bool f64) {
+  if (f64 && fft_cols_smem_c(g, f64, 2) <= 220 * 1024) return 2;
+  return 1;
+}
+size_t fft_cols_smem(int g, bool f64) { return fft_cols_smem_c(g, f64, 1); }
+
+// Position -> frequency of the in-place decimation-in-frequency transform:
+// after stage s (radix R_s, block length L_s -> L_s / R_s) the digit of
+// frequency weight R_0 ... R_{s-1} sits at position weight L_s / R_s.
+std::vector<int> fft_dif_order(const FftShape& sh) {
+  std::vector<int> fr(sh.n);
+  for (int p = 0; p < sh.n; ++p) {
+    int q = p, k = 0, prod = 1, L = sh.n;
+    for (int s = 0; s < sh.nst; ++s) {
+      L /= sh.radix[s];
+      const int d = q / L;
+      q -= d * L;
+      k += d * prod;
+      prod *= sh.radix[s];
+    }
+    fr[p] = k;
+  }
+  return fr;
+}
 
 bool fft_dd_configure() {
   const int bytes = 220 * 1024;
-  const void* fns[6] = {(const void*)fft_rows_fwd_kernel<DD>, (const void*)fft_rows_inv_kernel<DD>,
-                        (const void*)fft_cols_kernel<DD>,      (const void*)fft_rows_fwd_kernel<F32>,
-                        (const void*)fft_rows_inv_kernel<F32>, (const void*)fft_cols_kernel<F32>};
+  const void* fns[9] = {(const void*)fft_rows_fwd_kernel<DD>,  (const void*)fft_rows_inv_kernel<DD>,
+                        (const void*)fft_cols_kernel<DD, 1>,    (const void*)fft_cols_kernel<DD, 2>,
+                        (const void*)fft_rows_fwd_kernel<F32>, (const void*)fft_rows_inv_kernel<F32>,
+                        (const void*)fft_cols_kernel<F32, 1>,   (const void*)fft_cols_kernel<F32, 2>,
+                        (const void*)fft_cols_kernel<F32, 4>};
   for (const void* f : fns)
     if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return false;
   return true;
@@ -388,11 +570,22 @@ void launch_fft_rows_inv(const FftRowArgs& a, int nchan, bool f64, cudaStream_t 
 
 void launch_fft_cols(const FftColArgs& a, int njobs, bool f64, cudaStream_t s) {
   if (njobs <= 0) return;
-  const size_t smem = fft_cols_smem(a.full.n, f64);
-  if (f64)
-    fft_cols_kernel<DD><<<dim3(a.K + 1, njobs), kFftThreads, smem, s>>>(a);
-  else
-    fft_cols_kernel<F32><<<dim3(a.K + 1, njobs), kFftThreads, smem, s>>>(a);
+  const int C = fft_cols_per_cta(a.full.n, f64);
+  const size_t smem = fft_cols_smem_c(a.full.n, f64, C);
+  const dim3 grid((a.K + C) / C, njobs);  // ceil((K + 1) / C) column groups
+  if (f64) {
+    if (C == 2)
+      fft_cols_kernel<DD, 2><<<grid, kFftThreads * 2, smem, s>>>(a);
+    else
+      fft_cols_kernel<DD, 1><<<grid, kFftThreads, smem, s>>>(a);
+  } else {
+    if (C == 4)
+      fft_cols_kernel<F32, 4><<<grid, kFftThreads * 4, smem, s>>>(a);
+    else if (C == 2)
+      fft_cols_kernel<F32, 2><<<grid, kFftThreads * 2, smem, s>>>(a);
+    else
+      fft_cols_kernel<F32, 1><<<grid, kFftThreads, smem, s>>>(a);
+  }
 }
 
 }  // namespace lpg

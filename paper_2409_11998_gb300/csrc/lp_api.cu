@@ -148,6 +148,7 @@ void destroy_plan(Plan& P) {
     for (auto& c : G.chan) dfree(c);
     for (auto& c : G.spec) dfree(c);
     dfree(G.tw_dd);
+    dfree(G.freq);
     dfree(G.mtab_dd);
     dfree(G.mtab);
     dfree(G.mtab32);
@@ -416,6 +417,9 @@ lp_status setup_fft_chain(Plan& P) {
     const std::vector<float4> tw = fft_twiddles(G.g);
     if (!dalloc(P, (void**)&G.tw_dd, tw.size() * sizeof(float4))) return LP_ERR_NOMEM;
     cudaMemcpy(G.tw_dd, tw.data(), tw.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    const std::vector<int> fr = fft_dif_order(G.full);
+    if (!dalloc(P, (void**)&G.freq, fr.size() * sizeof(int))) return LP_ERR_NOMEM;
+    cudaMemcpy(G.freq, fr.data(), fr.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (f64) {
       const size_t ntab = (size_t)(G.K + 1) * (G.K + 1);
       if (!dalloc(P, (void**)&G.mtab_dd, ntab * sizeof(float2))) return LP_ERR_NOMEM;
@@ -470,6 +474,7 @@ void history_transforms(const Plan& P, bool wv, bool ws, bool wd, cudaStream_t s
     FftColArgs a{};
     a.full = G.full;
     a.tw = G.tw_dd;
+    a.freq = G.freq;
     a.tab = f64 ? (const void*)G.mtab_dd : (const void*)G.mtab32;
     a.dk = f64 ? split_host(G.dk) : make_float2((float)G.dk, 0.f);
     int nj = 0;

@@ -90,6 +90,7 @@ struct GridLevel {
   // columns [g][kp] (kp = K + 1 rounded up to even), df64 or FP32 complex
   FftShape full{}, half{};
   float4* tw_dd = nullptr;
+  int* freq = nullptr;  // digit-reversed order of the in-place column transform, [g]
   float2* mtab_dd = nullptr;
   void* spec[4] = {nullptr, nullptr, nullptr, nullptr};
   int kp = 0;
@@ -198,6 +199,7 @@ struct FftColJob {
 struct FftColArgs {
   FftShape full;
   const float4* tw;
+  const int* freq;    // frequency index of each position of the in-place forward transform's output
   const void* tab;    // deconvolved multiplier, (K+1)^2: df64 pairs (FP64) or floats without k = 0 (FP32)
   float2 dk;          // mode spacing (df64 pair; FP32 uses .x)
   FftColJob job[3];
@@ -463,6 +465,7 @@ size_t spread_sub_smem(const SubArgs& a, int w);
 void launch_spread_sub(const SubArgs& a, int w, cudaStream_t s);
 FftShape fft_shape(int n);
 std::vector<float4> fft_twiddles(int g);
+std::vector<int> fft_dif_order(const FftShape& sh);
 bool fft_dd_configure();
 size_t fft_rows_smem(int g, bool f64);
 size_t fft_cols_smem(int g, bool f64);
