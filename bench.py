@@ -298,30 +298,40 @@ def df64_peak_t():
     return 152 * 128 * sm_max_mhz() * 1e6 / DF64_FMA_INSTR / 1e12
 
 
+def fp32_fma_peak_t():
+    """FP32 multiply-adds per second: 152 SMs x 128 lanes x max SM clock (T/s)."""
+    return 152 * 128 * sm_max_mhz() * 1e6 / 1e12
+
+
 def roofline(info, st, nv, nb, nt, precision, n_out=3, workload="starfish"):
-    """Roofline of this library's dominant kernel.
+    """Roofline of this library's dominant kernel: among the candidates
+    below, the one whose stage takes longest in the live step.
 
-    FP64 plans with the double-float chain: the volume spread
-    (spread_sub_dd_kernel, both levels) or the interpolation
-    (interp_dd_kernel), whichever takes longer, bound by FP32 issue.  Work per
-    point and level, in double-float multiply-adds: 2 w (nc - 1) for the two
-    weight polynomials plus w (w + 1) per channel (w q*wy products and w^2
-    cell updates for the spread; w^2 products and w row combinations per
-    output for the interpolation).
-
-    FP32 plans: the binned volume spread (spread_sub_kernel, both levels)
-    against HBM bandwidth, with algorithmic bytes: positions (2b) and
-    strengths (b) of every volume node read once, the V grids of both levels
-    written once (b per cell)."""
+    FP64 plans with the double-float chain (bound by FP32 issue, in
+    double-float multiply-adds; work per point and level 2 w (nc - 1) for
+    the two weight polynomials plus w (w + 1) per channel -- w q*wy products
+    and w^2 cell updates for the spread, w^2 products and w row combinations
+    per output for the interpolation):
+      spread_sub_dd_kernel (volume spread, both levels), interp_dd_kernel.
+    FP32 plans:
+      spread_sub_kernel: FP32 multiply-adds, w^2 cell updates + 2 w (nc - 1)
+        weight terms per volume node and level, against the FP32 FMA peak;
+      fft_cols_kernel (column pass: forward column transforms, multiplier,
+        inverse): HBM, algorithmic bytes per level = the four input spectra
+        read and the three outputs written, g x kp complex values each;
+      interp_kernel: HBM, the three output grids of both levels read once,
+        the targets read and the three outputs written."""
     b = 8 if precision == "fp64" else 4
     W, nc = int(info["w"]), int(info["es_nc"])
-    g2 = info["g_nh"] ** 2 + info["g_fh"] ** 2
+    levels = [(info["g_nh"], info["K_nh"]), (info["g_fh"], info["K_fh"])]
+    levels = [(g, K) for g, K in levels if g > 0]
     hbm, hbm_kind = peaks()
     vol_ms = st.get("spread_volume", st["spread"])
     if precision == "fp64" and (info.get("own_fft") and info.get("precision") == 0):
-        cand = {"spread": (vol_ms, nv * 2 * (2 * W * (nc - 1) + W * (W + 1)),
+        nl = len(levels)
+        cand = {"spread": (vol_ms, nv * nl * (2 * W * (nc - 1) + W * (W + 1)),
                            "spread_sub_dd_kernel" if info.get("binned") else "spread_atomic_kernel"),
-                "interp": (st["interp"], nt * 2 * (2 * W * (nc - 1) + n_out * W * (W + 1)), "interp_dd_kernel")}
+                "interp": (st["interp"], nt * nl * (2 * W * (nc - 1) + n_out * W * (W + 1)), "interp_dd_kernel")}
         dom = max(cand, key=lambda k: cand[k][0])
         ms, ops, kname = cand[dom]
         ach = ops / (ms / 1e3) / 1e12
@@ -342,13 +352,28 @@ def roofline(info, st, nv, nb, nt, precision, n_out=3, workload="starfish"):
                 "traffic": kernel_traffic("spread_atomic_kernel", workload), "algorithmic_flops_per_step": int(flops),
                 "launch_ms": round(ms, 4), "stage": "spread",
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x sm_max_mhz"}
-    kname = "spread_sub_kernel" if info.get("binned") else "spread_atomic_kernel"
-    byts = nv * 3 * b + g2 * b
-    gbs = byts / (vol_ms / 1e3) / 1e9
+    kp = lambda K: (int(K) + 2) & ~1
+    cols_bytes = sum(7 * g * kp(K) * 2 * b for g, K in levels)
+    interp_bytes = sum(n_out * g * g * b for g, _ in levels) + nt * (16 + 8 * n_out)
+    spread_fma = nv * len(levels) * (W * W + 2 * W * (nc - 1))
+    cand = {"spread_volume": vol_ms, "multiplier": st["multiplier"], "interp": st["interp"]}
+    dom = max(cand, key=lambda k: cand[k])
+    ms = cand[dom]
+    if dom == "spread_volume":
+        kname = "spread_sub_kernel" if info.get("binned") else "spread_atomic_kernel"
+        ach = spread_fma / (ms / 1e3) / 1e12
+        peak = fp32_fma_peak_t()
+        return {"kernel": kname, "bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 4),
+                "unit": "T FP32-FMA/s", "frac": round(ach / peak, 5), "traffic": kernel_traffic(kname, workload),
+                "traffic_unit": "DRAM bytes per step (both launches)", "algorithmic_fma_per_step": int(spread_fma),
+                "launch_ms": round(ms, 4), "stage": dom,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x sm_max_mhz"}
+    kname, byts = ("fft_cols_kernel", cols_bytes) if dom == "multiplier" else ("interp_kernel", interp_bytes)
+    gbs = byts / (ms / 1e3) / 1e9
     return {"kernel": kname, "bound": "hbm", "achieved": round(gbs, 2), "peak": hbm, "unit": "GB/s",
             "frac": round(gbs / hbm, 5), "traffic": kernel_traffic(kname, workload),
-            "traffic_unit": "DRAM bytes per step (both launches)",
-            "algorithmic_bytes_per_step": int(byts), "launch_ms": round(vol_ms, 4), "stage": "spread_volume",
+            "traffic_unit": "DRAM bytes per step (all launches of the stage)",
+            "algorithmic_bytes_per_step": int(byts), "launch_ms": round(ms, 4), "stage": dom,
             "peak_source": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)"}
 
 

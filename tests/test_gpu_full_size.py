@@ -2,9 +2,10 @@
 times (device-resident inputs, one plan, V + S + D in one lp_execute), on
 sampled targets the oracle evaluates one by one.
 
-Workloads: the 1.2M-node starfish (FP64 at 1e-9 and FP32 at 1e-5) and the
-12M-node square with 1M vertex targets (geometry-only boundary, V only; FP64
-at 1e-9 and FP32 at 1e-5).  The sample mixes uniformly drawn targets with the
+Workloads: the 1.2M-node starfish (FP64 at 1e-9 and FP32 at 1e-5; also with
+three levels of dyadic refinement, one history level, and upsampling 1.25
+with the bin autotuner) and the 12M-node square with 1M vertex targets
+(geometry-only boundary, V only; FP64 at 1e-9 and FP32 at 1e-5).  The sample mixes uniformly drawn targets with the
 targets closest to the boundary (local expansions, on-surface points and, on
 the square, the corners).
 """
@@ -34,12 +35,12 @@ def _sample(prob, n_random=40, n_near=24, seed=17):
     return np.unique(np.concatenate([rand, near]))
 
 
-def _run(lp, prob, precision, tol, oracle_lib):
+def _run(lp, prob, precision, tol, oracle_lib, **plan):
     want = tuple(k for k in "VSD" if k == "V" or prob.get({"S": "sigma", "D": "mu"}[k]) is not None)
-    ev = lp.Evaluator(prob, precision=precision, tol=tol).bind()
+    ev = lp.Evaluator(prob, precision=precision, tol=tol, **plan).bind()
     out = ev.evaluate(want=want)
     idx = _sample(prob)
-    ref = oracle_lib.evaluate(prob, targets=idx, want=want)
+    ref = oracle_lib.evaluate(prob, targets=idx, want=want, refine_levels=ev.info()["refine_levels"])
     for k in want:
         got = out[k].cpu().numpy()[idx]
         l2 = np.linalg.norm(got - ref[k]) / np.linalg.norm(ref[k])
@@ -65,6 +66,16 @@ def square():
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 1e-5)])
 def test_starfish_full_size(lp, starfish, oracle_lib, precision, tol):
     _run(lp, starfish, precision, tol, oracle_lib)
+
+
+@pytest.mark.parametrize("precision,tol,plan", [("fp64", 1e-9, dict(refine_levels=3)),
+                                                ("fp32", 1e-5, dict(refine_levels=3)),
+                                                ("fp64", 1e-9, dict(levels=1)),
+                                                ("fp32", 1e-5, dict(upsampling=1.25, autotune=True))])
+def test_starfish_full_size_variants(lp, starfish, oracle_lib, precision, tol, plan):
+    """Dyadic refinement, one history level, other upsampling with the
+    bin autotuner, at the full starfish size."""
+    _run(lp, starfish, precision, tol, oracle_lib, **plan)
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 1e-5)])
