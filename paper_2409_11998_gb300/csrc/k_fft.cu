@@ -337,6 +337,12 @@ __global__ void __launch_bounds__(kFftThreads) fft_rows_fwd_kernel(const __grid_
   }
 }
 
+// strided column loads in flight per thread
+template <class A>
+constexpr int kColBatch = 4;
+template <>
+constexpr int kColBatch<F32> = 8;
+
 // Column pass: one CTA per (C adjacent kept columns, job), one shared-memory
 // buffer of g values per column (in-place transforms) and a group of
 // kFftThreads threads per column.  Loads and stores interleave the C columns,
@@ -360,16 +366,27 @@ __global__ void __launch_bounds__(kFftThreads * C) fft_cols_kernel(const __grid_
   if (kTwSmem<A>) load_twiddles<A>(twt, a.tw, g, 1);
   const SmemTw<A> tws{twt};
   const GlobTw<A> twg{a.tw, 1};
-  // element e of the CTA's C x g block: row e / C, column mx0 + e % C
+  // element e of the CTA's C x g block: row e / C, column mx0 + e % C; the
+  // strided loads are issued kColBatch at a time before their stores, so
+  // that several are in flight per thread
   auto load_cols = [&](const void* spec) {
     const S* sp = (const S*)spec;
-    for (int e = threadIdx.x; e < C * g; e += blockDim.x) {
-      const int r = e / C, c = e - r * C;
-      S* dst = sm + (size_t)c * g + r;
-      if (r >= a.row_lo && r < a.row_hi && mx0 + c < a.kp)
-        *dst = sp[(size_t)r * a.kp + mx0 + c];
-      else
-        A::store(dst, A::zero());
+    constexpr int U = kColBatch<A>;
+    for (int e0 = threadIdx.x; e0 < C * g; e0 += U * blockDim.x) {
+      S v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * blockDim.x, r = e / C, c = e - r * C;
+        if (e < C * g && r >= a.row_lo && r < a.row_hi && mx0 + c < a.kp)
+          v[u] = sp[(size_t)r * a.kp + mx0 + c];
+        else
+          A::store(v + u, A::zero());
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * blockDim.x, r = e / C, c = e - r * C;
+        if (e < C * g) sm[(size_t)c * g + r] = v[u];
+      }
     }
     __syncthreads();
   };
