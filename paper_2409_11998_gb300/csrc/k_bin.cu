@@ -233,10 +233,10 @@ __device__ __forceinline__ bool stencil_dd(dd u, int M, int& i0, dd& v) {
 // chains of its own point, x weights and q times y weights, into shared
 // memory -- and that patch cells hold df64 sums.  The CTA adds its patch to
 // the FP64 grid with FP64 atomics.
-template <int W>
-__global__ void __launch_bounds__(kSubDDThreads) spread_sub_dd_kernel(const __grid_constant__ SubDDArgs a) {
+template <int W, int NW>
+__global__ void __launch_bounds__(NW * 32) spread_sub_dd_kernel(const __grid_constant__ SubDDArgs a) {
   extern __shared__ float2 smd[];
-  constexpr int NC = W * W, NP = (NC + 31) / 32, NWARP = kSubDDThreads / 32;
+  constexpr int NC = W * W, NP = (NC + 31) / 32, NWARP = NW;
   constexpr int WS = 2 * W + 1;  // weight row stride (odd: conflict-free lane = point stores)
   const int M = a.M, MM = M * M, nc = a.nc;
   const int bx = blockIdx.x, by = blockIdx.y;
@@ -384,6 +384,23 @@ void launch_gather_q_dd(const double* q, const int* perm, int64_t n, float2* q_s
   if (n > 0) gather_q_dd_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(q, perm, n, q_s);
 }
 
+static size_t sub_dd_smem_nw(int M, int w, int nw) {
+  return (size_t)(kMaxNC * w + nw * 32 * (2 * w + 1) + nw * M * M) * sizeof(float2);
+}
+
+// Warps per CTA of the binned df64 spread: 4 or 5, whichever keeps more
+// warps resident per SM (228 KB of shared memory, 1 KB reserved per CTA);
+// each warp carries an M x M df64 patch and 32 weight rows.  The near level
+// (patch pitch ~44 at w = 12) fits two CTAs either way, so 5 warps give 10
+// resident warps instead of 8.
+int sub_dd_warps(int M, int w) {
+  auto resident = [&](int nw) {
+    const size_t b = sub_dd_smem_nw(M, w, nw);
+    return b > 220 * 1024 ? 0 : nw * (int)((228 * 1024) / (b + 1024));  // 220 KB: the configured maximum
+  };
+  return resident(5) > resident(4) ? 5 : 4;
+}
+
 size_t spread_sub_dd_smem(int M, int w) {
   return (size_t)(kMaxNC * w + (kSubDDThreads / 32) * 32 * (2 * w + 1) + (kSubDDThreads / 32) * M * M) *
          sizeof(float2);
@@ -397,7 +414,9 @@ bool spread_sub_dd_configure(int w) {
   switch (w) {
 #define LP_CASE(W)                                                                                     \
   case W:                                                                                              \
-    return cudaFuncSetAttribute(spread_sub_dd_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+    return cudaFuncSetAttribute(spread_sub_dd_kernel<W, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                bytes) == cudaSuccess &&                                                \
+           cudaFuncSetAttribute(spread_sub_dd_kernel<W, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                 bytes) == cudaSuccess;
     LP_SUB_DD_CASES
 #undef LP_CASE
@@ -407,11 +426,15 @@ bool spread_sub_dd_configure(int w) {
 
 void launch_spread_sub_dd(const SubDDArgs& a, int w, cudaStream_t s) {
   dim3 grid(a.nbx, a.nby);
-  const size_t smem = spread_sub_dd_smem(a.M, w);
+  const int nw = sub_dd_warps(a.M, w);
+  const size_t smem = sub_dd_smem_nw(a.M, w, nw);
   switch (w) {
-#define LP_CASE(W)                                                    \
-  case W:                                                             \
-    spread_sub_dd_kernel<W><<<grid, kSubDDThreads, smem, s>>>(a);     \
+#define LP_CASE(W)                                                      \
+  case W:                                                               \
+    if (nw == 5)                                                        \
+      spread_sub_dd_kernel<W, 5><<<grid, 5 * 32, smem, s>>>(a);         \
+    else                                                                \
+      spread_sub_dd_kernel<W, 4><<<grid, 4 * 32, smem, s>>>(a);         \
     break;
     LP_SUB_DD_CASES
 #undef LP_CASE
