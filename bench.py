@@ -543,7 +543,7 @@ def cpu_baseline(prob, budget_s=15.0, refine_levels=0):
             f"extrapolated linearly in targets to the full workload ({t_full:.0f} s)"}
 
 
-# ---------------------------------------------------------------- batched waves (config 4)
+# ---------------------------------------------------------------- batched waves of uneven problems
 def run_batch(args, rank, world, local_rank):
     """256 star domains r = 1 + a cos kt (a ~ U[0.1, 0.4], k in 3..9) of
     log-uniform 1k..200k triangles in one wave: one launch per kernel for
@@ -677,7 +677,7 @@ def run_solve(args, rank, world, local_rank):
             "gpu_launches": int(launches)}
 
 
-# ---------------------------------------------------------------- serving (config 5)
+# ---------------------------------------------------------------- serving a request stream
 def run_serve(args, rank, world, local_rank, pool=None, rates=(25, 50, 100, 200), seconds=None):
     """Poisson arrivals of V+S+D requests over a resident mesh pool (10k..5M
     triangles on the disk, starfish and square domains), FP32 at 1e-5 with
