@@ -713,10 +713,19 @@ def run_serve(args, rank, world, local_rank, pool=None, rates=(25, 50, 100, 200)
 
 
 # ---------------------------------------------------------------- reference arm
+REFERENCE_UNAVAILABLE = {
+    "batch": "the oracle evaluates one problem at a time; time it with --workload starfish|disk|square",
+    "serve": "a latency workload of the GPU serving layer; the oracle has no request loop",
+    "solve": "the oracle's Dirichlet solve is a dense direct solve, infeasible at 16k boundary nodes",
+}
+
+
 def run_reference(args, rank, world):
     import numpy as np
     if rank != 0:
         return None
+    if args.workload in REFERENCE_UNAVAILABLE:
+        return {"impl": "reference", "unavailable": REFERENCE_UNAVAILABLE[args.workload]}
     ncores = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(ncores))
     import oracle
