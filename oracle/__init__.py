@@ -238,3 +238,26 @@ def solve_dirichlet(bnd, g, delta, order=5, on_tol=1e-12, v_boundary=None, refin
     A = dirichlet_matrix(bnd, delta, order, on_tol, refine_levels)
     rhs = np.asarray(g, dtype=np.float64) - (0.0 if v_boundary is None else np.asarray(v_boundary))
     return np.linalg.solve(A, rhs)
+
+
+def solve_neumann(bnd, g, delta, order=5, on_tol=1e-12, v_boundary=None, refine_levels=0):
+    """u on the boundary nodes for the interior Neumann problem
+    (-lap u = f in the domain, du/dnu = g on the boundary), from the
+    boundary equation of Sec. 5: u/2 + D[u] = V[f] + S[g] (D the on-surface
+    principal value).  Constants are in the null space (D[1] = -1/2 on the
+    boundary); the rank-one term (sum_i w_i u_i / |Gamma|) 1 selects the
+    solution with zero boundary mean.  Dense direct solve, for small
+    boundaries only; v_boundary is V[f] at the nodes (None: f = 0)."""
+    xy, w = bnd["xy"], bnd["w"]
+    nb = len(xy)
+    A = dirichlet_matrix(bnd, delta, order, on_tol, refine_levels)  # -I/2 + D
+    A[np.diag_indices(nb)] += 1.0                                    # I/2 + D
+    A += np.outer(np.ones(nb), w) / np.sum(w)
+    SH = smooth_charge(xy, np.asarray(g) * w, xy, delta)
+    if refine_levels > 0:
+        SL, _ = local_dyadic(bnd, np.asarray(g, dtype=np.float64), None, xy, delta, refine_levels, order=order,
+                             on_tol=on_tol)
+    else:
+        _, SL, _, _, _ = local(bnd, np.asarray(g, dtype=np.float64), None, xy, None, delta, order, on_tol)
+    rhs = SH + SL + (0.0 if v_boundary is None else np.asarray(v_boundary))
+    return np.linalg.solve(A, rhs)
