@@ -55,6 +55,8 @@ def parse():
                     help="plan precision of the timed line (fp64: tol 1e-9; fp32: tol 1e-5)")
     ap.add_argument("--levels", default="auto", choices=["auto", "1", "2"],
                     help="history levels of every plan (auto: one level when its grid side is <= 1536)")
+    ap.add_argument("--bc", default="dirichlet", choices=["dirichlet", "neumann"],
+                    help="boundary condition of --workload solve")
     ap.add_argument("--autotune", action="store_true",
                     help="plans time three bin sides on their sources at the first lp_volume")
     ap.add_argument("--refine-levels", type=int, default=0,
@@ -629,9 +631,10 @@ def run_batch(args, rank, world, local_rank):
 
 # ---------------------------------------------------------------- Dirichlet solve
 def run_solve(args, rank, world, local_rank):
-    """Interior Dirichlet problem on the starfish (Sec. 5): GMRES on
-    -mu/2 + D[mu] = g - V[f] at the 16k boundary nodes, D applied by the
-    evaluator; one step = one solve to 1e-10 (FP64) from mu = 0."""
+    """Interior Dirichlet (-mu/2 + D[mu] = g - V[f]) or Neumann (u/2 + D[u] =
+    V[f] + S[g]) problem on the starfish (Sec. 5): GMRES at the 16k boundary
+    nodes, D applied by the evaluator; one step = one solve to 1e-10 (FP64)
+    from 0."""
     import numpy as np
     import torch
     import paper_2409_11998_gb300 as lp
@@ -645,7 +648,9 @@ def run_solve(args, rank, world, local_rank):
     ev = lp.Evaluator(prob, precision=args.precision, tol=1e-9 if fp64 else 1e-5, stream=stream.cuda_stream,
                       refine_levels=args.refine_levels, levels=levels_arg(args)).bind()
     T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
-    g, jb = T(prob["dirichlet_g"]), T(prob["bnd_jet"])
+    neumann = args.bc == "neumann"
+    g, jb = T(prob["neumann_g" if neumann else "dirichlet_g"]), T(prob["bnd_jet"])
+    solve = lp.lp_solve_neumann if neumann else lp.lp_solve_dirichlet
     mu = torch.empty(nb, dtype=torch.float64, device=dev)
     launches0 = None
     for k in range(max(args.warmup, 3) + args.steps):
@@ -654,7 +659,7 @@ def run_solve(args, rank, world, local_rank):
             launches0 = lp.lp_plan_info(ev.plan)["launches"]
             times, its, res = [], [], []
         t0 = time.perf_counter()
-        it, r = lp.lp_solve_dirichlet(ev.plan, g, mu, f_jet_b=jb, tol=tol, max_iter=300, restart=40)
+        it, r = solve(ev.plan, g, mu, f_jet_b=jb, tol=tol, max_iter=300, restart=40)
         dt = time.perf_counter() - t0      # the call synchronises the plan stream
         if launches0 is not None:
             times.append(dt)
@@ -668,9 +673,11 @@ def run_solve(args, rank, world, local_rank):
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dtype_of(info),
             "data": "synthetic (seeded generators; no dataset)",
-            "config": {"workload": "interior Dirichlet solve on the starfish (1.2M volume nodes, 1024x16 "
-                                   "boundary nodes): GMRES(40) from mu = 0 to a relative residual "
-                                   f"{tol:g}, g = cos x + sin 2y", **refine_desc(args),
+            "config": {"workload": f"interior {args.bc} solve on the starfish (1.2M volume nodes, 1024x16 "
+                                   "boundary nodes): GMRES(40) from 0 to a relative residual "
+                                   f"{tol:g}, " + ("g = cos x + sin 2y with its boundary mean removed and "
+                                                   "shifted to int f + int g = 0" if neumann else
+                                                   "g = cos x + sin 2y"), **refine_desc(args),
                        "levels": int(info["levels"]), "timing": "host wall time per solve (synchronising)"},
             "solve": {"iterations": its[-1], "residual": res[-1], "ms_per_iteration": ms / max(its[-1], 1),
                       "boundary_nodes": nb},

@@ -248,6 +248,24 @@ lp_status lp_batch_destroy(lp_batch_t batch);
 lp_status lp_solve_dirichlet(lp_plan_t plan, const double* g, const double* f_jet_b, double* mu, double tol,
                              int max_iter, int restart, int* iterations, double* residual);
 
+/* Interior Neumann problem (Sec. 5): for -lap u = f in the domain and
+ * du/dnu = g on the boundary (outward normal), Green's representation
+ * u = V[f] + S[g] - D[u] gives u/2 + D[u] = V[f] + S[g] at the boundary
+ * nodes, solved by restarted GMRES like lp_solve_dirichlet.  Constants are in
+ * the null space (D[1] = -1/2 on the boundary); the operator carries the
+ * rank-one term (sum_i w_i u_i / |Gamma|) 1 (w the boundary weights), so the
+ * returned u has zero weighted boundary mean.  The data should satisfy the
+ * compatibility condition int f + int g = 0.
+ *   g:        [n_b] normal derivative at the boundary nodes (host or device);
+ *   f_jet_b, tol, max_iter, restart, iterations, residual: as for
+ *             lp_solve_dirichlet;
+ *   u:        [n_b] out, the boundary values (host or device).
+ * On return the plan's single-layer density is g and its double-layer
+ * density u, so lp_execute with V, S and D gives u = V + S - D anywhere in
+ * the domain. */
+lp_status lp_solve_neumann(lp_plan_t plan, const double* g, const double* f_jet_b, double* u, double tol,
+                           int max_iter, int restart, int* iterations, double* residual);
+
 /* Wait for the plan's stream; return and clear the device status word. */
 lp_status lp_sync(lp_plan_t plan);
 

@@ -28,7 +28,7 @@ STATUS = {0: "LP_OK", 1: "LP_ERR_ARG", 2: "LP_ERR_OUT_OF_BOX", 3: "LP_ERR_NOMEM"
 EXPORTS = ("lp_plan", "lp_volume", "lp_single_layer", "lp_double_layer", "lp_execute", "lp_sync",
            "lp_destroy", "lp_status_string", "lp_plan_info", "lp_stage_times", "lp_execute_noalloc",
            "lp_batch_create", "lp_batch_execute", "lp_batch_sync", "lp_batch_stage_times",
-           "lp_batch_destroy", "lp_solve_dirichlet", "lp_execute_graph")
+           "lp_batch_destroy", "lp_solve_dirichlet", "lp_execute_graph", "lp_solve_neumann")
 
 
 class LpError(RuntimeError):
@@ -78,6 +78,7 @@ def _lib():
         L.lp_plan_info.argtypes = [vp, vp]
         L.lp_stage_times.argtypes = [vp, vp]
         L.lp_solve_dirichlet.argtypes = [vp, vp, vp, vp, d, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(d)]
+        L.lp_solve_neumann.argtypes = [vp, vp, vp, vp, d, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(d)]
         for name in EXPORTS:
             if name != "lp_status_string":
                 getattr(L, name).restype = i32
@@ -157,6 +158,17 @@ def lp_execute_noalloc(plan, n_t, t_xy, f_jet, V=None, S=None, D=None):
     (see include/lp.h)."""
     _check(_lib().lp_execute_noalloc(plan, int(n_t), _ptr(t_xy), _ptr(f_jet), _ptr(V), _ptr(S),
                                      _ptr(D)), "lp_execute_noalloc")
+
+
+def lp_solve_neumann(plan, g, u, f_jet_b=None, tol=1e-10, max_iter=200, restart=30):
+    """u/2 + D[u] = V[f] + S[g] at the plan's boundary nodes (Sec. 5) by GMRES;
+    writes u (zero boundary mean), returns (iterations, true relative residual)."""
+    it = ctypes.c_int(0)
+    res = ctypes.c_double(0.0)
+    _check(_lib().lp_solve_neumann(plan, _ptr(g), _ptr(f_jet_b), _ptr(u), ctypes.c_double(tol),
+                                   int(max_iter), int(restart), ctypes.byref(it), ctypes.byref(res)),
+           "lp_solve_neumann")
+    return it.value, res.value
 
 
 def lp_execute_graph(plan, n_t, t_xy, f_jet, V, S, D):
@@ -352,6 +364,20 @@ class Evaluator:
         it, res = lp_solve_dirichlet(self.plan, gd, mu, f_jet_b=fj, tol=tol, max_iter=max_iter, restart=restart)
         self._mu = mu
         return mu, it, res
+
+    def solve_neumann(self, g, f_jet_b=None, tol=1e-10, max_iter=200, restart=30):
+        """u (zero boundary mean) with u/2 + D[u] = V[f] + S[g] at the boundary
+        nodes (Sec. 5); returns (u, iterations, residual); g and u are left
+        bound as the plan's single- and double-layer densities."""
+        n = len(self.problem["bnd"]["w"])
+        conv = (lambda a: np.ascontiguousarray(a, dtype=np.float64)) if self.host else \
+            (lambda a: self.torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=self.device))
+        gd = conv(g)
+        fj = None if f_jet_b is None else conv(f_jet_b)
+        u = np.zeros(n) if self.host else self.torch.empty(n, dtype=self.torch.float64, device=self.device)
+        it, res = lp_solve_neumann(self.plan, gd, u, f_jet_b=fj, tol=tol, max_iter=max_iter, restart=restart)
+        self._sig, self._mu = gd, u
+        return u, it, res
 
     def info(self):
         return lp_plan_info(self.plan)

@@ -1,6 +1,13 @@
-// Interior Dirichlet problem by a boundary integral equation (Sec. 5):
-// u = V[f] + D[mu] in Omega, with mu solving
-//   -mu/2 + D[mu] = g - V[f]      at the boundary nodes (eq. dir_inteq).
+// Interior boundary value problems by boundary integral equations (Sec. 5),
+// for -lap u = f in Omega:
+//   Dirichlet (u = g):       u = V[f] + D[mu],  -mu/2 + D[mu] = g - V[f]
+//                            at the boundary nodes (eq. dir_inteq);
+//   Neumann (du/dnu = g):    u = V[f] + S[g] - D[u],  u/2 + D[u] = V[f] + S[g]
+//                            at the boundary nodes; constants are in the null
+//                            space (D[1] = -1/2 on the boundary), so the
+//                            operator carries the rank-one term
+//                            (sum_i w_i u_i / |Gamma|) 1, which selects the
+//                            solution of zero boundary mean.
 // Restarted GMRES (Saad and Schultz, SISSC 1986) with classical Gram-Schmidt
 // applied twice.  Each operator application binds the iterate as the
 // double-layer density and evaluates D at the plan's own boundary nodes
@@ -59,6 +66,17 @@ __global__ void axpby_kernel(double a, const double* __restrict__ x, double b, d
   if (k < n) y[k] = fma(a, x[k], b * y[k]);
 }
 
+// y += scale * (*a) (a device scalar)
+__global__ void add_scaled_kernel(const double* __restrict__ a, double scale, double* __restrict__ y, int64_t n) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) y[k] = fma(scale, *a, y[k]);
+}
+
+__global__ void fill_kernel(double* __restrict__ y, double v, int64_t n) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) y[k] = v;
+}
+
 unsigned blocks_for(int64_t n) { return (unsigned)((n + 255) / 256); }
 
 struct Solver {
@@ -86,16 +104,6 @@ struct Solver {
   }
   double* vec(int i) { return V + (int64_t)i * n; }
 
-  // out = -in/2 + D[in] at the boundary nodes
-  lp_status apply(const double* in, double* out) {
-    lp_status st = lp_double_layer(h, in);
-    if (st != LP_OK) return st;
-    st = lp_execute(h, n, P.d_bxy, nullptr, nullptr, nullptr, out);
-    if (st != LP_OK) return st;
-    axpby_kernel<<<blocks_for(n), 256, 0, P.stream>>>(-0.5, in, 1.0, out, n);
-    ++launches;
-    return LP_OK;
-  }
   // <a, a> through the device reduction, returned to the host
   double norm(const double* a) {
     dots_kernel<<<1, kDotThreads, 0, P.stream>>>(a, n, 1, a, n, dh);
@@ -107,38 +115,22 @@ struct Solver {
   }
 };
 
-}  // namespace
-
-extern "C" lp_status lp_solve_dirichlet(lp_plan_t h, const double* g, const double* f_jet_b, double* mu, double tol,
-                                        int max_iter, int restart, int* iterations, double* residual) {
-  if (!h || !g || !mu || !(tol > 0.0) || max_iter < 1 || restart < 0 || restart > kMaxRestart) return LP_ERR_ARG;
-  Plan& P = h->P;
-  if (P.n_panels == 0 || P.nb == 0) return LP_ERR_STATE;
-  if (f_jet_b && !P.have_volume) return LP_ERR_STATE;
-  const int m = restart == 0 ? 30 : restart;
-  const int64_t n = P.nb;
-  Solver S(h, n, m);
-  if (!S.alloc()) {
-    cudaGetLastError();
-    return LP_ERR_NOMEM;
-  }
+// Restarted GMRES for A x = b with A applied by `apply(in, out)` (device
+// vectors); x starts at 0.  Returns the status; *iterations and *rel receive
+// the iterations taken and the true relative residual of x (one more
+// application).
+template <class Op>
+lp_status gmres(Solver& S, const Op& apply, double tol, int max_iter, int* iterations, double* residual) {
+  Plan& P = S.P;
+  const int m = S.m;
+  const int64_t n = S.n;
   cudaStream_t s = P.stream;
-  // right-hand side b = g - V[f] at the boundary nodes
-  cudaMemcpyAsync(S.b, g, n * sizeof(double), cudaMemcpyDefault, s);
-  if (f_jet_b) {
-    lp_status st = lp_execute(h, n, P.d_bxy, f_jet_b, S.t, nullptr, nullptr);
-    if (st != LP_OK) return st;
-    axpby_kernel<<<blocks_for(n), 256, 0, s>>>(-1.0, S.t, 1.0, S.b, n);
-    ++S.launches;
-  }
   cudaMemsetAsync(S.x, 0, n * sizeof(double), s);
   const double bnorm = S.norm(S.b);
-  if (!(bnorm > 0.0)) {  // g = V[f]: mu = 0
-    cudaMemcpyAsync(mu, S.x, n * sizeof(double), cudaMemcpyDefault, s);
-    cudaStreamSynchronize(s);
+  if (!(bnorm > 0.0)) {  // b = 0: x = 0
     if (iterations) *iterations = 0;
     if (residual) *residual = 0.0;
-    return lp_sync(h);
+    return LP_OK;
   }
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gam(m + 1), y(m), hv(2 * (m + 1) + 1);
   int it = 0;
@@ -153,7 +145,7 @@ extern "C" lp_status lp_solve_dirichlet(lp_plan_t h, const double* g, const doub
       beta = bnorm;
       first = false;
     } else {
-      if ((st = S.apply(S.x, S.t)) != LP_OK) break;
+      if ((st = apply(S.x, S.t)) != LP_OK) break;
       cudaMemcpyAsync(S.vec(0), S.b, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
       axpby_kernel<<<blocks_for(n), 256, 0, s>>>(-1.0, S.t, 1.0, S.vec(0), n);
       ++S.launches;
@@ -168,7 +160,7 @@ extern "C" lp_status lp_solve_dirichlet(lp_plan_t h, const double* g, const doub
     int k = 0;
     for (; k < m && it < max_iter; ++k, ++it) {
       double* w = S.vec(k + 1);
-      if ((st = S.apply(S.vec(k), w)) != LP_OK) break;
+      if ((st = apply(S.vec(k), w)) != LP_OK) break;
       // two classical Gram-Schmidt passes against V_0..V_k, then |w|
       double* h1 = S.dh;
       double* h2 = S.dh + (m + 1);
@@ -227,19 +219,110 @@ extern "C" lp_status lp_solve_dirichlet(lp_plan_t h, const double* g, const doub
     if (rel <= tol) break;
   }
   // the true residual of the returned iterate
-  if (st == LP_OK) st = S.apply(S.x, S.t);
+  if (st == LP_OK) st = apply(S.x, S.t);
   if (st == LP_OK) {
     axpby_kernel<<<blocks_for(n), 256, 0, s>>>(1.0, S.b, -1.0, S.t, n);
     ++S.launches;
     rel = S.norm(S.t) / bnorm;
-    cudaMemcpyAsync(mu, S.x, n * sizeof(double), cudaMemcpyDefault, s);
-    // leave the solution bound as the plan's double-layer density
-    st = lp_double_layer(h, S.x);
   }
-  P.launches += S.launches;
-  const lp_status st_sync = lp_sync(h);
-  if (st == LP_OK) st = st_sync;
   if (iterations) *iterations = it;
   if (residual) *residual = rel;
   return st;
+}
+
+// out = c * in + D[in] at the boundary nodes (c = -1/2: Dirichlet; +1/2:
+// Neumann), plus, for Neumann, (sum_i w_i in_i / |Gamma|) 1
+struct LayerOp {
+  Solver* S;
+  double c;
+  bool mean_term;
+  double inv_len;
+  lp_status operator()(const double* in, double* out) const {
+    Plan& P = S->P;
+    lp_status st = lp_double_layer(S->h, in);
+    if (st != LP_OK) return st;
+    st = lp_execute(S->h, S->n, P.d_bxy, nullptr, nullptr, nullptr, out);
+    if (st != LP_OK) return st;
+    axpby_kernel<<<blocks_for(S->n), 256, 0, P.stream>>>(c, in, 1.0, out, S->n);
+    ++S->launches;
+    if (mean_term) {
+      dots_kernel<<<1, kDotThreads, 0, P.stream>>>(P.d_bw, S->n, 1, in, S->n, S->dh);
+      add_scaled_kernel<<<blocks_for(S->n), 256, 0, P.stream>>>(S->dh, inv_len, out, S->n);
+      S->launches += 2;
+    }
+    return LP_OK;
+  }
+};
+
+}  // namespace
+
+extern "C" lp_status lp_solve_dirichlet(lp_plan_t h, const double* g, const double* f_jet_b, double* mu, double tol,
+                                        int max_iter, int restart, int* iterations, double* residual) {
+  if (!h || !g || !mu || !(tol > 0.0) || max_iter < 1 || restart < 0 || restart > kMaxRestart) return LP_ERR_ARG;
+  Plan& P = h->P;
+  if (P.n_panels == 0 || P.nb == 0) return LP_ERR_STATE;
+  if (f_jet_b && !P.have_volume) return LP_ERR_STATE;
+  const int64_t n = P.nb;
+  Solver S(h, n, restart == 0 ? 30 : restart);
+  if (!S.alloc()) {
+    cudaGetLastError();
+    return LP_ERR_NOMEM;
+  }
+  cudaStream_t s = P.stream;
+  // right-hand side b = g - V[f] at the boundary nodes
+  cudaMemcpyAsync(S.b, g, n * sizeof(double), cudaMemcpyDefault, s);
+  if (f_jet_b) {
+    lp_status st = lp_execute(h, n, P.d_bxy, f_jet_b, S.t, nullptr, nullptr);
+    if (st != LP_OK) return st;
+    axpby_kernel<<<blocks_for(n), 256, 0, s>>>(-1.0, S.t, 1.0, S.b, n);
+    ++S.launches;
+  }
+  lp_status st = gmres(S, LayerOp{&S, -0.5, false, 0.0}, tol, max_iter, iterations, residual);
+  if (st == LP_OK) {
+    cudaMemcpyAsync(mu, S.x, n * sizeof(double), cudaMemcpyDefault, s);
+    st = lp_double_layer(h, S.x);  // leave the solution bound as the double-layer density
+  }
+  P.launches += S.launches;
+  const lp_status st_sync = lp_sync(h);
+  return st == LP_OK ? st_sync : st;
+}
+
+extern "C" lp_status lp_solve_neumann(lp_plan_t h, const double* g, const double* f_jet_b, double* u, double tol,
+                                      int max_iter, int restart, int* iterations, double* residual) {
+  if (!h || !g || !u || !(tol > 0.0) || max_iter < 1 || restart < 0 || restart > kMaxRestart) return LP_ERR_ARG;
+  Plan& P = h->P;
+  if (P.n_panels == 0 || P.nb == 0) return LP_ERR_STATE;
+  if (f_jet_b && !P.have_volume) return LP_ERR_STATE;
+  const int64_t n = P.nb;
+  Solver S(h, n, restart == 0 ? 30 : restart);
+  if (!S.alloc()) {
+    cudaGetLastError();
+    return LP_ERR_NOMEM;
+  }
+  cudaStream_t s = P.stream;
+  // |Gamma| = sum of the boundary weights
+  fill_kernel<<<blocks_for(n), 256, 0, s>>>(S.t, 1.0, n);
+  dots_kernel<<<1, kDotThreads, 0, s>>>(P.d_bw, n, 1, S.t, n, S.dh);
+  double len = 0.0;
+  cudaMemcpyAsync(&len, S.dh, sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  S.launches += 2;
+  if (!(len > 0.0)) return LP_ERR_STATE;
+  // right-hand side b = V[f] + S[g] at the boundary nodes
+  lp_status st = lp_single_layer(h, g);
+  if (st != LP_OK) return st;
+  st = lp_execute(h, n, P.d_bxy, f_jet_b, f_jet_b ? S.t : nullptr, S.b, nullptr);
+  if (st != LP_OK) return st;
+  if (f_jet_b) {
+    axpby_kernel<<<blocks_for(n), 256, 0, s>>>(1.0, S.t, 1.0, S.b, n);
+    ++S.launches;
+  }
+  st = gmres(S, LayerOp{&S, 0.5, true, 1.0 / len}, tol, max_iter, iterations, residual);
+  if (st == LP_OK) {
+    cudaMemcpyAsync(u, S.x, n * sizeof(double), cudaMemcpyDefault, s);
+    st = lp_double_layer(h, S.x);  // u bound as the double-layer density (and g as the single layer)
+  }
+  P.launches += S.launches;
+  const lp_status st_sync = lp_sync(h);
+  return st == LP_OK ? st_sync : st;
 }

@@ -113,3 +113,58 @@ def test_fp32_plan_and_host_buffers(lp):
     mu, it, res = ev.solve_dirichlet(g, tol=1e-12)
     assert isinstance(mu, np.ndarray) and res < 1e-11 and np.max(np.abs(mu + 2 * g)) < 5e-6
     ev.close()
+
+
+@pytest.mark.parametrize("levels", [0, 3])
+def test_neumann_circle_matches_oracle_and_closed_form(lp, oracle_lib, levels):
+    from workloads.curves import Circle
+    p = _layer_problem(Circle(1.0), 32, 1e-3)
+    t = p["bnd"]["t"]
+    g = 3 * np.cos(3 * t)
+    ev = lp.Evaluator(p, precision="fp64", refine_levels=levels).bind()
+    u, it, res = ev.solve_neumann(g, tol=1e-12)
+    u = u.cpu().numpy()
+    assert res < 1e-11 and 0 < it < 40, (it, res)
+    ref = oracle_lib.solve_neumann(p["bnd"], g, 1e-3, order=5, refine_levels=levels)
+    assert _rel(u, ref) < 1e-9, _rel(u, ref)
+    assert np.max(np.abs(u - np.cos(3 * t))) < (5e-6 if levels == 0 else 1e-9)
+    ev.close()
+
+
+def test_neumann_poisson_interior(lp, oracle_lib):
+    """u = exp(x) cos(y) + (x^2 + y^2) on the unit disk: f = -lap u = -4,
+    g = du/dr; u = V[f] + S[g] - D[u] inside, up to the constant fixed by
+    the zero boundary mean."""
+    from workloads import configs
+    p = dict(configs.disk())
+    p["src_f"] = np.full(len(p["src_w"]), -4.0)
+    b = p["bnd"]
+    nb = len(b["w"])
+    x, y = b["xy"][:, 0], b["xy"][:, 1]
+    ux = np.exp(x) * np.cos(y) + 2 * x
+    uy = -np.exp(x) * np.sin(y) + 2 * y
+    g = ux * b["normal"][:, 0] + uy * b["normal"][:, 1]
+    jet_b = np.zeros((nb, 6))
+    jet_b[:, 0] = -4.0
+    # the smooth part at 1e-11: the Neumann operator (singular up to its
+    # rank-one term) amplifies the evaluator's tolerance more than the
+    # Dirichlet one, and the comparison is with the oracle's exact sums
+    ev = lp.Evaluator(p, precision="fp64", tol=1e-11).bind()
+    u, it, res = ev.solve_neumann(g, f_jet_b=jet_b, tol=1e-12)
+    assert res < 1e-10
+    q = dict(p)
+    q["tgt_xy"], q["tgt_jet"] = b["xy"], jet_b
+    vb = oracle_lib.evaluate(q, want=("V",))["V"]
+    ref = oracle_lib.solve_neumann(b, g, p["delta"], order=5, on_tol=oracle_lib.on_tolerance(p), v_boundary=vb)
+    assert _rel(u.cpu().numpy(), ref) < 1e-9
+    exact_b = np.exp(x) * np.cos(y) + x ** 2 + y ** 2
+    shift = np.sum(b["w"] * exact_b) / np.sum(b["w"])
+    P = p["tgt_xy"]
+    tgt = P[np.hypot(P[:, 0], P[:, 1]) < 0.9]
+    jet = np.zeros((len(tgt), 6))
+    jet[:, 0] = -4.0
+    out = ev.evaluate(tgt_xy=tgt, tgt_jet=jet)
+    u_in = out["V"].cpu().numpy() + out["S"].cpu().numpy() - out["D"].cpu().numpy()
+    exact = np.exp(tgt[:, 0]) * np.cos(tgt[:, 1]) + tgt[:, 0] ** 2 + tgt[:, 1] ** 2 - shift
+    assert np.max(np.abs(u_in - exact)) < 5e-5
+    ev.close()

@@ -108,6 +108,11 @@ def starfish(seed=2000, n_interior=53700, n_boundary_vertices=930, n_panels=1024
     # f-jet at the boundary nodes (for V[f] there)
     out["dirichlet_g"] = np.cos(bnd["xy"][:, 0]) + np.sin(2 * bnd["xy"][:, 1])
     out["bnd_jet"] = np.ascontiguousarray(field.jet(bnd["xy"]), dtype=np.float64)
+    # interior Neumann data: the same function with its boundary mean removed,
+    # shifted so that int f + int g = 0 (compatibility)
+    h = out["dirichlet_g"]
+    length = float(np.sum(bnd["w"]))
+    out["neumann_g"] = h - float(np.sum(bnd["w"] * h)) / length - float(np.sum(w * f)) / length
     return out
 
 
