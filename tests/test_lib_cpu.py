@@ -87,6 +87,10 @@ def test_invalid_arguments_rejected_without_device(lib):
         assert fn(None) == 1
     assert L.lp_volume(None, 0, None, None, None) == 1
     assert L.lp_execute(None, 0, None, None, None, None, None) == 1
+    assert L.lp_execute_graph(None, 0, None, None, None, None, None) == 1
+    it, res = ctypes.c_int(), ctypes.c_double()
+    for solve in (L.lp_solve_dirichlet, L.lp_solve_neumann):
+        assert solve(None, None, None, None, 1e-10, 10, 0, ctypes.byref(it), ctypes.byref(res)) == 1
 
 
 def test_binding_rejects_wrong_dtypes(lib):
