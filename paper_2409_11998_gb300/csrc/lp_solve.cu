@@ -60,8 +60,8 @@ __global__ void subtract_kernel(const double* __restrict__ V, int64_t ld, int nv
   w[k] = s;
 }
 
-// y = a x + b y
-__global__ void axpby_kernel(double a, const double* __restrict__ x, double b, double* __restrict__ y, int64_t n) {
+// y = a x + b y (x may be y: no restrict qualifiers)
+__global__ void axpby_kernel(double a, const double* x, double b, double* y, int64_t n) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n) y[k] = fma(a, x[k], b * y[k]);
 }
