@@ -1,0 +1,42 @@
+"""bench.py's host-side arithmetic: the roofline picks the longest candidate
+stage and reports it against the right peak with the algorithmic work of
+that kernel."""
+import bench
+
+
+def _info(precision):
+    return {"w": 12 if precision == 0 else 7, "es_nc": 13 if precision == 0 else 9, "g_nh": 2592 if precision == 0
+            else 2916, "K_nh": 864 if precision == 0 else 729, "g_fh": 1024 if precision == 0 else 1152,
+            "K_fh": 342 if precision == 0 else 288, "own_fft": 1, "precision": precision, "binned": 1}
+
+
+def test_fp64_roofline_spread_or_interp():
+    st = {"spread": 1.2, "spread_volume": 1.0, "multiplier": 0.5, "interp": 0.8}
+    r = bench.roofline(_info(0), st, 1_000_000, 16384, 1_000_000, "fp64")
+    assert r["kernel"] == "spread_sub_dd_kernel" and r["bound"] == "alu"
+    ops = 1_000_000 * 2 * (2 * 12 * 12 + 12 * 13)
+    assert r["algorithmic_df64_fma_per_step"] == ops
+    assert abs(r["achieved"] - ops / 1.0e-3 / 1e12) < 1e-3
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-3
+    st["interp"] = 1.5
+    assert bench.roofline(_info(0), st, 1_000_000, 16384, 1_000_000, "fp64")["kernel"] == "interp_dd_kernel"
+
+
+def test_fp32_roofline_dominant_stage():
+    st = {"spread": 0.3, "spread_volume": 0.25, "multiplier": 0.28, "interp": 0.2}
+    r = bench.roofline(_info(1), st, 1_000_000, 16384, 1_000_000, "fp32")
+    assert r["kernel"] == "fft_cols_kernel" and r["bound"] == "hbm"
+    kp = lambda K: (K + 2) & ~1
+    byts = 7 * 2916 * kp(729) * 8 + 7 * 1152 * kp(288) * 8
+    assert r["algorithmic_bytes_per_step"] == byts
+    st["multiplier"] = 0.1
+    r = bench.roofline(_info(1), st, 1_000_000, 16384, 1_000_000, "fp32")
+    assert r["kernel"] == "spread_sub_kernel" and r["bound"] == "alu"
+    assert r["algorithmic_fma_per_step"] == 1_000_000 * 2 * (49 + 2 * 7 * 8)
+
+
+def test_single_level_plans_count_one_level():
+    info = dict(_info(0), g_nh=0, K_nh=0)
+    st = {"spread": 1.0, "spread_volume": 1.0, "multiplier": 0.5, "interp": 0.2}
+    r = bench.roofline(info, st, 1000, 0, 1000, "fp64")
+    assert r["algorithmic_df64_fma_per_step"] == 1000 * 1 * (2 * 12 * 12 + 12 * 13)
