@@ -49,16 +49,30 @@ __global__ void __launch_bounds__(128) interp_dd_kernel(const __grid_constant__ 
     dd_stencil_weights<W>(&a.coef[0][0], kMaxW, a.nc, vy, wy);
     // rows and channels stay rolled (wy spills to L1-resident local memory):
     // unrolling all w^2 C products overflows the instruction cache
+    // rows are read as 16-byte pairs of cells from the even cell at or below
+    // ix (grid rows start 16-byte aligned: the pitch is even), W/2 + 1 loads
+    // instead of W, and the W values picked by the parity of ix
+    const int ix0 = ix & ~1;
+    const bool odd = (ix & 1) != 0;
 #pragma unroll 1
     for (int c = 0; c < 3; ++c) {
       if (!a.out[c]) continue;
-      const float2* base = (const float2*)L.grid[c] + (size_t)iy * L.pitch + ix;
+      const float4* base = (const float4*)((const float2*)L.grid[c] + (size_t)iy * L.pitch + ix0);
 #pragma unroll 1
       for (int b = 0; b < W; ++b) {
-        const float2* row = base + (size_t)b * L.pitch;
+        const float4* row = base + (size_t)b * (L.pitch / 2);
+        float4 q[W / 2 + 1];
+#pragma unroll
+        for (int u = 0; u < W / 2 + 1; ++u)
+          if (2 * u < W + 1) q[u] = __ldg(row + u);
         float2 gv[W];
 #pragma unroll
-        for (int t = 0; t < W; ++t) gv[t] = __ldg(row + t);
+        for (int t = 0; t < W; ++t) {
+          const int e = t + 1;  // the value after t in the pair sequence
+          const float2 lo = (t & 1) ? make_float2(q[t / 2].z, q[t / 2].w) : make_float2(q[t / 2].x, q[t / 2].y);
+          const float2 hi = (e & 1) ? make_float2(q[e / 2].z, q[e / 2].w) : make_float2(q[e / 2].x, q[e / 2].y);
+          gv[t] = odd ? hi : lo;
+        }
         dd_acc r = {0.f, 0.f};
 #pragma unroll
         for (int t = 0; t < W; ++t) acc_fma(r, wx[t], dd{gv[t].x, gv[t].y});
