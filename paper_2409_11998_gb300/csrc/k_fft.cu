@@ -86,14 +86,93 @@ struct F32 {
   __device__ static V mul_conj(V a, V t) { return make_float2(a.x * t.x + a.y * t.y, a.y * t.x - a.x * t.y); }
 };
 
+// radices 8, 9 and 16 (two-level small DFTs) for the single-precision chain
+// only; the double-float chain is bound by its arithmetic, not by the number
+// of shared-memory passes, and keeps radices 2, 3 and 4
+template <class A>
+constexpr bool kHighRadix = false;
+template <>
+constexpr bool kHighRadix<F32> = true;
+
+// e^{-2 pi i m / R} for the two-level small DFTs of the single-precision
+// chain (R = 8, 9, 16; m < R)
+template <int R>
+__device__ __forceinline__ float2 small_tw(int m) {
+  constexpr float t8[8][2] = {{1.f, 0.f}, {7.071067812e-01f, -7.071067812e-01f}, {0.f, -1.f},
+                              {-7.071067812e-01f, -7.071067812e-01f}, {-1.f, 0.f},
+                              {-7.071067812e-01f, 7.071067812e-01f}, {0.f, 1.f},
+                              {7.071067812e-01f, 7.071067812e-01f}};
+  constexpr float t9[9][2] = {{1.f, 0.f}, {7.660444431e-01f, -6.427876097e-01f},
+                              {1.736481777e-01f, -9.848077530e-01f}, {-5.000000000e-01f, -8.660254038e-01f},
+                              {-9.396926208e-01f, -3.420201433e-01f}, {-9.396926208e-01f, 3.420201433e-01f},
+                              {-5.000000000e-01f, 8.660254038e-01f}, {1.736481777e-01f, 9.848077530e-01f},
+                              {7.660444431e-01f, 6.427876097e-01f}};
+  constexpr float t16[16][2] = {{1.f, 0.f}, {9.238795325e-01f, -3.826834324e-01f},
+                                {7.071067812e-01f, -7.071067812e-01f}, {3.826834324e-01f, -9.238795325e-01f},
+                                {0.f, -1.f}, {-3.826834324e-01f, -9.238795325e-01f},
+                                {-7.071067812e-01f, -7.071067812e-01f}, {-9.238795325e-01f, -3.826834324e-01f},
+                                {-1.f, 0.f}, {-9.238795325e-01f, 3.826834324e-01f},
+                                {-7.071067812e-01f, 7.071067812e-01f}, {-3.826834324e-01f, 9.238795325e-01f},
+                                {0.f, 1.f}, {3.826834324e-01f, 9.238795325e-01f},
+                                {7.071067812e-01f, 7.071067812e-01f}, {9.238795325e-01f, 3.826834324e-01f}};
+  if (R == 8) return make_float2(t8[m][0], t8[m][1]);
+  if (R == 9) return make_float2(t9[m][0], t9[m][1]);
+  return make_float2(t16[m][0], t16[m][1]);
+}
+
+template <class A, int R>
+__device__ __forceinline__ void dft_small(typename A::V* v, bool inv);
+
+// DFT of length R = R1 R2 in registers from R2 DFTs of length R1 (over the
+// inputs R2 n1 + n2), twiddles W_R^{n2 k1}, and R1 DFTs of length R2; the
+// output k1 + R1 k2 (Cooley-Tukey with the index split n = R2 n1 + n2,
+// k = k1 + R1 k2)
+template <class A, int R1, int R2>
+__device__ __forceinline__ void dft_two_level(typename A::V* v, bool inv) {
+  using V = typename A::V;
+  constexpr int R = R1 * R2;
+  V y[R];
+#pragma unroll
+  for (int n2 = 0; n2 < R2; ++n2) {
+    V t[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) t[n1] = v[R2 * n1 + n2];
+    dft_small<A, R1>(t, inv);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      V z = t[k1];
+      if (n2 * k1 != 0) {
+        const V w = small_tw<R>(n2 * k1);
+        z = inv ? A::mul_conj(z, w) : A::mul(z, w);
+      }
+      y[n2 * R1 + k1] = z;
+    }
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) {
+    V t[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) t[n2] = y[n2 * R1 + k1];
+    dft_small<A, R2>(t, inv);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) v[k1 + R1 * k2] = t[k2];
+  }
+}
+
 template <class A, int R>
 __device__ __forceinline__ void dft_small(typename A::V* v, bool inv) {
   using V = typename A::V;
-  if (R == 2) {
+  if constexpr (R == 8) {
+    dft_two_level<A, 4, 2>(v, inv);
+  } else if constexpr (R == 9) {
+    dft_two_level<A, 3, 3>(v, inv);
+  } else if constexpr (R == 16) {
+    dft_two_level<A, 4, 4>(v, inv);
+  } else if constexpr (R == 2) {
     const V a = v[0], b = v[1];
     v[0] = A::add(a, b);
     v[1] = A::sub(a, b);
-  } else if (R == 4) {
+  } else if constexpr (R == 4) {
     const V t0 = A::add(v[0], v[2]), t1 = A::sub(v[0], v[2]);
     const V t2 = A::add(v[1], v[3]);
     const V d = A::sub(v[1], v[3]);
@@ -173,8 +252,16 @@ __device__ typename A::S* fft_smem(typename A::S* a, typename A::S* b, const Fft
       for (int j = threadIdx.x; j < nb; j += blockDim.x) stockham_butterfly<A, 4>(a, b, j, N, Ns, tw, inv);
     } else if (R == 2) {
       for (int j = threadIdx.x; j < nb; j += blockDim.x) stockham_butterfly<A, 2>(a, b, j, N, Ns, tw, inv);
-    } else {
+    } else if (R == 3) {
       for (int j = threadIdx.x; j < nb; j += blockDim.x) stockham_butterfly<A, 3>(a, b, j, N, Ns, tw, inv);
+    } else if constexpr (kHighRadix<A>) {
+      if (R == 8) {
+        for (int j = threadIdx.x; j < nb; j += blockDim.x) stockham_butterfly<A, 8>(a, b, j, N, Ns, tw, inv);
+      } else if (R == 9) {
+        for (int j = threadIdx.x; j < nb; j += blockDim.x) stockham_butterfly<A, 9>(a, b, j, N, Ns, tw, inv);
+      } else {
+        for (int j = threadIdx.x; j < nb; j += blockDim.x) stockham_butterfly<A, 16>(a, b, j, N, Ns, tw, inv);
+      }
     }
     __syncthreads();
     typename A::S* t = a;
@@ -245,7 +332,12 @@ __device__ void fft_dif(typename A::S* x, const FftShape& sh, const TW& tw, int 
     const int R = sh.radix[s];
     if (R == 4) dif_stage<A, 4>(x, N, L, tw, t0, nt);
     else if (R == 2) dif_stage<A, 2>(x, N, L, tw, t0, nt);
-    else dif_stage<A, 3>(x, N, L, tw, t0, nt);
+    else if (R == 3) dif_stage<A, 3>(x, N, L, tw, t0, nt);
+    else if constexpr (kHighRadix<A>) {
+      if (R == 8) dif_stage<A, 8>(x, N, L, tw, t0, nt);
+      else if (R == 9) dif_stage<A, 9>(x, N, L, tw, t0, nt);
+      else dif_stage<A, 16>(x, N, L, tw, t0, nt);
+    }
     __syncthreads();
     L /= R;
   }
@@ -259,7 +351,12 @@ __device__ void fft_dit_inv(typename A::S* x, const FftShape& sh, const TW& tw, 
     const int R = sh.radix[s];
     if (R == 4) dit_stage_inv<A, 4>(x, N, L, tw, t0, nt);
     else if (R == 2) dit_stage_inv<A, 2>(x, N, L, tw, t0, nt);
-    else dit_stage_inv<A, 3>(x, N, L, tw, t0, nt);
+    else if (R == 3) dit_stage_inv<A, 3>(x, N, L, tw, t0, nt);
+    else if constexpr (kHighRadix<A>) {
+      if (R == 8) dit_stage_inv<A, 8>(x, N, L, tw, t0, nt);
+      else if (R == 9) dit_stage_inv<A, 9>(x, N, L, tw, t0, nt);
+      else dit_stage_inv<A, 16>(x, N, L, tw, t0, nt);
+    }
     __syncthreads();
     if (s > 0) L *= sh.radix[s - 1];
   }
@@ -484,22 +581,27 @@ void launch_split_table(const double* src, float2* dst, int64_t n, cudaStream_t 
   if (n > 0) split_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, dst, n);
 }
 
-FftShape fft_shape(int n) {
+FftShape fft_shape(int n, bool high) {
   FftShape s{};
   s.n = n;
   int m = n;
-  while (m % 4 == 0 && s.nst < kMaxFftStages) {
-    s.radix[s.nst++] = 4;
-    m /= 4;
+  auto take = [&](int r) {
+    while (m % r == 0 && s.nst < kMaxFftStages) {
+      s.radix[s.nst++] = r;
+      m /= r;
+    }
+  };
+  if (high) {  // powers of two as 16s, then one 8, 4 or 2; powers of three as 9s, then one 3
+    take(16);
+    if (m % 8 == 0) take(8);
   }
+  take(4);
   if (m % 2 == 0 && s.nst < kMaxFftStages) {
     s.radix[s.nst++] = 2;
     m /= 2;
   }
-  while (m % 3 == 0 && s.nst < kMaxFftStages) {
-    s.radix[s.nst++] = 3;
-    m /= 3;
-  }
+  if (high) take(9);
+  take(3);
   if (m != 1) s.nst = -1;  // not 3-smooth
   return s;
 }
@@ -555,11 +657,10 @@ std::vector<int> fft_dif_order(const FftShape& sh) {
 
 bool fft_dd_configure() {
   const int bytes = 220 * 1024;
-  const void* fns[9] = {(const void*)fft_rows_fwd_kernel<DD>,  (const void*)fft_rows_inv_kernel<DD>,
+  const void* fns[7] = {(const void*)fft_rows_fwd_kernel<DD>,  (const void*)fft_rows_inv_kernel<DD>,
                         (const void*)fft_cols_kernel<DD, 1>,    (const void*)fft_cols_kernel<DD, 2>,
                         (const void*)fft_rows_fwd_kernel<F32>, (const void*)fft_rows_inv_kernel<F32>,
-                        (const void*)fft_cols_kernel<F32, 1>,   (const void*)fft_cols_kernel<F32, 2>,
-                        (const void*)fft_cols_kernel<F32, 4>};
+                        (const void*)fft_cols_kernel<F32, 1>};
   for (const void* f : fns)
     if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return false;
   return true;
@@ -596,12 +697,7 @@ void launch_fft_cols(const FftColArgs& a, int njobs, bool f64, cudaStream_t s) {
     else
       fft_cols_kernel<DD, 1><<<grid, kFftThreads, smem, s>>>(a);
   } else {
-    if (C == 4)
-      fft_cols_kernel<F32, 4><<<grid, kFftThreads * 4, smem, s>>>(a);
-    else if (C == 2)
-      fft_cols_kernel<F32, 2><<<grid, kFftThreads * 2, smem, s>>>(a);
-    else
-      fft_cols_kernel<F32, 1><<<grid, kFftThreads, smem, s>>>(a);
+    fft_cols_kernel<F32, 1><<<grid, kFftThreads, smem, s>>>(a);  // fft_cols_per_cta is 1 for FP32
   }
 }
 
