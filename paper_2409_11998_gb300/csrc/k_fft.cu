@@ -240,7 +240,9 @@ __device__ __forceinline__ void stockham_butterfly(const typename A::S* in, type
 // Transform of length N held in a (scratch b); returns the buffer holding
 // the result.  All threads of the CTA take part; the caller synchronises
 // before (data in a) and the function synchronises after every stage.
-template <class A, class TW>
+// HIGH: the shape may hold radices 8, 9, 16 (compiled only where used, so
+// that the row kernels keep their registers)
+template <class A, bool HIGH, class TW>
 __device__ typename A::S* fft_smem(typename A::S* a, typename A::S* b, const FftShape& sh, const TW& tw,
                                    bool inv) {
   const int N = sh.n;
@@ -254,7 +256,7 @@ __device__ typename A::S* fft_smem(typename A::S* a, typename A::S* b, const Fft
       for (int j = threadIdx.x; j < nb; j += blockDim.x) stockham_butterfly<A, 2>(a, b, j, N, Ns, tw, inv);
     } else if (R == 3) {
       for (int j = threadIdx.x; j < nb; j += blockDim.x) stockham_butterfly<A, 3>(a, b, j, N, Ns, tw, inv);
-    } else if constexpr (kHighRadix<A>) {
+    } else if constexpr (HIGH) {
       if (R == 8) {
         for (int j = threadIdx.x; j < nb; j += blockDim.x) stockham_butterfly<A, 8>(a, b, j, N, Ns, tw, inv);
       } else if (R == 9) {
@@ -423,8 +425,8 @@ __global__ void __launch_bounds__(kFftThreads) fft_rows_fwd_kernel(const __grid_
   if (kTwSmem<A>) load_twiddles<A>(twt, a.tw, N, 2);
   for (int n = threadIdx.x; n < N; n += blockDim.x) A::store(buf0 + n, load_pair(src, n, A()));
   __syncthreads();
-  const S* Z = kTwSmem<A> ? fft_smem<A>(buf0, buf1, a.half, SmemTw<A>{twt}, false)
-                          : fft_smem<A>(buf0, buf1, a.half, GlobTw<A>{a.tw, 2}, false);
+  const S* Z = kTwSmem<A> ? fft_smem<A, false>(buf0, buf1, a.half, SmemTw<A>{twt}, false)
+                          : fft_smem<A, false>(buf0, buf1, a.half, GlobTw<A>{a.tw, 2}, false);
   S* dst = (S*)a.spec[c] + (size_t)row * a.kp;
   for (int k = threadIdx.x; k <= a.K; k += blockDim.x) {
     const V zk = A::load(Z + k), zn = A::conj(A::load(Z + (k == 0 ? 0 : N - k)));
@@ -562,8 +564,8 @@ __global__ void __launch_bounds__(kFftThreads) fft_rows_inv_kernel(const __grid_
     A::store(buf0 + k, A::add(A::add(xk, xn), A::pi(B)));
   }
   __syncthreads();
-  const S* z = kTwSmem<A> ? fft_smem<A>(buf0, buf1, a.half, SmemTw<A>{twt}, true)
-                          : fft_smem<A>(buf0, buf1, a.half, GlobTw<A>{a.tw, 2}, true);
+  const S* z = kTwSmem<A> ? fft_smem<A, false>(buf0, buf1, a.half, SmemTw<A>{twt}, true)
+                          : fft_smem<A, false>(buf0, buf1, a.half, GlobTw<A>{a.tw, 2}, true);
   char* dst = (char*)a.grid[c] + (size_t)row * a.pitch * (sizeof(S) / 2);
   for (int n = threadIdx.x; n < N; n += blockDim.x) store_pair(dst, n, A::load(z + n), A());
 }
