@@ -141,3 +141,34 @@ def test_far_interior_volume_formula(oracle_lib):
     bv = brute_volume(exit_far, fld.value, x, d, n_phi=64)
     far = oracle_lib.local(None, None, None, x[None, :], fld.jet(x[None, :]), d, order=5)[0][0]
     assert abs(far - bv) / abs(bv) < 1e-10
+
+
+def test_flat_boundary_polynomial_densities(oracle_lib):
+    """Straight boundary, polynomial densities in the tangent coordinate xi
+    (sigma of degree 3, mu of degree 4): the heat kernel separates, the
+    tangential Gaussian moments are 1, 0, 2t, 0, 12t^2, and the local
+    integrals (eq. sheatloc, eq. dheatloc) reduce to
+      S_L = int_0^d g_t(r) (s0 + s2 t) dt,
+      D_L = -sgn int_0^d r/(2t) g_t(r) (m0 + m2 t + m4 t^2/2) dt,
+    g_t the 1D heat kernel.  The printed expansions, all terms kept, give
+    these exactly (S's next term, s4 t^2/2, is O(delta^{5/2}))."""
+    delta = 2e-3
+    s0, s1, s2 = 1.3, -0.4, 0.9      # s1, m1 enter only with curvature terms
+    m0, m1, m2, m4 = -0.6, 0.5, 1.1, 2.3
+    for c in [0.0, 0.2, 0.9, 2.0, 4.5]:
+        r = c * math.sqrt(delta)
+        for sgn in ([0.0] if c == 0 else [1.0, -1.0]):
+            g = dict(r=r, sgn=sgn, s0=s0, s1=s1, s2=s2, m0=m0, m1=m1, m2=m2, m4=m4, Tx=0.0, Ty=1.0)
+            out = oracle_lib.local_formulas(g, None, delta, order=5)
+
+            def gt(t):
+                return math.exp(-r * r / (4 * t)) / math.sqrt(4 * math.pi * t)
+
+            S, _ = integrate.quad(lambda t: gt(t) * (s0 + s2 * t) if t > 0 else 0.0, 0, delta,
+                                  epsabs=1e-18, epsrel=1e-13, limit=200)
+            assert abs(out["S"] - S) < 1e-13 * math.sqrt(delta), (c, sgn, out["S"], S)
+            if c == 0:
+                continue  # on the surface D is the principal value (pinned by the corollary test)
+            D, _ = integrate.quad(lambda t: r / (2 * t) * gt(t) * (m0 + m2 * t + m4 * t * t / 2) if t > 0 else 0.0,
+                                  0, delta, epsabs=1e-18, epsrel=1e-13, limit=200)
+            assert abs(out["D"] - (-sgn * D)) < 1e-13, (c, sgn, out["D"], -sgn * D)
