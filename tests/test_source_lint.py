@@ -1,0 +1,33 @@
+"""Static checks of the CUDA sources (no GPU needed).
+
+A warp-synchronous intrinsic with a full mask must be executed by every lane
+of the warp.  Written as the right operand of && or ||, or as a branch of ?:,
+it is skipped by the lanes whose left operand decides the result, and the
+remaining lanes wait for them forever.  This check rejects those forms."""
+import os
+import re
+
+CSRC = os.path.join(os.path.dirname(__file__), "..", "paper_2409_11998_gb300", "csrc")
+SYNC = r"(__shfl\w*_sync|__ballot_sync|__any_sync|__all_sync|__match\w*_sync|__reduce\w*_sync|__syncwarp)"
+BAD = re.compile(r"(&&|\|\||\?)\s*!?\s*\(?\s*" + SYNC)
+
+
+def test_no_warp_collective_behind_short_circuit():
+    hits = []
+    for name in sorted(os.listdir(CSRC)):
+        if not name.endswith((".cu", ".cuh")):
+            continue
+        with open(os.path.join(CSRC, name)) as fh:
+            for no, line in enumerate(fh, 1):
+                code = line.split("//")[0]
+                if BAD.search(code):
+                    hits.append(f"{name}:{no}: {line.strip()}")
+    assert not hits, "\n".join(hits)
+
+
+def test_lint_pattern_catches_the_forms():
+    for bad in ["ok && __shfl_down_sync(0xffffffffu, x, 16)", "a || __ballot_sync(m, p)",
+                "c ? __shfl_sync(m, v, 0) : 0", "ok && !__any_sync(m, p)"]:
+        assert BAD.search(bad), bad
+    for good in ["const int y = __shfl_down_sync(0xffffffffu, x, 16);", "ok = ok && y;"]:
+        assert not BAD.search(good), good
