@@ -31,3 +31,17 @@ def test_lint_pattern_catches_the_forms():
         assert BAD.search(bad), bad
     for good in ["const int y = __shfl_down_sync(0xffffffffu, x, 16);", "ok = ok && y;"]:
         assert not BAD.search(good), good
+
+
+def test_no_trap_assert_or_unbounded_loop():
+    """Kernels report failures through status words, never by trapping, and
+    hold no loop without a bound (no spin-waits on flags)."""
+    bad = re.compile(r"__trap\s*\(|\bassert\s*\(|asm\s*(volatile\s*)?\(\s*\"trap|while\s*\(\s*(true|1)\s*\)|for\s*\(\s*;\s*;\s*\)")
+    hits = []
+    for name in sorted(os.listdir(CSRC)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(CSRC, name)) as fh:
+                for no, line in enumerate(fh, 1):
+                    if bad.search(line.split("//")[0]):
+                        hits.append(f"{name}:{no}: {line.strip()}")
+    assert not hits, "\n".join(hits)
