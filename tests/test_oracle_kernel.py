@@ -124,3 +124,26 @@ def test_far_multiplier_limit():
     lim = L * L * (1 - 2 * math.log(L)) / 4
     assert abs(W - lim) < 1e-6
     assert abs(lim - (-2.158883)) < 1e-6
+
+
+def test_single_level_multiplier_inverts_to_smooth_kernel(oracle_lib):
+    """The one-level alternative of Sec. 3 (delta_2 = delta_1, so the near
+    history vanishes): e^{-k^2 delta_1} W(k), W the transform of the log
+    kernel truncated at L = sqrt 2 D + R with R = sqrt(4 delta_1 ln(1/eps)),
+    inverts to G_H[delta_1] at every separation inside the box."""
+    d1 = 2e-3
+    D = 2.0
+    R = math.sqrt(4 * d1 * math.log(1e14))
+    L = math.sqrt(2) * D + R
+
+    def W(k):
+        if k < 1e-6:
+            return L * L * (1 - 2 * math.log(L)) / 4
+        return (1 - special.j0(L * k)) / (k * k) - L * math.log(L) * special.j1(L * k) / k
+
+    M = lambda k: math.exp(-k * k * d1) * W(k)
+    kmax = math.sqrt(40 / d1)
+    for r in [0.0, 0.02, 0.2, 1.0, math.sqrt(2) * D * 0.99]:
+        u = _fourier_inverse_radial(M, r, kmax)
+        ref = oracle_lib.green_smooth(r, d1)[0]
+        assert abs(u - ref) < 1e-9, (r, u, ref)
