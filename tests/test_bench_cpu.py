@@ -40,3 +40,28 @@ def test_single_level_plans_count_one_level():
     st = {"spread": 1.0, "spread_volume": 1.0, "multiplier": 0.5, "interp": 0.2}
     r = bench.roofline(info, st, 1000, 0, 1000, "fp64")
     assert r["algorithmic_df64_fma_per_step"] == 1000 * 1 * (2 * 12 * 12 + 12 * 13)
+
+
+def test_reference_arm_line_contract():
+    """`bench.py --impl reference` (the oracle on the host cores) prints one
+    JSON line with the keys of the GPU arm plus impl, cpu_baseline and an
+    e2e object with zero copy bytes."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "disk", "--steps", "1",
+                          "--warmup", "1"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["n_gpus"] == 1 and d["steps"] == 1 and d["value"] > 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert "workload" in d["config"]
