@@ -45,3 +45,24 @@ def test_two_rank_barrier_and_max():
     res = [json.loads(o.strip().splitlines()[-1]) for o, _ in outs]
     assert sorted(r["rank"] for r in res) == [0, 1]
     assert all(r["world"] == 2 and r["max"] == 2.5 for r in res)
+
+
+def test_reference_arm_under_two_ranks_prints_once():
+    """Under a two-rank launch the reference arm runs on rank 0 only: one JSON
+    line in all, both ranks exit 0."""
+    port = _free_port()
+    procs = []
+    for r in range(2):
+        env = dict(os.environ, RANK=str(r), LOCAL_RANK=str(r), WORLD_SIZE="2",
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+        procs.append(subprocess.Popen([sys.executable, "bench.py", "--impl", "reference", "--workload", "disk",
+                                       "--gpus", "2", "--steps", "1", "--warmup", "1"], cwd=ROOT, env=env,
+                                      stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
+    outs = [p.communicate(timeout=300) for p in procs]
+    for p, (o, e) in zip(procs, outs):
+        assert p.returncode == 0, e[-2000:]
+    lines = [ln for o, _ in outs for ln in o.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1
+    import json
+    assert json.loads(lines[0])["impl"] == "reference"
+    assert not outs[1][0].strip()
