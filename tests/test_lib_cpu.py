@@ -98,3 +98,32 @@ def test_binding_rejects_wrong_dtypes(lib):
         lib._ptr(np.zeros(3, dtype=np.float32))
     with pytest.raises(ValueError):
         lib._ptr(np.zeros((3, 2))[:, 0])
+
+
+def test_missing_library_fails_loudly():
+    """Without the built CUDA library the binding raises ImportError on first
+    use, from every entry point: there is no CPU path to fall back to."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    child = (
+        "import sys\n"
+        f"sys.path.insert(0, {root!r})\n"
+        "import paper_2409_11998_gb300 as lp\n"
+        "lp.LIB_PATH = '/nonexistent/liblp.so'\n"
+        "lp._LIB = None\n"
+        "from workloads import configs\n"
+        "p = configs.disk()\n"
+        "b = p['bnd']\n"
+        "plan = lambda: lp.lp_plan(p['box_lo'], p['box_hi'], p['delta'], 1e-9, precision=lp.LP_FP64,\n"
+        "                          n_panels=b['n_panels'], panel_order=b['order'], bnd_xy=b['xy'],\n"
+        "                          bnd_w=b['w'], bnd_normal=b['normal'])\n"
+        "for call in (lambda: lp.library(), plan):\n"
+        "    try:\n"
+        "        call()\n"
+        "    except ImportError:\n"
+        "        continue\n"
+        "    raise SystemExit('no ImportError')\n"
+        "print('ok')\n")
+    out = subprocess.run([sys.executable, "-c", child], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0 and out.stdout.strip().endswith("ok"), out.stdout + out.stderr[-2000:]
