@@ -45,3 +45,32 @@ def test_no_trap_assert_or_unbounded_loop():
                     if bad.search(line.split("//")[0]):
                         hits.append(f"{name}:{no}: {line.strip()}")
     assert not hits, "\n".join(hits)
+
+
+def test_oracle_separation():
+    """The oracle is test infrastructure: the package never imports it, the
+    oracle never reaches into the package, and bench.py runs it only in its
+    CPU-baseline leg and its reference arm."""
+    import ast
+    root = os.path.join(os.path.dirname(__file__), "..")
+    pkg = os.path.join(root, "paper_2409_11998_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for name in files:
+            if name.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, name)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), name
+                assert "oracle/" not in text and "liboracle" not in text, name
+    for name in os.listdir(os.path.join(root, "oracle")):
+        if name.endswith((".py", ".cpp", ".h")):
+            text = open(os.path.join(root, "oracle", name)).read()
+            assert "paper_2409_11998_gb300" not in text and "csrc" not in text, name
+    tree = ast.parse(open(os.path.join(root, "bench.py")).read())
+    users = set()
+    for fn in ast.walk(tree):
+        if isinstance(fn, ast.FunctionDef):
+            for node in ast.walk(fn):
+                if isinstance(node, ast.Import) and any(a.name == "oracle" for a in node.names):
+                    users.add(fn.name)
+    top = [n for n in tree.body if isinstance(n, (ast.Import, ast.ImportFrom))
+           and any(a.name == "oracle" for a in n.names)]
+    assert not top and users <= {"cpu_baseline", "run_reference"}, users
