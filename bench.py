@@ -160,23 +160,6 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_traffic(name, workload):
-    """DRAM bytes (read + write) of a kernel per bench step, summed over its
-    launches in the step, from the committed ncu summary profiles/traffic.json
-    (entries kernel@workload); valid only while the kernel's source file is
-    unchanged (its sha256 prefix is stored with the entry)."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(p):
-        return None
-    ent = json.load(open(p)).get(f"{name}@{workload}")
-    if not ent:
-        return None
-    src = os.path.join(ROOT, "paper_2409_11998_gb300", "csrc", ent["file"])
-    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != ent["file_sha"]:
-        return None
-    return ent.get("bytes_per_step")
-
-
 # ---------------------------------------------------------------- GPU arm
 def run_lp(args, rank, world, local_rank):
     import numpy as np
@@ -258,17 +241,21 @@ def run_lp(args, rank, world, local_rank):
            "roofline": roof, "gpu_launches": int(launches), "wall_s_timed_region": round(wall, 3),
            "clocks": clocks}
 
+    gpu_out = {args.precision: {k: o.cpu().numpy() for k, o in zip("VSD", outs) if o is not None}}
     if rank == 0 and not args.no_extras:
         res["e2e"] = run_e2e(args, prob, dev, ev, points)
         if fp64:
             res["fp32_same_workload"] = run_fp32(args, prob, dev, stream, points)
+            gpu_out["fp32"] = res["fp32_same_workload"].pop("_outputs")
         if args.workload == "starfish":
             from workloads import configs as _cfg
             small_pool = _cfg.serving_pool(n_meshes=6, t_min=10_000, t_max=300_000, seed=5300)
             res["served"] = run_serve(args, rank, world, local_rank, pool=small_pool, rates=(100, 400),
                                       seconds=3.0)
         if world == 1:
-            res["cpu_baseline"] = cpu_baseline(prob, budget_s=15.0, refine_levels=args.refine_levels)
+            res["cpu_baseline"] = cpu_baseline(prob, budget_s=15.0, refine_levels=args.refine_levels,
+                                               gpu_out=gpu_out)
+            res["parity"] = res["cpu_baseline"].pop("_parity")
     ev.close()
     return res
 
@@ -281,22 +268,10 @@ def sm_max_mhz():
     return mhz
 
 
-def fp64_peak_tflops():
-    """FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA per clock
-    per SM (the GB300 FP64 rate, 1.25 TFLOP/s nominal) x 2 FLOP x max SM clock."""
-    return 152 * 2 * 2 * sm_max_mhz() * 1e6 / 1e12
-
-
-# FP32 instructions of one double-float multiply-add as the kernels implement
-# it: two-product (multiply + 3 fused multiply-adds), two-sum (6), two adds and
-# the renormalising fast two-sum (3).
-DF64_FMA_INSTR = 15
-
-
-def df64_peak_t():
-    """Double-float multiply-adds per second the FP32 units can issue: 152 SMs
-    x 128 FP32 lanes x max SM clock / DF64_FMA_INSTR (T/s)."""
-    return 152 * 128 * sm_max_mhz() * 1e6 / DF64_FMA_INSTR / 1e12
+def issue_peak_t():
+    """Warp instructions per second the GPU can issue: 152 SMs x 4 schedulers
+    x one instruction per clock x max SM clock (T/s)."""
+    return 152 * 4 * sm_max_mhz() * 1e6 / 1e12
 
 
 def fp32_fma_peak_t():
@@ -304,78 +279,99 @@ def fp32_fma_peak_t():
     return 152 * 128 * sm_max_mhz() * 1e6 / 1e12
 
 
+def kernel_profile(name, workload):
+    """ncu counters of a kernel per bench step (summed over its launches in a
+    step) from profiles/traffic.json, valid only while the kernel's source
+    file is unchanged (its sha256 prefix is stored with the entry)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    ent = json.load(open(p)).get(f"{name}@{workload}")
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2409_11998_gb300", "csrc", ent["file"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != ent["file_sha"]:
+        return None
+    return ent
+
+
+def hbm_part(byts, ms):
+    """Achieved HBM bandwidth of algorithmic bytes in ms, against the measured copy peak."""
+    hbm, kind = peaks()
+    gbs = byts / (ms / 1e3) / 1e9
+    return {"achieved": round(gbs, 2), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 5),
+            "algorithmic_bytes_per_step": int(byts), "peak_source": f"{kind} (MEASURED_PEAKS.json hbm_gbs)"}
+
+
 def roofline(info, st, nv, nb, nt, precision, n_out=3, workload="starfish"):
     """Roofline of this library's dominant kernel: among the candidates
     below, the one whose stage takes longest in the live step.
 
-    FP64 plans with the double-float chain (bound by FP32 issue, in
-    double-float multiply-adds; work per point and level 2 w (nc - 1) for
-    the two weight polynomials plus w (w + 1) per channel -- w q*wy products
-    and w^2 cell updates for the spread, w^2 products and w row combinations
-    per output for the interpolation):
-      spread_sub_dd_kernel (volume spread, both levels), interp_dd_kernel.
-    FP32 plans:
-      spread_sub_kernel: FP32 multiply-adds, w^2 cell updates + 2 w (nc - 1)
-        weight terms per volume node and level, against the FP32 FMA peak;
-      fft_cols_kernel (column pass: forward column transforms, multiplier,
-        inverse): HBM, algorithmic bytes per level = the four input spectra
-        read and the three outputs written, g x kp complex values each;
-      interp_kernel: HBM, the three output grids of both levels read once,
-        the targets read and the three outputs written."""
+    Every candidate carries its HBM fraction ("hbm": algorithmic bytes per
+    step -- positions, strengths and the grids written once for the spread;
+    the grids read once, the targets read and the outputs written for the
+    interpolation; b = 8 bytes per value for FP64 plans, 4 for FP32 -- over
+    the live stage time, against the measured copy bandwidth).  The spreads
+    and interpolations are instruction-issue bound (2w weight polynomials and
+    w^2 cell updates per point, no reuse that HBM could feed), so their
+    reported bound is "alu": warp instructions per second -- the kernel's
+    instructions per step counted by ncu on this build (profiles/traffic.json,
+    matched by source hash) over the live stage time -- against the issue
+    peak of one instruction per scheduler per clock.  When no count matches
+    the current source, the instructions are estimated from the algorithm
+    and marked so.  The FP32 column pass is memory-bound and reported as
+    "hbm"."""
     b = 8 if precision == "fp64" else 4
     W, nc = int(info["w"]), int(info["es_nc"])
     levels = [(info["g_nh"], info["K_nh"]), (info["g_fh"], info["K_fh"])]
     levels = [(g, K) for g, K in levels if g > 0]
-    hbm, hbm_kind = peaks()
+    nl = len(levels)
+    grid_cells = sum(g * g for g, _ in levels)
     vol_ms = st.get("spread_volume", st["spread"])
-    if precision == "fp64" and (info.get("own_fft") and info.get("precision") == 0):
-        nl = len(levels)
-        cand = {"spread": (vol_ms, nv * nl * (2 * W * (nc - 1) + W * (W + 1)),
-                           "spread_sub_dd_kernel" if info.get("binned") else "spread_atomic_kernel"),
-                "interp": (st["interp"], nt * nl * (2 * W * (nc - 1) + n_out * W * (W + 1)), "interp_dd_kernel")}
-        dom = max(cand, key=lambda k: cand[k][0])
-        ms, ops, kname = cand[dom]
-        ach = ops / (ms / 1e3) / 1e12
-        peak = df64_peak_t()
-        return {"kernel": kname, "bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 4),
-                "unit": "T df64-FMA/s (FP32 units)", "frac": round(ach / peak, 4),
-                "traffic": kernel_traffic(kname, workload), "traffic_unit": "DRAM bytes per step (both launches)",
-                "algorithmic_df64_fma_per_step": int(ops), "launch_ms": round(ms, 4), "stage": dom,
-                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x sm_max_mhz / {DF64_FMA_INSTR} "
-                               "FP32 instructions per df64 multiply-add"}
-    if precision == "fp64":
-        flops = 2 * (2 * W * (nc - 1) * 2 * (nv + nb) + W * (W + 1) * 2 * (nv + 3 * nb))
-        ms = st["spread"]
-        tf = flops / (ms / 1e3) / 1e12
-        peak = fp64_peak_tflops()
-        return {"kernel": "spread_atomic_kernel", "bound": "alu", "achieved": round(tf, 4),
-                "peak": round(peak, 4), "unit": "TFLOP/s (FP64)", "frac": round(tf / peak, 4),
-                "traffic": kernel_traffic("spread_atomic_kernel", workload), "algorithmic_flops_per_step": int(flops),
-                "launch_ms": round(ms, 4), "stage": "spread",
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x sm_max_mhz"}
-    kp = lambda K: (int(K) + 2) & ~1
-    cols_bytes = sum(7 * g * kp(K) * 2 * b for g, K in levels)
-    interp_bytes = sum(n_out * g * g * b for g, _ in levels) + nt * (16 + 8 * n_out)
-    spread_fma = nv * len(levels) * (W * W + 2 * W * (nc - 1))
-    cand = {"spread_volume": vol_ms, "multiplier": st["multiplier"], "interp": st["interp"]}
-    dom = max(cand, key=lambda k: cand[k])
-    ms = cand[dom]
-    if dom == "spread_volume":
-        kname = "spread_sub_kernel" if info.get("binned") else "spread_atomic_kernel"
-        ach = spread_fma / (ms / 1e3) / 1e12
-        peak = fp32_fma_peak_t()
-        return {"kernel": kname, "bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 4),
-                "unit": "T FP32-FMA/s", "frac": round(ach / peak, 5), "traffic": kernel_traffic(kname, workload),
-                "traffic_unit": "DRAM bytes per step (both launches)", "algorithmic_fma_per_step": int(spread_fma),
-                "launch_ms": round(ms, 4), "stage": dom,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x sm_max_mhz"}
-    kname, byts = ("fft_cols_kernel", cols_bytes) if dom == "multiplier" else ("interp_kernel", interp_bytes)
-    gbs = byts / (ms / 1e3) / 1e9
-    return {"kernel": kname, "bound": "hbm", "achieved": round(gbs, 2), "peak": hbm, "unit": "GB/s",
-            "frac": round(gbs / hbm, 5), "traffic": kernel_traffic(kname, workload),
-            "traffic_unit": "DRAM bytes per step (all launches of the stage)",
-            "algorithmic_bytes_per_step": int(byts), "launch_ms": round(ms, 4), "stage": dom,
-            "peak_source": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+    df64 = precision == "fp64" and info.get("own_fft") and info.get("precision") == 0
+    binned = bool(info.get("binned"))
+    spread_bytes = nv * (2 * b + b) + grid_cells * b
+    interp_bytes = grid_cells * b * n_out + nt * (2 * 8 + 8 * n_out)
+    if df64:
+        spread_name = "spread_sub_dd_kernel" if binned else "spread_atomic_kernel"
+        # df64 multiply-adds per point and level: 2w (nc - 1) for the weight
+        # polynomials plus w (w + 1) per channel; about 15 FP32 instructions
+        # each (two-product 4, two-sum 6, two adds, renormalising sum 3)
+        cand = {"spread_volume": (vol_ms, spread_name, spread_bytes,
+                                  nv * nl * (2 * W * (nc - 1) + W * (W + 1)) * 15 / 32),
+                "interp": (st["interp"], "interp_dd_kernel", interp_bytes,
+                           nt * nl * (2 * W * (nc - 1) + n_out * W * (W + 1)) * 15 / 32)}
+    else:
+        kp = lambda K: (int(K) + 2) & ~1
+        cols_bytes = sum(7 * g * kp(K) * 2 * b for g, K in levels)
+        cand = {"spread_volume": (vol_ms, "spread_sub_kernel" if binned else "spread_atomic_kernel", spread_bytes,
+                                  nv * nl * (W * W + 2 * W * (nc - 1)) / 32),
+                "multiplier": (st["multiplier"], "fft_cols_kernel", cols_bytes, None),
+                "interp": (st["interp"], "interp_dd_kernel" if precision == "fp64" else "interp_kernel",
+                           interp_bytes, nt * nl * (2 * W * nc + n_out * W * W) / 32)}
+    dom = max(cand, key=lambda k: cand[k][0])
+    ms, kname, byts, inst_est = cand[dom]
+    prof = kernel_profile(kname, workload)
+    hbm = hbm_part(byts, ms)
+    out = {"kernel": kname, "stage": dom, "launch_ms": round(ms, 4),
+           "traffic": prof.get("bytes_per_step") if prof else None,
+           "traffic_unit": "DRAM bytes per step (ncu, all launches of the kernel in one step)",
+           "hbm_frac": hbm["frac"], "hbm": hbm}
+    if inst_est is None:   # memory-bound column pass
+        out.update({"bound": "hbm", "achieved": hbm["achieved"], "peak": hbm["peak"], "unit": "GB/s",
+                    "frac": hbm["frac"], "peak_source": hbm["peak_source"]})
+        return out
+    inst = prof.get("inst_per_step") if prof else None
+    src = "ncu smsp__inst_executed.sum of this build (profiles/traffic.json)"
+    if not inst:
+        inst, src = inst_est, "estimate from the algorithm (no ncu count for this source)"
+    ach = inst / (ms / 1e3) / 1e12
+    peak = issue_peak_t()
+    out.update({"bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 4), "unit": "T warp-instructions/s",
+                "frac": round(ach / peak, 4), "instructions_per_step": int(inst), "instructions_source": src,
+                "peak_source": "152 SMs x 4 schedulers x 1 warp instruction per clock x sm_max_mhz "
+                               "(MEASURED_PEAKS.json)"})
+    return out
 
 
 def layer_densities(prob, conv):
@@ -494,12 +490,50 @@ def run_fp32(args, prob, dev, stream, points):
     ev.close()
     return {"value": points / (statistics.mean(ms) / 1e3), "unit": UNIT, "dtype": "f32 (FP64 zero mode)",
             "tol": 1e-5, "ms_per_step": statistics.mean(ms),
-            "stages_ms": {k: round(v, 4) for k, v in st.items()}, "roofline": roof}
+            "stages_ms": {k: round(v, 4) for k, v in st.items()}, "roofline": roof,
+            "_outputs": {k: o.cpu().numpy() for k, o in zip("VSD", outs) if o is not None}}
 
 
-def cpu_baseline(prob, budget_s=15.0, refine_levels=0):
+def oracle_sample(prob, n, rng):
+    """n targets: nine tenths drawn uniformly, one tenth from the band near
+    the boundary (every k-th target by distance to the nearest boundary
+    node, the nearest first), so that the local expansions are sampled too."""
+    import numpy as np
+    nt = len(prob["tgt_xy"])
+    if n >= nt:
+        return np.arange(nt)
+    n_near = n // 10
+    near = np.empty(0, dtype=np.int64)
+    if prob.get("bnd") is not None and n_near > 0:
+        from scipy.spatial import cKDTree
+        d, _ = cKDTree(prob["bnd"]["xy"]).query(prob["tgt_xy"])
+        order = np.argsort(d, kind="stable")
+        band = order[: max(n_near, int(np.searchsorted(d[order], 12 * np.sqrt(prob["delta"]))))]
+        near = band[:: max(1, len(band) // n_near)][:n_near]
+    rest = np.setdiff1d(np.arange(nt), near)
+    return np.concatenate([near, rng.choice(rest, n - len(near), replace=False)])
+
+
+def parity(gpu, ref, idx):
+    """Relative L2 and max error of GPU results against the oracle on the
+    sampled targets, per output."""
+    import numpy as np
+    out = {}
+    for k, want in ref.items():
+        if k not in gpu:
+            continue
+        got = gpu[k][idx]
+        out[k] = {"rel_l2": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
+                  "rel_max": float(np.max(np.abs(got - want)) / np.max(np.abs(want))),
+                  "n_targets": int(len(idx))}
+    return out
+
+
+def cpu_baseline(prob, budget_s=15.0, refine_levels=0, gpu_out=None):
     """The oracle as it stands, on the host cores, on a bounded sample of
-    targets; extrapolated to the workload's points/s."""
+    targets; extrapolated to the workload's points/s.  The last (largest)
+    sample also gives the error of every GPU result of the run against the
+    oracle (outside every timed region)."""
     import numpy as np
     ncores = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(ncores))
@@ -508,9 +542,9 @@ def cpu_baseline(prob, budget_s=15.0, refine_levels=0):
     rng = np.random.default_rng(5)
     n = 32
     while True:
-        idx = rng.choice(nt, n, replace=False)
+        idx = oracle_sample(prob, n, rng)
         t0 = time.perf_counter()
-        oracle.evaluate(prob, targets=idx, refine_levels=refine_levels)
+        ref = oracle.evaluate(prob, targets=idx, refine_levels=refine_levels)
         dt = time.perf_counter() - t0
         if dt > budget_s / 4 or n >= nt:
             break
@@ -518,9 +552,12 @@ def cpu_baseline(prob, budget_s=15.0, refine_levels=0):
     per_target = dt / n
     t_full = per_target * nt
     points = len(prob["src_w"]) + len(prob["bnd"]["w"]) + nt
+    par = {prec: parity(out, ref, idx) for prec, out in (gpu_out or {}).items()}
+    par["sample"] = (f"{len(idx)} targets: {len(idx) - len(idx) // 10} uniform, {len(idx) // 10} from the "
+                     f"boundary band; oracle = direct FP64 sums + the same local expansions")
     return {"value": points / t_full, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", ncores)),
             "kind": "oracle", "sample": f"{n} of {nt} targets (all sources), {dt:.2f} s; "
-            f"extrapolated linearly in targets to the full workload ({t_full:.0f} s)"}
+            f"extrapolated linearly in targets to the full workload ({t_full:.0f} s)", "_parity": par}
 
 
 # ---------------------------------------------------------------- batched waves of uneven problems

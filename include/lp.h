@@ -37,9 +37,11 @@
  *
  * Errors: every call returns an lp_status.  No call launches work when it
  * returns LP_ERR_ARG.  Problems detected on the device (a point outside the
- * box, a band target outside the domain where V_L is undefined) set bits of a
- * plan status word that lp_sync returns.  Calls on one plan must not be made
- * concurrently from several host threads.
+ * box, a band target outside the domain where V_L is undefined, a closest-
+ * point search that did not converge) set bits of a plan status word that
+ * lp_sync returns.  No kernel waits on another kernel or on the host, so no
+ * device-side wait can hang; lp_sync_timeout bounds the host's wait.  Calls
+ * on one plan must not be made concurrently from several host threads.
  */
 #ifndef LP_H_
 #define LP_H_
@@ -62,7 +64,18 @@ typedef enum {
   LP_ERR_UNSUPPORTED = 5,    /* V requested at an exterior target within 12 sqrt(delta_1)
                                 of the boundary, where Sec. 4 gives no expansion; or a
                                 refined plan passed to lp_batch_execute */
-  LP_ERR_STATE = 6           /* call order violated (e.g. execute before lp_volume) */
+  LP_ERR_STATE = 6,          /* call order violated (e.g. execute before lp_volume) */
+  LP_ERR_NEWTON = 7,         /* the closest-point search (Sec. 2.2: nearest node, then
+                                Newton on the panel polynomial) failed for some target of
+                                the local band: 20 double-precision Newton steps ended with
+                                a step of 1e-6 or more in the panel parameter, the foot ran
+                                past the far end of the adjacent panel as well, or the foot
+                                lies where the panel's speed |gamma'| is below 1e-9 of the
+                                box side, so that the tangent frame of Sec. 4 is undefined
+                                (a cusp, or a panel of nearly coincident nodes); the local
+                                terms of those targets are unreliable */
+  LP_ERR_TIMEOUT = 8         /* lp_sync_timeout: the plan's work did not complete within
+                                the given time (it keeps running; nothing is cancelled) */
 } lp_status;
 
 enum { LP_FP64 = 0, LP_FP32 = 1 };
@@ -123,6 +136,13 @@ typedef struct {
                            (FP64 16/24/32, FP32 16/32/48 near-history cells)
                            on those sources and keeps the fastest (it
                            synchronises the plan's stream once) */
+  int64_t max_device_bytes; /* device-memory budget of the plan (0: none): an
+                           allocation that would take the plan's device
+                           footprint (lp_plan_info's device bytes) beyond it
+                           fails with LP_ERR_NOMEM before cudaMalloc is
+                           called, whether in lp_plan, lp_volume or
+                           lp_execute; a server uses it to keep a plan within
+                           the memory it admitted the plan for */
 } lp_domain;
 
 /* Create a plan: chooses the near/far-history grids (Sec. 3: delta_2 =
@@ -268,6 +288,14 @@ lp_status lp_solve_neumann(lp_plan_t plan, const double* g, const double* f_jet_
 
 /* Wait for the plan's stream; return and clear the device status word. */
 lp_status lp_sync(lp_plan_t plan);
+
+/* lp_sync with a bounded wait: polls the plan's stream for at most
+ * timeout_ms milliseconds of host time (timeout_ms < 0: wait without bound,
+ * as lp_sync).  Returns LP_ERR_TIMEOUT if the work queued on the plan's
+ * stream has not completed by then -- the work keeps running, and the device
+ * status word is left for a later lp_sync / lp_sync_timeout -- otherwise what
+ * lp_sync returns. */
+lp_status lp_sync_timeout(lp_plan_t plan, double timeout_ms);
 
 /* Release all plan resources (synchronises the plan's stream first). */
 lp_status lp_destroy(lp_plan_t plan);

@@ -24,11 +24,13 @@ LP_FP64, LP_FP32 = 0, 1
 LP_REFINE_AUTO = -1  # refine_levels: levels from tol and order (Sec. 4.4)
 LP_LEVELS_AUTO = -1  # levels: one history level when its grid is small
 STATUS = {0: "LP_OK", 1: "LP_ERR_ARG", 2: "LP_ERR_OUT_OF_BOX", 3: "LP_ERR_NOMEM",
-          4: "LP_ERR_CUDA", 5: "LP_ERR_UNSUPPORTED", 6: "LP_ERR_STATE"}
+          4: "LP_ERR_CUDA", 5: "LP_ERR_UNSUPPORTED", 6: "LP_ERR_STATE", 7: "LP_ERR_NEWTON",
+          8: "LP_ERR_TIMEOUT"}
 EXPORTS = ("lp_plan", "lp_volume", "lp_single_layer", "lp_double_layer", "lp_execute", "lp_sync",
            "lp_destroy", "lp_status_string", "lp_plan_info", "lp_stage_times", "lp_execute_noalloc",
            "lp_batch_create", "lp_batch_execute", "lp_batch_sync", "lp_batch_stage_times",
-           "lp_batch_destroy", "lp_solve_dirichlet", "lp_execute_graph", "lp_solve_neumann")
+           "lp_batch_destroy", "lp_solve_dirichlet", "lp_execute_graph", "lp_solve_neumann",
+           "lp_sync_timeout")
 
 
 class LpError(RuntimeError):
@@ -46,7 +48,8 @@ class lp_domain(ctypes.Structure):
                 ("refine_levels", ctypes.c_int),
                 ("levels", ctypes.c_int),
                 ("upsampling", ctypes.c_double),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int),
+                ("max_device_bytes", ctypes.c_int64)]
 
 
 _LIB = None
@@ -72,6 +75,7 @@ def _lib():
         L.lp_batch_stage_times.argtypes = [vp, vp]
         L.lp_batch_destroy.argtypes = [vp]
         L.lp_sync.argtypes = [vp]
+        L.lp_sync_timeout.argtypes = [vp, d]
         L.lp_destroy.argtypes = [vp]
         L.lp_status_string.argtypes = [i32]
         L.lp_status_string.restype = ctypes.c_char_p
@@ -115,7 +119,7 @@ def _ptr(a):
 
 def lp_plan(box_lo, box_hi, delta, tol, *, precision=LP_FP64, order=5, n_panels=0, panel_order=16,
             bnd_xy=None, bnd_w=None, bnd_normal=None, stream=0, refine_levels=0, levels=0, upsampling=0.0,
-            autotune=False):
+            autotune=False, max_device_bytes=0):
     dom = lp_domain()
     dom.precision = int(precision)
     dom.order = int(order)
@@ -131,6 +135,7 @@ def lp_plan(box_lo, box_hi, delta, tol, *, precision=LP_FP64, order=5, n_panels=
     dom.levels = LP_LEVELS_AUTO if levels == "auto" else int(levels)
     dom.upsampling = float(upsampling)
     dom.autotune = 1 if autotune else 0
+    dom.max_device_bytes = int(max_device_bytes)
     h = ctypes.c_void_p()
     _check(_lib().lp_plan(ctypes.byref(dom), float(delta), float(tol), ctypes.byref(h)), "lp_plan")
     return h
@@ -230,6 +235,16 @@ def lp_sync(plan):
     _check(_lib().lp_sync(plan), "lp_sync")
 
 
+def lp_sync_timeout(plan, timeout_ms):
+    """lp_sync with a bounded host wait; returns False (LP_ERR_TIMEOUT) if the
+    plan's work is still running after timeout_ms, True once it completed."""
+    code = _lib().lp_sync_timeout(plan, float(timeout_ms))
+    if code == 8:
+        return False
+    _check(code, "lp_sync_timeout")
+    return True
+
+
 def lp_destroy(plan):
     _check(_lib().lp_destroy(plan), "lp_destroy")
 
@@ -258,7 +273,7 @@ class Evaluator:
     ``host=True``, in which case the C ABI receives host pointers."""
 
     def __init__(self, problem, precision=None, order=5, tol=None, device="cuda", host=False,
-                 stream=None, refine_levels=0, levels=0, upsampling=0.0, autotune=False):
+                 stream=None, refine_levels=0, levels=0, upsampling=0.0, autotune=False, max_device_bytes=0):
         import torch
         self.torch = torch
         self.host = host
@@ -286,7 +301,7 @@ class Evaluator:
         self.plan = lp_plan(problem["box_lo"], problem["box_hi"], problem["delta"], self.tol,
                             precision=self.precision, order=order, stream=self.stream,
                             refine_levels=refine_levels, levels=levels, upsampling=upsampling,
-                            autotune=autotune, **kw)
+                            autotune=autotune, max_device_bytes=max_device_bytes, **kw)
         self.problem = problem
 
     def bind(self, src_xy=None, src_w=None, src_f=None, sigma=None, mu=None):

@@ -75,6 +75,8 @@ __device__ __forceinline__ void legendre_jets(const T* const* c, const T* ref, i
 struct Foot {
   int panel;
   double t, d2, gx, gy;
+  double s2;       // |gamma'|^2 at the last parameter
+  bool converged;  // the double-precision phase met its stopping rule
 };
 
 // Newton for the foot on panel ip from parameter t: a single-precision phase
@@ -84,7 +86,8 @@ struct Foot {
 // convergence leaves ~1e-12 in t after it -- with the foot offset at the last
 // parameter from the second-order Taylor expansion of that step (error ~|dt|^3
 // times the third derivative), so that the distance of on-boundary targets
-// and the side of the boundary are resolved to rounding.
+// and the side of the boundary are resolved to rounding.  Twenty double
+// steps without a step below 1e-6 leave `converged` false.
 __device__ Foot panel_foot(const LocalArgs& a, int ip, double t, double x, double y) {
   const size_t off = (size_t)(2 * ip) * a.p;
   const double rx = a.geo_ref[2 * ip], ry = a.geo_ref[2 * ip + 1];
@@ -112,6 +115,7 @@ __device__ Foot panel_foot(const LocalArgs& a, int ip, double t, double x, doubl
   const double ref[2] = {rx, ry};
   Foot r;
   r.panel = ip;
+  r.converged = false;
   for (int it = 0; it < 20; ++it) {
     double J[2][3];
     legendre_jets<2, 2, double>(c64, ref, a.p, t, J);
@@ -125,7 +129,11 @@ __device__ Foot panel_foot(const LocalArgs& a, int ip, double t, double x, doubl
     t = tn;
     r.gx = gx + dt * (J[0][1] + 0.5 * dt * J[0][2]);
     r.gy = gy + dt * (J[1][1] + 0.5 * dt * J[1][2]);
-    if (fabs(dt) < 1e-6) break;
+    r.s2 = s2;
+    if (fabs(dt) < 1e-6) {
+      r.converged = true;
+      break;
+    }
   }
   r.t = t;
   r.d2 = r.gx * r.gx + r.gy * r.gy;
@@ -164,7 +172,7 @@ __device__ void local_near_one(const LocalArgs& a, int64_t i, int best) {
   const double* J = a.jet ? a.jet + 6 * i : nullptr;
   T vl = 0, sl = 0, dlv = 0;
   bool far = false;
-  Foot ft{-1, 0.0, 1e300, 0.0, 0.0};
+  Foot ft{-1, 0.0, 1e300, 0.0, 0.0, 1.0, true};
   {
     const int p = a.p;
     const int ip0 = best / p;
@@ -183,9 +191,18 @@ __device__ void local_near_one(const LocalArgs& a, int64_t i, int best) {
         }
       }
       Foot f = panel_foot(a, ip, a.tau[kb], x, y);
+      // past the adjacent panel's far end as well: no foot on either panel
+      const bool beyond = ft.t > 0.0 ? f.t == 1.0 : f.t == -1.0;
+      if (!f.converged || beyond) atomicOr(a.status, kStatusNewton);
       if (f.d2 < ft.d2) ft = f;
+    } else if (!ft.converged) {
+      atomicOr(a.status, kStatusNewton);
     }
     if (sqrt(ft.d2) >= a.band) far = true;
+    // a foot where the parametrisation's speed vanishes (a cusp, a panel of
+    // nearly coincident nodes) has no tangent frame: the expansions below
+    // divide by that speed
+    if (!far && ft.s2 < 1e6 * a.on_tol * a.on_tol) atomicOr(a.status, kStatusNewton);
   }
 
   if (far) {

@@ -3,10 +3,12 @@
 //   spread -> forward FFT -> multiplier -> inverse FFT -> interpolate -> local
 // of Sec. 3 (history part, two levels) and Sec. 4 (local part).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "lp_internal.cuh"
@@ -69,7 +71,13 @@ bool is_device_ptr(const void* p) {
   return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
 }
 
+// Device allocation charged to the plan's footprint; refused (no cudaMalloc)
+// when it would take the footprint beyond the plan's budget.
 bool dalloc(Plan& P, void** ptr, size_t bytes) {
+  if (P.max_bytes && P.device_bytes + bytes > P.max_bytes) {
+    *ptr = nullptr;
+    return false;
+  }
   if (cudaMalloc(ptr, bytes) != cudaSuccess) {
     cudaGetLastError();
     *ptr = nullptr;
@@ -82,6 +90,16 @@ bool dalloc(Plan& P, void** ptr, size_t bytes) {
 
 void dfree(void* p) {
   if (p) cudaFree(p);
+}
+
+// Free a plan buffer of `bytes` bytes and take it off the plan's footprint.
+template <typename Tp>
+void drelease(Plan& P, Tp*& p, size_t bytes) {
+  if (p) {
+    cudaFree((void*)p);
+    P.device_bytes -= std::min(bytes, P.device_bytes);
+  }
+  p = nullptr;
 }
 
 // Stage timing event k on stream s; while lp_execute is captured into a
@@ -226,15 +244,11 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 void* g_noalloc_addr[kMaxDevices] = {};
 
-// Device address of the scratch on the current device.  In host code the
-// array's name is only a host-side stand-in, so the address is looked up once
-// per device (with that device current) and cached.
-lp_status noalloc_scratch(void** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    cudaGetLastError();
-    return LP_ERR_CUDA;
-  }
+// Device address of the scratch on device `dev`, which must be current.  In
+// host code the array's name is only a host-side stand-in, so the address is
+// looked up once per device (with that device current) and cached.
+lp_status noalloc_scratch(int dev, void** out) {
+  if (dev < 0 || dev >= kMaxDevices) return LP_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
   if (!g_noalloc_addr[dev]) {
     void* ptr = nullptr;
@@ -543,6 +557,8 @@ const char* lp_status_string(lp_status s) {
     case LP_ERR_UNSUPPORTED:
       return "volume potential requested at an exterior target inside the local band";
     case LP_ERR_STATE: return "call order violated";
+    case LP_ERR_NEWTON: return "closest-point search did not converge for a target near the boundary";
+    case LP_ERR_TIMEOUT: return "the plan's work did not complete within the time limit";
   }
   return "unknown status";
 }
@@ -570,7 +586,7 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
     if (!(dom->box_hi[d] > dom->box_lo[d]) || !std::isfinite(dom->box_lo[d]) ||
         !std::isfinite(dom->box_hi[d]))
       return LP_ERR_ARG;
-  if (dom->n_panels < 0) return LP_ERR_ARG;
+  if (dom->n_panels < 0 || dom->max_device_bytes < 0) return LP_ERR_ARG;
   if (dom->refine_levels < LP_REFINE_AUTO || dom->refine_levels > kMaxDyLevels) return LP_ERR_ARG;
   if (dom->levels < LP_LEVELS_AUTO || dom->levels > 2) return LP_ERR_ARG;
   if (dom->upsampling != 0.0 && !(dom->upsampling >= 1.25 && dom->upsampling <= 3.0)) return LP_ERR_ARG;
@@ -596,6 +612,7 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
   P.side = std::max(P.box_hi[0] - P.box_lo[0], P.box_hi[1] - P.box_lo[1]);
   P.on_tol = 1e-12 * P.side;
   P.stream = (cudaStream_t)dom->stream;
+  P.max_bytes = dom->max_device_bytes > 0 ? (size_t)dom->max_device_bytes : 0;
   // Kernel width and upsampling.  FP64 is bound by cuFFT's FP64 arithmetic,
   // so its grids use sigma = 1.5 (0.56x the modes of sigma = 2) and wider
   // kernels; FP32 keeps sigma = 2.  Measured (disk, tol 1e-9): sigma 2, w 10
@@ -618,6 +635,11 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
     }
   }
   w = std::min(std::max(w, 4), kMaxW);
+  if (cudaGetDevice(&P.device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return LP_ERR_CUDA;
+  }
   P.ker.w = w;
   P.ker.beta = 2.30 * w;  // refined by choose_levels for the realised sigma
   P.ker.half_w = 0.5 * w;
@@ -641,7 +663,6 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
     G.chan_bytes = (size_t)G.g * G.pitch * rs;
     for (int c = 0; c < 4 && st == LP_OK; ++c)
       if (!dalloc(P, &G.chan[c], G.chan_bytes)) st = LP_ERR_NOMEM;
-    if (st == LP_OK) st = make_fft_plans(P, G);
   }
   if (st == LP_OK) {
     if (!dalloc(P, (void**)&P.d_status, sizeof(unsigned)) ||
@@ -681,6 +702,8 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
   }
   if (st == LP_OK) st = setup_bins(P);
   if (st == LP_OK) st = setup_fft_chain(P);
+  // cuFFT plans only for grids the library's own FFT chain cannot hold
+  for (int l = P.l0; l < 2 && st == LP_OK && !P.own_fft; ++l) st = make_fft_plans(P, P.lv[l]);
   if (st == LP_OK) st = status_from_cuda();
   if (st != LP_OK) {
     destroy_plan(P);
@@ -748,19 +771,25 @@ lp_status lp_volume(lp_plan_t h, int64_t n, const double* xy, const double* w, c
   if (!h || n < 0) return LP_ERR_ARG;
   if (n > 0 && (!xy || !w || !f)) return LP_ERR_ARG;
   Plan& P = h->P;
-  if (n > P.nv) {
+  if (n > P.v_cap) {
     cudaStreamSynchronize(P.stream);
-    dfree(P.d_vxy);
-    dfree(P.d_vq);
-    P.d_vxy = P.d_vq = nullptr;
+    drelease(P, P.d_vxy, P.v_cap * 2 * sizeof(double));
+    drelease(P, P.d_vq, P.v_cap * sizeof(double));
+    P.v_cap = 0;
+    P.nv = 0;
+    P.have_volume = false;
     if (!dalloc(P, (void**)&P.d_vxy, n * 2 * sizeof(double)) ||
         !dalloc(P, (void**)&P.d_vq, n * sizeof(double)))
       return LP_ERR_NOMEM;
+    P.v_cap = n;
   }
   P.nv = n;
   if (n > 0) {
-    if (!ensure_stage(P, round256(n * 2 * sizeof(double)) + 2 * round256(n * sizeof(double))))
-      return LP_ERR_NOMEM;
+    // staging only for the arrays that are in host memory
+    const size_t stage = (is_device_ptr(xy) ? 0 : round256(n * 2 * sizeof(double))) +
+                         (is_device_ptr(w) ? 0 : round256(n * sizeof(double))) +
+                         (is_device_ptr(f) ? 0 : round256(n * sizeof(double)));
+    if (!ensure_stage(P, stage)) return LP_ERR_NOMEM;
     size_t off = 0;
     const double* dxy = device_view(P, xy, n * 2, &off, P.stream);
     const double* dw = device_view(P, w, n, &off, P.stream);
@@ -774,18 +803,18 @@ lp_status lp_volume(lp_plan_t h, int64_t n, const double* xy, const double* w, c
     if ((size_t)n > P.key_cap || (size_t)n > P.vsort_cap) {
       cudaStreamSynchronize(P.stream);
       if ((size_t)n > P.key_cap) {
-        dfree(P.d_keys);
-        P.d_keys = nullptr;
+        drelease(P, P.d_keys, P.key_cap * sizeof(int));
+        P.key_cap = 0;
         if (!dalloc(P, (void**)&P.d_keys, n * sizeof(int))) return LP_ERR_NOMEM;
         P.key_cap = n;
       }
       if ((size_t)n > P.vsort_cap) {
-        void** bufs[5] = {(void**)&P.d_vrel_s, (void**)&P.d_vperm, (void**)&P.d_vq_s, (void**)&P.d_vrel_dd,
-                          (void**)&P.d_vq_dd};
-        for (void** b : bufs) {
-          dfree(*b);
-          *b = nullptr;
-        }
+        const size_t c = P.vsort_cap;
+        drelease(P, P.d_vperm, c * sizeof(int));
+        drelease(P, P.d_vrel_s, f64 ? 0 : c * sizeof(float2));
+        drelease(P, P.d_vq_s, f64 ? 0 : c * sizeof(float));
+        drelease(P, P.d_vrel_dd, f64 ? c * sizeof(float4) : 0);
+        drelease(P, P.d_vq_dd, f64 ? c * sizeof(float2) : 0);
         P.vsort_cap = 0;
         const bool ok = dalloc(P, (void**)&P.d_vperm, n * sizeof(int)) &&
                         (f64 ? dalloc(P, (void**)&P.d_vrel_dd, n * sizeof(float4)) &&
@@ -811,7 +840,7 @@ static lp_status bind_layer(lp_plan_t h, const double* dens, int kind) {
   if (!h || !dens) return LP_ERR_ARG;
   Plan& P = h->P;
   if (P.nb == 0) return LP_ERR_STATE;
-  if (!ensure_stage(P, round256(P.nb * sizeof(double)))) return LP_ERR_NOMEM;
+  if (!is_device_ptr(dens) && !ensure_stage(P, round256(P.nb * sizeof(double)))) return LP_ERR_NOMEM;
   size_t off = 0;
   const double* d = device_view(P, dens, P.nb, &off, P.stream);
   double* dst = kind == 0 ? P.d_sigma : P.d_mu;
@@ -836,69 +865,18 @@ static lp_status bind_layer(lp_plan_t h, const double* dens, int kind) {
 lp_status lp_single_layer(lp_plan_t h, const double* sigma) { return bind_layer(h, sigma, 0); }
 lp_status lp_double_layer(lp_plan_t h, const double* mu) { return bind_layer(h, mu, 1); }
 
-lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* jet, double* V,
-                     double* S, double* D) {
-  if (!h || nt < 0 || nt > (int64_t)INT32_MAX) return LP_ERR_ARG;
-  if (nt > 0 && !txy) return LP_ERR_ARG;
-  Plan& P = h->P;
-  const bool wv = V != nullptr, ws = S != nullptr, wd = D != nullptr;
-  if (wv && nt > 0 && !jet) return LP_ERR_ARG;
-  if ((wv && !P.have_volume) || (ws && !P.have_sigma) || (wd && !P.have_mu)) return LP_ERR_STATE;
-  if (nt == 0 || (!wv && !ws && !wd)) return LP_OK;
-  cudaStream_t s = P.stream;
-  // staging: targets, jet, and host outputs
-  size_t need = round256(nt * 2 * sizeof(double)) + round256(nt * 6 * sizeof(double));
-  if (!ensure_stage(P, need)) return LP_ERR_NOMEM;
-  double* outs[3] = {V, S, D};
-  bool host_out[3];
-  bool any_host = false;
-  for (int c = 0; c < 3; ++c) {
-    host_out[c] = outs[c] && !is_device_ptr(outs[c]);
-    any_host |= host_out[c];
-  }
-  if (any_host && (size_t)nt > P.out_cap) {
-    cudaStreamSynchronize(s);
-    dfree(P.d_out);
-    P.d_out = nullptr;
-    P.out_cap = 0;
-    if (!dalloc(P, (void**)&P.d_out, 3 * nt * sizeof(double))) return LP_ERR_NOMEM;
-    P.out_cap = nt;
-  }
-  if ((size_t)nt > P.near_cap) {
-    cudaStreamSynchronize(s);
-    dfree(P.d_near);
-    P.d_near = nullptr;
-    P.near_cap = 0;
-    if (!dalloc(P, (void**)&P.d_near, nt * sizeof(int2))) return LP_ERR_NOMEM;
-    P.near_cap = nt;
-  }
-  if (!P.d_near_count && !dalloc(P, (void**)&P.d_near_count, sizeof(int))) return LP_ERR_NOMEM;
-  record_stage(P, 0, s);
-  // Host targets and jets are copied on the plan's copy stream, overlapping
-  // the spreads and transforms; the staging buffer is free once the work
-  // already queued on the plan's stream has run, and the interpolation
-  // waits for the copies.
-  const bool host_in = !is_device_ptr(txy) || (wv && !is_device_ptr(jet));
-  cudaStream_t cs = s;
-  if (host_in) {
-    if (!P.copy_stream) {
-      if (cudaStreamCreateWithFlags(&P.copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
-          cudaEventCreateWithFlags(&P.ev_in, cudaEventDisableTiming) != cudaSuccess ||
-          cudaEventCreateWithFlags(&P.ev_staged, cudaEventDisableTiming) != cudaSuccess)
-        return LP_ERR_CUDA;
-    }
-    cudaEventRecord(P.ev_in, s);
-    cudaStreamWaitEvent(P.copy_stream, P.ev_in, 0);
-    cs = P.copy_stream;
-  }
-  size_t off = 0;
-  const double* dt = device_view(P, txy, nt * 2, &off, cs);
-  const double* dj = wv ? device_view(P, jet, nt * 6, &off, cs) : nullptr;
-  if (host_in) cudaEventRecord(P.ev_staged, cs);
-  double* dout[3];
-  for (int c = 0; c < 3; ++c) dout[c] = host_out[c] ? P.d_out + c * nt : outs[c];
-  record_stage(P, 1, s);
-
+// Steps 2-4 and the local part on device buffers (stage events 2 .. 8):
+// zero the grids of the requested channels, spread (volume nodes through the
+// bins, or point-parallel with global atomics; boundary nodes
+// point-parallel), transform with the multiplier (the library's FFT chain,
+// or cuFFT with the multiplier kernel), interpolate, then the local
+// correction and the refinement sums.  dt, dj, dout: device targets, jets
+// and outputs; list, count: the near-boundary list of the local pass (one
+// int2 per target) and its counter; staged: an event the interpolation waits
+// for (targets copied on another stream), or null.  Allocates nothing.
+static void device_pipeline(Plan& P, int64_t nt, const double* dt, const double* dj, double* const* dout,
+                            bool wv, bool ws, bool wd, int2* list, int* count, cudaEvent_t staged,
+                            cudaStream_t s) {
   // Steps 2-3: spread every requested channel onto both history grids:
   // volume nodes through the bins (FP32 plans) or point-parallel with global
   // atomics; boundary nodes point-parallel.
@@ -945,7 +923,7 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
   record_stage(P, 3, s);
   if (P.own_fft) {
     history_transforms(P, wv, ws, wd, s, true);
-    if (host_in) cudaStreamWaitEvent(s, P.ev_staged, 0);
+    if (staged) cudaStreamWaitEvent(s, staged, 0);
     history_interp(P, nt, dt, dout, s);
   } else {
     for (int l = P.l0; l < 2; ++l) {
@@ -966,14 +944,79 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
       if (wd) fft_inverse(P, l, 2);
     }
     record_stage(P, 6, s);
-    if (host_in) cudaStreamWaitEvent(s, P.ev_staged, 0);
+    if (staged) cudaStreamWaitEvent(s, staged, 0);
     launch_interp(P, nt, dt, dout[0], dout[1], dout[2], s);
   }
   record_stage(P, 7, s);
-  launch_local(P, nt, dt, dj, dout[0], dout[1], dout[2], s);
+  launch_local_list(P, nt, dt, dj, dout[0], dout[1], dout[2], list, count, s);
   record_stage(P, 11, s);
-  launch_dyadic(P, nt, dt, dout[1], dout[2], P.d_near, P.d_near_count, s);
+  launch_dyadic(P, nt, dt, dout[1], dout[2], list, count, s);
   record_stage(P, 8, s);
+}
+
+lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* jet, double* V,
+                     double* S, double* D) {
+  if (!h || nt < 0 || nt > (int64_t)INT32_MAX) return LP_ERR_ARG;
+  if (nt > 0 && !txy) return LP_ERR_ARG;
+  Plan& P = h->P;
+  const bool wv = V != nullptr, ws = S != nullptr, wd = D != nullptr;
+  if (wv && nt > 0 && !jet) return LP_ERR_ARG;
+  if ((wv && !P.have_volume) || (ws && !P.have_sigma) || (wd && !P.have_mu)) return LP_ERR_STATE;
+  if (nt == 0 || (!wv && !ws && !wd)) return LP_OK;
+  cudaStream_t s = P.stream;
+  // staging for the targets and jets that are in host memory
+  const size_t need = (is_device_ptr(txy) ? 0 : round256(nt * 2 * sizeof(double))) +
+                      (!wv || is_device_ptr(jet) ? 0 : round256(nt * 6 * sizeof(double)));
+  if (!ensure_stage(P, need)) return LP_ERR_NOMEM;
+  double* outs[3] = {V, S, D};
+  bool host_out[3];
+  bool any_host = false;
+  for (int c = 0; c < 3; ++c) {
+    host_out[c] = outs[c] && !is_device_ptr(outs[c]);
+    any_host |= host_out[c];
+  }
+  if (any_host && (size_t)nt > P.out_cap) {
+    cudaStreamSynchronize(s);
+    drelease(P, P.d_out, 3 * P.out_cap * sizeof(double));
+    P.out_cap = 0;
+    if (!dalloc(P, (void**)&P.d_out, 3 * nt * sizeof(double))) return LP_ERR_NOMEM;
+    P.out_cap = nt;
+  }
+  if ((size_t)nt > P.near_cap) {
+    cudaStreamSynchronize(s);
+    drelease(P, P.d_near, P.near_cap * sizeof(int2));
+    P.near_cap = 0;
+    if (!dalloc(P, (void**)&P.d_near, nt * sizeof(int2))) return LP_ERR_NOMEM;
+    P.near_cap = nt;
+  }
+  if (!P.d_near_count && !dalloc(P, (void**)&P.d_near_count, sizeof(int))) return LP_ERR_NOMEM;
+  record_stage(P, 0, s);
+  // Host targets and jets are copied on the plan's copy stream, overlapping
+  // the spreads and transforms; the staging buffer is free once the work
+  // already queued on the plan's stream has run, and the interpolation
+  // waits for the copies.
+  const bool host_in = !is_device_ptr(txy) || (wv && !is_device_ptr(jet));
+  cudaStream_t cs = s;
+  if (host_in) {
+    if (!P.copy_stream) {
+      if (cudaStreamCreateWithFlags(&P.copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&P.ev_in, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&P.ev_staged, cudaEventDisableTiming) != cudaSuccess)
+        return LP_ERR_CUDA;
+    }
+    cudaEventRecord(P.ev_in, s);
+    cudaStreamWaitEvent(P.copy_stream, P.ev_in, 0);
+    cs = P.copy_stream;
+  }
+  size_t off = 0;
+  const double* dt = device_view(P, txy, nt * 2, &off, cs);
+  const double* dj = wv ? device_view(P, jet, nt * 6, &off, cs) : nullptr;
+  if (host_in) cudaEventRecord(P.ev_staged, cs);
+  double* dout[3];
+  for (int c = 0; c < 3; ++c) dout[c] = host_out[c] ? P.d_out + c * nt : outs[c];
+  record_stage(P, 1, s);
+
+  device_pipeline(P, nt, dt, dj, dout, wv, ws, wd, P.d_near, P.d_near_count, host_in ? P.ev_staged : nullptr, s);
   for (int c = 0; c < 3; ++c)
     if (host_out[c]) cudaMemcpyAsync(outs[c], dout[c], nt * sizeof(double), cudaMemcpyDeviceToHost, s);
   record_stage(P, 9, s);
@@ -1069,71 +1112,23 @@ lp_status lp_execute_noalloc(lp_plan_t h, int64_t nt, const double* txy, const d
   const void* bufs[5] = {txy, wv ? jet : nullptr, V, S, D};
   for (const void* b : bufs)
     if (b && !is_device_ptr(b)) return LP_ERR_ARG;
+  // the scratch array is per device: only the plan's device may run it
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return LP_ERR_CUDA;
+  }
+  if (cur != P.device) return LP_ERR_ARG;
   void* scratch = nullptr;
-  lp_status st = noalloc_scratch(&scratch);
+  lp_status st = noalloc_scratch(P.device, &scratch);
   if (st != LP_OK) return st;
   int2* list = (int2*)scratch;
   int* count = (int*)((char*)scratch + kNoAllocListBytes);
   cudaStream_t s = P.stream;
   record_stage(P, 0, s);
   record_stage(P, 1, s);
-  for (int l = P.l0; l < 2; ++l) {
-    GridLevel& G = P.lv[l];
-    if (wv) cudaMemsetAsync(G.chan[0], 0, G.chan_bytes, s);
-    if (ws) cudaMemsetAsync(G.chan[1], 0, G.chan_bytes, s);
-    if (wd) {
-      cudaMemsetAsync(G.chan[2], 0, G.chan_bytes, s);
-      cudaMemsetAsync(G.chan[3], 0, G.chan_bytes, s);
-    }
-  }
-  record_stage(P, 2, s);
-  for (int l = P.l0; l < 2; ++l) {
-    GridLevel& G = P.lv[l];
-    if (wv && P.nv > 0) {
-      const double* q[1] = {P.d_vq};
-      void* g[1] = {G.chan[0]};
-      launch_spread(P, l, P.d_vxy, q, 1, g, P.nv, s);
-    }
-  }
-  record_stage(P, 10, s);
-  for (int l = P.l0; l < 2; ++l) {
-    GridLevel& G = P.lv[l];
-    const double* bq[3];
-    void* bg[3];
-    int nq = 0;
-    if (ws) {
-      bq[nq] = P.d_bq;
-      bg[nq++] = G.chan[1];
-    }
-    if (wd) {
-      bq[nq] = P.d_bq + P.nb;
-      bg[nq++] = G.chan[2];
-      bq[nq] = P.d_bq + 2 * P.nb;
-      bg[nq++] = G.chan[3];
-    }
-    if (nq) launch_spread(P, l, P.d_bxy, bq, nq, bg, P.nb, s);
-  }
-  record_stage(P, 3, s);
-  for (int l = P.l0; l < 2; ++l) {
-    const int chans[4] = {wv ? 0 : -1, ws ? 1 : -1, wd ? 2 : -1, wd ? 3 : -1};
-    for (int c : chans)
-      if (c >= 0) fft_forward(P, l, c);
-  }
-  record_stage(P, 4, s);
-  for (int l = P.l0; l < 2; ++l) launch_multiplier(P, l, wv, ws, wd, s);
-  record_stage(P, 5, s);
-  for (int l = P.l0; l < 2; ++l) {
-    const int chans[3] = {wv ? 0 : -1, ws ? 1 : -1, wd ? 2 : -1};
-    for (int c : chans)
-      if (c >= 0) fft_inverse(P, l, c);
-  }
-  record_stage(P, 6, s);
-  launch_interp(P, nt, txy, V, S, D, s);
-  record_stage(P, 7, s);
-  launch_local_list(P, nt, txy, wv ? jet : nullptr, V, S, D, list, count, s);
-  record_stage(P, 11, s);
-  launch_dyadic(P, nt, txy, S, D, list, count, s);
-  record_stage(P, 8, s);
+  double* dout[3] = {V, S, D};
+  device_pipeline(P, nt, txy, wv ? jet : nullptr, dout, wv, ws, wd, list, count, nullptr, s);
   record_stage(P, 9, s);
   return status_from_cuda();
 }
@@ -1148,7 +1143,27 @@ lp_status lp_sync(lp_plan_t h) {
   if (cudaGetLastError() != cudaSuccess) return LP_ERR_CUDA;
   if (st & kStatusOutOfBox) return LP_ERR_OUT_OF_BOX;
   if (st & kStatusExteriorBandV) return LP_ERR_UNSUPPORTED;
+  if (st & kStatusNewton) return LP_ERR_NEWTON;
   return LP_OK;
+}
+
+lp_status lp_sync_timeout(lp_plan_t h, double timeout_ms) {
+  if (!h || std::isnan(timeout_ms)) return LP_ERR_ARG;
+  if (timeout_ms < 0.0) return lp_sync(h);
+  Plan& P = h->P;
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaError_t e = cudaStreamQuery(P.stream);
+  while (e == cudaErrorNotReady) {  // bounded by timeout_ms of host time
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (ms >= timeout_ms) return LP_ERR_TIMEOUT;
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+    e = cudaStreamQuery(P.stream);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return LP_ERR_CUDA;
+  }
+  return lp_sync(h);
 }
 
 lp_status lp_destroy(lp_plan_t h) {

@@ -39,6 +39,7 @@ constexpr int kMaxFftStages = 24;   // radix stages of one df64 transform
 enum : unsigned {
   kStatusOutOfBox = 1u,
   kStatusExteriorBandV = 2u,
+  kStatusNewton = 4u,  // closest-point Newton did not converge (Sec. 2.2)
 };
 
 // Exponential-of-semicircle spreading kernel phi(z) = exp(beta (sqrt(1-z^2) - 1))
@@ -367,6 +368,7 @@ struct Plan {
 
   // bound sources
   int64_t nv = 0;
+  int64_t v_cap = 0;         // capacity of d_vxy / d_vq
   double* d_vxy = nullptr;   // [nv][2]
   double* d_vq = nullptr;    // [nv] f w
   bool have_volume = false;
@@ -408,6 +410,8 @@ struct Plan {
   long long graph_launches = 0;
   bool capturing = false;          // lp_execute is being captured into a graph
   size_t device_bytes = 0;
+  size_t max_bytes = 0;            // device-memory budget (0: none)
+  int device = 0;                  // CUDA device current at lp_plan
   mutable long long launches = 0;  // kernels launched by this plan (all calls)
 };
 

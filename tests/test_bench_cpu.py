@@ -12,34 +12,54 @@ def _info(precision):
 
 def test_fp64_roofline_spread_or_interp():
     st = {"spread": 1.2, "spread_volume": 1.0, "multiplier": 0.5, "interp": 0.8}
-    r = bench.roofline(_info(0), st, 1_000_000, 16384, 1_000_000, "fp64")
+    r = bench.roofline(_info(0), st, 1_000_000, 16384, 1_000_000, "fp64", workload="none")
     assert r["kernel"] == "spread_sub_dd_kernel" and r["bound"] == "alu"
-    ops = 1_000_000 * 2 * (2 * 12 * 12 + 12 * 13)
-    assert r["algorithmic_df64_fma_per_step"] == ops
-    assert abs(r["achieved"] - ops / 1.0e-3 / 1e12) < 1e-3
+    # no ncu count for workload "none": the algorithmic estimate, 15 FP32
+    # instructions per df64 multiply-add, 32 lanes per warp instruction
+    inst = 1_000_000 * 2 * (2 * 12 * 12 + 12 * 13) * 15 / 32
+    assert r["instructions_per_step"] == int(inst) and r["instructions_source"].startswith("estimate")
+    assert abs(r["achieved"] - inst / 1.0e-3 / 1e12) < 1e-3
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-3
+    assert abs(r["peak"] - 152 * 4 * bench.sm_max_mhz() * 1e6 / 1e12) < 1e-3
+    # HBM fraction beside it: positions and strengths (24 B per node) and
+    # both grids written once (8 B per cell)
+    byts = 1_000_000 * 24 + (2592 ** 2 + 1024 ** 2) * 8
+    assert r["hbm"]["algorithmic_bytes_per_step"] == byts
+    assert abs(r["hbm_frac"] - byts / 1e-3 / 1e9 / r["hbm"]["peak"]) < 1e-4
     st["interp"] = 1.5
-    assert bench.roofline(_info(0), st, 1_000_000, 16384, 1_000_000, "fp64")["kernel"] == "interp_dd_kernel"
+    r = bench.roofline(_info(0), st, 1_000_000, 16384, 1_000_000, "fp64", workload="none")
+    assert r["kernel"] == "interp_dd_kernel"
+    assert r["hbm"]["algorithmic_bytes_per_step"] == (2592 ** 2 + 1024 ** 2) * 8 * 3 + 1_000_000 * (16 + 24)
 
 
 def test_fp32_roofline_dominant_stage():
     st = {"spread": 0.3, "spread_volume": 0.25, "multiplier": 0.28, "interp": 0.2}
-    r = bench.roofline(_info(1), st, 1_000_000, 16384, 1_000_000, "fp32")
+    r = bench.roofline(_info(1), st, 1_000_000, 16384, 1_000_000, "fp32", workload="none")
     assert r["kernel"] == "fft_cols_kernel" and r["bound"] == "hbm"
     kp = lambda K: (K + 2) & ~1
     byts = 7 * 2916 * kp(729) * 8 + 7 * 1152 * kp(288) * 8
-    assert r["algorithmic_bytes_per_step"] == byts
+    assert r["hbm"]["algorithmic_bytes_per_step"] == byts and r["frac"] == r["hbm_frac"]
     st["multiplier"] = 0.1
-    r = bench.roofline(_info(1), st, 1_000_000, 16384, 1_000_000, "fp32")
+    r = bench.roofline(_info(1), st, 1_000_000, 16384, 1_000_000, "fp32", workload="none")
     assert r["kernel"] == "spread_sub_kernel" and r["bound"] == "alu"
-    assert r["algorithmic_fma_per_step"] == 1_000_000 * 2 * (49 + 2 * 7 * 8)
+    assert r["instructions_per_step"] == int(1_000_000 * 2 * (49 + 2 * 7 * 8) / 32)
 
 
 def test_single_level_plans_count_one_level():
     info = dict(_info(0), g_nh=0, K_nh=0)
     st = {"spread": 1.0, "spread_volume": 1.0, "multiplier": 0.5, "interp": 0.2}
-    r = bench.roofline(info, st, 1000, 0, 1000, "fp64")
-    assert r["algorithmic_df64_fma_per_step"] == 1000 * 1 * (2 * 12 * 12 + 12 * 13)
+    r = bench.roofline(info, st, 1000, 0, 1000, "fp64", workload="none")
+    assert r["instructions_per_step"] == int(1000 * 1 * (2 * 12 * 12 + 12 * 13) * 15 / 32)
+    assert r["hbm"]["algorithmic_bytes_per_step"] == 1000 * 24 + 1024 ** 2 * 8
+
+
+def test_parity_block():
+    import numpy as np
+    gpu = {"V": np.array([1.0, 2.0, 3.0, 4.0]), "S": np.array([1.0, 1.0, 1.0, 1.0])}
+    ref = {"V": np.array([2.0, 3.0]), "S": np.array([1.0, 2.0]), "D": np.array([0.5, 0.5])}
+    p = bench.parity(gpu, ref, np.array([1, 2]))
+    assert set(p) == {"V", "S"} and p["V"]["rel_l2"] == 0.0 and p["V"]["n_targets"] == 2
+    assert abs(p["S"]["rel_max"] - 0.5) < 1e-15
 
 
 def test_reference_arm_line_contract():

@@ -43,8 +43,9 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_status_strings(lib):
     L = lib.library()
-    for code in range(7):
+    for code in range(9):
         assert len(L.lp_status_string(code)) > 0
+        assert L.lp_status_string(code) != b"unknown status"
     assert L.lp_status_string(99) == b"unknown status"
 
 
@@ -85,6 +86,10 @@ def test_invalid_arguments_rejected_without_device(lib):
     dom.upsampling = 0.0
     for fn in (L.lp_sync, L.lp_destroy):
         assert fn(None) == 1
+    assert L.lp_sync_timeout(None, 1.0) == 1
+    dom.max_device_bytes = -1
+    assert L.lp_plan(ctypes.byref(dom), 1e-3, 1e-9, ctypes.byref(h)) == 1
+    dom.max_device_bytes = 0
     assert L.lp_volume(None, 0, None, None, None) == 1
     assert L.lp_execute(None, 0, None, None, None, None, None) == 1
     assert L.lp_execute_graph(None, 0, None, None, None, None, None) == 1
