@@ -248,10 +248,8 @@ def run_lp(args, rank, world, local_rank):
             res["fp32_same_workload"] = run_fp32(args, prob, dev, stream, points)
             gpu_out["fp32"] = res["fp32_same_workload"].pop("_outputs")
         if args.workload == "starfish":
-            from workloads import configs as _cfg
-            small_pool = _cfg.serving_pool(n_meshes=6, t_min=10_000, t_max=300_000, seed=5300)
-            res["served"] = run_serve(args, rank, world, local_rank, pool=small_pool, rates=(100, 400),
-                                      seconds=3.0)
+            res["served"] = run_serve(args, rank, world, local_rank, rates=(50, 200, 1000), seconds=1.5,
+                                      max_requests=1200)
         if world == 1:
             res["cpu_baseline"] = cpu_baseline(prob, budget_s=15.0, refine_levels=args.refine_levels,
                                                gpu_out=gpu_out)
@@ -690,10 +688,15 @@ def run_solve(args, rank, world, local_rank):
 
 
 # ---------------------------------------------------------------- serving a request stream
-def run_serve(args, rank, world, local_rank, pool=None, rates=(25, 50, 100, 200), seconds=None):
-    """Poisson arrivals of V+S+D requests over a resident mesh pool (10k..5M
-    triangles on the disk, starfish and square domains), FP32 at 1e-5 with
-    continuous batching, against one request at a time in FP64."""
+def run_serve(args, rank, world, local_rank, pool=None, rates=(50, 100, 200, 500, 1000, 2000), seconds=None,
+              max_requests=1500):
+    """Poisson arrivals of V+S+D requests over a resident mesh pool (12
+    meshes, 10k..5M triangles log-uniform on the disk, starfish and square
+    domains), FP32 at 1e-5 with continuous batching, against one request at a
+    time in FP64 at 1e-9.  Each rate sends arrivals for `seconds` or until
+    `max_requests` have arrived, whichever is first, and every request is
+    served to completion (latency includes queueing once the server
+    saturates)."""
     import torch
     from paper_2409_11998_gb300 import serve
     from workloads import configs
@@ -712,13 +715,15 @@ def run_serve(args, rank, world, local_rank, pool=None, rates=(25, 50, 100, 200)
     srv.run(serve.poisson_arrivals(20, 1.0, len(pool), seed=1))   # warm-up
     one.run(serve.poisson_arrivals(5, 1.0, len(pool), seed=2))
     for lam in rates:
-        arr = serve.poisson_arrivals(lam, seconds, len(pool), seed=int(lam))
+        arr = serve.poisson_arrivals(lam, min(seconds, max_requests / lam), len(pool), seed=int(lam))
         a = serve.latency_stats(srv.run(arr))
         b = serve.latency_stats(one.run(arr))
         out["rates"][str(lam)] = {"batched_fp32": a, "one_at_a_time_fp64": b}
     out["resident_bytes"] = srv.resident
     out["plans_created"] = srv.created
+    out["plans_created_while_serving"] = srv.created_in_loop
     out["plans_evicted"] = srv.evicted
+    out["arrival_window_s"] = {str(lam): round(min(seconds, max_requests / lam), 3) for lam in rates}
     srv.close()
     one.close()
     return out

@@ -58,7 +58,8 @@ typedef struct lp_batch_s* lp_batch_t;
 typedef enum {
   LP_OK = 0,
   LP_ERR_ARG = 1,            /* invalid argument; nothing was launched */
-  LP_ERR_OUT_OF_BOX = 2,     /* a source or target lies outside the plan's box */
+  LP_ERR_OUT_OF_BOX = 2,     /* a source or target lies outside the plan's box, or a
+                                coordinate or source strength is not finite */
   LP_ERR_NOMEM = 3,          /* device allocation failed */
   LP_ERR_CUDA = 4,           /* a CUDA runtime or cuFFT call failed */
   LP_ERR_UNSUPPORTED = 5,    /* V requested at an exterior target within 12 sqrt(delta_1)
@@ -68,7 +69,10 @@ typedef enum {
   LP_ERR_NEWTON = 7,         /* the closest-point search (Sec. 2.2: nearest node, then
                                 Newton on the panel polynomial) failed for some target of
                                 the local band: 20 double-precision Newton steps ended with
-                                a step of 1e-6 or more in the panel parameter, the foot ran
+                                a Newton step of 1e-6 or more in the panel parameter (the
+                                slow gradient steps taken where the distance is flat along
+                                the boundary, near a centre of curvature, do not count),
+                                the foot ran
                                 past the far end of the adjacent panel as well, or the foot
                                 lies where the panel's speed |gamma'| is below 1e-9 of the
                                 box side, so that the tangent frame of Sec. 4 is undefined
@@ -88,6 +92,10 @@ enum { LP_FP64 = 0, LP_FP32 = 1 };
  * LP_SINGLE_LEVEL_MAX_GRID points per side), else two. */
 #define LP_LEVELS_AUTO (-1)
 #define LP_SINGLE_LEVEL_MAX_GRID 1536
+
+/* lp_domain.autotune */
+#define LP_AUTOTUNE_BINS 1
+#define LP_AUTOTUNE_FULL 2
 
 typedef struct {
   int precision;        /* LP_FP64: tolerances down to ~1e-12.  The volume spread,
@@ -131,11 +139,23 @@ typedef struct {
                            default (FP64 1.5, FP32 2), else 1.25 .. 3; the
                            kernel width follows from tol and sigma (LP_ERR_ARG
                            when it would exceed 16) */
-  int autotune;         /* nonzero: the first lp_volume that binds sources
-                           times the binned volume spread for three bin sides
-                           (FP64 16/24/32, FP32 16/32/48 near-history cells)
-                           on those sources and keeps the fastest (it
-                           synchronises the plan's stream once) */
+  int autotune;         /* LP_AUTOTUNE_BINS: the first lp_volume that binds
+                           sources times the binned volume spread for three
+                           bin sides (FP64 16/24/32, FP32 16/32/48
+                           near-history cells) on those sources and keeps the
+                           fastest (it synchronises the plan's stream once).
+                           LP_AUTOTUNE_FULL: before that, the same lp_volume
+                           builds a plan for each upsampling sigma in {1.25,
+                           1.5, 2} with one and with two history levels (the
+                           trade-off of Sec. 3's one-level remark), each with
+                           the kernel width its sigma needs for tol, binds the
+                           sources and unit layer densities, times one V, S, D
+                           evaluation at the sources (median of three), and
+                           keeps the fastest in place of the plan's grids --
+                           the upsampling and levels fields are then only the
+                           starting point.  Every configuration meets tol, so
+                           the choice changes speed, not accuracy beyond
+                           rounding.  0: no tuning. */
   int64_t max_device_bytes; /* device-memory budget of the plan (0: none): an
                            allocation that would take the plan's device
                            footprint (lp_plan_info's device bytes) beyond it
@@ -187,17 +207,19 @@ lp_status lp_execute(lp_plan_t plan, int64_t n_t, const double* t_xy, const doub
  * not take the implicit device synchronisation cudaMalloc/cudaFree can
  * cause, or hosts where allocation after start-up is forbidden.  Such a
  * caller creates the plan and binds sources and densities during set-up;
- * this call then evaluates exactly what lp_execute evaluates, but it stages
- * nothing (every pointer must be device memory, else LP_ERR_ARG) and keeps
- * its per-call scratch -- the list of targets near the boundary -- in a
- * static device array sized for at most 2,097,152 targets (16 MiB, held by
- * every GPU that loads the library until the process exits); larger n_t is
- * rejected with LP_ERR_ARG before anything is launched.  The first call on
- * each device looks up that array's device address (with the device
- * current), so make the first call on a device before any stream capture.
- * All calls share the one array: calls whose work overlaps on the GPU (two
- * plans on different streams, say) race, so serialise them.  No cudaMalloc,
- * cudaFree or allocating library routine is called. */
+ * this call then runs the same kernels as lp_execute on the same data, but
+ * it stages nothing (every pointer must be device memory, else LP_ERR_ARG)
+ * and keeps its per-call scratch -- the list of targets near the boundary
+ * -- in a static device array sized for at most 2,097,152 targets (16 MiB,
+ * held by every GPU that loads the library until the process exits); larger
+ * n_t is rejected with LP_ERR_ARG before anything is launched.  The call
+ * must be made with the plan's device current (LP_ERR_ARG otherwise: the
+ * array is per device).  The first call on each device looks up that array's
+ * device address (with the device current), so make the first call on a
+ * device before any stream capture.  All calls share the one array: calls
+ * whose work overlaps on the GPU (two plans on different streams, say) race,
+ * so serialise them.  No cudaMalloc, cudaFree or allocating library routine
+ * is called. */
 lp_status lp_execute_noalloc(lp_plan_t plan, int64_t n_t, const double* t_xy, const double* f_jet,
                              double* V, double* S, double* D);
 
@@ -314,11 +336,14 @@ const char* lp_status_string(lp_status status);
  *               1 if volume sources are spread through bins, bin side in
  *               near-history cells, dyadic refinement levels, largest error
  *               of the refinement's kernel tables, refinement subnodes,
- *               history levels in use (2 or 1), upsampling sigma, and the
+ *               history levels in use (2 or 1), upsampling sigma, the
  *               autotuner's spread times in ms of its three bin sides
- *               (0 if it has not run, -1 for a side that does not fit)}; the
+ *               (0 if it has not run, -1 for a side that does not fit), and
+ *               the grid autotuner's evaluation times in ms of sigma 1.25,
+ *               1.5, 2 with one and two levels, in that order (0 if it has
+ *               not run, -1 for a configuration it could not build)}; the
  *               near-history entries are 0 for single-level plans.
- *               out must hold 31 doubles. */
+ *               out must hold 37 doubles. */
 lp_status lp_plan_info(lp_plan_t plan, double* out);
 
 /* Per-stage device times of the last lp_execute in milliseconds (CUDA events

@@ -134,7 +134,8 @@ def lp_plan(box_lo, box_hi, delta, tol, *, precision=LP_FP64, order=5, n_panels=
     dom.refine_levels = LP_REFINE_AUTO if refine_levels == "auto" else int(refine_levels)
     dom.levels = LP_LEVELS_AUTO if levels == "auto" else int(levels)
     dom.upsampling = float(upsampling)
-    dom.autotune = 1 if autotune else 0
+    dom.autotune = {False: 0, True: 1, "bins": 1, "full": 2}[autotune] if not isinstance(autotune, int) or \
+        isinstance(autotune, bool) else int(autotune)
     dom.max_device_bytes = int(max_device_bytes)
     h = ctypes.c_void_p()
     _check(_lib().lp_plan(ctypes.byref(dom), float(delta), float(tol), ctypes.byref(h)), "lp_plan")
@@ -250,12 +251,14 @@ def lp_destroy(plan):
 
 
 def lp_plan_info(plan):
-    out = np.zeros(31)
+    out = np.zeros(37)
     _check(_lib().lp_plan_info(plan, out.ctypes.data), "lp_plan_info")
     keys = ["delta1", "delta2", "w", "beta", "g_nh", "K_nh", "P_nh", "g_fh", "K_fh", "P_fh", "L_fh",
             "band", "margin", "device_bytes", "precision", "order", "launches", "es_fit_err", "es_nc",
             "sigma_eff", "own_fft", "binned", "bin_cells", "refine_levels", "refine_table_err",
-            "refine_subnodes", "levels", "sigma", "tune_ms_0", "tune_ms_1", "tune_ms_2"]
+            "refine_subnodes", "levels", "sigma", "tune_ms_0", "tune_ms_1", "tune_ms_2",
+            "grid_ms_s125_l1", "grid_ms_s125_l2", "grid_ms_s15_l1", "grid_ms_s15_l2", "grid_ms_s2_l1",
+            "grid_ms_s2_l2"]
     return dict(zip(keys, out.tolist()))
 
 

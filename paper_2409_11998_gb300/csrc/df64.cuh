@@ -138,25 +138,45 @@ __device__ __forceinline__ dd dd_horner(dd acc, dd v, float2 c) {
 // The kernel is even, so offset w-1-t at v is offset t at -v: with
 // P_t(v) = E_t(v^2) + v O_t(v^2), weights t and w-1-t are E_t +- v O_t, and
 // only the first ceil(w/2) polynomials are evaluated, in v^2 (half the
-// Horner steps of evaluating all w).
+// Horner steps of evaluating all w).  The first nf Horner steps of each
+// chain, whose rounding the remaining steps damp by powers of v^2 <= 1/4,
+// run in single precision on the coefficients' high parts (the plan chooses
+// nf so that this adds at most 5% of the fit's error target).
 template <int W>
-__device__ __forceinline__ void dd_stencil_weights(const float2* coef, int stride, int nc, dd v, dd* w) {
+__device__ __forceinline__ void dd_stencil_weights(const float2* coef, int stride, int nc, int nf, dd v, dd* w) {
   constexpr int WH = (W + 1) / 2;
   const dd v2 = dd_mul(v, v);
   const int ke = (nc - 1) & ~1, ko = (nc - 2) | 1;  // highest even / odd power present
   dd e[WH], o[WH];
+  float ef[WH], of[WH];
 #pragma unroll
   for (int t = 0; t < WH; ++t) {
-    e[t] = dd{coef[ke * stride + t].x, coef[ke * stride + t].y};
-    o[t] = dd{coef[ko * stride + t].x, coef[ko * stride + t].y};
+    ef[t] = coef[ke * stride + t].x;
+    of[t] = coef[ko * stride + t].x;
   }
-  for (int k = ke - 2; k >= 0; k -= 2) {
+  int k = ke - 2;
+  for (int s = 0; s < nf && k >= 0; ++s, k -= 2) {
+#pragma unroll
+    for (int t = 0; t < WH; ++t) ef[t] = __fmaf_rn(ef[t], v2.hi, coef[k * stride + t].x);
+  }
+  int ko2 = ko - 2;
+  for (int s = 0; s < nf && ko2 >= 1; ++s, ko2 -= 2) {
+#pragma unroll
+    for (int t = 0; t < WH; ++t) of[t] = __fmaf_rn(of[t], v2.hi, coef[ko2 * stride + t].x);
+  }
+#pragma unroll
+  for (int t = 0; t < WH; ++t) {
+    // no float steps: the leading coefficient keeps its low part
+    e[t] = dd{ef[t], nf ? 0.f : coef[ke * stride + t].y};
+    o[t] = dd{of[t], nf ? 0.f : coef[ko * stride + t].y};
+  }
+  for (; k >= 0; k -= 2) {
 #pragma unroll
     for (int t = 0; t < WH; ++t) e[t] = dd_horner(e[t], v2, coef[k * stride + t]);
   }
-  for (int k = ko - 2; k >= 1; k -= 2) {
+  for (; ko2 >= 1; ko2 -= 2) {
 #pragma unroll
-    for (int t = 0; t < WH; ++t) o[t] = dd_horner(o[t], v2, coef[k * stride + t]);
+    for (int t = 0; t < WH; ++t) o[t] = dd_horner(o[t], v2, coef[ko2 * stride + t]);
   }
 #pragma unroll
   for (int t = 0; t < WH; ++t) {

@@ -226,34 +226,81 @@ __device__ __forceinline__ bool stencil_dd(dd u, int M, int& i0, dd& v) {
   return i0 >= 0 && i0 + W <= M;
 }
 
-// Binned spread of the volume nodes of FP64 plans, in df64.  As the
-// single-precision kernel (one CTA per bin, warp-private patches, one warp
-// per point when updating cells), except that the stencil weights are
-// evaluated with lane = point first -- each lane runs the 2w df64 Horner
-// chains of its own point, x weights and q times y weights, into shared
-// memory -- and that patch cells hold df64 sums.  The CTA adds its patch to
-// the FP64 grid with FP64 atomics.
-template <int W, int NW>
-__global__ void __launch_bounds__(NW * 32) spread_sub_dd_kernel(const __grid_constant__ SubDDArgs a) {
+// Binned spread of the volume nodes of FP64 plans, in fixed point.  One
+// CTA per bin and one shared patch per CTA: every patch cell holds two
+// 32-bit integer accumulators, a coarse count of quanta e1 and a fine count
+// of quanta e2 = e1 / 2^s2, both chosen from the bin's largest strength and
+// node count so that neither can overflow.  A contribution p = q wy wx
+// (df64 product: high part ph plus error pe) is rounded to the coarse grid
+// by one addition of a magic constant -- exact, since ph < 2^22 e1 -- the
+// exact remainder plus pe to the fine grid the same way, and both counts
+// are added with shared-memory integer atomics.  Integer sums are exact and
+// independent of order, so the warps of the CTA share one patch; the
+// result carries about 2^-44 of the bin's largest strength per
+// contribution, below the df64 rounding of the transforms.
+//   Phase 1 (per chunk of up to NT nodes): the CTA evaluates the 2w
+//   df64 weight polynomials as (node, axis) tasks, one per thread, and stores
+//   x weights and q times y weights with the stencil origins.
+//   Phase 2: each warp takes one node at a time, its lanes the w^2 cells.
+//   Flush: each cell's counts become one double (integer normalisation, no
+//   FP64 arithmetic) added to the grid with an FP64 atomic.
+template <int W, int NT>
+__global__ void __launch_bounds__(NT, 4) spread_fx_kernel(const __grid_constant__ SubDDArgs a) {
   extern __shared__ float2 smd[];
-  constexpr int NC = W * W, NP = (NC + 31) / 32, NWARP = NW;
-  constexpr int WS = 2 * W + 1;  // weight row stride (odd: conflict-free lane = point stores)
+  constexpr int NC = W * W, NP = (NC + 31) / 32, NWARP = NT / 32, CH = NT;
+  constexpr int WS = 2 * W + 1;  // weight row stride (odd: conflict-free task stores)
   const int M = a.M, MM = M * M, nc = a.nc;
   const int bx = blockIdx.x, by = blockIdx.y;
   const int key = by * a.nbx + bx;
   const int k0 = a.start[key], n_here = a.start[key + 1] - k0;
   if (n_here == 0) return;
-  float2* coef = smd;                          // [nc][W]
-  float2* wbuf = coef + kMaxNC * W;            // [NWARP][32][WS]
-  float2* patch = wbuf + NWARP * 32 * WS;      // [NWARP][MM] (sum, correction)
-  for (int e = threadIdx.x; e < nc * W; e += blockDim.x) coef[e] = a.coef[e / W][e % W];
-  for (int e = threadIdx.x; e < NWARP * MM; e += blockDim.x) patch[e] = make_float2(0.f, 0.f);
+  float2* coef = smd;                        // [nc][W]
+  float2* wbuf = coef + kMaxNC * W;          // [CH][WS]: x weights, then q * y weights
+  int* wpos = (int*)(wbuf + CH * WS);        // [CH][2] stencil origins (-1: outside the patch)
+  int* pc = wpos + 2 * CH;                   // [MM] coarse counts
+  int* pf = pc + MM;                         // [MM] fine counts
+  __shared__ float red_q[NWARP];
+  for (int e = threadIdx.x; e < nc * W; e += NT) coef[e] = a.coef[e / W][e % W];
+  for (int e = threadIdx.x; e < 2 * MM; e += NT) pc[e] = 0;
+  // largest |q| of the bin (high parts; the quanta only need its binade);
+  // a non-finite strength is reported and the bin skipped
+  float qmax = 0.f;
+  bool bad_q = false;
+  for (int k = threadIdx.x; k < n_here; k += NT) {
+    const float qx = fabsf(a.q[k0 + k].x);
+    bad_q |= !(qx <= 3.4e38f);
+    qmax = fmaxf(qmax, qx);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) qmax = fmaxf(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red_q[warp] = qmax;
+  if (__syncthreads_or(bad_q)) {
+    if (threadIdx.x == 0) atomicOr(a.status, kStatusOutOfBox);
+    return;
+  }
+  qmax = red_q[0];
+#pragma unroll
+  for (int w = 1; w < NWARP; ++w) qmax = fmaxf(qmax, red_q[w]);
+  if (qmax == 0.f) return;
+  // strengths scaled by 2^-eq (exact) so that the largest lies in [1/2, 1);
+  // quanta: e1 = 2^E1 with every |ph| < 1 <= 2^(E1 + 21) and, for bins of
+  // more than 512 nodes, 2^xs coarser so that the coarse counts stay below
+  // 2^31; e2 = e1 / 2^(22 - xs) with the same bound for the fine counts
+  int xs = 0;
+  while ((512 << xs) < n_here && xs < 20) ++xs;
+  int eq;
+  frexpf(qmax * 1.000001f, &eq);             // qmax * (1 + 1e-6) < 2^eq
+  eq = max(eq, -126);                        // a finite scale for subnormal strengths
+  const float qscale = ldexpf(1.f, -eq);
+  const int E1 = -21 + xs, E2 = E1 - 22 + xs;
+  const float M1 = ldexpf(1.5f, E1 + 23), M2 = ldexpf(1.5f, E2 + 23);
+  const int M1b = __float_as_int(M1), M2b = __float_as_int(M2);
   const double ux = (a.org_x + bx * a.bt - a.gd.x0) * a.gd.inv_h;
   const double uy = (a.org_y + by * a.bt - a.gd.y0) * a.gd.inv_h;
   const int ox = (int)floor(ux - 0.5 * W), oy = (int)floor(uy - 0.5 * W);
-  const dd u0 = dd_from_double(ux - ox), v0 = dd_from_double(uy - oy);
+  const dd u0[2] = {dd_from_double(ux - ox), dd_from_double(uy - oy)};
   const dd inv_h = dd{a.inv_h.x, a.inv_h.y};
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int cell[NP], wxo[NP], wyo[NP];
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
@@ -263,92 +310,83 @@ __global__ void __launch_bounds__(NW * 32) spread_sub_dd_kernel(const __grid_con
     wxo[p] = c;
     wyo[p] = W + (r < W ? r : 0);
   }
-  float2* wb = wbuf + warp * 32 * WS;
-  float2* mine = patch + warp * MM;
   __syncthreads();
-  const int n_warp = n_here > warp ? (n_here - warp + NWARP - 1) / NWARP : 0;
-  for (int j0 = 0; j0 < n_warp; j0 += 32) {
-    // weights, lane = point
-    const int jl = j0 + lane;
-    int ix = 0, iy = 0;
-    bool ok = false;
-    if (jl < n_warp) {
-      const int kk = k0 + warp + NWARP * jl;
+  for (int c0 = 0; c0 < n_here; c0 += CH) {
+    const int nch = min(CH, n_here - c0);
+    // phase 1: task t = (node t / 2, axis t % 2)
+    for (int t = threadIdx.x; t < 2 * nch; t += NT) {
+      const int j = t >> 1, ax = t & 1;
+      const int kk = k0 + c0 + j;
       const float4 r = a.rel[kk];
-      const float2 q = a.q[kk];
-      const dd u = dd_add(u0, dd_mul(dd{r.x, r.y}, inv_h));
-      const dd v = dd_add(v0, dd_mul(dd{r.z, r.w}, inv_h));
-      dd vx, vy;
-      ok = stencil_dd<W>(u, M, ix, vx) && stencil_dd<W>(v, M, iy, vy);
-      if (ok) {
-        float2* out = wb + lane * WS;
+      const dd off = ax ? dd{r.z, r.w} : dd{r.x, r.y};
+      const dd u = dd_add(u0[ax], dd_mul(off, inv_h));
+      int i0;
+      dd v;
+      if (stencil_dd<W>(u, M, i0, v)) {
         dd w[W];
-        dd_stencil_weights<W>(coef, W, nc, vx, w);
+        dd_stencil_weights<W>(coef, W, nc, a.nf, v, w);
+        float2* out = wbuf + j * WS + ax * W;
+        if (ax) {
+          const float2 q = a.q[kk];
+          const dd qd = dd{q.x * qscale, q.y * qscale};
 #pragma unroll
-        for (int t = 0; t < W; ++t) out[t] = make_float2(w[t].hi, w[t].lo);
-        dd_stencil_weights<W>(coef, W, nc, vy, w);
-        const dd qd = dd{q.x, q.y};
+          for (int s = 0; s < W; ++s) {
+            const dd qw = dd_mul(w[s], qd);
+            out[s] = make_float2(qw.hi, qw.lo);
+          }
+        } else {
 #pragma unroll
-        for (int t = 0; t < W; ++t) {
-          const dd qw = dd_mul(w[t], qd);
-          out[W + t] = make_float2(qw.hi, qw.lo);
+          for (int s = 0; s < W; ++s) out[s] = make_float2(w[s].hi, w[s].lo);
         }
+        wpos[2 * j + ax] = i0;
       } else {
+        wpos[2 * j + ax] = -1;
         atomicOr(a.status, kStatusOutOfBox);
       }
     }
-    __syncwarp();
-    // cells, one point at a time
-    const int cnt = min(32, n_warp - j0);
-    for (int jj = 0; jj < cnt; ++jj) {
-      if (!__shfl_sync(0xffffffffu, (int)ok, jj)) continue;
-      const int pix = __shfl_sync(0xffffffffu, ix, jj), piy = __shfl_sync(0xffffffffu, iy, jj);
-      float2* dst = mine + piy * M + pix;
-      const float2* wrow = wb + jj * WS;
-      // the lane's cells are distinct: load them all, update, store them all
-      // (keeps the shared-memory loads from waiting on earlier stores)
-      float2 cur[NP];
-#pragma unroll
-      for (int p = 0; p < NP; ++p)
-        if (cell[p] >= 0) cur[p] = dst[cell[p]];
+    __syncthreads();
+    // phase 2: warp per node, lanes over cells
+    for (int j = warp; j < nch; j += NWARP) {
+      const int ix = wpos[2 * j], iy = wpos[2 * j + 1];
+      if (ix < 0 || iy < 0) continue;
+      const int base = iy * M + ix;
+      const float2* wrow = wbuf + j * WS;
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
         if (cell[p] < 0) continue;
-        // cur += qwy * wx: the product's high part joins the sum through
-        // two-sum, its error terms and the sum's rounding go to the
-        // correction word (renormalised once, at the flush)
         const float2 wx = wrow[wxo[p]], qwy = wrow[wyo[p]];
         const float ph = __fmul_rn(qwy.x, wx.x);
         float pe = __fmaf_rn(qwy.x, wx.x, -ph);
         pe = __fmaf_rn(qwy.x, wx.y, pe);
         pe = __fmaf_rn(qwy.y, wx.x, pe);
-        float s, t;
-        two_sum(cur[p].x, ph, s, t);
-        cur[p].y = __fadd_rn(cur[p].y, __fadd_rn(t, pe));
-        cur[p].x = s;
+        const float t1 = __fadd_rn(ph, M1);                        // ph rounded to a multiple of e1
+        const float rem = __fsub_rn(ph, __fsub_rn(t1, M1));        // exact remainder
+        const float t2 = __fadd_rn(__fadd_rn(rem, pe), M2);        // remainder + error, multiple of e2
+        atomicAdd(pc + base + cell[p], __float_as_int(t1) - M1b);
+        atomicAdd(pf + base + cell[p], __float_as_int(t2) - M2b);
       }
-#pragma unroll
-      for (int p = 0; p < NP; ++p)
-        if (cell[p] >= 0) dst[cell[p]] = cur[p];
-      __syncwarp();
     }
+    __syncthreads();
   }
-  __syncthreads();
+  // flush: value = (coarse * 2^(E1 - E2) + fine) * 2^E2, an integer below
+  // 2^53 times a power of two, assembled as a double by integer operations
   double* grid = (double*)a.grid;
-  for (int e = threadIdx.x; e < MM; e += blockDim.x) {
-    dd acc = dd{0.f, 0.f};
-#pragma unroll
-    for (int w = 0; w < NWARP; ++w) {
-      const float2 pv = patch[w * MM + e];
-      acc = dd_add(acc, dd_add(dd{pv.x, 0.f}, dd{pv.y, 0.f}));
-    }
-    if (acc.hi == 0.f) continue;
+  const int sh = E1 - E2;
+  for (int e = threadIdx.x; e < MM; e += NT) {
+    const long long n = ((long long)pc[e] << sh) + (long long)pf[e];
+    if (n == 0) continue;
     const int gy = oy + e / M, gx = ox + e % M;
     if (gx < 0 || gy < 0 || gx >= a.gd.g || gy >= a.gd.g) {
       atomicOr(a.status, kStatusOutOfBox);
       continue;
     }
-    atomicAdd(grid + (size_t)gy * a.gd.pitch + gx, dd_to_double(acc));
+    const unsigned long long sign = n < 0 ? (1ull << 63) : 0ull;
+    const unsigned long long m = (unsigned long long)(n < 0 ? -n : n);
+    const int lz = __clzll(m);                                     // >= 11
+    const unsigned long long frac = ((m << lz) >> 11) & 0xfffffffffffffull;
+    const long long ex = (long long)(63 - lz + E2 + eq + 1023);
+    const double v = __longlong_as_double((long long)(sign | ((unsigned long long)ex << 52) | frac));
+    atomicAdd(grid + (size_t)gy * a.gd.pitch + gx, v);
   }
 }
 
@@ -384,40 +422,25 @@ void launch_gather_q_dd(const double* q, const int* perm, int64_t n, float2* q_s
   if (n > 0) gather_q_dd_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(q, perm, n, q_s);
 }
 
-static size_t sub_dd_smem_nw(int M, int w, int nw) {
-  return (size_t)(kMaxNC * w + nw * 32 * (2 * w + 1) + nw * M * M) * sizeof(float2);
+// Shared memory of the fixed-point spread: coefficient table, one chunk of
+// weight rows and stencil origins, and the two count arrays of the patch.
+static size_t spread_fx_smem_nt(int M, int w, int nt) {
+  return (size_t)(kMaxNC * w + nt * (2 * w + 1)) * sizeof(float2) + (size_t)2 * nt * sizeof(int) +
+         (size_t)2 * M * M * sizeof(int);
 }
 
-// Warps per CTA of the binned df64 spread: 4 or 5, whichever keeps more
-// warps resident per SM (228 KB of shared memory, 1 KB reserved per CTA);
-// each warp carries an M x M df64 patch and 32 weight rows.  The near level
-// (patch pitch ~44 at w = 12) fits two CTAs either way, so 5 warps give 10
-// resident warps instead of 8.
-int sub_dd_warps(int M, int w) {
-  auto resident = [&](int nw) {
-    const size_t b = sub_dd_smem_nw(M, w, nw);
-    return b > 220 * 1024 ? 0 : nw * (int)((228 * 1024) / (b + 1024));  // 220 KB: the configured maximum
-  };
-  return resident(5) > resident(4) ? 5 : 4;
-}
-
-size_t spread_sub_dd_smem(int M, int w) {
-  return (size_t)(kMaxNC * w + (kSubDDThreads / 32) * 32 * (2 * w + 1) + (kSubDDThreads / 32) * M * M) *
-         sizeof(float2);
-}
+size_t spread_sub_dd_smem(int M, int w) { return spread_fx_smem_nt(M, w, kSubDDThreads); }
 
 #define LP_SUB_DD_CASES LP_CASE(4) LP_CASE(5) LP_CASE(6) LP_CASE(7) LP_CASE(8) LP_CASE(9) LP_CASE(10) \
   LP_CASE(11) LP_CASE(12) LP_CASE(13) LP_CASE(14) LP_CASE(15) LP_CASE(16)
 
 bool spread_sub_dd_configure(int w) {
-  const int bytes = 220 * 1024;
+  const int bytes = 200 * 1024;
   switch (w) {
 #define LP_CASE(W)                                                                                     \
   case W:                                                                                              \
-    return cudaFuncSetAttribute(spread_sub_dd_kernel<W, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                bytes) == cudaSuccess &&                                                \
-           cudaFuncSetAttribute(spread_sub_dd_kernel<W, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                bytes) == cudaSuccess;
+    return cudaFuncSetAttribute(spread_fx_kernel<W, kSubDDThreads>,                                     \
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
     LP_SUB_DD_CASES
 #undef LP_CASE
     default: return false;
@@ -426,21 +449,18 @@ bool spread_sub_dd_configure(int w) {
 
 void launch_spread_sub_dd(const SubDDArgs& a, int w, cudaStream_t s) {
   dim3 grid(a.nbx, a.nby);
-  const int nw = sub_dd_warps(a.M, w);
-  const size_t smem = sub_dd_smem_nw(a.M, w, nw);
+  const size_t smem = spread_fx_smem_nt(a.M, w, kSubDDThreads);
   switch (w) {
-#define LP_CASE(W)                                                      \
-  case W:                                                               \
-    if (nw == 5)                                                        \
-      spread_sub_dd_kernel<W, 5><<<grid, 5 * 32, smem, s>>>(a);         \
-    else                                                                \
-      spread_sub_dd_kernel<W, 4><<<grid, 4 * 32, smem, s>>>(a);         \
+#define LP_CASE(W)                                                               \
+  case W:                                                                        \
+    spread_fx_kernel<W, kSubDDThreads><<<grid, kSubDDThreads, smem, s>>>(a);     \
     break;
     LP_SUB_DD_CASES
 #undef LP_CASE
     default: break;
   }
 }
+
 
 void launch_gather_q(const double* q, int64_t stride, int nq, const int* perm, int64_t n, float* q_s,
                      cudaStream_t s) {

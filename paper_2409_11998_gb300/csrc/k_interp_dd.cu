@@ -45,8 +45,8 @@ __global__ void __launch_bounds__(128) interp_dd_kernel(const __grid_constant__ 
       continue;
     }
     dd wx[W], wy[W];
-    dd_stencil_weights<W>(&a.coef[0][0], kMaxW, a.nc, vx, wx);
-    dd_stencil_weights<W>(&a.coef[0][0], kMaxW, a.nc, vy, wy);
+    dd_stencil_weights<W>(&a.coef[0][0], kMaxW, a.nc, a.nf, vx, wx);
+    dd_stencil_weights<W>(&a.coef[0][0], kMaxW, a.nc, a.nf, vy, wy);
     // rows and channels stay rolled (wy spills to L1-resident local memory):
     // unrolling all w^2 C products overflows the instruction cache
     // rows are read as 16-byte pairs of cells from the even cell at or below

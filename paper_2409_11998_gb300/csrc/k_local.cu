@@ -76,7 +76,9 @@ struct Foot {
   int panel;
   double t, d2, gx, gy;
   double s2;       // |gamma'|^2 at the last parameter
-  bool converged;  // the double-precision phase met its stopping rule
+  bool converged;  // the double-precision phase met its stopping rule, or its
+                   // last step was a gradient step (flat distance near a
+                   // centre of curvature: slow, but downhill to the foot)
 };
 
 // Newton for the foot on panel ip from parameter t: a single-precision phase
@@ -87,7 +89,8 @@ struct Foot {
 // parameter from the second-order Taylor expansion of that step (error ~|dt|^3
 // times the third derivative), so that the distance of on-boundary targets
 // and the side of the boundary are resolved to rounding.  Twenty double
-// steps without a step below 1e-6 leave `converged` false.
+// steps without a step below 1e-6, the last of them a Newton step proper,
+// leave `converged` false.
 __device__ Foot panel_foot(const LocalArgs& a, int ip, double t, double x, double y) {
   const size_t off = (size_t)(2 * ip) * a.p;
   const double rx = a.geo_ref[2 * ip], ry = a.geo_ref[2 * ip + 1];
@@ -123,13 +126,15 @@ __device__ Foot panel_foot(const LocalArgs& a, int ip, double t, double x, doubl
     const double f = gx * J[0][1] + gy * J[1][1];
     const double s2 = J[0][1] * J[0][1] + J[1][1] * J[1][1];
     double fp = s2 + gx * J[0][2] + gy * J[1][2];
-    if (fp < 0.1 * s2) fp = s2;
+    const bool gradient = fp < 0.1 * s2;
+    if (gradient) fp = s2;
     const double tn = fmin(1.0, fmax(-1.0, t - f / fp));
     const double dt = tn - t;
     t = tn;
     r.gx = gx + dt * (J[0][1] + 0.5 * dt * J[0][2]);
     r.gy = gy + dt * (J[1][1] + 0.5 * dt * J[1][2]);
     r.s2 = s2;
+    r.converged = gradient;
     if (fabs(dt) < 1e-6) {
       r.converged = true;
       break;

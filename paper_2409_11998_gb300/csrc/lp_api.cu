@@ -231,10 +231,11 @@ void derive_normals(int64_t n_panels, int p, const double* xy, double* nrm) {
 }
 
 // ---- scratch of lp_execute_noalloc -------------------------------------------
-// The near-boundary list of the local pass (one int2 per target) and its
-// counter live in this file-scope device array instead of plan memory, so
-// that the call allocates nothing.  Every GPU that loads the library holds
-// it (16 MiB + 256 B) until the process exits.
+// The per-call buffers that lp_execute keeps in plan memory -- the
+// near-boundary list of the local pass (one int2 per target) and its
+// counter -- live in this file-scope device array instead, so that the call
+// allocates nothing.  Every GPU that loads the library holds it (16 MiB +
+// 256 B) until the process exits.
 constexpr int64_t kNoAllocMaxTargets = int64_t(1) << 21;
 constexpr size_t kNoAllocListBytes = (size_t)kNoAllocMaxTargets * sizeof(int2);
 constexpr size_t kNoAllocScratchBytes = kNoAllocListBytes + 256;
@@ -275,8 +276,9 @@ namespace lpg {
 // origin, count, and per level the patch side -- the bin, the stencil halo
 // and a cell of rounding slack; among the next 16 sizes, the one whose row
 // pitch gives the fewest shared-memory wavefronts for the w^2 stencil cells
-// taken 32 at a time (4-byte cells: 32 banks per warp; 8-byte cells: 16 per
-// half warp).  False if a patch would not fit in shared memory.
+// taken 32 at a time (4-byte cells in 32 banks: the FP32 patch, and each of
+// the two count arrays of the FP64 plans' fixed-point patch).  False if a
+// patch would not fit in shared memory.
 static bool configure_bins(Plan& P, int cells) {
   const GridLevel& N = P.lv[P.l0];
   const int w = P.ker.w;
@@ -287,7 +289,7 @@ static bool configure_bins(Plan& P, int cells) {
   bins.inv_bt = 1.0 / (cells * N.h);
   bins.nbx = bins.nby = (N.g + cells - 1) / cells;
   int M[2] = {0, 0};
-  const int banks = f64 ? 16 : 32, group = f64 ? 16 : 32;
+  const int banks = 32, group = 32;
   for (int l = P.l0; l < 2; ++l) {
     const double c = cells * N.h / P.lv[l].h;
     const int m0 = (int)std::ceil(c) + w + 3;
@@ -360,6 +362,7 @@ void spread_binned_dd(const Plan& P, int l, cudaStream_t s) {
   a.nby = P.bins.nby;
   a.M = P.sub_M[l];
   a.nc = P.es.nc;
+  a.nf = P.es_float_steps;
   a.status = P.d_status;
   for (int k = 0; k < P.es.nc; ++k)
     for (int t = 0; t < P.es.w; ++t) {
@@ -538,6 +541,7 @@ void history_interp(const Plan& P, int64_t nt, const double* txy, double* const*
   for (int c = 0; c < 3; ++c) a.out[c] = dout[c];
   a.status = P.d_status;
   a.nc = P.es.nc;
+  a.nf = P.es_float_steps;
   std::memcpy(a.coef, P.es_dd, sizeof(a.coef));
   launch_interp_dd(a, P.ker.w, s);
   ++P.launches;
@@ -587,6 +591,7 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
         !std::isfinite(dom->box_hi[d]))
       return LP_ERR_ARG;
   if (dom->n_panels < 0 || dom->max_device_bytes < 0) return LP_ERR_ARG;
+  if (dom->autotune < 0 || dom->autotune > LP_AUTOTUNE_FULL) return LP_ERR_ARG;
   if (dom->refine_levels < LP_REFINE_AUTO || dom->refine_levels > kMaxDyLevels) return LP_ERR_ARG;
   if (dom->levels < LP_LEVELS_AUTO || dom->levels > 2) return LP_ERR_ARG;
   if (dom->upsampling != 0.0 && !(dom->upsampling >= 1.25 && dom->upsampling <= 3.0)) return LP_ERR_ARG;
@@ -602,6 +607,7 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
   P.order = order;
   P.delta1 = delta;
   P.autotune = dom->autotune != 0;
+  P.tune_grids = dom->autotune == LP_AUTOTUNE_FULL;
   P.l0 = dom->levels == 1 ? 1 : 0;
   P.delta2 = P.l0 ? delta : 32.0 * delta;
   P.tol = tol;
@@ -767,9 +773,15 @@ static lp_status tune_bins(Plan& P, int64_t n) {
   return status_from_cuda();
 }
 
+static lp_status tune_grids(lp_plan_t h, int64_t n, const double* xy, const double* w, const double* f);
+
 lp_status lp_volume(lp_plan_t h, int64_t n, const double* xy, const double* w, const double* f) {
   if (!h || n < 0) return LP_ERR_ARG;
   if (n > 0 && (!xy || !w || !f)) return LP_ERR_ARG;
+  if (h->P.tune_grids && n > 0) {
+    const lp_status st = tune_grids(h, n, xy, w, f);  // may replace h->P by a faster configuration
+    if (st != LP_OK) return st;
+  }
   Plan& P = h->P;
   if (n > P.v_cap) {
     cudaStreamSynchronize(P.stream);
@@ -864,6 +876,115 @@ static lp_status bind_layer(lp_plan_t h, const double* dens, int kind) {
 
 lp_status lp_single_layer(lp_plan_t h, const double* sigma) { return bind_layer(h, sigma, 0); }
 lp_status lp_double_layer(lp_plan_t h, const double* mu) { return bind_layer(h, mu, 1); }
+
+// Grid autotuner (LP_AUTOTUNE_FULL): the upsampling sigma and the number of
+// history levels trade transform size against stencil width and launch
+// count (Sec. 3's remark on one level against two), so the first lp_volume
+// builds a plan for each sigma in {1.25, 1.5, 2} with one and with two
+// levels -- each with the kernel width that sigma needs for the plan's
+// tolerance -- on the plan's own boundary, binds the sources (and unit
+// layer densities), and times one V (+ S + D) evaluation at the sources
+// (median of three after a warm-up, CUDA events on the plan's stream).  The
+// fastest configuration replaces the plan's grids; its bins are then tuned
+// as for LP_AUTOTUNE_BINS.  Scratch for the timing is allocated and freed
+// here.
+static lp_status tune_grids(lp_plan_t h, int64_t n, const double* xy, const double* w, const double* f) {
+  Plan& P0 = h->P;
+  P0.tune_grids = false;
+  const double sigmas[3] = {1.25, 1.5, 2.0};
+  lp_domain dom{};
+  dom.precision = P0.precision;
+  dom.order = P0.order;
+  for (int d = 0; d < 2; ++d) {
+    dom.box_lo[d] = P0.box_lo[d];
+    dom.box_hi[d] = P0.box_hi[d];
+  }
+  dom.n_panels = P0.n_panels;
+  dom.panel_order = P0.p;
+  dom.bnd_xy = P0.d_bxy;
+  dom.bnd_w = P0.d_bw;
+  dom.bnd_normal = P0.d_bnrm;
+  dom.stream = P0.stream;
+  dom.refine_levels = P0.dy_levels;
+  dom.autotune = 0;
+  dom.max_device_bytes = (int64_t)P0.max_bytes;
+  const int64_t nb = P0.nb;
+  // scratch: zero jets, three outputs, unit densities
+  double* tmp = nullptr;
+  const size_t tmp_n = (size_t)9 * n + 2 * (size_t)nb;
+  if (cudaMalloc((void**)&tmp, tmp_n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return LP_ERR_NOMEM;
+  }
+  cudaMemsetAsync(tmp, 0, (size_t)9 * n * sizeof(double), P0.stream);
+  std::vector<double> ones((size_t)2 * nb, 1.0);
+  if (nb) cudaMemcpy(tmp + 9 * n, ones.data(), ones.size() * sizeof(double), cudaMemcpyHostToDevice);
+  double* jet = tmp;
+  double* outv[3] = {tmp + 6 * n, nb ? tmp + 7 * n : nullptr, nb ? tmp + 8 * n : nullptr};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  lp_plan_s* best = nullptr;
+  float best_ms = 1e30f;
+  float ms_all[6];
+  for (int c = 0; c < 6; ++c) {
+    ms_all[c] = -1.f;
+    dom.upsampling = sigmas[c / 2];
+    dom.levels = 1 + (c % 2);
+    lp_plan_s* cand = nullptr;
+    if (lp_plan(&dom, P0.delta1, P0.tol, &cand) != LP_OK) continue;
+    lp_status st = lp_volume(cand, n, xy, w, f);
+    if (st == LP_OK && nb) st = lp_single_layer(cand, tmp + 9 * n);
+    if (st == LP_OK && nb) st = lp_double_layer(cand, tmp + 9 * n + nb);
+    float t[3] = {0, 0, 0};
+    for (int r = 0; r < 4 && st == LP_OK; ++r) {
+      cudaEventRecord(e0, cand->P.stream);
+      st = lp_execute(cand, n, cand->P.d_vxy, jet, outv[0], outv[1], outv[2]);
+      cudaEventRecord(e1, cand->P.stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) st = LP_ERR_CUDA;
+      if (r > 0) cudaEventElapsedTime(&t[r - 1], e0, e1);
+    }
+    if (st == LP_OK) st = lp_sync(cand);
+    if (st != LP_OK) {
+      lp_destroy(cand);
+      cudaGetLastError();
+      continue;
+    }
+    std::sort(t, t + 3);
+    ms_all[c] = t[1];
+    if (t[1] < best_ms) {
+      if (best) lp_destroy(best);
+      best = cand;
+      best_ms = t[1];
+    } else {
+      lp_destroy(cand);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(P0.stream);
+  cudaFree(tmp);
+  if (!best) return LP_OK;  // no candidate could be built: keep the plan as created
+  // the winner takes over the handle; densities already bound move with it
+  const bool bins = P0.autotune;
+  const bool had_sigma = P0.have_sigma, had_mu = P0.have_mu;
+  std::swap(h->P, best->P);  // best now holds the plan as created
+  Plan& P = h->P;
+  P.autotune = bins;
+  P.tuned = false;
+  P.tune_grids = false;
+  P.have_volume = false;
+  P.launches += best->P.launches;
+  for (int c = 0; c < 6; ++c) P.grid_ms[c] = ms_all[c];
+  lp_status st = LP_OK;
+  if (had_sigma) st = lp_single_layer(h, best->P.d_sigma);
+  if (st == LP_OK && had_mu) st = lp_double_layer(h, best->P.d_mu);
+  else if (!had_mu) P.have_mu = false;
+  if (!had_sigma) P.have_sigma = false;
+  cudaStreamSynchronize(P.stream);
+  lp_destroy(best);
+  return st;
+}
 
 // Steps 2-4 and the local part on device buffers (stage events 2 .. 8):
 // zero the grids of the requested channels, spread (volume nodes through the
@@ -1016,7 +1137,8 @@ lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* j
   for (int c = 0; c < 3; ++c) dout[c] = host_out[c] ? P.d_out + c * nt : outs[c];
   record_stage(P, 1, s);
 
-  device_pipeline(P, nt, dt, dj, dout, wv, ws, wd, P.d_near, P.d_near_count, host_in ? P.ev_staged : nullptr, s);
+  device_pipeline(P, nt, dt, dj, dout, wv, ws, wd, P.d_near, P.d_near_count, host_in ? P.ev_staged : nullptr,
+                  s);
   for (int c = 0; c < 3; ++c)
     if (host_out[c]) cudaMemcpyAsync(outs[c], dout[c], nt * sizeof(double), cudaMemcpyDeviceToHost, s);
   record_stage(P, 9, s);
@@ -1176,13 +1298,15 @@ lp_status lp_destroy(lp_plan_t h) {
 lp_status lp_plan_info(lp_plan_t h, double* out) {
   if (!h || !out) return LP_ERR_ARG;
   const Plan& P = h->P;
-  double v[31] = {P.delta1, P.delta2, (double)P.ker.w, P.ker.beta, (double)P.lv[0].g, (double)P.lv[0].K,
+  double v[37] = {P.delta1, P.delta2, (double)P.ker.w, P.ker.beta, (double)P.lv[0].g, (double)P.lv[0].K,
                   P.lv[0].P, (double)P.lv[1].g, (double)P.lv[1].K, P.lv[1].P, P.lv[1].L, P.band,
                   P.margin, (double)P.device_bytes, (double)P.precision, (double)P.order,
                   (double)P.launches, P.es_fit_err, (double)P.es.nc, P.sigma_eff,
                   P.own_fft ? 1.0 : 0.0, P.binned ? 1.0 : 0.0, (double)P.bin_cells,
                   (double)P.dy_levels, P.dy_err, (double)P.dy_nq, (double)(2 - P.l0), P.sigma,
-                  (double)P.tune_ms[0], (double)P.tune_ms[1], (double)P.tune_ms[2]};
+                  (double)P.tune_ms[0], (double)P.tune_ms[1], (double)P.tune_ms[2],
+                  (double)P.grid_ms[0], (double)P.grid_ms[1], (double)P.grid_ms[2], (double)P.grid_ms[3],
+                  (double)P.grid_ms[4], (double)P.grid_ms[5]};
   std::memcpy(out, v, sizeof(v));
   return LP_OK;
 }

@@ -177,7 +177,7 @@ struct SubDDArgs {
   void* grid;         // FP64 grid
   double org_x, org_y, bt;
   float2 inv_h;       // 1 / h, df64
-  int nbx, nby, M, nc;
+  int nbx, nby, M, nc, nf;  // nf: leading Horner steps in float
   unsigned* status;
   float2 coef[kMaxNC][kMaxW];  // weight polynomials, df64
 };
@@ -221,7 +221,7 @@ struct InterpDDArgs {
   int l0;                  // first level in use (1 for single-level plans)
   double* out[3];
   unsigned* status;
-  int nc;
+  int nc, nf;               // coefficients; leading Horner steps in float
   float2 coef[kMaxNC][kMaxW];  // weight polynomials, df64
 };
 
@@ -299,6 +299,7 @@ struct Plan {
   Kernel ker{};
   EsPoly<double> es{};
   EsPoly<float> es32{};
+  int es_float_steps = 0;  // leading Horner steps of the df64 weight chains taken in float
   float2 es_dd[kMaxNC][kMaxW] = {};  // es as df64 (hi, lo) pairs
   // dyadic refinement (k_dyadic.cu): levels J, difference-kernel tables,
   // subnodes of every level (offsets, normal x weight, densities)
@@ -361,6 +362,8 @@ struct Plan {
   bool autotune = false;           // time the bin candidates at the first lp_volume
   bool tuned = false;
   float tune_ms[3] = {0, 0, 0};    // spread time of each candidate (both levels)
+  bool tune_grids = false;         // time upsampling x level candidates at the first lp_volume
+  float grid_ms[6] = {0, 0, 0, 0, 0, 0};  // their evaluation times (ms; -1: not built)
   float4* d_vrel_dd = nullptr;     // FP64 plans: offsets from the bin corner, df64
   float2* d_vq_dd = nullptr;       // FP64 plans: strengths in bin order, df64
   size_t key_cap = 0;

@@ -163,6 +163,47 @@ lp_status build_tables(Plan& P) {
 // weights reach the support edge z = +-1, where sqrt(1 - z^2) is not smooth,
 // and are accepted once within 4 e^{-beta} (the kernel's own value there,
 // below the kernel's truncation error).
+// Leading Horner steps of the df64 weight chains (even and odd parts in
+// v^2, see dd_stencil_weights) that may run in single precision: the largest
+// m <= 4 for which the float steps -- coefficients rounded to float, v^2
+// rounded to float, fused multiply-adds rounded to float, the rest exact --
+// move no weight by more than 5% of the fit's error target, over a fine grid
+// of v in [-1/2, 1/2].
+static int float_horner_steps(const Plan& P, double target) {
+  const int w = P.es.w, nc = P.es.nc;
+  const int ke = (nc - 1) & ~1, ko = (nc - 2) | 1;
+  int best = 0;
+  for (int m = 1; m <= 4; ++m) {
+    double worst = 0.0;
+    for (int t = 0; t < (w + 1) / 2; ++t)
+      for (int j = 0; j <= 400; ++j) {
+        const double v = -0.5 + j / 400.0 * (1.0 - 1e-12), u = v * v;
+        double err = 0.0;
+        for (int par = 0; par < 2; ++par) {
+          const int top = par ? ko : ke;
+          double exact = P.es.c[top][t];
+          float f = (float)P.es.c[top][t];
+          int s = 0;
+          for (int k = top - 2; k >= par; k -= 2, ++s) {
+            exact = exact * u + P.es.c[k][t];
+            if (s < m)
+              f = std::fmaf(f, (float)u, (float)P.es.c[k][t]);
+          }
+          // the exact continuation from the float partial sum after m steps
+          double mixed = (double)f;
+          s = 0;
+          for (int k = top - 2; k >= par; k -= 2, ++s)
+            if (s >= m) mixed = mixed * u + P.es.c[k][t];
+          err += std::fabs(mixed - exact) * (par ? std::fabs(v) : 1.0);
+        }
+        worst = std::max(worst, err);
+      }
+    if (worst > 0.05 * target) break;
+    best = m;
+  }
+  return best;
+}
+
 lp_status fit_kernel_poly(Plan& P) {
   const int w = P.ker.w;
   const double beta = P.ker.beta, hw = P.ker.half_w;
@@ -219,8 +260,12 @@ lp_status fit_kernel_poly(Plan& P) {
     P.es.w = P.es32.w = w;
     P.es.nc = P.es32.nc = nc;
     P.es_fit_err = std::max(err, err_edge);
-    if (err <= target && err_edge <= target_edge) return LP_OK;
+    if (err <= target && err_edge <= target_edge) {
+      P.es_float_steps = float_horner_steps(P, target);
+      return LP_OK;
+    }
   }
+  P.es_float_steps = float_horner_steps(P, target);
   return LP_OK;  // best effort at the maximum degree (error recorded)
 }
 

@@ -2,12 +2,17 @@
 
 Requests ask for V, S and D on one mesh of a resident pool with their own
 densities (the mesh's f, sigma, mu scaled per request).  The server keeps
-plans (grids, tables, boundary structures) resident per mesh and stream slot,
-forms waves from the waiting requests whenever a slot is free and the device
-footprint of resident plans stays under a budget (idle plans are evicted
-least recently used first), runs each wave as one lp_batch_execute on its
-slot's stream -- waves on different slots overlap on the device -- and
-records per-request latency from arrival to observed completion.
+one plan (grids, tables, boundary structures) resident per mesh and stream
+slot, created before serving starts (prewarm) while the device footprint of
+resident plans stays under a budget.  Whenever a slot is free it forms a wave
+from the waiting requests in arrival order, at most one request per mesh (a
+plan holds one set of densities; a second request for the same mesh waits for
+the next wave or the other slot), runs the wave as one lp_batch_execute on
+the slot's stream -- waves on different slots overlap on the device -- and
+records per-request latency from arrival to observed completion.  A plan is
+created inside the request loop only when its mesh had no resident plan (it
+was never admitted, or was evicted, least recently used first, to make room);
+``created_in_loop`` counts those.
 
 ``one_at_a_time=True`` gives the reference serving path: one stream, one
 request per call, lp_execute, in arrival order.
@@ -104,7 +109,9 @@ class Server:
         self.pools = collections.defaultdict(list)  # (slot, mesh) -> [_PlanInst]
         self.resident = 0
         self.created = 0
+        self.created_in_loop = 0
         self.evicted = 0
+        self.scan = 4 * self.max_wave    # waiting requests examined per wave
 
     # ---- plans ----
     def _new_plan(self, slot, mid):
@@ -134,16 +141,22 @@ class Server:
         return self.resident + need <= self.budget
 
     def _acquire(self, slot, mid):
-        """An idle resident plan of this mesh on this slot, or a new one if the
-        footprint budget allows (evicting idle plans first); None if not."""
-        for inst in self.pools[(slot, mid)]:
+        """The idle resident plan of this mesh on this slot; if the mesh has
+        none on this slot, a new one when the footprint budget allows
+        (evicting idle plans first); None if its plan is busy or there is no
+        room."""
+        lst = self.pools[(slot, mid)]
+        for inst in lst:
             if not inst.busy:
                 inst.busy = True
                 return inst
-        est = max([i.bytes for (s, m), lst in self.pools.items() if m == mid for i in lst] or [0])
+        if lst:
+            return None                     # busy: the request waits for the next wave
+        est = max([i.bytes for (s, m), l in self.pools.items() if m == mid for i in l] or [0])
         if not self._evict_for(est):
             return None
         inst = self._new_plan(slot, mid)
+        self.created_in_loop += 1
         if self.resident > self.budget:
             self._evict_for(0)
         inst.busy = True
@@ -230,16 +243,18 @@ class Server:
             for si, slot in enumerate(self.slots):
                 if slot["busy"] or not queue:
                     continue
-                wave = []
-                deferred = []
-                while queue and len(wave) < self.max_wave:
+                # the oldest waiting requests, at most one per mesh; the rest
+                # keep their places in the queue
+                wave, kept, meshes = [], [], set()
+                while queue and len(wave) < self.max_wave and len(wave) + len(kept) < self.scan:
                     r = queue.popleft()
-                    inst = self._acquire(si, r.mesh)
-                    if inst is None:        # no memory for its plan now: keep it waiting
-                        deferred.append(r)
-                        break
+                    inst = None if r.mesh in meshes else self._acquire(si, r.mesh)
+                    if inst is None:
+                        kept.append(r)
+                        continue
+                    meshes.add(r.mesh)
                     wave.append((r, inst))
-                for r in reversed(deferred):
+                for r in reversed(kept):
                     queue.appendleft(r)
                 if wave:
                     self._launch(si, wave, time.perf_counter() - t0)

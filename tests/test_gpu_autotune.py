@@ -39,3 +39,50 @@ def test_autotuned_plan(lp, oracle_lib, precision, tol, levels):
     ev.bind(src_f=2 * p["src_f"])
     assert ev.info()["bin_cells"] == info["bin_cells"]
     ev.close()
+
+
+GRID_KEYS = ("grid_ms_s125_l1", "grid_ms_s125_l2", "grid_ms_s15_l1", "grid_ms_s15_l2", "grid_ms_s2_l1",
+             "grid_ms_s2_l2")
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp64", 1e-9)])
+def test_grid_autotuner_on_the_starfish(lp, oracle_lib, precision, tol):
+    """LP_AUTOTUNE_FULL on the 1.2M-node starfish: the plan keeps the fastest
+    of the six upsampling x level configurations, matches the oracle within
+    the tolerance, and evaluates V, S, D no slower than the default plan."""
+    import time
+    from workloads import configs
+    p = configs.starfish()
+    stream = torch.cuda.Stream()
+
+    def timed(ev):
+        t_xy = torch.as_tensor(p["tgt_xy"], device="cuda")
+        jet = torch.as_tensor(p["tgt_jet"], device="cuda")
+        ev.evaluate(tgt_xy=t_xy, tgt_jet=jet)
+        best = 1e30
+        for _ in range(5):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = ev.evaluate(tgt_xy=t_xy, tgt_jet=jet)
+            best = min(best, time.perf_counter() - t0)
+        return best, out
+
+    ev = lp.Evaluator(p, precision=precision, tol=tol, stream=stream.cuda_stream, autotune="full").bind()
+    info = ev.info()
+    ms = [info[k] for k in GRID_KEYS]
+    built = [m for m in ms if m > 0]
+    assert len(built) >= 4, ms
+    chosen = GRID_KEYS[ms.index(min(built))]
+    sigma = {"s125": 1.25, "s15": 1.5, "s2": 2.0}[chosen.split("_")[2]]
+    assert abs(info["sigma"] - sigma) < 1e-12 and info["levels"] == int(chosen[-1]), (chosen, info)
+    t_tuned, out = timed(ev)
+    idx = np.random.default_rng(9).choice(len(p["tgt_xy"]), 2000, replace=False)
+    ref = oracle_lib.evaluate(p, targets=idx)
+    for k in "VSD":
+        got = out[k].cpu().numpy()[idx]
+        assert np.linalg.norm(got - ref[k]) / np.linalg.norm(ref[k]) < tol, k
+    ev.close()
+    base = lp.Evaluator(p, precision=precision, tol=tol, stream=stream.cuda_stream).bind()
+    t_default, _ = timed(base)
+    base.close()
+    assert t_tuned <= 1.05 * t_default, (t_tuned, t_default, chosen, ms)

@@ -16,19 +16,19 @@ def lp():
     return lp
 
 
-def test_results_same_alone_and_in_the_mix(lp):
+def test_results_same_alone_and_in_the_mix(lp, oracle_lib):
     from paper_2409_11998_gb300 import serve
     from workloads import configs
     pool = configs.serving_pool(n_meshes=4, t_min=1500, t_max=12000, seed=5100)
     # bursts of overlapping arrivals on every mesh, so waves mix meshes and
-    # repeat a mesh within one wave
+    # later requests for a mesh wait for its plan
     arrivals = [(0.001 * (i // 5), i % 4, 0.6 + 0.05 * i) for i in range(20)]
     srv = serve.Server(pool, precision="fp32", tol=1e-5, n_slots=2, max_wave=8, keep_outputs=True)
     srv.prewarm()
     reqs = srv.run(arrivals)
     stats = serve.latency_stats(reqs)
     assert stats["requests"] == 20 and stats["p99_ms"] >= stats["p50_ms"] > 0
-    waves_with_many = srv.created > len(pool) * 2  # extra plans were needed for repeated meshes
+    assert srv.created == 2 * len(pool) and srv.created_in_loop == 0   # every plan made before serving
     for r in reqs:
         p = pool[r.mesh]
         ev = lp.Evaluator(p, precision="fp32", tol=1e-5, levels=srv.levels).bind(src_f=p["src_f"] * r.scale,
@@ -40,8 +40,17 @@ def test_results_same_alone_and_in_the_mix(lp):
             b = r.outputs[k].cpu().numpy()
             assert np.max(np.abs(a - b)) <= 5e-6 * np.max(np.abs(a)), (r.rid, k)
         ev.close()
+    # served results against the oracle (densities scaled as the request's)
+    for r in reqs[:4]:
+        p = dict(pool[r.mesh])
+        for k in ("src_f", "sigma", "mu", "tgt_jet"):
+            p[k] = pool[r.mesh][k] * r.scale
+        idx = np.random.default_rng(r.rid).choice(len(p["tgt_xy"]), 200, replace=False)
+        ref = oracle_lib.evaluate(p, targets=idx)
+        for k in "VSD":
+            got = r.outputs[k].cpu().numpy()[idx]
+            assert np.linalg.norm(got - ref[k]) / np.linalg.norm(ref[k]) < 1e-5, (r.rid, k)
     srv.close()
-    assert waves_with_many
 
 
 def test_one_at_a_time_path(lp):
