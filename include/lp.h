@@ -308,6 +308,25 @@ lp_status lp_solve_dirichlet(lp_plan_t plan, const double* g, const double* f_je
 lp_status lp_solve_neumann(lp_plan_t plan, const double* g, const double* f_jet_b, double* u, double tol,
                            int max_iter, int restart, int* iterations, double* residual);
 
+/* f-jets at targets estimated from the bound node values, for callers that
+ * have f only at the quadrature nodes (the paper computes the jets of
+ * Sec. 4's volume expansion analytically, Sec. 6.1).  At each target t_xy[i]:
+ * weighted least squares of the nodes' f over the nodes within
+ * rho = sqrt(3 delta_1) (three mean node spacings for the paper's delta_1 =
+ * 3 x mean weight), weights (1 - r^2/rho^2)^2, on a quadratic in the offset
+ * when at least 10 nodes are that close, a linear function with 4 to 9, the
+ * weighted mean with 1 to 3, and zero with none (targets away from every
+ * node, e.g. outside the domain); at a target within 1e-12 of the box side
+ * of a node, the value is that node's f.  The normal equations are summed
+ * in single precision and solved in double.
+ *   f_jet: [n_t][6] out, (f, f_x, f_y, f_xx, f_xy, f_yy), ready for
+ *          lp_execute.
+ * Requires lp_volume (LP_ERR_STATE); host or device pointers.  Allocates
+ * scratch for the call (a cell index of the nodes) and frees it before
+ * returning; synchronises the plan's stream.  LP_ERR_UNSUPPORTED when the
+ * box holds more than 6.4e7 cells of side rho. */
+lp_status lp_volume_jets(lp_plan_t plan, int64_t n_t, const double* t_xy, double* f_jet);
+
 /* Wait for the plan's stream; return and clear the device status word. */
 lp_status lp_sync(lp_plan_t plan);
 

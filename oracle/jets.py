@@ -30,6 +30,27 @@ def jet_radius(delta):
     return float(np.sqrt(3.0 * delta))
 
 
+def _cholesky_solve(A, b):
+    """Solution of A c = b by Cholesky factorisation, or None when a pivot is
+    not above 1e-12 A[0, 0]."""
+    n = len(b)
+    L = np.zeros((n, n))
+    for j in range(n):
+        d = A[j, j] - np.dot(L[j, :j], L[j, :j])
+        if not d > 1e-12 * A[0, 0]:
+            return None
+        L[j, j] = np.sqrt(d)
+        for i in range(j + 1, n):
+            L[i, j] = (A[i, j] - np.dot(L[i, :j], L[j, :j])) / L[j, j]
+    y = np.zeros(n)
+    for i in range(n):
+        y[i] = (b[i] - np.dot(L[i, :i], y[:i])) / L[i, i]
+    c = np.zeros(n)
+    for i in range(n - 1, -1, -1):
+        c[i] = (y[i] - np.dot(L[i + 1:, i], c[i + 1:])) / L[i, i]
+    return c
+
+
 def estimate_jets(src_xy, src_f, tgt_xy, delta, box_side):
     from scipy.spatial import cKDTree
     src_xy = np.asarray(src_xy, dtype=np.float64)
@@ -52,15 +73,14 @@ def estimate_jets(src_xy, src_f, tgt_xy, delta, box_side):
         w = (1.0 - r2) ** 2
         fj = src_f[idx]
         u, v = d[:, 0], d[:, 1]
-        if n >= 10:
-            B = np.stack([np.ones(n), u, v, u * u, u * v, v * v], axis=1)
-        elif n >= 4:
-            B = np.stack([np.ones(n), u, v], axis=1)
-        else:
-            B = np.ones((n, 1))
+        B = np.stack([np.ones(n), u, v, u * u, u * v, v * v], axis=1)
         A = B.T @ (w[:, None] * B)
         b = B.T @ (w * fj)
-        c = np.linalg.solve(A, b)
+        c = _cholesky_solve(A, b) if n >= 10 else None
+        if c is None and n >= 4:
+            c = _cholesky_solve(A[:3, :3], b[:3])
+        if c is None:
+            c = np.array([b[0] / A[0, 0]])
         jet = np.zeros(6)
         jet[0] = c[0]
         if c.size >= 3:

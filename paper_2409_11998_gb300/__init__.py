@@ -30,7 +30,7 @@ EXPORTS = ("lp_plan", "lp_volume", "lp_single_layer", "lp_double_layer", "lp_exe
            "lp_destroy", "lp_status_string", "lp_plan_info", "lp_stage_times", "lp_execute_noalloc",
            "lp_batch_create", "lp_batch_execute", "lp_batch_sync", "lp_batch_stage_times",
            "lp_batch_destroy", "lp_solve_dirichlet", "lp_execute_graph", "lp_solve_neumann",
-           "lp_sync_timeout")
+           "lp_sync_timeout", "lp_volume_jets")
 
 
 class LpError(RuntimeError):
@@ -76,6 +76,7 @@ def _lib():
         L.lp_batch_destroy.argtypes = [vp]
         L.lp_sync.argtypes = [vp]
         L.lp_sync_timeout.argtypes = [vp, d]
+        L.lp_volume_jets.argtypes = [vp, i64, vp, vp]
         L.lp_destroy.argtypes = [vp]
         L.lp_status_string.argtypes = [i32]
         L.lp_status_string.restype = ctypes.c_char_p
@@ -234,6 +235,12 @@ def lp_batch_destroy(batch):
 
 def lp_sync(plan):
     _check(_lib().lp_sync(plan), "lp_sync")
+
+
+def lp_volume_jets(plan, n_t, t_xy, f_jet):
+    """f-jets [n_t][6] at the targets estimated from the bound node values
+    (weighted quadratic least squares within sqrt(3 delta_1)); writes f_jet."""
+    _check(_lib().lp_volume_jets(plan, int(n_t), _ptr(t_xy), _ptr(f_jet)), "lp_volume_jets")
 
 
 def lp_sync_timeout(plan, timeout_ms):

@@ -181,7 +181,7 @@ void destroy_plan(Plan& P) {
                   P.d_geo_coef32, P.d_keys, P.d_counts, P.d_cursor, P.d_vrel_s, P.d_vperm, P.d_vq_s,
                   P.d_vstart, P.d_sigma_coef32, P.d_mu_coef32, P.d_vrel_dd, P.d_vq_dd,
                   P.d_dy_tab, P.d_dy_rel, P.d_dy_nw, P.d_dy_sig, P.d_dy_mu,
-                  P.d_dy_rad, P.d_dy_wgl, P.d_dy_cell_start, P.d_dy_cell_panel, P.d_dy_ref};
+                  P.d_dy_rad, P.d_dy_wgl, P.d_dy_cell_start, P.d_dy_cell_panel, P.d_dy_ref, P.d_vf};
   for (void* b : bufs) dfree(b);
   if (P.h_status) cudaFreeHost(P.h_status);
   for (auto& e : P.ev)
@@ -787,11 +787,12 @@ lp_status lp_volume(lp_plan_t h, int64_t n, const double* xy, const double* w, c
     cudaStreamSynchronize(P.stream);
     drelease(P, P.d_vxy, P.v_cap * 2 * sizeof(double));
     drelease(P, P.d_vq, P.v_cap * sizeof(double));
+    drelease(P, P.d_vf, P.v_cap * sizeof(double));
     P.v_cap = 0;
     P.nv = 0;
     P.have_volume = false;
     if (!dalloc(P, (void**)&P.d_vxy, n * 2 * sizeof(double)) ||
-        !dalloc(P, (void**)&P.d_vq, n * sizeof(double)))
+        !dalloc(P, (void**)&P.d_vq, n * sizeof(double)) || !dalloc(P, (void**)&P.d_vf, n * sizeof(double)))
       return LP_ERR_NOMEM;
     P.v_cap = n;
   }
@@ -807,6 +808,7 @@ lp_status lp_volume(lp_plan_t h, int64_t n, const double* xy, const double* w, c
     const double* dw = device_view(P, w, n, &off, P.stream);
     const double* df = device_view(P, f, n, &off, P.stream);
     cudaMemcpyAsync(P.d_vxy, dxy, n * 2 * sizeof(double), cudaMemcpyDeviceToDevice, P.stream);
+    cudaMemcpyAsync(P.d_vf, df, n * sizeof(double), cudaMemcpyDeviceToDevice, P.stream);
     launch_volume_q(P, df, dw, P.d_vq, n, P.stream);
   }
   if (P.binned && n > 0) {
@@ -1252,6 +1254,86 @@ lp_status lp_execute_noalloc(lp_plan_t h, int64_t nt, const double* txy, const d
   double* dout[3] = {V, S, D};
   device_pipeline(P, nt, txy, wv ? jet : nullptr, dout, wv, ws, wd, list, count, nullptr, s);
   record_stage(P, 9, s);
+  return status_from_cuda();
+}
+
+lp_status lp_volume_jets(lp_plan_t h, int64_t nt, const double* txy, double* jet) {
+  if (!h || nt < 0 || nt > (int64_t)INT32_MAX) return LP_ERR_ARG;
+  if (nt > 0 && (!txy || !jet)) return LP_ERR_ARG;
+  Plan& P = h->P;
+  if (!P.have_volume) return LP_ERR_STATE;
+  if (nt == 0) return LP_OK;
+  cudaStream_t s = P.stream;
+  // cells of side rho over the box with one cell of margin on every side
+  const double rho = std::sqrt(3.0 * P.delta1);
+  BinGeom bg;
+  bg.x0 = P.box_lo[0] - rho;
+  bg.y0 = P.box_lo[1] - rho;
+  bg.inv_bt = 1.0 / rho;
+  const double nx = std::ceil((P.box_hi[0] - P.box_lo[0]) / rho) + 3.0;
+  const double ny = std::ceil((P.box_hi[1] - P.box_lo[1]) / rho) + 3.0;
+  if (nx * ny > 6.4e7) return LP_ERR_UNSUPPORTED;  // cells far below the node spacing
+  bg.nbx = (int)nx;
+  bg.nby = (int)ny;
+  const int64_t n = P.nv;
+  const size_t ncell = (size_t)bg.nbx * bg.nby + 1;
+  // scratch, freed before return: keys, counts, cursor, starts, offsets,
+  // permutation; targets and jets when in host memory
+  const bool host_t = !is_device_ptr(txy), host_j = !is_device_ptr(jet);
+  const size_t bytes = round256(n * sizeof(int)) * 2 + round256(ncell * sizeof(int)) * 2 +
+                       round256((ncell + 1) * sizeof(int)) + round256(n * sizeof(float2)) +
+                       (host_t ? round256(nt * 2 * sizeof(double)) : 0) +
+                       (host_j ? round256(nt * 6 * sizeof(double)) : 0);
+  char* tmp = nullptr;
+  if (cudaMalloc((void**)&tmp, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return LP_ERR_NOMEM;
+  }
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    char* p = tmp + off;
+    off += round256(b);
+    return p;
+  };
+  int* keys = (int*)take(n * sizeof(int));
+  int* perm = (int*)take(n * sizeof(int));
+  int* counts = (int*)take(ncell * sizeof(int));
+  int* cursor = (int*)take(ncell * sizeof(int));
+  int* starts = (int*)take((ncell + 1) * sizeof(int));
+  float2* rel = (float2*)take(n * sizeof(float2));
+  const double* dt = txy;
+  if (host_t) {
+    double* d = (double*)take(nt * 2 * sizeof(double));
+    cudaMemcpyAsync(d, txy, nt * 2 * sizeof(double), cudaMemcpyHostToDevice, s);
+    dt = d;
+  }
+  double* dj = host_j ? (double*)take(nt * 6 * sizeof(double)) : jet;
+  launch_bin_sort(P.d_vxy, n, bg, keys, counts, cursor, starts, rel, perm, P.d_status, s);
+  JetArgs a;
+  a.txy = dt;
+  a.n = nt;
+  a.jet = dj;
+  a.rel = rel;
+  a.perm = perm;
+  a.start = starts;
+  a.vxy = P.d_vxy;
+  a.vf = P.d_vf;
+  a.x0 = bg.x0;
+  a.y0 = bg.y0;
+  a.bt = 1.0 / bg.inv_bt;
+  a.rho = rho;
+  a.on_tol = P.on_tol;
+  a.nbx = bg.nbx;
+  a.nby = bg.nby;
+  launch_jet_fit(a, s);
+  P.launches += 4;
+  if (host_j) cudaMemcpyAsync(jet, dj, nt * 6 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  const cudaError_t e = cudaStreamSynchronize(s);
+  cudaFree(tmp);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return LP_ERR_CUDA;
+  }
   return status_from_cuda();
 }
 

@@ -225,6 +225,22 @@ struct InterpDDArgs {
   float2 coef[kMaxNC][kMaxW];  // weight polynomials, df64
 };
 
+// f-jet estimation from node values (k_jets.cu): nodes sorted into square
+// cells of side bt >= rho from (x0, y0), offsets from their cell corner.
+struct JetArgs {
+  const double* txy;
+  int64_t n;
+  double* jet;         // [n][6] out
+  const float2* rel;   // node offsets from their cell's corner, in cell order
+  const int* perm;     // node index of each sorted entry
+  const int* start;    // [ncells + 2] cell starts
+  const double* vxy;   // node coordinates (input order)
+  const double* vf;    // f at the nodes (input order)
+  double x0, y0, bt, rho, on_tol;
+  int nbx, nby;
+};
+void launch_jet_fit(const JetArgs& a, cudaStream_t s);
+
 // Argument record of the local pass (one per plan).
 struct LocalArgs {
   const double* txy;
@@ -374,6 +390,7 @@ struct Plan {
   int64_t v_cap = 0;         // capacity of d_vxy / d_vq
   double* d_vxy = nullptr;   // [nv][2]
   double* d_vq = nullptr;    // [nv] f w
+  double* d_vf = nullptr;    // [nv] f (node values, for lp_volume_jets)
   bool have_volume = false;
   double* d_sigma = nullptr;   // [nb]
   double* d_sigma_coef = nullptr;  // [n_panels][p] Legendre coefficients (centred)
