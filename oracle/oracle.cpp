@@ -437,7 +437,108 @@ void oracle_gl_weights(int p, const double* x, double* w) { gl_weights(p, x, w);
 // closed counter-clockwise curve; sigma/mu may be NULL.  jet: nt x 6 (may be
 // NULL -> volume part skipped).  Outputs (any may be NULL): VL, SL, DL.
 // info[i*4 + {0,1,2,3}] = {panel or -1 if far, t*, r, sgn}.  status bit 1:
+// Right-angle corners of a polygonal boundary (reading of C15): a junction
+// of two straight panels (every node on the chord to 1e-12 of its length)
+// whose directions are perpendicular to 1e-9 and turn left (a convex corner
+// of a counter-clockwise curve).  For each: the corner point (the two lines'
+// intersection) and the inward unit normals of the edge before (n1) and after
+// (n2) it.
+struct Corner {
+  double cx, cy, n1x, n1y, n2x, n2y;
+};
+
+static bool straight_panel(const Panels& P, int ip, double* tx, double* ty) {
+  const double* a = P.xy + (size_t)ip * P.p * 2;
+  const double* b = a + (size_t)(P.p - 1) * 2;
+  const double L = std::hypot(b[0] - a[0], b[1] - a[1]);
+  if (!(L > 0.0)) return false;
+  *tx = (b[0] - a[0]) / L;
+  *ty = (b[1] - a[1]) / L;
+  for (int k = 1; k + 1 < P.p; ++k) {
+    const double* q = a + 2 * k;
+    const double off = (q[0] - a[0]) * (-*ty) + (q[1] - a[1]) * (*tx);
+    if (std::fabs(off) > 1e-12 * L) return false;
+  }
+  return true;
+}
+
+static std::vector<Corner> right_angle_corners(const Panels& P) {
+  std::vector<Corner> out;
+  for (int i = 0; i < P.n_panels; ++i) {
+    const int j = (i + 1) % P.n_panels;
+    double t1x, t1y, t2x, t2y;
+    if (!straight_panel(P, i, &t1x, &t1y) || !straight_panel(P, j, &t2x, &t2y)) continue;
+    if (std::fabs(t1x * t2x + t1y * t2y) > 1e-9 || t1x * t2y - t1y * t2x <= 0.0) continue;
+    // intersection of the line through panel i's last node along t1 and the
+    // line through panel j's first node along t2
+    const double* a = P.xy + ((size_t)i * P.p + P.p - 1) * 2;
+    const double* b = P.xy + (size_t)j * P.p * 2;
+    const double det = t1x * (-t2y) - t1y * (-t2x);
+    const double s = ((b[0] - a[0]) * (-t2y) - (b[1] - a[1]) * (-t2x)) / det;
+    Corner c;
+    c.cx = a[0] + s * t1x;
+    c.cy = a[1] + s * t1y;
+    c.n1x = -t1y;  // inward normal: the tangent turned left
+    c.n1y = t1x;
+    c.n2x = -t2y;
+    c.n2y = t2x;
+    out.push_back(c);
+  }
+  return out;
+}
+
+// Local volume integral over the quadrant {(y - c).n1 >= 0, (y - c).n2 >= 0}
+// for the quadratic f of the jet at x, at distances a = (x - c).n1 and
+// b = (x - c).n2 from the two edges: the heat kernel separates along n1 and
+// n2, so
+//   V = int_0^delta [f A0 B0 + f_1 A1 B0 + f_2 A0 B1 + f_11 A2 B0 / 2
+//                    + f_12 A1 B1 + f_22 A0 B2 / 2] dt,
+// with the one-dimensional moments M_k(e, t) = int_{-e}^inf s^k g_t(s) ds of
+// g_t(s) = exp(-s^2 / 4t) / sqrt(4 pi t):
+//   M0 = 1 - erfc(e / 2 sqrt t) / 2, M1 = sqrt(t / pi) exp(-e^2 / 4t),
+//   M2 = 2 t M0 - 2 t e g_t(e),
+// and derivatives of f along n1, n2.  The time integral: t = delta s^2,
+// composite Gauss-Legendre (16 points per piece) on s in [0, 1] with pieces
+// graded towards s = 0, where the moments behave like exp(-e^2 / 4 delta s^2).
+static double quadrant_volume(const double* J, double a, double b, const Corner& c, double delta) {
+  const double f = J[0];
+  const double f1 = J[1] * c.n1x + J[2] * c.n1y, f2 = J[1] * c.n2x + J[2] * c.n2y;
+  auto hess = [&](double ux, double uy, double vx, double vy) {
+    return J[3] * ux * vx + J[4] * (ux * vy + uy * vx) + J[5] * uy * vy;
+  };
+  const double f11 = hess(c.n1x, c.n1y, c.n1x, c.n1y), f22 = hess(c.n2x, c.n2y, c.n2x, c.n2y);
+  const double f12 = hess(c.n1x, c.n1y, c.n2x, c.n2y);
+  const double pi = 3.14159265358979323846;
+  auto moments = [&](double e, double t, double* m) {
+    const double g = std::exp(-e * e / (4.0 * t)) / std::sqrt(4.0 * pi * t);
+    m[0] = 1.0 - 0.5 * std::erfc(e / (2.0 * std::sqrt(t)));
+    m[1] = std::sqrt(t / pi) * std::exp(-e * e / (4.0 * t));
+    m[2] = 2.0 * t * m[0] - 2.0 * t * e * g;
+  };
+  double x16[16], w16[16];
+  gl_nodes(16, x16);
+  gl_weights(16, x16, w16);
+  const double edges[8] = {0.0, 1.0 / 1024, 1.0 / 256, 1.0 / 64, 1.0 / 16, 0.25, 0.5, 1.0};
+  double v = 0.0;
+  for (int piece = 0; piece < 7; ++piece)
+    for (int k = 0; k < 16; ++k) {
+      const double h = edges[piece + 1] - edges[piece];
+      const double sv = edges[piece] + 0.5 * h * (x16[k] + 1.0);
+      const double t = delta * sv * sv;
+      double A[3], B[3];
+      moments(a, t, A);
+      moments(b, t, B);
+      const double F = f * A[0] * B[0] + f1 * A[1] * B[0] + f2 * A[0] * B[1] + 0.5 * f11 * A[2] * B[0] +
+                       f12 * A[1] * B[1] + 0.5 * f22 * A[0] * B[2];
+      v += 0.5 * h * w16[k] * F * 2.0 * delta * sv;  // dt = 2 delta s ds; ds = (h/2) dx
+    }
+  return v;
+}
+
 // an exterior target lies inside the band where V_L is not available.
+// At order 5, a target within 12 sqrt(delta) of both edges of a convex
+// right-angle corner takes the quadrant integral (reading of C15) instead of
+// the nearest edge's half-plane.
 int oracle_local(int n_panels, int p, const double* bxy, const double* sigma, const double* mu,
                  int64_t nt, const double* txy, const double* jet, double delta, int order,
                  double on_tol, double* VL, double* SL, double* DL, double* info) {
@@ -457,6 +558,7 @@ int oracle_local(int n_panels, int p, const double* bxy, const double* sigma, co
     margin = std::max(margin, std::hypot(bxy[2 * k] - bxy[2 * j], bxy[2 * k + 1] - bxy[2 * j + 1]));
   }
   const double band = 12.0 * std::sqrt(delta);
+  const std::vector<Corner> corners = (jet && order >= 5 && p > 1) ? right_angle_corners(P) : std::vector<Corner>();
   int status = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(| : status)
   for (int64_t i = 0; i < nt; ++i) {
@@ -522,6 +624,14 @@ int oracle_local(int n_panels, int p, const double* bxy, const double* sigma, co
           vl = 0.0;
         } else {
           vl = local_volume(g, jet + 6 * i, delta, order);
+          for (const Corner& c : corners) {
+            const double a = (x - c.cx) * c.n1x + (y - c.cy) * c.n1y;
+            const double b = (x - c.cx) * c.n2x + (y - c.cy) * c.n2y;
+            if (a > -on_tol && b > -on_tol && a < band && b < band) {
+              vl = quadrant_volume(jet + 6 * i, std::max(a, 0.0), std::max(b, 0.0), c, delta);
+              break;
+            }
+          }
         }
       }
       if (info) {

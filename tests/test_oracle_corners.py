@@ -2,11 +2,14 @@
 boundary (the configuration of the 12M-node square).
 
 The paper's expansions (Sec. 4, eq. vplocO5) assume a smooth boundary.  The
-reading used at corners: the foot is the perpendicular foot on the nearest
-edge, with kappa = gamma''' = gamma'''' = 0, i.e. the local integral over the
-half-plane of that edge.  For a straight edge and a quadratic f the printed
-expansion with every term is that half-plane integral exactly, so the oracle
-must reproduce it to rounding:
+readings used at corners: a target within 12 sqrt(delta) of only one edge
+takes the perpendicular foot on that edge, with kappa = 0 and no higher
+derivatives of the curve, i.e. the local integral over the half-plane of
+that edge; a target within 12 sqrt(delta) of both edges of a convex
+right-angle corner takes the exact local integral over the quadrant (order
+5).  For a straight edge and a quadratic f the printed expansion with every
+term is that half-plane integral exactly, so the oracle must reproduce it to
+rounding:
 
   V_half(eta) = int_0^delta [(f + t f_xixi) M0 + f_eta M1 + f_etaeta M2 / 2] dt,
 
@@ -14,14 +17,13 @@ with the 1D heat kernel g_t(s) = exp(-s^2/4t)/sqrt(4 pi t), eta the distance to
 the edge and M_k = int_{-eta}^inf s^k g_t(s) ds:
 M0 = 1 - erfc(eta/(2 sqrt t))/2, M1 = sqrt(t/pi) exp(-eta^2/4t),
 M2 = 2t M0 - 2t eta g_t(eta).  Here the tangential moments of the Gaussian are
-0 and 2t, and the two directions separate.  This test checks that identity at
-targets in the corner region, where the nearest-edge choice matters.
+0 and 2t, and the two directions separate.
 
-It also measures what the reading misses.  For a right-angle corner the
-exact local integral runs over the quadrant and separates into the moments
-of both edges.  The gap is confined to targets within 12 sqrt(delta) of both
-edges; for constant f it is f int_0^delta M0(a) (1 - M0(b)) dt, at most
-delta f / 4, reached at the corner itself.
+For a right-angle corner the exact local integral runs over the quadrant and
+separates into the moments of both edges; the oracle must match it (here by
+scipy's adaptive quadrature in t) to rounding.  The test also measures what
+the nearest-edge reading alone would miss there: for constant f,
+f int_0^delta M0(a) (1 - M0(b)) dt, at most delta f / 4, at the corner.
 """
 import math
 
@@ -77,7 +79,8 @@ def _quadrant(jet, a, b, N1, N2, delta=DELTA):
 def _targets():
     """Points near the corner (1, 1) of [-1, 1]^2 at distances (a, b) from the
     edges x = 1 and y = 1, plus mirrored copies near the other corners."""
-    ab = [(0.02, 0.05), (0.05, 0.02), (0.1, 0.3), (0.3, 0.1), (0.004, 0.011), (0.2, 0.21), (0.06, 0.5)]
+    ab = [(0.02, 0.05), (0.05, 0.02), (0.1, 0.3), (0.3, 0.1), (0.004, 0.011), (0.2, 0.21), (0.06, 0.5),
+          (0.03, 0.45), (0.45, 0.01), (0.2, 0.6), (0.0, 0.1), (0.1, 0.0), (0.0, 0.0)]
     pts, dist = [], []
     for sx, sy in [(1, 1), (-1, 1), (-1, -1), (1, -1)]:
         for a, b in ab:
@@ -93,13 +96,40 @@ def test_nearest_edge_reading_is_the_half_plane_integral(oracle_lib):
     jet = np.column_stack([rng.uniform(0.5, 2.0, len(txy)), rng.uniform(-1, 1, (len(txy), 5))])
     VL, _, _, info, st = oracle_lib.local(bnd, None, None, txy, jet, DELTA, order=5, on_tol=1e-12)
     assert st == 0
+    band = 12 * math.sqrt(DELTA)
+    checked = 0
     for i, (a, b, sx, sy) in enumerate(dist):
+        if max(a, b) < band:
+            continue  # both edges in the band: the quadrant reading (next test)
+        checked += 1
         if a <= b:  # nearest edge x = sx: inward normal (-sx, 0), tangent along y
             eta, N, T = a, np.array([-sx, 0.0]), np.array([0.0, 1.0])
         else:       # nearest edge y = sy
             eta, N, T = b, np.array([0.0, -sy]), np.array([1.0, 0.0])
         ref = _half_plane(jet[i], eta, N, T)
         assert abs(VL[i] - ref) <= 1e-12 * DELTA * np.max(np.abs(jet[i])), (i, VL[i], ref)
+    assert checked == 16
+
+
+def test_quadrant_reading_at_right_angle_corners(oracle_lib):
+    """Targets within 12 sqrt(delta) of both edges of a corner of the square
+    (including the corner and points on either edge): the oracle's V_L is the
+    exact quadrant integral of the target's quadratic f."""
+    bnd = make_square_panels(1.0, 8, 16)
+    txy, dist = _targets()
+    rng = np.random.default_rng(13)
+    jet = np.column_stack([rng.uniform(0.5, 2.0, len(txy)), rng.uniform(-1, 1, (len(txy), 5))])
+    VL = oracle_lib.local(bnd, None, None, txy, jet, DELTA, order=5, on_tol=1e-12)[0]
+    band = 12 * math.sqrt(DELTA)
+    checked = 0
+    for i, (a, b, sx, sy) in enumerate(dist):
+        if max(a, b) >= band:
+            continue
+        checked += 1
+        # inward normals of the edges x = sx and y = sy
+        ref = _quadrant(jet[i], a, b, np.array([-sx, 0.0]), np.array([0.0, -sy]))
+        assert abs(VL[i] - ref) <= 1e-13 * np.max(np.abs(jet[i])), (i, a, b, VL[i], ref)
+    assert checked == 36
 
 
 def test_corner_gap_of_the_reading(oracle_lib):
@@ -117,8 +147,11 @@ def test_corner_gap_of_the_reading(oracle_lib):
     assert abs(gaps[0] - 0.25) < 1e-6          # at the corner: half of the half-plane's delta f / 2
     assert np.all(np.diff(gaps) < 0) and np.all(gaps[:-1] > 0)
     assert abs(gaps[-1]) < 1e-12               # second edge beyond 12 sqrt(delta): no gap
-    # the oracle itself follows the reading there as well (the gap is the reading's, not a bug)
+    # the oracle takes the quadrant there, closing the gap
     bnd = make_square_panels(1.0, 8, 16)
     x = np.array([[1 - 0.01, 1 - 0.01]])
     VL = oracle_lib.local(bnd, None, None, x, jet[None, :], DELTA, order=5, on_tol=1e-12)[0][0]
-    assert abs(VL - _half_plane(jet, 0.01, N1, T1)) < 1e-12 * DELTA
+    assert abs(VL - _quadrant(jet, 0.01, 0.01, N1, N2)) < 1e-13 * jet[0]
+    # order 4 keeps the nearest-edge reading (no quadrant form is truncated)
+    VL4 = oracle_lib.local(bnd, None, None, x, jet[None, :], DELTA, order=4, on_tol=1e-12)[0][0]
+    assert abs(VL4 - _half_plane(jet, 0.01, N1, T1)) < 1e-12 * DELTA
