@@ -163,6 +163,35 @@ __device__ void compose4(const T* F, const T* c, T* o) {
          F[4] * c[1] * c[1] * c[1] * c[1];
 }
 
+// Local volume integral over the quadrant of a convex right-angle corner
+// (C15) for the quadratic f of the jet J, at distances ea, eb from the edges
+// with inward normals n1, n2: the heat kernel separates along n1 and n2, so
+// the integrand at time t is the product of the one-dimensional moments
+// M_k(e) = int_{-e}^inf s^k g_t(s) ds of the Gaussian g_t of variance 2t,
+//   M0 = erfc(-e / 2 sqrt t) / 2, M1 = sqrt(t / pi) exp(-e^2 / 4t),
+//   M2 = 2t (M0 - e g_t(e)),
+// contracted with f and its derivatives along n1, n2; the time integral on
+// the plan's graded nodes.
+__device__ double corner_volume(const LocalArgs& a, const double* J, const double* c, double ea, double eb) {
+  const double f = J[0];
+  const double d1 = J[1] * c[2] + J[2] * c[3], d2 = J[1] * c[4] + J[2] * c[5];
+  const double h11 = J[3] * c[2] * c[2] + 2.0 * J[4] * c[2] * c[3] + J[5] * c[3] * c[3];
+  const double h22 = J[3] * c[4] * c[4] + 2.0 * J[4] * c[4] * c[5] + J[5] * c[5] * c[5];
+  const double h12 = J[3] * c[2] * c[4] + J[4] * (c[2] * c[5] + c[3] * c[4]) + J[5] * c[3] * c[5];
+  const double inv_sqrt_pi = 0.56418958354775628695;
+  double v = 0.0;
+  for (int k = 0; k < kCornerQuad; ++k) {
+    const double t = a.corner_q[k], st = sqrt(t);
+    const double ga = exp(-ea * ea / (4.0 * t)), gb = exp(-eb * eb / (4.0 * t));
+    const double A0 = 0.5 * erfc(-ea / (2.0 * st)), B0 = 0.5 * erfc(-eb / (2.0 * st));
+    const double A1 = st * inv_sqrt_pi * ga, B1 = st * inv_sqrt_pi * gb;
+    const double A2 = 2.0 * t * A0 - ea * st * inv_sqrt_pi * ga, B2 = 2.0 * t * B0 - eb * st * inv_sqrt_pi * gb;
+    v += a.corner_q[kCornerQuad + k] *
+         (f * A0 * B0 + d1 * A1 * B0 + d2 * A0 * B1 + 0.5 * h11 * A2 * B0 + h12 * A1 * B1 + 0.5 * h22 * A0 * B2);
+  }
+  return v;
+}
+
 __device__ __forceinline__ double far_volume(const LocalArgs& a, const double* J) {
   // delta f + delta^2/2 lap f (Sec. 4, after eq. vplocO5)
   double v = a.delta * J[0];
@@ -325,6 +354,17 @@ __device__ void local_near_one(const LocalArgs& a, int64_t i, int best) {
                 T(24.0) * (fxx + fee));
         }
         vl = v;
+        // within the band of both edges of a right-angle corner: the quadrant
+        if (a.order >= 5)
+          for (int q = 0; q < a.n_corners; ++q) {
+            const double* c = a.corners + 6 * q;
+            const double ea = (x - c[0]) * c[2] + (y - c[1]) * c[3];
+            const double eb = (x - c[0]) * c[4] + (y - c[1]) * c[5];
+            if (ea > -a.on_tol && eb > -a.on_tol && ea < a.band && eb < a.band) {
+              vl = (T)corner_volume(a, J, c, fmax(ea, 0.0), fmax(eb, 0.0));
+              break;
+            }
+          }
       }
     }
   }
@@ -491,6 +531,9 @@ LocalArgs make_local_args(const Plan& P, int64_t nt, const double* txy, const do
   a.on_tol = P.on_tol;
   a.order = P.order;
   a.status = P.d_status;
+  a.corners = P.d_corners;
+  a.n_corners = P.d_corner_q ? P.n_corners : 0;
+  a.corner_q = P.d_corner_q;
   return a;
 }
 

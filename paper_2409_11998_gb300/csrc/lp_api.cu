@@ -181,7 +181,8 @@ void destroy_plan(Plan& P) {
                   P.d_geo_coef32, P.d_keys, P.d_counts, P.d_cursor, P.d_vrel_s, P.d_vperm, P.d_vq_s,
                   P.d_vstart, P.d_sigma_coef32, P.d_mu_coef32, P.d_vrel_dd, P.d_vq_dd,
                   P.d_dy_tab, P.d_dy_rel, P.d_dy_nw, P.d_dy_sig, P.d_dy_mu,
-                  P.d_dy_rad, P.d_dy_wgl, P.d_dy_cell_start, P.d_dy_cell_panel, P.d_dy_ref, P.d_vf};
+                  P.d_dy_rad, P.d_dy_wgl, P.d_dy_cell_start, P.d_dy_cell_panel, P.d_dy_ref, P.d_vf,
+                  P.d_corners, P.d_corner_q};
   for (void* b : bufs) dfree(b);
   if (P.h_status) cudaFreeHost(P.h_status);
   for (auto& e : P.ev)

@@ -34,6 +34,7 @@ constexpr int kDyMaxDeg = 15;       // highest polynomial degree of a table piec
 constexpr int kDyTabVec = 5;        // float4 per table piece: c0..c3 as df64 pairs, c4..c15 as floats
 constexpr int kDyThreads = 256;     // threads per block of the refinement sums
 constexpr int kMaxFftStages = 24;   // radix stages of one df64 transform
+constexpr int kCornerQuad = 96;     // nodes of the corner time integral (6 graded pieces x 16)
 
 // Device status bits (OR-ed by kernels, read by lp_sync).
 enum : unsigned {
@@ -270,6 +271,11 @@ struct LocalArgs {
   double delta_sd;  // delta of the S and D expansions (delta / 4^J with dyadic refinement)
   int order;
   unsigned* status;
+  // convex right-angle corners [n_corners][6]: corner point, inward normals
+  // of the edge before and after it; time integral nodes t_k and weights
+  const double* corners;
+  int n_corners;
+  const double* corner_q;  // [2][kCornerQuad]: t, weight (dt included)
 };
 
 // Dyadic refinement sums over the band targets (k_dyadic.cu).
@@ -362,6 +368,9 @@ struct Plan {
   float* d_geo_coef32 = nullptr;  // FP32 copy of d_geo_coef (Newton start)
   float* d_sigma_coef32 = nullptr;  // FP32 copies of the density coefficients (FP32 local pass)
   float* d_mu_coef32 = nullptr;
+  double* d_corners = nullptr;   // [n_corners][6] convex right-angle corners (V_L by the quadrant)
+  int n_corners = 0;
+  double* d_corner_q = nullptr;  // [2][kCornerQuad] quadrature of the corner time integral
 
   // sorted-bin spread (FP32 path)
   BinGeom bins{};

@@ -269,9 +269,73 @@ lp_status fit_kernel_poly(Plan& P) {
   return LP_OK;  // best effort at the maximum degree (error recorded)
 }
 
+// Convex right-angle corners of a polygonal boundary (C15): consecutive
+// panels whose nodes lie on their chords (to 1e-12 of the chord) with
+// perpendicular directions (to 1e-9) turning left (counter-clockwise
+// curve).  Each: the intersection of the two edge lines and the inward
+// normals of the edge before and after the corner.  Targets within 12
+// sqrt(delta) of both edges take the quadrant form of the local volume
+// integral (order 5).
+static std::vector<double> find_corners(int64_t n_panels, int p, const double* xy) {
+  std::vector<double> out;
+  auto dir = [&](int64_t ip, double& tx, double& ty) {
+    const double* a = xy + (size_t)ip * p * 2;
+    const double* b = a + (size_t)(p - 1) * 2;
+    const double len = std::hypot(b[0] - a[0], b[1] - a[1]);
+    if (!(len > 0.0)) return false;
+    tx = (b[0] - a[0]) / len;
+    ty = (b[1] - a[1]) / len;
+    for (int k = 1; k < p - 1; ++k) {
+      const double* q = a + 2 * k;
+      if (std::fabs((q[1] - a[1]) * tx - (q[0] - a[0]) * ty) > 1e-12 * len) return false;
+    }
+    return true;
+  };
+  for (int64_t i = 0; i < n_panels && p > 1; ++i) {
+    const int64_t j = (i + 1) % n_panels;
+    double ux, uy, vx, vy;
+    if (!dir(i, ux, uy) || !dir(j, vx, vy)) continue;
+    if (std::fabs(ux * vx + uy * vy) > 1e-9 || ux * vy - uy * vx <= 0.0) continue;
+    const double* e = xy + ((size_t)i * p + p - 1) * 2;  // last node of the edge before
+    const double* f = xy + (size_t)j * p * 2;            // first node of the edge after
+    // e + s u = f + r v  =>  s = ((f - e) x v) / (u x v)
+    const double s = ((f[0] - e[0]) * vy - (f[1] - e[1]) * vx) / (ux * vy - uy * vx);
+    const double c[6] = {e[0] + s * ux, e[1] + s * uy, -uy, ux, -vy, vx};
+    out.insert(out.end(), c, c + 6);
+  }
+  return out;
+}
+
 lp_status build_boundary(Plan& P, const double* h_xy, const double* h_w, const double* h_nrm) {
   const int p = P.p;
   const int64_t nb = P.nb;
+  {
+    const std::vector<double> cor = find_corners(P.n_panels, p, h_xy);
+    if (!cor.empty()) {
+      P.n_corners = (int)(cor.size() / 6);
+      // time integral: t = delta s^2 on six pieces of s in [0, 1] graded
+      // towards 0, 16 Gauss-Legendre nodes each; weight = piece / 2 * w * 2 delta s
+      double x[16], w[16];
+      gauss_legendre(16, x, w);
+      const double edges[7] = {0.0, 1.0 / 2048, 1.0 / 128, 1.0 / 32, 1.0 / 8, 0.375, 1.0};
+      std::vector<double> q(2 * kCornerQuad);
+      for (int piece = 0; piece < 6; ++piece)
+        for (int k = 0; k < 16; ++k) {
+          const double h = edges[piece + 1] - edges[piece];
+          const double sv = edges[piece] + 0.5 * h * (x[k] + 1.0);
+          q[piece * 16 + k] = P.delta1 * sv * sv;
+          q[kCornerQuad + piece * 16 + k] = 0.5 * h * w[k] * 2.0 * P.delta1 * sv;
+        }
+      if (cudaMalloc((void**)&P.d_corners, cor.size() * sizeof(double)) != cudaSuccess ||
+          cudaMalloc((void**)&P.d_corner_q, q.size() * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return LP_ERR_NOMEM;
+      }
+      P.device_bytes += cor.size() * sizeof(double) + q.size() * sizeof(double);
+      cudaMemcpy(P.d_corners, cor.data(), cor.size() * sizeof(double), cudaMemcpyHostToDevice);
+      cudaMemcpy(P.d_corner_q, q.data(), q.size() * sizeof(double), cudaMemcpyHostToDevice);
+    }
+  }
   // margin: longest chord between consecutive nodes along the curve; any
   // point of the curve is within it of a node, so a target whose nearest
   // node is farther than band + margin is outside the band.
