@@ -308,6 +308,36 @@ lp_status lp_solve_dirichlet(lp_plan_t plan, const double* g, const double* f_je
 lp_status lp_solve_neumann(lp_plan_t plan, const double* g, const double* f_jet_b, double* u, double tol,
                            int max_iter, int restart, int* iterations, double* residual);
 
+/* Source sharding across GPUs with one exchange step (one process per GPU).
+ * Every rank holds a plan of the same domain, delta, tol, precision and
+ * options -- hence the same grids -- binds its own share of the volume nodes
+ * with lp_volume and the full layer densities with lp_single_layer /
+ * lp_double_layer (the local part of its targets needs them), and then:
+ *   lp_spread(plan, outputs, spread_layers): zero the grids of the outputs
+ *     (bit mask: 1 V, 2 S, 4 D) and spread the bound volume nodes into them,
+ *     and the boundary nodes too when spread_layers is nonzero (on exactly
+ *     one rank, so that the sum counts them once) -- Sec. 3, steps 2-3;
+ *   lp_grid_buffers(plan, ptrs, bytes, dtypes, n): the device buffers whose
+ *     elementwise sum over the ranks (an all-reduce) makes every rank's grids
+ *     those of all the sources: per history level the spread channels (V;
+ *     S; D as two dipole channels) in the plan's padded layout, dtype 0 for
+ *     double, 1 for float; and, last, two doubles of zero-mode strength sums
+ *     (used by FP32 plans).  *n: in, the capacity of the arrays; out, the
+ *     count (LP_ERR_ARG with *n set when the capacity is short; at most 9).
+ *     The buffers belong to the plan; reduce them in place on the plan's
+ *     stream (or after lp_sync).  LP_ERR_STATE before lp_spread;
+ *   lp_finish(plan, n_t, t_xy, f_jet, V, S, D): transforms, multiplier,
+ *     interpolation and local part from the grids as they stand (step 4 and
+ *     Sec. 4), for this rank's targets; outputs must be among the spread
+ *     ones (LP_ERR_STATE otherwise); device pointers only (LP_ERR_ARG).
+ * Without the all-reduce, lp_spread + lp_finish on one plan is lp_execute.
+ * The spread is linear in the sources, so the sum of the ranks' grids is the
+ * grid of all of them; only the volume and boundary spreads are sharded. */
+lp_status lp_spread(lp_plan_t plan, int outputs, int spread_layers);
+lp_status lp_grid_buffers(lp_plan_t plan, void** ptrs, int64_t* bytes, int* dtypes, int* n);
+lp_status lp_finish(lp_plan_t plan, int64_t n_t, const double* t_xy, const double* f_jet, double* V, double* S,
+                    double* D);
+
 /* f-jets at targets estimated from the bound node values, for callers that
  * have f only at the quadrature nodes (the paper computes the jets of
  * Sec. 4's volume expansion analytically, Sec. 6.1).  At each target t_xy[i]:

@@ -30,7 +30,7 @@ EXPORTS = ("lp_plan", "lp_volume", "lp_single_layer", "lp_double_layer", "lp_exe
            "lp_destroy", "lp_status_string", "lp_plan_info", "lp_stage_times", "lp_execute_noalloc",
            "lp_batch_create", "lp_batch_execute", "lp_batch_sync", "lp_batch_stage_times",
            "lp_batch_destroy", "lp_solve_dirichlet", "lp_execute_graph", "lp_solve_neumann",
-           "lp_sync_timeout", "lp_volume_jets")
+           "lp_sync_timeout", "lp_volume_jets", "lp_spread", "lp_grid_buffers", "lp_finish")
 
 
 class LpError(RuntimeError):
@@ -77,6 +77,9 @@ def _lib():
         L.lp_sync.argtypes = [vp]
         L.lp_sync_timeout.argtypes = [vp, d]
         L.lp_volume_jets.argtypes = [vp, i64, vp, vp]
+        L.lp_spread.argtypes = [vp, i32, i32]
+        L.lp_grid_buffers.argtypes = [vp, vp, vp, vp, ctypes.POINTER(i32)]
+        L.lp_finish.argtypes = [vp, i64, vp, vp, vp, vp, vp]
         L.lp_destroy.argtypes = [vp]
         L.lp_status_string.argtypes = [i32]
         L.lp_status_string.restype = ctypes.c_char_p
@@ -235,6 +238,28 @@ def lp_batch_destroy(batch):
 
 def lp_sync(plan):
     _check(_lib().lp_sync(plan), "lp_sync")
+
+
+def lp_spread(plan, outputs="VSD", spread_layers=True):
+    """Zero and spread the grids of the outputs (any of "V", "S", "D"): the
+    bound volume nodes, and the boundary nodes when spread_layers."""
+    mask = ("V" in outputs) * 1 + ("S" in outputs) * 2 + ("D" in outputs) * 4
+    _check(_lib().lp_spread(plan, int(mask), 1 if spread_layers else 0), "lp_spread")
+
+
+def lp_grid_buffers(plan):
+    """[(device pointer, bytes, dtype)] of the buffers to sum across ranks
+    (dtype "float64" or "float32")."""
+    n = ctypes.c_int(9)
+    ptrs = (ctypes.c_void_p * 9)()
+    nbytes = (ctypes.c_int64 * 9)()
+    dtypes = (ctypes.c_int * 9)()
+    _check(_lib().lp_grid_buffers(plan, ptrs, nbytes, dtypes, ctypes.byref(n)), "lp_grid_buffers")
+    return [(ptrs[i], nbytes[i], "float64" if dtypes[i] == 0 else "float32") for i in range(n.value)]
+
+
+def lp_finish(plan, n_t, t_xy, f_jet, V=None, S=None, D=None):
+    _check(_lib().lp_finish(plan, int(n_t), _ptr(t_xy), _ptr(f_jet), _ptr(V), _ptr(S), _ptr(D)), "lp_finish")
 
 
 def lp_volume_jets(plan, n_t, t_xy, f_jet):

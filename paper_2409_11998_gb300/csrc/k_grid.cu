@@ -314,7 +314,7 @@ InterpArgs<T> make_interp_args(const Plan& P, int64_t nt, const double* txy, dou
   a.zero_factor = P.lv[0].zero_mode + P.lv[1].zero_mode;  // 0 for an unused level
   a.l0 = P.l0;
   // FP32 path: the zero mode was removed from the FP32 tables
-  a.qsum = sizeof(T) == 8 ? nullptr : P.d_qsum;
+  a.qsum = sizeof(T) == 8 ? nullptr : (P.use_qred ? P.d_qred : P.d_qsum);
   if constexpr (sizeof(T) == 8) a.es = P.es; else a.es = P.es32;
   return a;
 }

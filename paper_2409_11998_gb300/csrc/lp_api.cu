@@ -182,7 +182,7 @@ void destroy_plan(Plan& P) {
                   P.d_vstart, P.d_sigma_coef32, P.d_mu_coef32, P.d_vrel_dd, P.d_vq_dd,
                   P.d_dy_tab, P.d_dy_rel, P.d_dy_nw, P.d_dy_sig, P.d_dy_mu,
                   P.d_dy_rad, P.d_dy_wgl, P.d_dy_cell_start, P.d_dy_cell_panel, P.d_dy_ref, P.d_vf,
-                  P.d_corners, P.d_corner_q};
+                  P.d_corners, P.d_corner_q, P.d_qred};
   for (void* b : bufs) dfree(b);
   if (P.h_status) cudaFreeHost(P.h_status);
   for (auto& e : P.ev)
@@ -989,21 +989,11 @@ static lp_status tune_grids(lp_plan_t h, int64_t n, const double* xy, const doub
   return st;
 }
 
-// Steps 2-4 and the local part on device buffers (stage events 2 .. 8):
-// zero the grids of the requested channels, spread (volume nodes through the
-// bins, or point-parallel with global atomics; boundary nodes
-// point-parallel), transform with the multiplier (the library's FFT chain,
-// or cuFFT with the multiplier kernel), interpolate, then the local
-// correction and the refinement sums.  dt, dj, dout: device targets, jets
-// and outputs; list, count: the near-boundary list of the local pass (one
-// int2 per target) and its counter; staged: an event the interpolation waits
-// for (targets copied on another stream), or null.  Allocates nothing.
-static void device_pipeline(Plan& P, int64_t nt, const double* dt, const double* dj, double* const* dout,
-                            bool wv, bool ws, bool wd, int2* list, int* count, cudaEvent_t staged,
-                            cudaStream_t s) {
-  // Steps 2-3: spread every requested channel onto both history grids:
-  // volume nodes through the bins (FP32 plans) or point-parallel with global
-  // atomics; boundary nodes point-parallel.
+// Steps 2-3 on device buffers (stage events 2, 10, 3): zero the grids of the
+// requested channels and spread onto them the bound volume nodes (when
+// `volume`: through the bins, or point-parallel with global atomics) and
+// boundary nodes (when `layers`: point-parallel).  Allocates nothing.
+static void spread_part(Plan& P, bool wv, bool ws, bool wd, bool volume, bool layers, cudaStream_t s) {
   for (int l = P.l0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
     if (wv) cudaMemsetAsync(G.chan[0], 0, G.chan_bytes, s);
@@ -1016,7 +1006,7 @@ static void device_pipeline(Plan& P, int64_t nt, const double* dt, const double*
   record_stage(P, 2, s);
   for (int l = P.l0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
-    if (wv && P.nv > 0) {
+    if (wv && volume && P.nv > 0) {
       if (P.binned) {
         spread_volume_binned(P, l, s);
       } else {
@@ -1042,9 +1032,20 @@ static void device_pipeline(Plan& P, int64_t nt, const double* dt, const double*
       bq[nq] = P.d_bq + 2 * P.nb;
       bg[nq++] = G.chan[3];
     }
-    if (nq) launch_spread(P, l, P.d_bxy, bq, nq, bg, P.nb, s);
+    if (nq && layers) launch_spread(P, l, P.d_bxy, bq, nq, bg, P.nb, s);
   }
   record_stage(P, 3, s);
+}
+
+// Step 4 and the local part from the spread grids (stage events 4 .. 8):
+// transform with the multiplier (the library's FFT chain, or cuFFT with the
+// multiplier kernel), interpolate, then the local correction and the
+// refinement sums.  dt, dj, dout: device targets, jets and outputs; list,
+// count: the near-boundary list of the local pass (one int2 per target) and
+// its counter; staged: an event the interpolation waits for (targets copied
+// on another stream), or null.  Allocates nothing.
+static void finish_part(Plan& P, int64_t nt, const double* dt, const double* dj, double* const* dout, bool wv,
+                        bool ws, bool wd, int2* list, int* count, cudaEvent_t staged, cudaStream_t s) {
   if (P.own_fft) {
     history_transforms(P, wv, ws, wd, s, true);
     if (staged) cudaStreamWaitEvent(s, staged, 0);
@@ -1076,6 +1077,13 @@ static void device_pipeline(Plan& P, int64_t nt, const double* dt, const double*
   record_stage(P, 11, s);
   launch_dyadic(P, nt, dt, dout[1], dout[2], list, count, s);
   record_stage(P, 8, s);
+}
+
+static void device_pipeline(Plan& P, int64_t nt, const double* dt, const double* dj, double* const* dout,
+                            bool wv, bool ws, bool wd, int2* list, int* count, cudaEvent_t staged,
+                            cudaStream_t s) {
+  spread_part(P, wv, ws, wd, true, true, s);
+  finish_part(P, nt, dt, dj, dout, wv, ws, wd, list, count, staged, s);
 }
 
 lp_status lp_execute(lp_plan_t h, int64_t nt, const double* txy, const double* jet, double* V,
@@ -1254,6 +1262,94 @@ lp_status lp_execute_noalloc(lp_plan_t h, int64_t nt, const double* txy, const d
   record_stage(P, 1, s);
   double* dout[3] = {V, S, D};
   device_pipeline(P, nt, txy, wv ? jet : nullptr, dout, wv, ws, wd, list, count, nullptr, s);
+  record_stage(P, 9, s);
+  return status_from_cuda();
+}
+
+lp_status lp_spread(lp_plan_t h, int outputs, int spread_layers) {
+  if (!h || outputs <= 0 || outputs > 7) return LP_ERR_ARG;
+  Plan& P = h->P;
+  const bool wv = outputs & 1, ws = outputs & 2, wd = outputs & 4;
+  if ((wv && !P.have_volume) || (spread_layers && ((ws && !P.have_sigma) || (wd && !P.have_mu))))
+    return LP_ERR_STATE;
+  if ((ws || wd) && P.nb == 0) return LP_ERR_STATE;
+  if (!P.d_qred && !dalloc(P, (void**)&P.d_qred, 2 * sizeof(double))) return LP_ERR_NOMEM;
+  cudaStream_t s = P.stream;
+  record_stage(P, 0, s);
+  record_stage(P, 1, s);
+  spread_part(P, wv, ws, wd, true, spread_layers != 0, s);
+  // the zero-mode sums this plan contributes (FP32 plans add the k = 0 term
+  // from them): the volume strengths when it spread V, sigma w when it
+  // spread the layers
+  cudaMemsetAsync(P.d_qred, 0, 2 * sizeof(double), s);
+  if (wv) cudaMemcpyAsync(P.d_qred, P.d_qsum, sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (ws && spread_layers) cudaMemcpyAsync(P.d_qred + 1, P.d_qsum + 1, sizeof(double), cudaMemcpyDeviceToDevice, s);
+  P.spread_outputs = outputs;
+  return status_from_cuda();
+}
+
+lp_status lp_grid_buffers(lp_plan_t h, void** ptrs, int64_t* bytes, int* dtypes, int* n) {
+  if (!h || !n || *n < 0) return LP_ERR_ARG;
+  const Plan& P = h->P;
+  if (!P.spread_outputs) return LP_ERR_STATE;
+  void* p[9];
+  int64_t b[9];
+  int t[9], k = 0;
+  const int gtype = P.precision == LP_FP64 ? 0 : 1;
+  for (int l = P.l0; l < 2; ++l) {
+    const GridLevel& G = P.lv[l];
+    const int chans[4] = {P.spread_outputs & 1 ? 0 : -1, P.spread_outputs & 2 ? 1 : -1,
+                          P.spread_outputs & 4 ? 2 : -1, P.spread_outputs & 4 ? 3 : -1};
+    for (int c : chans)
+      if (c >= 0) {
+        p[k] = G.chan[c];
+        b[k] = (int64_t)G.chan_bytes;
+        t[k++] = gtype;
+      }
+  }
+  p[k] = P.d_qred;
+  b[k] = 2 * sizeof(double);
+  t[k++] = 0;
+  if (*n < k || (k > 0 && (!ptrs || !bytes || !dtypes))) {
+    *n = k;
+    return *n == 0 ? LP_OK : LP_ERR_ARG;
+  }
+  for (int i = 0; i < k; ++i) {
+    ptrs[i] = p[i];
+    bytes[i] = b[i];
+    dtypes[i] = t[i];
+  }
+  *n = k;
+  return LP_OK;
+}
+
+lp_status lp_finish(lp_plan_t h, int64_t nt, const double* txy, const double* jet, double* V, double* S,
+                    double* D) {
+  if (!h || nt < 0 || nt > (int64_t)INT32_MAX) return LP_ERR_ARG;
+  if (nt > 0 && !txy) return LP_ERR_ARG;
+  Plan& P = h->P;
+  const bool wv = V != nullptr, ws = S != nullptr, wd = D != nullptr;
+  if (wv && nt > 0 && !jet) return LP_ERR_ARG;
+  const int want = (wv ? 1 : 0) | (ws ? 2 : 0) | (wd ? 4 : 0);
+  if (want & ~P.spread_outputs) return LP_ERR_STATE;
+  if ((ws && !P.have_sigma) || (wd && !P.have_mu)) return LP_ERR_STATE;  // their local parts
+  if (nt == 0 || !want) return LP_OK;
+  const void* bufs[5] = {txy, wv ? jet : nullptr, V, S, D};
+  for (const void* b : bufs)
+    if (b && !is_device_ptr(b)) return LP_ERR_ARG;
+  cudaStream_t s = P.stream;
+  if ((size_t)nt > P.near_cap) {
+    cudaStreamSynchronize(s);
+    drelease(P, P.d_near, P.near_cap * sizeof(int2));
+    P.near_cap = 0;
+    if (!dalloc(P, (void**)&P.d_near, nt * sizeof(int2))) return LP_ERR_NOMEM;
+    P.near_cap = nt;
+  }
+  if (!P.d_near_count && !dalloc(P, (void**)&P.d_near_count, sizeof(int))) return LP_ERR_NOMEM;
+  double* dout[3] = {V, S, D};
+  P.use_qred = true;
+  finish_part(P, nt, txy, wv ? jet : nullptr, dout, wv, ws, wd, P.d_near, P.d_near_count, nullptr, s);
+  P.use_qred = false;
   record_stage(P, 9, s);
   return status_from_cuda();
 }

@@ -410,6 +410,9 @@ struct Plan {
   double* d_bq = nullptr;    // [3][nb]: sigma w, mu nu1 w, mu nu2 w
   bool have_sigma = false, have_mu = false;
   double* d_qsum = nullptr;  // [2] FP64 sums of the V and S strengths (zero mode)
+  double* d_qred = nullptr;  // [2] the sums this plan's lp_spread contributed (summed across ranks)
+  int spread_outputs = 0;    // outputs (1 V, 2 S, 4 D) of the last lp_spread; 0: none
+  bool use_qred = false;     // lp_finish: the zero mode from d_qred
 
   // staging for host pointers
   void* d_stage = nullptr;

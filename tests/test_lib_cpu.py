@@ -87,6 +87,11 @@ def test_invalid_arguments_rejected_without_device(lib):
     for fn in (L.lp_sync, L.lp_destroy):
         assert fn(None) == 1
     assert L.lp_sync_timeout(None, 1.0) == 1
+    assert L.lp_volume_jets(None, 0, None, None) == 1
+    assert L.lp_spread(None, 7, 1) == 1
+    assert L.lp_finish(None, 0, None, None, None, None, None) == 1
+    n = ctypes.c_int(9)
+    assert L.lp_grid_buffers(None, None, None, None, ctypes.byref(n)) == 1
     dom.max_device_bytes = -1
     assert L.lp_plan(ctypes.byref(dom), 1e-3, 1e-9, ctypes.byref(h)) == 1
     dom.max_device_bytes = 0
