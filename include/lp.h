@@ -238,27 +238,31 @@ lp_status lp_execute_graph(lp_plan_t plan, int64_t n_t, const double* t_xy, cons
 
 /* Batched evaluation of a wave of independent problems (many uneven
  * problems, one launch per kernel per wave).  A batch owns only the
- * wave's argument records and candidate list; the member plans are ordinary
- * plans (each bound with lp_volume / lp_single_layer / lp_double_layer on a
- * stream the batch stream is ordered after, e.g. the same stream).
+ * wave's argument records, candidate list and worker streams; the member
+ * plans are ordinary plans (each bound with lp_volume / lp_single_layer /
+ * lp_double_layer on a stream the batch stream is ordered after, e.g. the
+ * same stream).
  *   lp_batch_create(stream, &b): the batch's work runs on stream.
  *   lp_batch_execute(b, n, plans, n_t, t_xy, f_jet, V, S, D): evaluates, for
  *     every member i, exactly what lp_execute(plans[i], n_t[i], t_xy[i],
  *     f_jet[i], V[i], S[i], D[i]) evaluates (Sec. 3 and Sec. 4 per problem),
- *     with one zeroing, one spread, one multiplier, one interpolation and one
- *     local classify + near launch for the whole wave; each member's FFTs are
- *     issued on the batch stream.  Arrays have n entries; V, S, D (and their
- *     entries) may be NULL; all buffers must be device memory (LP_ERR_ARG
- *     otherwise); all members must share precision and tolerance (one kernel
- *     shape per wave) and be distinct.  Asynchronous: lp_batch_sync waits,
- *     lp_sync(member) returns that member's device status.
+ *     with one zeroing launch, one spread launch for the boundary nodes (and
+ *     the volume nodes of plans without bins), one launch for the binned
+ *     volume spreads of every member and level, one interpolation launch
+ *     per arithmetic (df64, and the cuFFT path's), and one local classify +
+ *     near launch for the whole wave; each member's transform chain is
+ *     issued on one of 8 worker streams that fork from the batch stream
+ *     after the spreads and join it before the interpolation (plans on
+ *     cuFFT: on the batch stream, with one multiplier launch for them all).
+ *     Arrays have n entries; V, S, D (and their entries) may be NULL; all
+ *     buffers must be device memory (LP_ERR_ARG otherwise); all members must
+ *     share precision and kernel width (one kernel shape per wave) and be
+ *     distinct.  Asynchronous: lp_batch_sync waits, lp_sync(member) returns
+ *     that member's device status.
  *   lp_batch_stage_times(b, out[9]): {zeroing+record copy, spread, forward
  *     FFTs, multiplier, inverse FFTs, interpolation, local, total} in ms of
- *     the last wave, and the launches issued so far.  Zeroing, the boundary
- *     spread, the local pass and (for plans on cuFFT) the multiplier and
- *     interpolation are one launch each per wave; binned volume spreads, the
- *     library's FFT chain (timed as forward FFTs) and the double-float
- *     interpolation run per member on the batch stream. */
+ *     the last wave, and the launches issued so far.  With the library's
+ *     FFT chain the transforms are timed as forward FFTs. */
 lp_status lp_batch_create(void* stream, lp_batch_t* batch);
 lp_status lp_batch_execute(lp_batch_t batch, int n, const lp_plan_t* plans, const int64_t* n_t,
                            const double* const* t_xy, const double* const* f_jet, double* const* V,

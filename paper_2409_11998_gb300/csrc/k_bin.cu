@@ -91,12 +91,11 @@ __global__ void gather_q_kernel(const double* __restrict__ q, int64_t stride, in
 // its warps' patches at the end and adds the sum to the grid with global
 // atomics (neighbouring bins' patches overlap in the halo).
 template <int W, int NCW>
-__global__ void __launch_bounds__(kSubThreads) spread_sub_kernel(const __grid_constant__ SubArgs a) {
+__device__ __forceinline__ void spread_sub_bin(const SubArgs& a, int bx, int by) {
   extern __shared__ float smem[];  // [NCW][W] weight coefficients, then [nwarp][M*M] patches
   constexpr int NC = W * W, NP = (NC + 31) / 32;
   constexpr int NWARP = kSubThreads / 32;
   const int M = a.M, MM = M * M;
-  const int bx = blockIdx.x, by = blockIdx.y;
   const int key = by * a.nbx + bx;
   const int k0 = a.start[key], n_here = a.start[key + 1] - k0;
   if (n_here == 0) return;
@@ -245,12 +244,11 @@ __device__ __forceinline__ bool stencil_dd(dd u, int M, int& i0, dd& v) {
 //   Flush: each cell's counts become one double (integer normalisation, no
 //   FP64 arithmetic) added to the grid with an FP64 atomic.
 template <int W, int NT>
-__global__ void __launch_bounds__(NT, 4) spread_fx_kernel(const __grid_constant__ SubDDArgs a) {
+__device__ __forceinline__ void spread_fx_bin(const SubDDArgs& a, int bx, int by) {
   extern __shared__ float2 smd[];
   constexpr int NC = W * W, NP = (NC + 31) / 32, NWARP = NT / 32, CH = NT;
   constexpr int WS = 2 * W + 1;  // weight row stride (odd: conflict-free task stores)
   const int M = a.M, MM = M * M, nc = a.nc;
-  const int bx = blockIdx.x, by = blockIdx.y;
   const int key = by * a.nbx + bx;
   const int k0 = a.start[key], n_here = a.start[key + 1] - k0;
   if (n_here == 0) return;
@@ -390,6 +388,48 @@ __global__ void __launch_bounds__(NT, 4) spread_fx_kernel(const __grid_constant_
   }
 }
 
+
+// The binned spreads as kernels: one CTA per bin of one plan (grid = bins),
+// or, for a wave of plans, one CTA per bin of every record of the wave: the
+// record of block b is the last r with first[r] <= b (first[] holds each
+// record's first block, ascending; first[nrec] the total).
+__device__ __forceinline__ int wave_record(const int* __restrict__ first, int nrec, int b) {
+  int lo = 0, hi = nrec - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int W, int NCW>
+__global__ void __launch_bounds__(kSubThreads) spread_sub_kernel(const __grid_constant__ SubArgs a) {
+  spread_sub_bin<W, NCW>(a, blockIdx.x, blockIdx.y);
+}
+
+template <int W, int NCW>
+__global__ void __launch_bounds__(kSubThreads) spread_sub_wave_kernel(const SubArgs* __restrict__ recs,
+                                                                      const int* __restrict__ first, int nrec) {
+  const int r = wave_record(first, nrec, blockIdx.x);
+  const SubArgs& a = recs[r];
+  const int key = blockIdx.x - first[r];
+  spread_sub_bin<W, NCW>(a, key % a.nbx, key / a.nbx);
+}
+
+template <int W, int NT>
+__global__ void __launch_bounds__(NT, 4) spread_fx_kernel(const __grid_constant__ SubDDArgs a) {
+  spread_fx_bin<W, NT>(a, blockIdx.x, blockIdx.y);
+}
+
+template <int W, int NT>
+__global__ void __launch_bounds__(NT, 4) spread_fx_wave_kernel(const SubDDArgs* __restrict__ recs,
+                                                               const int* __restrict__ first, int nrec) {
+  const int r = wave_record(first, nrec, blockIdx.x);
+  const SubDDArgs& a = recs[r];
+  const int key = blockIdx.x - first[r];
+  spread_fx_bin<W, NT>(a, key % a.nbx, key / a.nbx);
+}
+
 }  // namespace
 
 void launch_bin_sort(const double* xy, int64_t n, const BinGeom& bg, int* keys, int* counts, int* cursor,
@@ -431,6 +471,12 @@ static size_t spread_fx_smem_nt(int M, int w, int nt) {
 
 size_t spread_sub_dd_smem(int M, int w) { return spread_fx_smem_nt(M, w, kSubDDThreads); }
 
+// dynamic shared memory of either binned spread for patch side M
+size_t spread_sub_smem(int M, int w, bool f64) {
+  if (f64) return spread_fx_smem_nt(M, w, kSubDDThreads);
+  return (size_t)(((sub_ncw(w) * w + 3) & ~3) + (kSubThreads / 32) * M * M) * sizeof(float);
+}
+
 #define LP_SUB_DD_CASES LP_CASE(4) LP_CASE(5) LP_CASE(6) LP_CASE(7) LP_CASE(8) LP_CASE(9) LP_CASE(10) \
   LP_CASE(11) LP_CASE(12) LP_CASE(13) LP_CASE(14) LP_CASE(15) LP_CASE(16)
 
@@ -440,6 +486,8 @@ bool spread_sub_dd_configure(int w) {
 #define LP_CASE(W)                                                                                     \
   case W:                                                                                              \
     return cudaFuncSetAttribute(spread_fx_kernel<W, kSubDDThreads>,                                     \
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&   \
+           cudaFuncSetAttribute(spread_fx_wave_kernel<W, kSubDDThreads>,                                \
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
     LP_SUB_DD_CASES
 #undef LP_CASE
@@ -479,6 +527,8 @@ bool spread_sub_configure(int w) {
 #define LP_CASE(W)                                                                         \
   case W:                                                                                  \
     return cudaFuncSetAttribute(spread_sub_kernel<W, W + 3>,                               \
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess && \
+           cudaFuncSetAttribute(spread_sub_wave_kernel<W, W + 3>,                          \
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
     LP_SUB_CASES
 #undef LP_CASE
@@ -497,6 +547,35 @@ void launch_spread_sub(const SubArgs& a, int w, cudaStream_t s) {
     LP_SUB_CASES
 #undef LP_CASE
     default: break;
+  }
+}
+
+// One launch for the binned spreads of a wave: recs[nrec] in device memory,
+// first[nrec + 1] their first blocks; smem: the largest record's need.
+void launch_spread_wave(int precision, int w, const void* recs, const int* first, int nrec, int nblocks,
+                        size_t smem, cudaStream_t s) {
+  if (nrec <= 0 || nblocks <= 0) return;
+  if (precision == LP_FP64) {
+    switch (w) {
+#define LP_CASE(W)                                                                                       \
+  case W:                                                                                                \
+    spread_fx_wave_kernel<W, kSubDDThreads><<<nblocks, kSubDDThreads, smem, s>>>((const SubDDArgs*)recs, \
+                                                                                 first, nrec);          \
+    break;
+      LP_SUB_DD_CASES
+#undef LP_CASE
+      default: break;
+    }
+  } else {
+    switch (w) {
+#define LP_CASE(W)                                                                                           \
+  case W:                                                                                                    \
+    spread_sub_wave_kernel<W, W + 3><<<nblocks, kSubThreads, smem, s>>>((const SubArgs*)recs, first, nrec); \
+    break;
+      LP_SUB_CASES
+#undef LP_CASE
+      default: break;
+    }
   }
 }
 

@@ -28,9 +28,7 @@ __device__ __forceinline__ bool dd_stencil(dd u, int g, int& i0, dd& v) {
 }
 
 template <int W>
-__global__ void __launch_bounds__(128) interp_dd_kernel(const __grid_constant__ InterpDDArgs a) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
+__device__ __forceinline__ void interp_dd_target(const InterpDDArgs& a, int64_t i) {
   const dd X = dd_from_double(a.txy[2 * i]), Y = dd_from_double(a.txy[2 * i + 1]);
   dd_acc acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   bool bad = false;
@@ -88,6 +86,28 @@ __global__ void __launch_bounds__(128) interp_dd_kernel(const __grid_constant__ 
     if (a.out[c]) a.out[c][i] = dd_to_double(acc_value(acc[c]));
 }
 
+template <int W>
+__global__ void __launch_bounds__(128) interp_dd_kernel(const __grid_constant__ InterpDDArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.n) interp_dd_target<W>(a, i);
+}
+
+// A wave of plans in one launch: block b serves record r = the last with
+// first[r] <= b (first[] ascending, each record's first block), targets
+// 128 (b - first[r]) + threadIdx.x of it.
+template <int W>
+__global__ void __launch_bounds__(128) interp_dd_wave_kernel(const InterpDDArgs* __restrict__ recs,
+                                                             const int* __restrict__ first, int nrec) {
+  int lo = 0, hi = nrec - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const InterpDDArgs& a = recs[lo];
+  const int64_t i = (int64_t)(blockIdx.x - first[lo]) * 128 + threadIdx.x;
+  if (i < a.n) interp_dd_target<W>(a, i);
+}
+
 }  // namespace
 
 void launch_interp_dd(const InterpDDArgs& a, int w, cudaStream_t s) {
@@ -97,6 +117,21 @@ void launch_interp_dd(const InterpDDArgs& a, int w, cudaStream_t s) {
 #define LP_CASE(W)                                         \
   case W:                                                  \
     interp_dd_kernel<W><<<blocks, 128, 0, s>>>(a);         \
+    break;
+    LP_CASE(4) LP_CASE(5) LP_CASE(6) LP_CASE(7) LP_CASE(8) LP_CASE(9) LP_CASE(10) LP_CASE(11) LP_CASE(12)
+    LP_CASE(13) LP_CASE(14) LP_CASE(15) LP_CASE(16)
+#undef LP_CASE
+    default: break;
+  }
+}
+
+void launch_interp_dd_wave(const InterpDDArgs* recs, const int* first, int nrec, int nblocks, int w,
+                           cudaStream_t s) {
+  if (nrec <= 0 || nblocks <= 0) return;
+  switch (w) {
+#define LP_CASE(W)                                                       \
+  case W:                                                                \
+    interp_dd_wave_kernel<W><<<nblocks, 128, 0, s>>>(recs, first, nrec); \
     break;
     LP_CASE(4) LP_CASE(5) LP_CASE(6) LP_CASE(7) LP_CASE(8) LP_CASE(9) LP_CASE(10) LP_CASE(11) LP_CASE(12)
     LP_CASE(13) LP_CASE(14) LP_CASE(15) LP_CASE(16)

@@ -344,8 +344,9 @@ lp_status setup_bins(Plan& P) {
   return LP_OK;
 }
 
-// FP64 plans: df64 spread of the volume channel on one level.
-void spread_binned_dd(const Plan& P, int l, cudaStream_t s) {
+// FP64 plans: argument record of the fixed-point spread of the volume
+// channel on one level.
+SubDDArgs make_spread_dd_args(const Plan& P, int l) {
   const GridLevel& G = P.lv[l];
   SubDDArgs a{};
   a.gd = grid_dev(G);
@@ -371,8 +372,12 @@ void spread_binned_dd(const Plan& P, int l, cudaStream_t s) {
       const float ch = (float)c;
       a.coef[k][t] = make_float2(ch, (float)(c - (double)ch));
     }
+  return a;
+}
+
+void spread_binned_dd(const Plan& P, int l, cudaStream_t s) {
   ++P.launches;
-  launch_spread_sub_dd(a, P.ker.w, s);
+  launch_spread_sub_dd(make_spread_dd_args(P, l), P.ker.w, s);
 }
 
 void spread_binned(const Plan& P, int l, cudaStream_t s);
@@ -385,8 +390,9 @@ void spread_volume_binned(const Plan& P, int l, cudaStream_t s) {
     spread_binned(P, l, s);
 }
 
-// FP32 spread of the volume channel on one level from the sorted nodes.
-void spread_binned(const Plan& P, int l, cudaStream_t s) {
+// FP32 plans: argument record of the spread of the volume channel on one
+// level from the sorted nodes.
+SubArgs make_spread_sub_args(const Plan& P, int l) {
   const GridLevel& G = P.lv[l];
   SubArgs a;
   a.gd = grid_dev(G);
@@ -402,8 +408,12 @@ void spread_binned(const Plan& P, int l, cudaStream_t s) {
   a.nby = P.bins.nby;
   a.M = P.sub_M[l];
   a.status = P.d_status;
+  return a;
+}
+
+void spread_binned(const Plan& P, int l, cudaStream_t s) {
   ++P.launches;
-  launch_spread_sub(a, P.ker.w, s);
+  launch_spread_sub(make_spread_sub_args(P, l), P.ker.w, s);
 }
 
 float2 split_host(double x) {
@@ -520,11 +530,8 @@ void history_transforms(const Plan& P, bool wv, bool ws, bool wd, cudaStream_t s
 
 // Step 4 after the FFT chain: interpolation from the chain's grids (df64
 // pairs for FP64 plans, floats for FP32 plans).
-void history_interp(const Plan& P, int64_t nt, const double* txy, double* const* dout, cudaStream_t s) {
-  if (P.precision != LP_FP64) {
-    launch_interp(P, nt, txy, dout[0], dout[1], dout[2], s);
-    return;
-  }
+// Argument record of the df64 interpolation of an FP64 plan on the FFT chain.
+InterpDDArgs make_interp_dd_args(const Plan& P, int64_t nt, const double* txy, double* const* dout) {
   InterpDDArgs a{};
   a.txy = txy;
   a.n = nt;
@@ -544,7 +551,15 @@ void history_interp(const Plan& P, int64_t nt, const double* txy, double* const*
   a.nc = P.es.nc;
   a.nf = P.es_float_steps;
   std::memcpy(a.coef, P.es_dd, sizeof(a.coef));
-  launch_interp_dd(a, P.ker.w, s);
+  return a;
+}
+
+void history_interp(const Plan& P, int64_t nt, const double* txy, double* const* dout, cudaStream_t s) {
+  if (P.precision != LP_FP64) {
+    launch_interp(P, nt, txy, dout[0], dout[1], dout[2], s);
+    return;
+  }
+  launch_interp_dd(make_interp_dd_args(P, nt, txy, dout), P.ker.w, s);
   ++P.launches;
 }
 

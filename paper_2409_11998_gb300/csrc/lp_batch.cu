@@ -1,9 +1,12 @@
 // Batched evaluation of a wave of independent plans (problems of different
-// sizes): one zeroing launch, one spread launch, one multiplier launch, one
+// sizes): one zeroing launch, one point-parallel spread launch (boundary
+// nodes), one binned-spread launch over every bin of every plan, one
 // interpolation launch and one local classify + one near launch for the whole
-// wave, each over an array of per-plan argument records with a per-block work
-// list; each plan's pruned FFTs are issued on the batch stream in between.
-// The arithmetic per item is the single-plan kernels' (same device functions).
+// wave, each over an array of per-plan argument records (with a per-block
+// work list, or each record's first block); each plan's transform chain runs
+// in between on one of several worker streams, so that small plans' chains
+// overlap.  The arithmetic per item is the single-plan kernels' (same device
+// functions).
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -17,8 +20,12 @@ struct lp_plan_s {
   Plan P;
 };
 
+constexpr int kBatchWorkers = 8;  // streams the plans' transform chains are spread over
+
 struct lp_batch_s {
   cudaStream_t stream = nullptr;
+  cudaStream_t work[kBatchWorkers] = {};
+  cudaEvent_t fork = nullptr, join[kBatchWorkers] = {};
   void* d_buf = nullptr;  // per-wave records and work lists
   void* h_buf = nullptr;  // pinned mirror
   size_t buf_cap = 0;
@@ -72,6 +79,15 @@ lp_status lp_batch_create(void* stream, lp_batch_t* out) {
     return LP_ERR_NOMEM;
   }
   for (auto& e : b->ev) cudaEventCreate(&e);
+  bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; k < kBatchWorkers && ok; ++k)
+    ok = cudaStreamCreateWithFlags(&b->work[k], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    lp_batch_destroy(b);
+    return LP_ERR_CUDA;
+  }
   *out = b;
   return LP_OK;
 }
@@ -86,6 +102,11 @@ lp_status lp_batch_destroy(lp_batch_t b) {
   if (b->d_count) cudaFree(b->d_count);
   for (auto& e : b->ev)
     if (e) cudaEventDestroy(e);
+  for (int k = 0; k < kBatchWorkers; ++k) {
+    if (b->work[k]) cudaStreamDestroy(b->work[k]);
+    if (b->join[k]) cudaEventDestroy(b->join[k]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   delete b;
   return LP_OK;
 }
@@ -137,6 +158,14 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
   std::vector<int2> iwork;
   std::vector<LocalArgs> loc;
   std::vector<int2> lwork;
+  // binned volume spreads and df64 interpolations: one record per plan and
+  // level (per plan), each with its first block in the wave's launch
+  std::vector<SubDDArgs> bdd;
+  std::vector<SubArgs> b32;
+  std::vector<int> bfirst(1, 0);
+  size_t bsmem = 0;
+  std::vector<InterpDDArgs> idd;
+  std::vector<int> ifirst(1, 0);
   const bool f64 = prec == LP_FP64;
   for (int i = 0; i < n; ++i) {
     const Plan& P = plans[i]->P;
@@ -161,10 +190,16 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
         else sp32.push_back(make_spread_args<float>(P, l, xy, q, nq, grids, cnt));
         for (int64_t j = 0; j < cnt; j += kBatchThreads) swork.push_back(make_int2(rec, (int)j));
       };
-      if (wv && !P.binned) {  // binned plans spread their volume nodes per plan below
+      if (wv && !P.binned) {  // binned plans: one launch over every bin of the wave below
         const double* q[1] = {P.d_vq};
         void* g[1] = {G.chan[0]};
         add_spread(P.d_vxy, q, 1, g, P.nv);
+      }
+      if (wv && P.binned && P.nv > 0) {
+        if (f64) bdd.push_back(make_spread_dd_args(P, l));
+        else b32.push_back(make_spread_sub_args(P, l));
+        bfirst.push_back(bfirst.back() + P.bins.nbx * P.bins.nby);
+        bsmem = std::max(bsmem, spread_sub_smem(P.sub_M[l], P.ker.w, f64));
       }
       const double* bq[3];
       void* bg[3];
@@ -190,8 +225,13 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
     double* vo = wv ? V[i] : nullptr;
     double* so = ws ? S[i] : nullptr;
     double* dout = wd ? D[i] : nullptr;
-    // FP64 plans on the FFT chain interpolate from df64 grids, per plan below
-    if (!(f64 && P.own_fft)) {
+    // FP64 plans on the FFT chain interpolate from df64 grids: one launch
+    // over all of them below
+    if (f64 && P.own_fft) {
+      double* outs[3] = {vo, so, dout};
+      idd.push_back(make_interp_dd_args(P, nt, t_xy[i], outs));
+      ifirst.push_back(ifirst.back() + (int)((nt + 127) / 128));
+    } else {
       int rec = f64 ? (int)in64.size() : (int)in32.size();
       if (f64) in64.push_back(make_interp_args<double>(P, nt, t_xy[i], vo, so, dout));
       else in32.push_back(make_interp_args<float>(P, nt, t_xy[i], vo, so, dout));
@@ -208,6 +248,9 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
   const size_t o_ma = pk.put(mult), o_mw = pk.put(mwork);
   const size_t o_ia = f64 ? pk.put(in64) : pk.put(in32), o_iw = pk.put(iwork);
   const size_t o_la = pk.put(loc), o_lw = pk.put(lwork);
+  const size_t o_ba = f64 ? pk.put(bdd) : pk.put(b32), o_bf = pk.put(bfirst);
+  const size_t o_da = pk.put(idd), o_df = pk.put(ifirst);
+  const int nbrec = (int)(f64 ? bdd.size() : b32.size()), ndrec = (int)idd.size();
   const size_t bytes = align_up(pk.img.size(), 256);
   if (bytes > b->buf_cap) {
     cudaStreamSynchronize(s);
@@ -241,21 +284,24 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
   cudaEventRecord(b->ev[1], s);
   launch_spread_batch(prec, w, d + o_sa, (const int2*)(d + o_sw), (int)swork.size(), s);
   b->launches += 2;
+  launch_spread_wave(prec, w, d + o_ba, (const int*)(d + o_bf), nbrec, bfirst.back(), bsmem, s);
+  if (nbrec) ++b->launches;
   const long long before = sum_launches(plans, n);
-  for (int i = 0; i < n; ++i) {
-    const Plan& P = plans[i]->P;
-    if (n_t[i] > 0 && V && V[i] && P.binned && P.nv > 0)
-      for (int l = P.l0; l < 2; ++l) spread_volume_binned(P, l, s);
-  }
   cudaEventRecord(b->ev[2], s);
-  // each plan's transforms on the batch stream: the whole FFT chain for plans
-  // on it (counted as forward transforms), else pruned cuFFT transforms
+  // each plan's transforms: the whole FFT chain for plans on it (counted as
+  // forward transforms), spread round-robin over the worker streams, which
+  // fork from the batch stream here and join it after; else pruned cuFFT
+  // transforms on the batch stream
+  cudaEventRecord(b->fork, s);
+  for (int k = 0; k < kBatchWorkers; ++k) cudaStreamWaitEvent(b->work[k], b->fork, 0);
+  int next = 0;
   for (int i = 0; i < n; ++i) {
     const Plan& P = plans[i]->P;
     const bool wv = V && V[i], ws = S && S[i], wd = D && D[i];
     if (n_t[i] == 0 || (!wv && !ws && !wd)) continue;
     if (P.own_fft) {
-      history_transforms(P, wv, ws, wd, s, false);
+      history_transforms(P, wv, ws, wd, b->work[next], false);
+      next = (next + 1) % kBatchWorkers;
       continue;
     }
     for (int l = P.l0; l < 2; ++l) {
@@ -269,6 +315,10 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
         fft_forward(P, l, 3);
       }
     }
+  }
+  for (int k = 0; k < kBatchWorkers; ++k) {
+    cudaEventRecord(b->join[k], b->work[k]);
+    cudaStreamWaitEvent(s, b->join[k], 0);
   }
   cudaEventRecord(b->ev[3], s);
   launch_multiplier_batch(prec, (const MultArgs*)(d + o_ma), (const int2*)(d + o_mw), (int)mwork.size(), s);
@@ -290,13 +340,8 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
   }
   cudaEventRecord(b->ev[5], s);
   launch_interp_batch(prec, w, d + o_ia, (const int2*)(d + o_iw), (int)iwork.size(), s);
-  for (int i = 0; i < n; ++i) {
-    const Plan& P = plans[i]->P;
-    const bool wv = V && V[i], ws = S && S[i], wd = D && D[i];
-    if (n_t[i] == 0 || (!wv && !ws && !wd) || !(f64 && P.own_fft)) continue;
-    double* outs[3] = {wv ? V[i] : nullptr, ws ? S[i] : nullptr, wd ? D[i] : nullptr};
-    history_interp(P, n_t[i], t_xy[i], outs, s);
-  }
+  launch_interp_dd_wave((const InterpDDArgs*)(d + o_da), (const int*)(d + o_df), ndrec, ifirst.back(), w, s);
+  if (ndrec) ++b->launches;
   cudaEventRecord(b->ev[6], s);
   launch_local_batch(prec, (const LocalArgs*)(d + o_la), (const int2*)(d + o_lw), (int)lwork.size(), b->d_list,
                      b->d_count, total_t, s);

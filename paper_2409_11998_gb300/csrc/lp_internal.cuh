@@ -510,6 +510,14 @@ void launch_fft_rows_inv(const FftRowArgs& a, int nchan, bool f64, cudaStream_t 
 void launch_fft_cols(const FftColArgs& a, int njobs, bool f64, cudaStream_t s);
 void launch_split_table(const double* src, float2* dst, int64_t n, cudaStream_t s);
 void launch_interp_dd(const InterpDDArgs& a, int w, cudaStream_t s);
+void launch_interp_dd_wave(const InterpDDArgs* recs, const int* first, int nrec, int nblocks, int w,
+                           cudaStream_t s);
+void launch_spread_wave(int precision, int w, const void* recs, const int* first, int nrec, int nblocks,
+                        size_t smem, cudaStream_t s);
+size_t spread_sub_smem(int M, int w, bool f64);
+SubDDArgs make_spread_dd_args(const Plan& P, int l);
+SubArgs make_spread_sub_args(const Plan& P, int l);
+InterpDDArgs make_interp_dd_args(const Plan& P, int64_t nt, const double* txy, double* const* dout);
 lp_status setup_dyadic(Plan& P, int levels);
 void launch_dyadic_dens(const Plan& P, int kind, cudaStream_t s);
 void launch_dyadic(const Plan& P, int64_t nt, const double* txy, double* S, double* D, const int2* list,

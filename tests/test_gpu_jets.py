@@ -45,11 +45,13 @@ def test_jets_and_volume_potential_from_node_values(lp, oracle_lib, name):
     scale = np.max(np.abs(ref), axis=0) + 1e-300
     err = np.max(np.abs(got[idx] - ref), axis=0) / scale
     assert err[0] < 1e-9 and np.all(err[1:] < 1e-5), err
-    # against the analytic jets the fit is a method error: small, not zero
+    # against the analytic jets the fit is a method error of a quadratic over
+    # three node spacings (starfish: RMS ~5% in the first derivatives, ~20%
+    # in the second, which enter V at delta^{3/2} and delta^2)
     inside = np.any(np.abs(p["tgt_jet"][idx]) > 0, axis=1)
     ana = p["tgt_jet"][idx][inside]
-    rel = np.max(np.abs(ref[inside] - ana), axis=0) / (np.max(np.abs(ana), axis=0) + 1e-300)
-    assert rel[0] < 0.05 and np.all(rel[1:3] < 0.3), rel
+    rel = np.sqrt(np.mean((ref[inside] - ana) ** 2, axis=0)) / (np.sqrt(np.mean(ana ** 2, axis=0)) + 1e-300)
+    assert rel[0] < 0.02 and np.all(rel[1:3] < 0.1) and np.all(rel[3:] < 0.5), rel
     # V from the estimated jets, against the oracle fed its own estimated jets
     out = ev.evaluate(tgt_xy=txy, tgt_jet=jet, want=("V",))
     q = dict(p)
