@@ -62,6 +62,29 @@ struct DD {
   __device__ static void store_tw(S* p, float4 v) { *p = v; }
   __device__ static V mul(V a, V t) { return cdd_mul(a, t); }
   __device__ static V mul_conj(V a, V t) { return cdd_mul_conj(a, t); }
+  // e^{-2 pi i m / R} (R = 8, 9) as df64 pairs (re.hi, re.lo, im.hi, im.lo)
+  template <int R>
+  __device__ static V stw(int m) {
+    constexpr float t8[8][4] = {{1.f, 0.f, 0.f, 0.f},
+                                {7.071067691e-01f, 1.210161749e-08f, -7.071067691e-01f, -1.210161749e-08f},
+                                {0.f, 0.f, -1.f, 0.f},
+                                {-7.071067691e-01f, -1.210161749e-08f, -7.071067691e-01f, -1.210161749e-08f},
+                                {-1.f, 0.f, 0.f, 0.f},
+                                {-7.071067691e-01f, -1.210161749e-08f, 7.071067691e-01f, 1.210161749e-08f},
+                                {0.f, 0.f, 1.f, 0.f},
+                                {7.071067691e-01f, 1.210161749e-08f, 7.071067691e-01f, 1.210161749e-08f}};
+    constexpr float t9[9][4] = {{1.f, 0.f, 0.f, 0.f},
+                                {7.660444379e-01f, 5.233693479e-09f, -6.427876353e-01f, 2.563984580e-08f},
+                                {1.736481786e-01f, -9.104927368e-10f, -9.848077297e-01f, -2.329113791e-08f},
+                                {-0.5f, 0.f, -8.660253882e-01f, -1.554362505e-08f},
+                                {-9.396926165e-01f, -4.323200908e-09f, -3.420201540e-01f, 1.067366018e-08f},
+                                {-9.396926165e-01f, -4.323200908e-09f, 3.420201540e-01f, -1.067366018e-08f},
+                                {-0.5f, 0.f, 8.660253882e-01f, 1.554362505e-08f},
+                                {1.736481786e-01f, -9.104927368e-10f, 9.848077297e-01f, 2.329113791e-08f},
+                                {7.660444379e-01f, 5.233693479e-09f, 6.427876353e-01f, -2.563984580e-08f}};
+    const float* e = R == 8 ? t8[m] : t9[m];
+    return cdd{dd{e[0], e[1]}, dd{e[2], e[3]}};
+  }
 };
 
 struct F32 {
@@ -84,15 +107,19 @@ struct F32 {
   __device__ static void store_tw(S* p, float4 v) { *p = make_float2(v.x, v.z); }
   __device__ static V mul(V a, V t) { return make_float2(a.x * t.x - a.y * t.y, a.x * t.y + a.y * t.x); }
   __device__ static V mul_conj(V a, V t) { return make_float2(a.x * t.x + a.y * t.y, a.y * t.x - a.x * t.y); }
+  template <int R>
+  __device__ static V stw(int m);
 };
 
-// radices 8, 9 and 16 (two-level small DFTs) for the single-precision chain
-// only; the double-float chain is bound by its arithmetic, not by the number
-// of shared-memory passes, and keeps radices 2, 3 and 4
+// radices 8 and 9 (two-level small DFTs) in the column transforms of both
+// chains, and 16 in the single-precision chain only (a double-float radix-16
+// butterfly would raise the register count of every stage of its kernel)
 template <class A>
-constexpr bool kHighRadix = false;
+constexpr bool kHighRadix = true;
+template <class A>
+constexpr bool kRadix16 = false;
 template <>
-constexpr bool kHighRadix<F32> = true;
+constexpr bool kRadix16<F32> = true;
 
 // e^{-2 pi i m / R} for the two-level small DFTs of the single-precision
 // chain (R = 8, 9, 16; m < R)
@@ -120,6 +147,11 @@ __device__ __forceinline__ float2 small_tw(int m) {
   return make_float2(t16[m][0], t16[m][1]);
 }
 
+template <int R>
+__device__ float2 F32::stw(int m) {
+  return small_tw<R>(m);
+}
+
 template <class A, int R>
 __device__ __forceinline__ void dft_small(typename A::V* v, bool inv);
 
@@ -142,7 +174,7 @@ __device__ __forceinline__ void dft_two_level(typename A::V* v, bool inv) {
     for (int k1 = 0; k1 < R1; ++k1) {
       V z = t[k1];
       if (n2 * k1 != 0) {
-        const V w = small_tw<R>(n2 * k1);
+        const V w = A::template stw<R>(n2 * k1);
         z = inv ? A::mul_conj(z, w) : A::mul(z, w);
       }
       y[n2 * R1 + k1] = z;
@@ -338,7 +370,7 @@ __device__ void fft_dif(typename A::S* x, const FftShape& sh, const TW& tw, int 
     else if constexpr (kHighRadix<A>) {
       if (R == 8) dif_stage<A, 8>(x, N, L, tw, t0, nt);
       else if (R == 9) dif_stage<A, 9>(x, N, L, tw, t0, nt);
-      else dif_stage<A, 16>(x, N, L, tw, t0, nt);
+      else if constexpr (kRadix16<A>) dif_stage<A, 16>(x, N, L, tw, t0, nt);
     }
     __syncthreads();
     L /= R;
@@ -357,7 +389,7 @@ __device__ void fft_dit_inv(typename A::S* x, const FftShape& sh, const TW& tw, 
     else if constexpr (kHighRadix<A>) {
       if (R == 8) dit_stage_inv<A, 8>(x, N, L, tw, t0, nt);
       else if (R == 9) dit_stage_inv<A, 9>(x, N, L, tw, t0, nt);
-      else dit_stage_inv<A, 16>(x, N, L, tw, t0, nt);
+      else if constexpr (kRadix16<A>) dit_stage_inv<A, 16>(x, N, L, tw, t0, nt);
     }
     __syncthreads();
     if (s > 0) L *= sh.radix[s - 1];
@@ -583,7 +615,7 @@ void launch_split_table(const double* src, float2* dst, int64_t n, cudaStream_t 
   if (n > 0) split_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, dst, n);
 }
 
-FftShape fft_shape(int n, bool high) {
+FftShape fft_shape(int n, bool high, bool r16) {
   FftShape s{};
   s.n = n;
   int m = n;
@@ -593,8 +625,8 @@ FftShape fft_shape(int n, bool high) {
       m /= r;
     }
   };
-  if (high) {  // powers of two as 16s, then one 8, 4 or 2; powers of three as 9s, then one 3
-    take(16);
+  if (high) {  // powers of two as 16s (if r16) or 8s, then one 8, 4 or 2; powers of three as 9s, then one 3
+    if (r16) take(16);
     if (m % 8 == 0) take(8);
   }
   take(4);

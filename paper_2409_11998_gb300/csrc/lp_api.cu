@@ -430,11 +430,11 @@ lp_status setup_fft_chain(Plan& P) {
   const bool f64 = P.precision == LP_FP64;
   for (int l = P.l0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
-    // FP32 column transforms use radices 8, 9, 16 as well (fewer passes:
-    // 0.278 -> 0.229 ms on the starfish); the half-length row transforms keep
-    // 2, 3, 4 (radix-9 rows of 1458 leave a third of the threads idle and
-    // measured slower, 0.189 -> 0.222 ms)
-    G.full = fft_shape(G.g, !f64);
+    // column transforms use radices 8, 9 (and for FP32 16) as well: fewer
+    // shared-memory passes (FP32: 0.278 -> 0.229 ms on the starfish); the
+    // half-length row transforms keep 2, 3, 4 (radix-9 rows of 1458 leave a
+    // third of the threads idle and measured slower, 0.189 -> 0.222 ms)
+    G.full = fft_shape(G.g, true, !f64);
     G.half = fft_shape(G.g / 2, false);
     if (G.full.nst <= 0 || G.half.nst <= 0 || (G.g & 1)) return LP_OK;
     if (fft_cols_smem(G.g, f64) > limit || fft_rows_smem(G.g, f64) > limit) return LP_OK;
@@ -677,8 +677,8 @@ lp_status lp_plan(const lp_domain* dom, double delta, double tol, lp_plan_t* out
     }
   }
   lp_status st = choose_levels(P);
+  if (st == LP_OK) st = fit_kernel_poly(P);  // the tables deconvolve by the fitted kernel
   if (st == LP_OK) st = build_tables(P);
-  if (st == LP_OK) st = fit_kernel_poly(P);
   const size_t rs = P.precision == LP_FP64 ? sizeof(double) : sizeof(float);
   for (int l = P.l0; l < 2 && st == LP_OK; ++l) {
     GridLevel& G = P.lv[l];

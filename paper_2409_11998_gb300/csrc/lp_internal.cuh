@@ -499,7 +499,7 @@ void launch_bin_sort_dd(const double* xy, int64_t n, const BinGeom& bg, int* key
 void launch_gather_q_dd(const double* q, const int* perm, int64_t n, float2* q_s, cudaStream_t s);
 size_t spread_sub_smem(const SubArgs& a, int w);
 void launch_spread_sub(const SubArgs& a, int w, cudaStream_t s);
-FftShape fft_shape(int n, bool high = false);  // high: radices 8, 9, 16 too (FP32 chain)
+FftShape fft_shape(int n, bool high = false, bool r16 = true);  // high: radices 8, 9 (and 16 if r16) too
 std::vector<float4> fft_twiddles(int g);
 std::vector<int> fft_dif_order(const FftShape& sh);
 bool fft_dd_configure();

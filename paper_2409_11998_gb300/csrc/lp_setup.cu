@@ -27,12 +27,6 @@ double fourier_cutoff(double delta, double eps) {
   return hi;
 }
 
-// ES kernel and its Fourier transform in grid-index units:
-// phihat(xi) = int_{-w/2}^{w/2} phi(2x/w) cos(xi x) dx, by Gauss-Legendre.
-double es_phi(double z, double beta) {
-  if (std::fabs(z) >= 1.0) return 0.0;
-  return std::exp(beta * (std::sqrt(1.0 - z * z) - 1.0));
-}
 }  // namespace
 
 void gauss_legendre(int p, double* x, double* w) {
@@ -118,23 +112,41 @@ lp_status choose_levels(Plan& P) {
   return LP_OK;
 }
 
+// Deconvolution factors: the Fourier transform, at the kept modes, of the
+// kernel the spread and the interpolation evaluate -- the fitted piecewise
+// polynomial (double coefficients for FP64 plans, their float roundings for
+// FP32 plans), not the exponential of semicircle it approximates.  Weight t
+// of a point at offset v in [-1/2, 1/2) is the kernel at grid distance
+// x = v + (w-1)/2 - t, so piece t covers x in [w/2 - t - 1, w/2 - t); the
+// kernel is even, and its cosine transform is summed piece by piece with 16
+// Gauss-Legendre nodes each.  Deconvolving by the kernel actually used
+// removes the fit error from the normalisation of every mode (measured on the
+// FP32 starfish: a systematic relative error of ~2.7e-6, proportional to the
+// potential itself, from a fit to 1e-7).
 lp_status build_tables(Plan& P) {
-  const int w = P.ker.w;
-  const double beta = P.ker.beta;
-  const int nq = 4 * w + 8;
-  std::vector<double> qx(nq), qw(nq);
-  gauss_legendre(nq, qx.data(), qw.data());
+  const int w = P.es.w, nc = P.es.nc;
+  const bool f32 = P.precision == LP_FP32;
+  double gx[16], gw[16];
+  gauss_legendre(16, gx, gw);
+  std::vector<double> px((size_t)w * 16), pv((size_t)w * 16), pw((size_t)w * 16);
+  for (int t = 0; t < w; ++t)
+    for (int q = 0; q < 16; ++q) {
+      const double v = 0.5 * gx[q];
+      double acc = f32 ? (double)P.es32.c[nc - 1][t] : P.es.c[nc - 1][t];
+      for (int k = nc - 2; k >= 0; --k) acc = acc * v + (f32 ? (double)P.es32.c[k][t] : P.es.c[k][t]);
+      px[t * 16 + q] = v + 0.5 * (w - 1) - t;
+      pv[t * 16 + q] = acc;
+      pw[t * 16 + q] = 0.5 * gw[q];
+    }
   for (int l = P.l0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
     const int K = G.K;
     std::vector<double> ph(K + 1);
     for (int m = 0; m <= K; ++m) {
-      double xi = 2.0 * kPi * m / G.g, s = 0.0;
-      for (int i = 0; i < nq; ++i) {
-        double x = 0.25 * w * (qx[i] + 1.0);  // [0, w/2]
-        s += qw[i] * es_phi(2.0 * x / w, beta) * std::cos(xi * x);
-      }
-      ph[m] = 2.0 * 0.25 * w * s;  // even integrand over [-w/2, w/2]
+      const double xi = 2.0 * kPi * m / G.g;
+      double s = 0.0;
+      for (size_t i = 0; i < px.size(); ++i) s += pw[i] * pv[i] * std::cos(xi * px[i]);
+      ph[m] = s;
     }
     const double scale = (G.dk / (2.0 * kPi)) * (G.dk / (2.0 * kPi));
     // the k = 0 multiplier without deconvolution (FP32 path adds it in FP64)
@@ -157,12 +169,6 @@ lp_status build_tables(Plan& P) {
   return LP_OK;
 }
 
-// Chebyshev interpolation of each stencil weight phi_t(v), v in [-1/2, 1/2),
-// converted to monomials in v (long double on the host).  The degree grows
-// until the interior weights are within tol/100 of the kernel; the two edge
-// weights reach the support edge z = +-1, where sqrt(1 - z^2) is not smooth,
-// and are accepted once within 4 e^{-beta} (the kernel's own value there,
-// below the kernel's truncation error).
 // Leading Horner steps of the df64 weight chains (even and odd parts in
 // v^2, see dd_stencil_weights) that may run in single precision: the largest
 // m <= 4 for which the float steps -- coefficients rounded to float, v^2
@@ -204,6 +210,12 @@ static int float_horner_steps(const Plan& P, double target) {
   return best;
 }
 
+// Chebyshev interpolation of each stencil weight phi_t(v), v in [-1/2, 1/2),
+// converted to monomials in v (long double on the host).  The degree grows
+// until the interior weights are within tol/100 of the kernel; the two edge
+// weights reach the support edge z = +-1, where sqrt(1 - z^2) is not smooth,
+// and are accepted once within 4 e^{-beta} (the kernel's own value there,
+// below the kernel's truncation error).
 lp_status fit_kernel_poly(Plan& P) {
   const int w = P.ker.w;
   const double beta = P.ker.beta, hw = P.ker.half_w;
