@@ -62,29 +62,6 @@ struct DD {
   __device__ static void store_tw(S* p, float4 v) { *p = v; }
   __device__ static V mul(V a, V t) { return cdd_mul(a, t); }
   __device__ static V mul_conj(V a, V t) { return cdd_mul_conj(a, t); }
-  // e^{-2 pi i m / R} (R = 8, 9) as df64 pairs (re.hi, re.lo, im.hi, im.lo)
-  template <int R>
-  __device__ static V stw(int m) {
-    constexpr float t8[8][4] = {{1.f, 0.f, 0.f, 0.f},
-                                {7.071067691e-01f, 1.210161749e-08f, -7.071067691e-01f, -1.210161749e-08f},
-                                {0.f, 0.f, -1.f, 0.f},
-                                {-7.071067691e-01f, -1.210161749e-08f, -7.071067691e-01f, -1.210161749e-08f},
-                                {-1.f, 0.f, 0.f, 0.f},
-                                {-7.071067691e-01f, -1.210161749e-08f, 7.071067691e-01f, 1.210161749e-08f},
-                                {0.f, 0.f, 1.f, 0.f},
-                                {7.071067691e-01f, 1.210161749e-08f, 7.071067691e-01f, 1.210161749e-08f}};
-    constexpr float t9[9][4] = {{1.f, 0.f, 0.f, 0.f},
-                                {7.660444379e-01f, 5.233693479e-09f, -6.427876353e-01f, 2.563984580e-08f},
-                                {1.736481786e-01f, -9.104927368e-10f, -9.848077297e-01f, -2.329113791e-08f},
-                                {-0.5f, 0.f, -8.660253882e-01f, -1.554362505e-08f},
-                                {-9.396926165e-01f, -4.323200908e-09f, -3.420201540e-01f, 1.067366018e-08f},
-                                {-9.396926165e-01f, -4.323200908e-09f, 3.420201540e-01f, -1.067366018e-08f},
-                                {-0.5f, 0.f, 8.660253882e-01f, 1.554362505e-08f},
-                                {1.736481786e-01f, -9.104927368e-10f, 9.848077297e-01f, 2.329113791e-08f},
-                                {7.660444379e-01f, 5.233693479e-09f, 6.427876353e-01f, -2.563984580e-08f}};
-    const float* e = R == 8 ? t8[m] : t9[m];
-    return cdd{dd{e[0], e[1]}, dd{e[2], e[3]}};
-  }
 };
 
 struct F32 {
@@ -111,15 +88,16 @@ struct F32 {
   __device__ static V stw(int m);
 };
 
-// radices 8 and 9 (two-level small DFTs) in the column transforms of both
-// chains, and 16 in the single-precision chain only (a double-float radix-16
-// butterfly would raise the register count of every stage of its kernel)
+// radices 8, 9 and 16 (two-level small DFTs) for the single-precision chain
+// only; the double-float chain is bound by its arithmetic, not by the number
+// of shared-memory passes, and keeps radices 2, 3 and 4 (its radix-8/9
+// butterflies, with df64 internal twiddles, measured slower)
 template <class A>
-constexpr bool kHighRadix = true;
-template <class A>
-constexpr bool kRadix16 = false;
+constexpr bool kHighRadix = false;
 template <>
-constexpr bool kRadix16<F32> = true;
+constexpr bool kHighRadix<F32> = true;
+template <class A>
+constexpr bool kRadix16 = kHighRadix<A>;
 
 // e^{-2 pi i m / R} for the two-level small DFTs of the single-precision
 // chain (R = 8, 9, 16; m < R)

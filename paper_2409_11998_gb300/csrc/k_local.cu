@@ -68,6 +68,51 @@ __device__ __forceinline__ void legendre_jets(const T* const* c, const T* ref, i
   }
 }
 
+// legendre_jets in double-float arithmetic (the FP32 units; GB300's FP64 rate
+// is 1/58 of theirs): the same recurrence, the stored coefficients as df64
+// pairs, the sums accumulated with error-free transforms; out = ref + sum in
+// double.  ~48 bits: the fourth derivatives, which enter at delta^2 and
+// reach ~8e3 at the starfish's concave tips, keep ~1e-12 relative.
+template <int ND, int NS>
+__device__ __forceinline__ void legendre_jets_dd(const float2* const* c, const double* ref, int p, double t,
+                                                 double (*out)[ND + 1]) {
+  const dd td = dd_from_double(t);
+  dd qm[ND + 1], qk[ND + 1];
+  dd_acc acc[NS][ND + 1];
+#pragma unroll
+  for (int j = 0; j <= ND; ++j) {
+    qm[j] = dd{0.f, 0.f};
+    qk[j] = dd{j == 0 ? 1.f : 0.f, 0.f};
+  }
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+#pragma unroll
+    for (int j = 0; j <= ND; ++j) acc[q][j] = dd_acc{0.f, 0.f};
+    acc[q][0] = dd_acc{c[q][0].x, c[q][0].y};
+  }
+  for (int k = 0; k + 1 < p; ++k) {
+    const float a = (float)(2 * k + 1), b = (float)(k * k);
+#pragma unroll
+    for (int j = ND; j >= 0; --j) {
+      dd tq = dd_mul(td, qk[j]);
+      if (j) tq = dd_add(tq, dd_mul_f(qk[j - 1], (float)j));
+      const dd qn = dd_sub(dd_mul_f(tq, a), dd_mul_f(qm[j], b));
+      qm[j] = qk[j];
+      qk[j] = qn;
+    }
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      const float2 ck = c[q][k + 1];
+#pragma unroll
+      for (int j = 0; j <= ND; ++j) acc_fma(acc[q][j], dd{ck.x, ck.y}, qk[j]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NS; ++q)
+#pragma unroll
+    for (int j = 0; j <= ND; ++j) out[q][j] = (j == 0 ? ref[q] : 0.0) + dd_to_double(acc_value(acc[q][j]));
+}
+
 // Foot of the perpendicular: panel, parameter, and the offset from the target
 // to the foot (gx, gy) with its squared length, always evaluated in double
 // precision so that the side of the boundary and the distance are exact to
@@ -114,14 +159,14 @@ __device__ Foot panel_foot(const LocalArgs& a, int ip, double t, double x, doubl
     }
     if (tf == tf) t = (double)tf;  // keep the node start if the phase failed
   }
-  const double* c64[2] = {a.geo_coef + off, a.geo_coef + off + a.p};
+  const float2* cdd[2] = {a.geo_coef_dd + off, a.geo_coef_dd + off + a.p};
   const double ref[2] = {rx, ry};
   Foot r;
   r.panel = ip;
   r.converged = false;
   for (int it = 0; it < 20; ++it) {
     double J[2][3];
-    legendre_jets<2, 2, double>(c64, ref, a.p, t, J);
+    legendre_jets_dd<2, 2>(cdd, ref, a.p, t, J);
     const double gx = J[0][0] - x, gy = J[1][0] - y;
     const double f = gx * J[0][1] + gy * J[1][1];
     const double s2 = J[0][1] * J[0][1] + J[1][1] * J[1][1];
@@ -251,7 +296,16 @@ __device__ void local_near_one(const LocalArgs& a, int64_t i, int best) {
                       want_d ? coef_ptr<T>(a.mu_coef, a.mu_coef32) + (size_t)ip * p : cgx};
     const T rs[4] = {T(0), T(0), want_s ? (T)a.sig_ref[ip] : T(0), want_d ? (T)a.mu_ref[ip] : T(0)};
     T JJ[4][5];
-    legendre_jets<4, 4, T>(cs, rs, p, (T)ft.t, JJ);
+    if constexpr (sizeof(T) == 8) {
+      // FP64 plans: the jets in double-float (the expansions themselves in double)
+      const float2* gdd = a.geo_coef_dd + (size_t)(2 * ip) * p;
+      const float2* cd[4] = {gdd, gdd + p, want_s ? a.sig_coef_dd + (size_t)ip * p : gdd,
+                             want_d ? a.mu_coef_dd + (size_t)ip * p : gdd};
+      const double rd[4] = {0.0, 0.0, want_s ? a.sig_ref[ip] : 0.0, want_d ? a.mu_ref[ip] : 0.0};
+      legendre_jets_dd<4, 4>(cd, rd, p, ft.t, JJ);
+    } else {
+      legendre_jets<4, 4, T>(cs, rs, p, (T)ft.t, JJ);
+    }
     const T* X = JJ[0];
     const T* Y = JJ[1];
     const T sp = hypot(X[1], Y[1]);
@@ -522,6 +576,9 @@ LocalArgs make_local_args(const Plan& P, int64_t nt, const double* txy, const do
   a.geo_coef32 = P.d_geo_coef32;
   a.sig_coef32 = P.d_sigma_coef32;
   a.mu_coef32 = P.d_mu_coef32;
+  a.geo_coef_dd = P.d_geo_coef_dd;
+  a.sig_coef_dd = P.d_sigma_coef_dd;
+  a.mu_coef_dd = P.d_mu_coef_dd;
   a.margin = P.margin;
   a.band = P.band;
   a.margin32 = (float)P.margin;

@@ -182,7 +182,8 @@ void destroy_plan(Plan& P) {
                   P.d_vstart, P.d_sigma_coef32, P.d_mu_coef32, P.d_vrel_dd, P.d_vq_dd,
                   P.d_dy_tab, P.d_dy_rel, P.d_dy_nw, P.d_dy_sig, P.d_dy_mu,
                   P.d_dy_rad, P.d_dy_wgl, P.d_dy_cell_start, P.d_dy_cell_panel, P.d_dy_ref, P.d_vf,
-                  P.d_corners, P.d_corner_q, P.d_qred};
+                  P.d_corners, P.d_corner_q, P.d_qred, P.d_geo_coef_dd, P.d_sigma_coef_dd,
+                  P.d_mu_coef_dd};
   for (void* b : bufs) dfree(b);
   if (P.h_status) cudaFreeHost(P.h_status);
   for (auto& e : P.ev)
@@ -430,11 +431,13 @@ lp_status setup_fft_chain(Plan& P) {
   const bool f64 = P.precision == LP_FP64;
   for (int l = P.l0; l < 2; ++l) {
     GridLevel& G = P.lv[l];
-    // column transforms use radices 8, 9 (and for FP32 16) as well: fewer
-    // shared-memory passes (FP32: 0.278 -> 0.229 ms on the starfish); the
-    // half-length row transforms keep 2, 3, 4 (radix-9 rows of 1458 leave a
-    // third of the threads idle and measured slower, 0.189 -> 0.222 ms)
-    G.full = fft_shape(G.g, true, !f64);
+    // FP32 column transforms use radices 8, 9, 16 as well (fewer passes:
+    // 0.278 -> 0.229 ms on the starfish); the half-length row transforms keep
+    // 2, 3, 4 (radix-9 rows of 1458 leave a third of the threads idle and
+    // measured slower, 0.189 -> 0.222 ms).  Double-float columns keep 2, 3, 4:
+    // radices 8 and 9 (df64 internal twiddles, 92 registers) measured slower
+    // on the starfish, 0.53 -> 0.66 ms
+    G.full = fft_shape(G.g, !f64);
     G.half = fft_shape(G.g / 2, false);
     if (G.full.nst <= 0 || G.half.nst <= 0 || (G.g & 1)) return LP_OK;
     if (fft_cols_smem(G.g, f64) > limit || fft_rows_smem(G.g, f64) > limit) return LP_OK;
@@ -881,6 +884,8 @@ static lp_status bind_layer(lp_plan_t h, const double* dens, int kind) {
   // single-precision copy for the local expansions (both precisions)
   launch_to_float(kind == 0 ? P.d_sigma_coef : P.d_mu_coef, kind == 0 ? P.d_sigma_coef32 : P.d_mu_coef32,
                   P.n_panels * P.p, P.stream);
+  launch_split_table(kind == 0 ? P.d_sigma_coef : P.d_mu_coef, kind == 0 ? P.d_sigma_coef_dd : P.d_mu_coef_dd,
+                     P.n_panels * P.p, P.stream);
   ++P.launches;
   launch_strengths(P, kind, P.stream);
   if (kind == 0) {

@@ -267,6 +267,9 @@ struct LocalArgs {
   const float* geo_coef32;   // FP32 copy of geo_coef
   const float* sig_coef32;   // FP32 copies of sig_coef / mu_coef (FP32 plans)
   const float* mu_coef32;
+  const float2* geo_coef_dd;  // df64 copies of geo_coef, sig_coef, mu_coef
+  const float2* sig_coef_dd;
+  const float2* mu_coef_dd;
   double margin, band, delta, on_tol;
   double delta_sd;  // delta of the S and D expansions (delta / 4^J with dyadic refinement)
   int order;
@@ -366,6 +369,9 @@ struct Plan {
   int* d_cell_node = nullptr;   // [nb] node ids sorted by cell
   float2* d_cell_xy32 = nullptr;  // [nb] node coordinates relative to their cell's origin (FP32)
   float* d_geo_coef32 = nullptr;  // FP32 copy of d_geo_coef (Newton start)
+  float2* d_geo_coef_dd = nullptr;    // df64 copies of the panel coefficients (foot search,
+  float2* d_sigma_coef_dd = nullptr;  // jets of the FP64 expansions)
+  float2* d_mu_coef_dd = nullptr;
   float* d_sigma_coef32 = nullptr;  // FP32 copies of the density coefficients (FP32 local pass)
   float* d_mu_coef32 = nullptr;
   double* d_corners = nullptr;   // [n_corners][6] convex right-angle corners (V_L by the quadrant)

@@ -445,7 +445,10 @@ lp_status build_boundary(Plan& P, const double* h_xy, const double* h_w, const d
       !dmalloc((void**)&P.d_mu_coef, (size_t)P.n_panels * p * sizeof(double)) ||
       !dmalloc((void**)&P.d_mu_ref, (size_t)P.n_panels * sizeof(double)) ||
       !dmalloc((void**)&P.d_sigma_coef32, (size_t)P.n_panels * p * sizeof(float)) ||
-      !dmalloc((void**)&P.d_mu_coef32, (size_t)P.n_panels * p * sizeof(float)))
+      !dmalloc((void**)&P.d_mu_coef32, (size_t)P.n_panels * p * sizeof(float)) ||
+      !dmalloc((void**)&P.d_geo_coef_dd, (size_t)P.n_panels * 2 * p * sizeof(float2)) ||
+      !dmalloc((void**)&P.d_sigma_coef_dd, (size_t)P.n_panels * p * sizeof(float2)) ||
+      !dmalloc((void**)&P.d_mu_coef_dd, (size_t)P.n_panels * p * sizeof(float2)))
     return LP_ERR_NOMEM;
   cudaMemcpy(P.d_bxy, h_xy, nb * 2 * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemcpy(P.d_bw, h_w, nb * sizeof(double), cudaMemcpyHostToDevice);
@@ -457,6 +460,7 @@ lp_status build_boundary(Plan& P, const double* h_xy, const double* h_w, const d
   if (nb) cudaMemcpy(P.d_cell_xy32, rel.data(), nb * sizeof(float2), cudaMemcpyHostToDevice);
   launch_panel_coef(P, P.d_bxy, 2, 2, P.d_geo_coef, P.d_geo_ref, P.stream);
   launch_to_float(P.d_geo_coef, P.d_geo_coef32, P.n_panels * 2 * p, P.stream);
+  launch_split_table(P.d_geo_coef, P.d_geo_coef_dd, P.n_panels * 2 * p, P.stream);
   if (cudaStreamSynchronize(P.stream) != cudaSuccess) return LP_ERR_CUDA;
   return LP_OK;
 }
