@@ -248,12 +248,24 @@ def run_lp(args, rank, world, local_rank):
             res["fp32_same_workload"] = run_fp32(args, prob, dev, stream, points)
             gpu_out["fp32"] = res["fp32_same_workload"].pop("_outputs")
         if args.workload == "starfish":
+            res["square"] = run_square(args, dev, stream)
+            wave = run_batch(args, rank, world, local_rank)
+            res["batch"] = {"workload": wave["config"]["workload"], "points_per_wave": wave["config"]["points_per_wave"],
+                            **wave["batch"]}
             res["served"] = run_serve(args, rank, world, local_rank, rates=(50, 200, 1000), seconds=1.5,
                                       max_requests=1200)
         if world == 1:
+            checks = {}
+            if "square" in res:
+                checks["square"] = res["square"].pop("_check")
             res["cpu_baseline"] = cpu_baseline(prob, budget_s=15.0, refine_levels=args.refine_levels,
-                                               gpu_out=gpu_out)
+                                               gpu_out=gpu_out, checks=checks)
             res["parity"] = res["cpu_baseline"].pop("_parity")
+            for name, par in res["cpu_baseline"].pop("_checks").items():
+                for prec, p in par.items():
+                    res[name][prec]["parity"] = p
+        elif "square" in res:
+            res["square"].pop("_check")
     ev.close()
     return res
 
@@ -492,6 +504,59 @@ def run_fp32(args, prob, dev, stream, points):
             "_outputs": {k: o.cpu().numpy() for k, o in zip("VSD", outs) if o is not None}}
 
 
+def run_square(args, dev, stream, steps=10):
+    """The 12M-node square (2M jittered triangles, 1M vertex targets, V
+    only) at FP64 1e-9 and FP32 1e-5: device-resident inputs, CUDA events
+    around bind + execute, L2 flushed between steps.  The outputs go back
+    with the result for the CPU-baseline leg to compare with the oracle."""
+    import numpy as np
+    import torch
+    import paper_2409_11998_gb300 as lp
+    from workloads import configs
+    prob = configs.square(precision="fp64", tol=1e-9)
+    nv, nt = len(prob["src_w"]), len(prob["tgt_xy"])
+    nb = len(prob["bnd"]["w"])
+    points = nv + nb + nt
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    sxy, sw, sf, txy, jet = (T(prob[k]) for k in ("src_xy", "src_w", "src_f", "tgt_xy", "tgt_jet"))
+    out = torch.empty(nt, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res = {"workload": "[-1,1]^2, 2M jittered triangles (12M nodes), f = 1 + 32 Gaussians, targets = 1,002,001 "
+                       "vertices (corners and edges included), V only",
+           "points_per_step": points}
+    outs = {}
+    for prec, tol in (("fp64", 1e-9), ("fp32", 1e-5)):
+        ev = lp.Evaluator(prob, precision=prec, tol=tol, stream=stream.cuda_stream)
+        plan = ev.plan
+
+        def step():
+            lp.lp_volume(plan, nv, sxy, sw, sf)
+            lp.lp_execute(plan, nt, txy, jet, out, None, None)
+
+        for _ in range(3):
+            step()
+            lp.lp_sync(plan)
+        ms = []
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                step()
+                b.record(stream)
+            lp.lp_sync(plan)
+            ms.append(a.elapsed_time(b))
+        outs[prec] = {"V": out.cpu().numpy()}
+        res[prec] = {"ms_per_step": statistics.mean(ms), "points_per_s": points / (statistics.mean(ms) / 1e3),
+                     "tol": tol, "stages_ms": {k: round(v, 4) for k, v in lp.lp_stage_times(plan).items()},
+                     "grids": {"g_nh": int(ev.info()["g_nh"]), "g_fh": int(ev.info()["g_fh"]),
+                               "w": int(ev.info()["w"])}}
+        ev.close()
+    del flush
+    res["_check"] = (prob, outs)   # compared with the oracle in the CPU-baseline leg
+    return res
+
+
 def oracle_sample(prob, n, rng):
     """n targets: nine tenths drawn uniformly, one tenth from the band near
     the boundary (every k-th target by distance to the nearest boundary
@@ -527,11 +592,13 @@ def parity(gpu, ref, idx):
     return out
 
 
-def cpu_baseline(prob, budget_s=15.0, refine_levels=0, gpu_out=None):
+def cpu_baseline(prob, budget_s=15.0, refine_levels=0, gpu_out=None, checks=None):
     """The oracle as it stands, on the host cores, on a bounded sample of
     targets; extrapolated to the workload's points/s.  The last (largest)
     sample also gives the error of every GPU result of the run against the
-    oracle (outside every timed region)."""
+    oracle, and `checks` ({name: (problem, {precision: outputs})}) the error
+    of other workloads' results on a 2000-target sample each (outside every
+    timed region)."""
     import numpy as np
     ncores = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(ncores))
@@ -551,11 +618,17 @@ def cpu_baseline(prob, budget_s=15.0, refine_levels=0, gpu_out=None):
     t_full = per_target * nt
     points = len(prob["src_w"]) + len(prob["bnd"]["w"]) + nt
     par = {prec: parity(out, ref, idx) for prec, out in (gpu_out or {}).items()}
+    extra = {}
+    for name, (q, outs) in (checks or {}).items():
+        qidx = oracle_sample(q, 2000, np.random.default_rng(11))
+        qref = oracle.evaluate(q, targets=qidx, want=tuple(next(iter(outs.values())).keys()))
+        extra[name] = {prec: parity(o, qref, qidx) for prec, o in outs.items()}
     par["sample"] = (f"{len(idx)} targets: {len(idx) - len(idx) // 10} uniform, {len(idx) // 10} from the "
                      f"boundary band; oracle = direct FP64 sums + the same local expansions")
     return {"value": points / t_full, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", ncores)),
             "kind": "oracle", "sample": f"{n} of {nt} targets (all sources), {dt:.2f} s; "
-            f"extrapolated linearly in targets to the full workload ({t_full:.0f} s)", "_parity": par}
+            f"extrapolated linearly in targets to the full workload ({t_full:.0f} s)", "_parity": par,
+            "_checks": extra}
 
 
 # ---------------------------------------------------------------- batched waves of uneven problems
