@@ -13,10 +13,11 @@ def _info(precision):
 def test_fp64_roofline_spread_or_interp():
     st = {"spread": 1.2, "spread_volume": 1.0, "multiplier": 0.5, "interp": 0.8}
     r = bench.roofline(_info(0), st, 1_000_000, 16384, 1_000_000, "fp64", workload="none")
-    assert r["kernel"] == "spread_sub_dd_kernel" and r["bound"] == "alu"
+    assert r["kernel"] == "spread_fx_kernel" and r["bound"] == "alu"
     # no ncu count for workload "none": the algorithmic estimate, 15 FP32
-    # instructions per df64 multiply-add, 32 lanes per warp instruction
-    inst = 1_000_000 * 2 * (2 * 12 * 12 + 12 * 13) * 15 / 32
+    # instructions per df64 multiply-add of the weight polynomials and 14
+    # per fixed-point cell update, 32 lanes per warp instruction
+    inst = 1_000_000 * 2 * (2 * 12 * 12 * 15 + 12 * 12 * 14) / 32
     assert r["instructions_per_step"] == int(inst) and r["instructions_source"].startswith("estimate")
     assert abs(r["achieved"] - inst / 1.0e-3 / 1e12) < 1e-3
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-3
@@ -49,7 +50,7 @@ def test_single_level_plans_count_one_level():
     info = dict(_info(0), g_nh=0, K_nh=0)
     st = {"spread": 1.0, "spread_volume": 1.0, "multiplier": 0.5, "interp": 0.2}
     r = bench.roofline(info, st, 1000, 0, 1000, "fp64", workload="none")
-    assert r["instructions_per_step"] == int(1000 * 1 * (2 * 12 * 12 + 12 * 13) * 15 / 32)
+    assert r["instructions_per_step"] == int(1000 * 1 * (2 * 12 * 12 * 15 + 12 * 12 * 14) / 32)
     assert r["hbm"]["algorithmic_bytes_per_step"] == 1000 * 24 + 1024 ** 2 * 8
 
 
