@@ -437,7 +437,7 @@ void oracle_gl_weights(int p, const double* x, double* w) { gl_weights(p, x, w);
 // closed counter-clockwise curve; sigma/mu may be NULL.  jet: nt x 6 (may be
 // NULL -> volume part skipped).  Outputs (any may be NULL): VL, SL, DL.
 // info[i*4 + {0,1,2,3}] = {panel or -1 if far, t*, r, sgn}.  status bit 1:
-// Right-angle corners of a polygonal boundary (reading of C15): a junction
+// Right-angle corners of a polygonal boundary (a reading beyond Sec. 4, which assumes a smooth curve): a junction
 // of two straight panels (every node on the chord to 1e-12 of its length)
 // whose directions are perpendicular to 1e-9 and turn left (a convex corner
 // of a counter-clockwise curve).  For each: the corner point (the two lines'
@@ -537,7 +537,7 @@ static double quadrant_volume(const double* J, double a, double b, const Corner&
 
 // an exterior target lies inside the band where V_L is not available.
 // At order 5, a target within 12 sqrt(delta) of both edges of a convex
-// right-angle corner takes the quadrant integral (reading of C15) instead of
+// right-angle corner takes the quadrant integral (the same reading) instead of
 // the nearest edge's half-plane.
 int oracle_local(int n_panels, int p, const double* bxy, const double* sigma, const double* mu,
                  int64_t nt, const double* txy, const double* jet, double delta, int order,

@@ -209,31 +209,43 @@ __device__ void compose4(const T* F, const T* c, T* o) {
 }
 
 // Local volume integral over the quadrant of a convex right-angle corner
-// (C15) for the quadratic f of the jet J, at distances ea, eb from the edges
+// (the expansions of Sec. 4 assume a smooth boundary) for the quadratic f of the jet J, at distances ea, eb from the edges
 // with inward normals n1, n2: the heat kernel separates along n1 and n2, so
 // the integrand at time t is the product of the one-dimensional moments
 // M_k(e) = int_{-e}^inf s^k g_t(s) ds of the Gaussian g_t of variance 2t,
 //   M0 = erfc(-e / 2 sqrt t) / 2, M1 = sqrt(t / pi) exp(-e^2 / 4t),
 //   M2 = 2t (M0 - e g_t(e)),
 // contracted with f and its derivatives along n1, n2; the time integral on
-// the plan's graded nodes.
-__device__ double corner_volume(const LocalArgs& a, const double* J, const double* c, double ea, double eb) {
-  const double f = J[0];
-  const double d1 = J[1] * c[2] + J[2] * c[3], d2 = J[1] * c[4] + J[2] * c[5];
-  const double h11 = J[3] * c[2] * c[2] + 2.0 * J[4] * c[2] * c[3] + J[5] * c[3] * c[3];
-  const double h22 = J[3] * c[4] * c[4] + 2.0 * J[4] * c[4] * c[5] + J[5] * c[5] * c[5];
-  const double h12 = J[3] * c[2] * c[4] + J[4] * (c[2] * c[5] + c[3] * c[4]) + J[5] * c[3] * c[5];
-  const double inv_sqrt_pi = 0.56418958354775628695;
+// the plan's graded nodes.  Evaluated by a whole warp (every lane calls it,
+// with the same target): lane l takes the nodes l, l + 32, ..., and the
+// partial sums are combined by shuffles; every lane returns the total.
+// The integrand is evaluated in single precision for both plan precisions
+// and summed in double: the quadrant term is of size delta f (the heat
+// kernel's mass over the quadrant), so single-precision rounding perturbs V
+// by ~1e-7 delta |f|, far below the FP64 plans' tolerance, while the FP64
+// erfc and exp cost ten times the rest of the local pass.
+__device__ double corner_volume_warp(const LocalArgs& a, const double* J, const double* c, double ea, double eb,
+                                     int lane) {
+  const float f = (float)J[0];
+  const float d1 = (float)(J[1] * c[2] + J[2] * c[3]), d2 = (float)(J[1] * c[4] + J[2] * c[5]);
+  const float h11 = (float)(J[3] * c[2] * c[2] + 2.0 * J[4] * c[2] * c[3] + J[5] * c[3] * c[3]);
+  const float h22 = (float)(J[3] * c[4] * c[4] + 2.0 * J[4] * c[4] * c[5] + J[5] * c[5] * c[5]);
+  const float h12 = (float)(J[3] * c[2] * c[4] + J[4] * (c[2] * c[5] + c[3] * c[4]) + J[5] * c[3] * c[5]);
+  const float inv_sqrt_pi = 0.5641895835f;
+  const float eaf = (float)ea, ebf = (float)eb;
   double v = 0.0;
-  for (int k = 0; k < kCornerQuad; ++k) {
-    const double t = a.corner_q[k], st = sqrt(t);
-    const double ga = exp(-ea * ea / (4.0 * t)), gb = exp(-eb * eb / (4.0 * t));
-    const double A0 = 0.5 * erfc(-ea / (2.0 * st)), B0 = 0.5 * erfc(-eb / (2.0 * st));
-    const double A1 = st * inv_sqrt_pi * ga, B1 = st * inv_sqrt_pi * gb;
-    const double A2 = 2.0 * t * A0 - ea * st * inv_sqrt_pi * ga, B2 = 2.0 * t * B0 - eb * st * inv_sqrt_pi * gb;
-    v += a.corner_q[kCornerQuad + k] *
-         (f * A0 * B0 + d1 * A1 * B0 + d2 * A0 * B1 + 0.5 * h11 * A2 * B0 + h12 * A1 * B1 + 0.5 * h22 * A0 * B2);
+  for (int k = lane; k < kCornerQuad; k += 32) {
+    const float t = (float)a.corner_q[k], st = sqrtf(t), is = 1.0f / st;
+    const float xa = eaf * is, xb = ebf * is;  // e / sqrt t
+    const float ga = expf(-0.25f * xa * xa), gb = expf(-0.25f * xb * xb);
+    const float A0 = 0.5f * erfcf(-0.5f * xa), B0 = 0.5f * erfcf(-0.5f * xb);
+    const float A1 = st * inv_sqrt_pi * ga, B1 = st * inv_sqrt_pi * gb;
+    const float A2 = 2.0f * t * A0 - eaf * A1, B2 = 2.0f * t * B0 - ebf * B1;
+    const float I = f * A0 * B0 + d1 * A1 * B0 + d2 * A0 * B1 + 0.5f * h11 * A2 * B0 + h12 * A1 * B1 +
+                    0.5f * h22 * A0 * B2;
+    v += a.corner_q[kCornerQuad + k] * (double)I;
   }
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
@@ -244,13 +256,16 @@ __device__ __forceinline__ double far_volume(const LocalArgs& a, const double* J
   return v;
 }
 
+// Returns the index of the corner whose quadrant holds the target (its V
+// term is then left to the corner pass), or -1.
 template <typename T>
-__device__ void local_near_one(const LocalArgs& a, int64_t i, int best) {
+__device__ int local_near_one(const LocalArgs& a, int64_t i, int best) {
   const double x = a.txy[2 * i], y = a.txy[2 * i + 1];
   const T dl = (T)a.delta_sd;  // S and D expansions (V uses a.delta)
   const double* J = a.jet ? a.jet + 6 * i : nullptr;
   T vl = 0, sl = 0, dlv = 0;
   bool far = false;
+  int corner = -1;
   Foot ft{-1, 0.0, 1e300, 0.0, 0.0, 1.0, true};
   {
     const int p = a.p;
@@ -408,14 +423,16 @@ __device__ void local_near_one(const LocalArgs& a, int64_t i, int best) {
                 T(24.0) * (fxx + fee));
         }
         vl = v;
-        // within the band of both edges of a right-angle corner: the quadrant
+        // within the band of both edges of a right-angle corner: the
+        // quadrant integral replaces the expansion (corner pass)
         if (a.order >= 5)
           for (int q = 0; q < a.n_corners; ++q) {
             const double* c = a.corners + 6 * q;
             const double ea = (x - c[0]) * c[2] + (y - c[1]) * c[3];
             const double eb = (x - c[0]) * c[4] + (y - c[1]) * c[5];
             if (ea > -a.on_tol && eb > -a.on_tol && ea < a.band && eb < a.band) {
-              vl = (T)corner_volume(a, J, c, fmax(ea, 0.0), fmax(eb, 0.0));
+              vl = 0;
+              corner = q;
               break;
             }
           }
@@ -425,6 +442,7 @@ __device__ void local_near_one(const LocalArgs& a, int64_t i, int best) {
   if (a.out[0]) a.out[0][i] += (double)vl;
   if (a.out[1]) a.out[1][i] += (double)sl;
   if (a.out[2]) a.out[2][i] += (double)dlv;
+  return corner;
 }
 
 // Pass 1: nearest boundary node among the 3x3 hash cells, by a single-
@@ -512,23 +530,81 @@ __global__ void local_classify_batch_kernel(const LocalArgs* __restrict__ args, 
   list[base + g.thread_rank()] = make_int4(wk.x, (int)i, best, 0);
 }
 
-// Pass 2: closest point, frame and expansions for the listed targets.
+// Pass 2: closest point, frame and expansions for the listed targets.  A
+// target in a corner's quadrant gets its entry marked for pass 3: the
+// nearest-node field (no longer needed) becomes -1 - corner.
 template <typename T>
-__global__ void local_near_kernel(const __grid_constant__ LocalArgs a, const int2* __restrict__ list,
+__global__ void local_near_kernel(const __grid_constant__ LocalArgs a, int2* __restrict__ list,
                                   const int* __restrict__ count) {
   const int n_near = *count;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n_near; idx += gridDim.x * blockDim.x)
-    local_near_one<T>(a, list[idx].x, list[idx].y);
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n_near; idx += gridDim.x * blockDim.x) {
+    const int q = local_near_one<T>(a, list[idx].x, list[idx].y);
+    if (q >= 0) list[idx].y = -1 - q;
+  }
 }
 
 template <typename T>
-__global__ void local_near_batch_kernel(const LocalArgs* __restrict__ args, const int4* __restrict__ list,
+__global__ void local_near_batch_kernel(const LocalArgs* __restrict__ args, int4* __restrict__ list,
                                         const int* __restrict__ count) {
   const int n_near = *count;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n_near; idx += gridDim.x * blockDim.x) {
     const int4 e = list[idx];
-    local_near_one<T>(args[e.x], e.y, e.z);
+    const int q = local_near_one<T>(args[e.x], e.y, e.z);
+    if (q >= 0) list[idx].w = 1 + q;
   }
+}
+
+// Pass 3: the quadrant integrals of the marked entries, one warp per target.
+// Each warp scans 32 list entries per round (the round count depends only on
+// the warp, so every lane takes part in the ballot and the shuffles) and
+// evaluates the marked ones one after the other with all its lanes.
+__device__ __forceinline__ void corner_entry(int2 e, int& plan, int& t, int& q) {
+  plan = 0;
+  t = e.x;
+  q = e.y < 0 ? -1 - e.y : -1;
+}
+__device__ __forceinline__ void corner_entry(int4 e, int& plan, int& t, int& q) {
+  plan = e.x;
+  t = e.y;
+  q = e.w > 0 ? e.w - 1 : -1;
+}
+
+template <typename E>
+__device__ void corner_pass(const LocalArgs* one, const LocalArgs* args, const E* __restrict__ list,
+                            const int* __restrict__ count) {
+  const int n = *count;
+  const int lane = threadIdx.x & 31;
+  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int base = warp * 32; base < n; base += nwarps * 32) {
+    int plan = 0, t = 0, q = -1;
+    if (base + lane < n) corner_entry(list[base + lane], plan, t, q);
+    unsigned m = __ballot_sync(0xffffffffu, q >= 0);
+    while (m != 0u) {
+      const int src = __ffs(m) - 1;
+      m &= m - 1u;
+      const int pp = __shfl_sync(0xffffffffu, plan, src);
+      const int tt = __shfl_sync(0xffffffffu, t, src);
+      const int qq = __shfl_sync(0xffffffffu, q, src);
+      const LocalArgs& a = one ? *one : args[pp];
+      const double x = a.txy[2 * (int64_t)tt], y = a.txy[2 * (int64_t)tt + 1];
+      const double* c = a.corners + 6 * qq;
+      const double ea = (x - c[0]) * c[2] + (y - c[1]) * c[3];
+      const double eb = (x - c[0]) * c[4] + (y - c[1]) * c[5];
+      const double v = corner_volume_warp(a, a.jet + 6 * (int64_t)tt, c, fmax(ea, 0.0), fmax(eb, 0.0), lane);
+      if (lane == 0) a.out[0][tt] += v;
+    }
+  }
+}
+
+__global__ void local_corner_kernel(const __grid_constant__ LocalArgs a, const int2* __restrict__ list,
+                                    const int* __restrict__ count) {
+  corner_pass(&a, nullptr, list, count);
+}
+
+__global__ void local_corner_batch_kernel(const LocalArgs* __restrict__ args, const int4* __restrict__ list,
+                                          const int* __restrict__ count) {
+  corner_pass<int4>(nullptr, args, list, count);
 }
 
 template <typename T>
@@ -539,6 +615,8 @@ void local_two_pass(const LocalArgs& a, int64_t nt, int2* list, int* count, cuda
   local_classify_kernel<<<blocks, threads, 0, s>>>(a, list, count);
   const unsigned nblk = std::min<unsigned>(blocks, 152u * 16u);
   local_near_kernel<T><<<nblk, threads, 0, s>>>(a, list, count);
+  if (a.n_corners > 0 && a.out[0] && a.jet && a.order >= 5)
+    local_corner_kernel<<<std::min<unsigned>(blocks, 152u * 4u), threads, 0, s>>>(a, list, count);
 }
 
 }  // namespace
@@ -605,7 +683,7 @@ void launch_local_list(const Plan& P, int64_t nt, const double* txy, const doubl
                        double* S, double* D, int2* list, int* count, cudaStream_t s) {
   if (nt <= 0) return;
   LocalArgs a = make_local_args(P, nt, txy, jet, V, S, D);
-  P.launches += 2;
+  P.launches += 2 + (a.n_corners > 0 && a.out[0] && a.jet && a.order >= 5 ? 1 : 0);
   if (P.precision == LP_FP64)
     local_two_pass<double>(a, nt, list, count, s);
   else
@@ -616,7 +694,7 @@ void launch_local_list(const Plan& P, int64_t nt, const double* txy, const doubl
 // plan's targets (work entries of kBatchThreads targets), one near launch over
 // the combined candidate list.
 void launch_local_batch(int precision, const LocalArgs* d_args, const int2* d_work, int nwork, int4* d_list,
-                        int* d_count, int64_t n_total, cudaStream_t s) {
+                        int* d_count, int64_t n_total, bool corners, cudaStream_t s) {
   if (nwork <= 0) return;
   cudaMemsetAsync(d_count, 0, sizeof(int), s);
   const unsigned nblk = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_total + 127) / 128, 152 * 16));
@@ -625,6 +703,7 @@ void launch_local_batch(int precision, const LocalArgs* d_args, const int2* d_wo
     local_near_batch_kernel<double><<<nblk, 128, 0, s>>>(d_args, d_list, d_count);
   else
     local_near_batch_kernel<float><<<nblk, 128, 0, s>>>(d_args, d_list, d_count);
+  if (corners) local_corner_batch_kernel<<<std::min<unsigned>(nblk, 152u * 4u), 128, 0, s>>>(d_args, d_list, d_count);
 }
 
 }  // namespace lpg

@@ -343,10 +343,12 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
   launch_interp_dd_wave((const InterpDDArgs*)(d + o_da), (const int*)(d + o_df), ndrec, ifirst.back(), w, s);
   if (ndrec) ++b->launches;
   cudaEventRecord(b->ev[6], s);
+  bool corners = false;
+  for (const LocalArgs& la : loc) corners = corners || (la.n_corners > 0 && la.out[0] && la.jet && la.order >= 5);
   launch_local_batch(prec, (const LocalArgs*)(d + o_la), (const int2*)(d + o_lw), (int)lwork.size(), b->d_list,
-                     b->d_count, total_t, s);
+                     b->d_count, total_t, corners, s);
   cudaEventRecord(b->ev[7], s);
-  b->launches += 5 + (sum_launches(plans, n) - before);
+  b->launches += 5 + (corners ? 1 : 0) + (sum_launches(plans, n) - before);
   b->pending = true;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LP_OK : LP_ERR_CUDA;

@@ -479,7 +479,7 @@ void launch_multiplier_batch(int precision, const MultArgs* d_args, const int2* 
 void launch_interp_batch(int precision, int w, const void* d_args, const int2* d_work, int nwork,
                          cudaStream_t s);
 void launch_local_batch(int precision, const LocalArgs* d_args, const int2* d_work, int nwork, int4* d_list,
-                        int* d_count, int64_t n_total, cudaStream_t s);
+                        int* d_count, int64_t n_total, bool corners, cudaStream_t s);
 
 // ---- launches (kernels in k_*.cu) ----
 void launch_spread(const Plan& P, int level, const double* xy, const double* const* q, int nq,

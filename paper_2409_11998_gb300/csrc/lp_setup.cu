@@ -281,7 +281,7 @@ lp_status fit_kernel_poly(Plan& P) {
   return LP_OK;  // best effort at the maximum degree (error recorded)
 }
 
-// Convex right-angle corners of a polygonal boundary (C15): consecutive
+// Convex right-angle corners of a polygonal boundary (outside the smooth-curve setting of Sec. 4): consecutive
 // panels whose nodes lie on their chords (to 1e-12 of the chord) with
 // perpendicular directions (to 1e-9) turning left (counter-clockwise
 // curve).  Each: the intersection of the two edge lines and the inward

@@ -1,4 +1,4 @@
-"""V at the corners of the square (C15 reading): targets within 12 sqrt(delta)
+"""V at the corners of the square (quadrant reading): targets within 12 sqrt(delta)
 of both edges of a corner take the exact quadrant integral of the local
 volume potential, on the GPU as in the oracle, in both precisions."""
 import numpy as np
