@@ -244,7 +244,8 @@ __device__ __forceinline__ bool stencil_dd(dd u, int M, int& i0, dd& v) {
 //   Flush: each cell's counts become one double (integer normalisation, no
 //   FP64 arithmetic) added to the grid with an FP64 atomic.
 template <int W, int NT>
-__device__ __forceinline__ void spread_fx_bin(const SubDDArgs& a, int bx, int by) {
+__device__ __forceinline__ void spread_fx_bin(const SubDDArgs& a, const float2* __restrict__ q_s, void* grid_out,
+                                              int bx, int by) {
   extern __shared__ float2 smd[];
   constexpr int NC = W * W, NP = (NC + 31) / 32, NWARP = NT / 32, CH = NT;
   constexpr int WS = 2 * W + 1;  // weight row stride (odd: conflict-free task stores)
@@ -265,7 +266,7 @@ __device__ __forceinline__ void spread_fx_bin(const SubDDArgs& a, int bx, int by
   float qmax = 0.f;
   bool bad_q = false;
   for (int k = threadIdx.x; k < n_here; k += NT) {
-    const float qx = fabsf(a.q[k0 + k].x);
+    const float qx = fabsf(q_s[k0 + k].x);
     bad_q |= !(qx <= 3.4e38f);
     qmax = fmaxf(qmax, qx);
   }
@@ -325,7 +326,7 @@ __device__ __forceinline__ void spread_fx_bin(const SubDDArgs& a, int bx, int by
         dd_stencil_weights<W>(coef, W, nc, a.nf, v, w);
         float2* out = wbuf + j * WS + ax * W;
         if (ax) {
-          const float2 q = a.q[kk];
+          const float2 q = q_s[kk];
           const dd qd = dd{q.x * qscale, q.y * qscale};
 #pragma unroll
           for (int s = 0; s < W; ++s) {
@@ -368,7 +369,7 @@ __device__ __forceinline__ void spread_fx_bin(const SubDDArgs& a, int bx, int by
   }
   // flush: value = (coarse * 2^(E1 - E2) + fine) * 2^E2, an integer below
   // 2^53 times a power of two, assembled as a double by integer operations
-  double* grid = (double*)a.grid;
+  double* grid = (double*)grid_out;
   const int sh = E1 - E2;
   for (int e = threadIdx.x; e < MM; e += NT) {
     const long long n = ((long long)pc[e] << sh) + (long long)pf[e];
@@ -418,7 +419,15 @@ __global__ void __launch_bounds__(kSubThreads) spread_sub_wave_kernel(const SubA
 
 template <int W, int NT>
 __global__ void __launch_bounds__(NT, 4) spread_fx_kernel(const __grid_constant__ SubDDArgs a) {
-  spread_fx_bin<W, NT>(a, blockIdx.x, blockIdx.y);
+  spread_fx_bin<W, NT>(a, a.q, a.grid, blockIdx.x, blockIdx.y);
+}
+
+// Listed bins x channels: block (b, c) spreads channel c of bin bins[b].
+template <int W, int NT>
+__global__ void __launch_bounds__(NT, 4) spread_fx_list_kernel(const __grid_constant__ SubDDArgs a,
+                                                               const int2* __restrict__ bins, FxChan ch) {
+  const int2 b = bins[blockIdx.x];
+  spread_fx_bin<W, NT>(a, ch.q[blockIdx.y], ch.grid[blockIdx.y], b.x, b.y);
 }
 
 template <int W, int NT>
@@ -427,7 +436,7 @@ __global__ void __launch_bounds__(NT, 4) spread_fx_wave_kernel(const SubDDArgs* 
   const int r = wave_record(first, nrec, blockIdx.x);
   const SubDDArgs& a = recs[r];
   const int key = blockIdx.x - first[r];
-  spread_fx_bin<W, NT>(a, key % a.nbx, key / a.nbx);
+  spread_fx_bin<W, NT>(a, a.q, a.grid, key % a.nbx, key / a.nbx);
 }
 
 }  // namespace
@@ -488,10 +497,28 @@ bool spread_sub_dd_configure(int w) {
     return cudaFuncSetAttribute(spread_fx_kernel<W, kSubDDThreads>,                                     \
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&   \
            cudaFuncSetAttribute(spread_fx_wave_kernel<W, kSubDDThreads>,                                \
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&   \
+           cudaFuncSetAttribute(spread_fx_list_kernel<W, kSubDDThreads>,                                \
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
     LP_SUB_DD_CASES
 #undef LP_CASE
     default: return false;
+  }
+}
+
+void launch_spread_fx_list(const SubDDArgs& a, const int2* bins, int nbins, const FxChan& ch, int nch, int w,
+                           cudaStream_t s) {
+  if (nbins <= 0 || nch <= 0) return;
+  dim3 grid(nbins, nch);
+  const size_t smem = spread_fx_smem_nt(a.M, w, kSubDDThreads);
+  switch (w) {
+#define LP_CASE(W)                                                                      \
+  case W:                                                                               \
+    spread_fx_list_kernel<W, kSubDDThreads><<<grid, kSubDDThreads, smem, s>>>(a, bins, ch); \
+    break;
+    LP_SUB_DD_CASES
+#undef LP_CASE
+    default: break;
   }
 }
 

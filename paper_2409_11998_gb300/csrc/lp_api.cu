@@ -183,7 +183,7 @@ void destroy_plan(Plan& P) {
                   P.d_dy_tab, P.d_dy_rel, P.d_dy_nw, P.d_dy_sig, P.d_dy_mu,
                   P.d_dy_rad, P.d_dy_wgl, P.d_dy_cell_start, P.d_dy_cell_panel, P.d_dy_ref, P.d_vf,
                   P.d_corners, P.d_corner_q, P.d_qred, P.d_geo_coef_dd, P.d_sigma_coef_dd,
-                  P.d_mu_coef_dd};
+                  P.d_mu_coef_dd, P.d_bkeys, P.d_bstart, P.d_brel_dd, P.d_bperm, P.d_bq_dd, P.d_bbins};
   for (void* b : bufs) dfree(b);
   if (P.h_status) cudaFreeHost(P.h_status);
   for (auto& e : P.ev)
@@ -270,6 +270,48 @@ lp_status noalloc_scratch(int dev, void** out) {
 
 namespace lpg {
 
+// FP64 plans: counting sort of the boundary nodes into the current bins, the
+// list of bins that hold some (read back once: the layer spread launches one
+// CTA per listed bin and channel), and the bound layer strengths in bin
+// order.  Runs at plan creation and whenever the bins change (autotuner);
+// synchronises the plan's stream.  A node outside the bins keeps the
+// point-parallel layer spread, which reports it at every evaluation.
+static void gather_layer_strengths(Plan& P, int kind) {
+  if (!P.bbinned) return;
+  if (kind == 0) {
+    launch_gather_q_dd(P.d_bq, P.d_bperm, P.nb, P.d_bq_dd, P.stream);
+    ++P.launches;
+  } else {
+    launch_gather_q_dd(P.d_bq + P.nb, P.d_bperm, P.nb, P.d_bq_dd + P.nb, P.stream);
+    launch_gather_q_dd(P.d_bq + 2 * P.nb, P.d_bperm, P.nb, P.d_bq_dd + 2 * P.nb, P.stream);
+    P.launches += 2;
+  }
+}
+
+static lp_status bin_boundary(Plan& P) {
+  P.bbinned = false;
+  if (!P.d_bkeys || P.nb <= 0) return LP_OK;
+  unsigned* scratch_status = (unsigned*)(P.d_bkeys + P.nb);
+  cudaMemsetAsync(scratch_status, 0, sizeof(unsigned), P.stream);
+  launch_bin_sort_dd(P.d_bxy, P.nb, P.bins, P.d_bkeys, P.d_counts, P.d_cursor, P.d_bstart, P.d_brel_dd, P.d_bperm,
+                     scratch_status, P.stream);
+  const int nbins = P.bins.nbx * P.bins.nby;
+  std::vector<int> st((size_t)nbins + 2);
+  cudaMemcpyAsync(st.data(), P.d_bstart, st.size() * sizeof(int), cudaMemcpyDeviceToHost, P.stream);
+  if (cudaStreamSynchronize(P.stream) != cudaSuccess) return status_from_cuda();
+  if (st[nbins + 1] != st[nbins]) return LP_OK;  // nodes outside the bins
+  std::vector<int2> list;
+  for (int k = 0; k < nbins; ++k)
+    if (st[k + 1] > st[k]) list.push_back(make_int2(k % P.bins.nbx, k / P.bins.nbx));
+  if (list.empty()) return LP_OK;
+  cudaMemcpy(P.d_bbins, list.data(), list.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  P.n_bbins = (int)list.size();
+  P.bbinned = true;
+  if (P.have_sigma) gather_layer_strengths(P, 0);
+  if (P.have_mu) gather_layer_strengths(P, 1);
+  return status_from_cuda();
+}
+
 // Bins of the binned volume spread: squares of bin_cells near-history cells
 // (32 for FP32 plans; 24 for FP64 plans, whose df64 patches take twice the
 // shared memory).  FP32 plans whose kernel fit needs more coefficients than
@@ -342,6 +384,16 @@ lp_status setup_bins(Plan& P) {
     return LP_ERR_NOMEM;
   cudaMemset(P.d_vstart, 0, (nbins + 1) * sizeof(int));
   P.binned = true;
+  if (f64 && P.nb > 0) {
+    const size_t nb = (size_t)P.nb;
+    if (!dalloc(P, (void**)&P.d_bkeys, (nb + 1) * sizeof(int)) ||
+        !dalloc(P, (void**)&P.d_bstart, (nbins + 1) * sizeof(int)) ||
+        !dalloc(P, (void**)&P.d_brel_dd, nb * sizeof(float4)) || !dalloc(P, (void**)&P.d_bperm, nb * sizeof(int)) ||
+        !dalloc(P, (void**)&P.d_bq_dd, 3 * nb * sizeof(float2)) ||
+        !dalloc(P, (void**)&P.d_bbins, std::min(nb, nbins) * sizeof(int2)))
+      return LP_ERR_NOMEM;
+    return bin_boundary(P);
+  }
   return LP_OK;
 }
 
@@ -789,6 +841,8 @@ static lp_status tune_bins(Plan& P, int64_t n) {
   if (!configure_bins(P, best)) configure_bins(P, base);
   bin_volume(P, n);
   P.tuned = true;
+  const lp_status bs = bin_boundary(P);
+  if (bs != LP_OK) return bs;
   return status_from_cuda();
 }
 
@@ -888,6 +942,7 @@ static lp_status bind_layer(lp_plan_t h, const double* dens, int kind) {
                      P.n_panels * P.p, P.stream);
   ++P.launches;
   launch_strengths(P, kind, P.stream);
+  gather_layer_strengths(P, kind);
   if (kind == 0) {
     launch_sum(P, P.d_bq, P.nb, P.d_qsum + 1, P.stream);
     P.have_sigma = true;
@@ -1052,7 +1107,28 @@ static void spread_part(Plan& P, bool wv, bool ws, bool wd, bool volume, bool la
       bq[nq] = P.d_bq + 2 * P.nb;
       bg[nq++] = G.chan[3];
     }
-    if (nq && layers) launch_spread(P, l, P.d_bxy, bq, nq, bg, P.nb, s);
+    if (!nq || !layers) continue;
+    if (P.bbinned) {
+      SubDDArgs a = make_spread_dd_args(P, l);
+      a.rel = P.d_brel_dd;
+      a.start = P.d_bstart;
+      FxChan ch{};
+      int k = 0;
+      if (ws) {
+        ch.q[k] = P.d_bq_dd;
+        ch.grid[k++] = G.chan[1];
+      }
+      if (wd) {
+        ch.q[k] = P.d_bq_dd + P.nb;
+        ch.grid[k++] = G.chan[2];
+        ch.q[k] = P.d_bq_dd + 2 * P.nb;
+        ch.grid[k++] = G.chan[3];
+      }
+      ++P.launches;
+      launch_spread_fx_list(a, P.d_bbins, P.n_bbins, ch, k, P.ker.w, s);
+    } else {
+      launch_spread(P, l, P.d_bxy, bq, nq, bg, P.nb, s);
+    }
   }
   record_stage(P, 3, s);
 }

@@ -397,6 +397,16 @@ struct Plan {
   float grid_ms[6] = {0, 0, 0, 0, 0, 0};  // their evaluation times (ms; -1: not built)
   float4* d_vrel_dd = nullptr;     // FP64 plans: offsets from the bin corner, df64
   float2* d_vq_dd = nullptr;       // FP64 plans: strengths in bin order, df64
+  // FP64 plans: the boundary nodes sorted into the same bins (fixed-point
+  // spread of the layers over the non-empty bins); re-sorted when the bins change
+  bool bbinned = false;
+  int* d_bkeys = nullptr;          // [nb + 1] sort scratch (the last entry: its status word)
+  int* d_bstart = nullptr;         // [nbins + 2]
+  float4* d_brel_dd = nullptr;     // [nb] offsets from the bin corner, df64
+  int* d_bperm = nullptr;          // [nb]
+  float2* d_bq_dd = nullptr;       // [3][nb] sigma w, mu nu_x w, mu nu_y w in bin order, df64
+  int2* d_bbins = nullptr;         // [n_bbins] the bins holding boundary nodes
+  int n_bbins = 0;
   size_t key_cap = 0;
   size_t vsort_cap = 0;
 
@@ -500,6 +510,14 @@ bool spread_sub_configure(int w);
 bool spread_sub_dd_configure(int w);
 size_t spread_sub_dd_smem(int M, int w);
 void launch_spread_sub_dd(const SubDDArgs& a, int w, cudaStream_t s);
+// up to three channels (strengths in bin order, FP64 grid) spread over a
+// list of bins with the fixed-point kernel: one CTA per (bin, channel)
+struct FxChan {
+  const float2* q[3];
+  void* grid[3];
+};
+void launch_spread_fx_list(const SubDDArgs& a, const int2* bins, int nbins, const FxChan& ch, int nch, int w,
+                           cudaStream_t s);
 void launch_bin_sort_dd(const double* xy, int64_t n, const BinGeom& bg, int* keys, int* counts, int* cursor,
                         int* starts, float4* rel_s, int* perm, unsigned* status, cudaStream_t s);
 void launch_gather_q_dd(const double* q, const int* perm, int64_t n, float2* q_s, cudaStream_t s);
