@@ -20,20 +20,36 @@ namespace {
 
 // Key = bin of the point; points outside the bin grid (or NaN) go to the
 // overflow bin nbx*nby, which no CTA reads, and are reported.
+// Warp-aggregated reservation: the lanes holding the same key (-1: none)
+// share one atomic add of their number on ctr[key]; returns the lane's slot
+// (the counter's old value plus its rank among those lanes).  Every lane of
+// the warp calls it.  Consecutive nodes (the six of a triangle) mostly share
+// a bin, so this divides the atomics on the bin counters several-fold.
+__device__ __forceinline__ int warp_reserve(int* ctr, int key) {
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (key >= 0 && lane == leader) base = atomicAdd(ctr + key, __popc(peers));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  return base + __popc(peers & ((1u << lane) - 1u));
+}
+
 __global__ void bin_keys_kernel(const double* __restrict__ xy, int64_t n, double x0, double y0, double inv_bt,
                                 int nbx, int nby, int* keys, int* counts, unsigned* status) {
-  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  double fx = (xy[2 * j] - x0) * inv_bt, fy = (xy[2 * j + 1] - y0) * inv_bt;
-  int key;
-  if (fx >= 0.0 && fx < nbx && fy >= 0.0 && fy < nby) {
-    key = (int)fy * nbx + (int)fx;
-  } else {
-    key = nbx * nby;
-    atomicOr(status, kStatusOutOfBox);
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int key = -1;
+  if (j < n) {
+    const double fx = (xy[2 * j] - x0) * inv_bt, fy = (xy[2 * j + 1] - y0) * inv_bt;
+    if (fx >= 0.0 && fx < nbx && fy >= 0.0 && fy < nby) {
+      key = (int)fy * nbx + (int)fx;
+    } else {
+      key = nbx * nby;
+      atomicOr(status, kStatusOutOfBox);
+    }
+    keys[j] = key;
   }
-  keys[j] = key;
-  atomicAdd(&counts[key], 1);
+  warp_reserve(counts, key);
 }
 
 // Exclusive scan of counts[0..n) into starts[0..n], one block.
@@ -63,10 +79,11 @@ __global__ void scan_kernel(const int* __restrict__ counts, int n, int* starts) 
 __global__ void scatter_kernel(const double* __restrict__ xy, int64_t n, const int* __restrict__ keys,
                                const int* __restrict__ starts, int* cursor, BinGeom bg, float2* rel_s,
                                int* perm) {
-  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  const int key = keys[j];
-  const int pos = starts[key] + atomicAdd(&cursor[key], 1);
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int key = j < n ? keys[j] : -1;
+  const int slot = warp_reserve(cursor, key);
+  if (key < 0) return;
+  const int pos = starts[key] + slot;
   const int bx = key % bg.nbx, by = key / bg.nbx;  // overflow bin: never read
   const double bt = 1.0 / bg.inv_bt;
   rel_s[pos] = make_float2((float)(xy[2 * j] - (bg.x0 + bx * bt)), (float)(xy[2 * j + 1] - (bg.y0 + by * bt)));
@@ -191,10 +208,11 @@ __device__ __forceinline__ void spread_sub_bin(const SubArgs& a, int bx, int by)
 __global__ void scatter_dd_kernel(const double* __restrict__ xy, int64_t n, const int* __restrict__ keys,
                                   const int* __restrict__ starts, int* cursor, BinGeom bg, float4* rel_s,
                                   int* perm) {
-  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  const int key = keys[j];
-  const int pos = starts[key] + atomicAdd(&cursor[key], 1);
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int key = j < n ? keys[j] : -1;
+  const int slot = warp_reserve(cursor, key);
+  if (key < 0) return;
+  const int pos = starts[key] + slot;
   const int bx = key % bg.nbx, by = key / bg.nbx;  // overflow bin: never read
   const double bt = 1.0 / bg.inv_bt;
   const dd rx = dd_from_double(xy[2 * j] - (bg.x0 + bx * bt));
