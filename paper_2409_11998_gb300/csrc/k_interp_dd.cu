@@ -46,12 +46,22 @@ __device__ __forceinline__ void interp_dd_target(const InterpDDArgs& a, int64_t 
     dd_stencil_weights<W>(&a.coef[0][0], kMaxW, a.nc, a.nf, vx, wx);
     dd_stencil_weights<W>(&a.coef[0][0], kMaxW, a.nc, a.nf, vy, wy);
     // rows and channels stay rolled (wy spills to L1-resident local memory):
-    // unrolling all w^2 C products overflows the instruction cache
-    // rows are read as 16-byte pairs of cells from the even cell at or below
-    // ix (grid rows start 16-byte aligned: the pitch is even), W/2 + 1 loads
-    // instead of W, and the W values picked by the parity of ix
+    // unrolling all w^2 C products overflows the instruction cache.
+    // Rows are read as 16-byte pairs of cells from the even cell ix0 at or
+    // below ix (grid rows start 16-byte aligned: the pitch is even), W/2 + 1
+    // loads instead of W.  The x weights are shifted once per target onto
+    // the W + 1 cells ix0 .. ix0 + W (a zero weight at the unused end), so
+    // that every row takes the loaded values in a fixed order.
     const int ix0 = ix & ~1;
     const bool odd = (ix & 1) != 0;
+    dd ws[W + 1];
+#pragma unroll
+    for (int t = 0; t <= W; ++t) {
+      const dd here = t < W ? wx[t] : dd{0.f, 0.f};
+      const dd prev = t > 0 ? wx[t - 1] : dd{0.f, 0.f};
+      ws[t] = odd ? prev : here;
+    }
+    constexpr int NQ = (W + 2) / 2;  // 16-byte loads covering cells 0 .. W
 #pragma unroll 1
     for (int c = 0; c < 3; ++c) {
       if (!a.out[c]) continue;
@@ -59,21 +69,19 @@ __device__ __forceinline__ void interp_dd_target(const InterpDDArgs& a, int64_t 
 #pragma unroll 1
       for (int b = 0; b < W; ++b) {
         const float4* row = base + (size_t)b * (L.pitch / 2);
-        float4 q[W / 2 + 1];
+        float4 q[NQ];
 #pragma unroll
-        for (int u = 0; u < W / 2 + 1; ++u)
-          if (2 * u < W + 1) q[u] = __ldg(row + u);
-        float2 gv[W];
-#pragma unroll
-        for (int t = 0; t < W; ++t) {
-          const int e = t + 1;  // the value after t in the pair sequence
-          const float2 lo = (t & 1) ? make_float2(q[t / 2].z, q[t / 2].w) : make_float2(q[t / 2].x, q[t / 2].y);
-          const float2 hi = (e & 1) ? make_float2(q[e / 2].z, q[e / 2].w) : make_float2(q[e / 2].x, q[e / 2].y);
-          gv[t] = odd ? hi : lo;
-        }
+        for (int u = 0; u < NQ; ++u) q[u] = __ldg(row + u);
         dd_acc r = {0.f, 0.f};
 #pragma unroll
-        for (int t = 0; t < W; ++t) acc_fma(r, wx[t], dd{gv[t].x, gv[t].y});
+        for (int t = 0; t <= W; ++t) {
+          const float4 qq = q[t / 2];
+          dd gv = (t & 1) ? dd{qq.z, qq.w} : dd{qq.x, qq.y};
+          // cell ix0 + W of an even origin may be the row's padding, whose
+          // bits need not be finite floats: its (zero-weight) value is dropped
+          if (t == W) gv = odd ? gv : dd{0.f, 0.f};
+          acc_fma(r, ws[t], gv);
+        }
         acc_fma(acc[c], wy[b], acc_value(r));
       }
     }
