@@ -23,6 +23,7 @@
 // transformed as the complex sequence x_2n + i x_2n+1 of length N followed by
 // the usual even/odd split; the inverse runs the same steps backwards.
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <vector>
 
@@ -408,6 +409,25 @@ __device__ __forceinline__ float2 dipole_mode(float2 f1, float2 f2, float m, flo
   return make_float2(m * (kx * f1.y + ky * f2.y), -m * (kx * f1.x + ky * f2.x));
 }
 
+// Single-precision chain, low modes: the FP64 table entry, the product in
+// double, one rounding to float (k = 0 is excluded: its term is added in
+// FP64 at the targets)
+__device__ __forceinline__ float2 scale_low(float2 z, double m) {
+  return make_float2((float)((double)z.x * m), (float)((double)z.y * m));
+}
+// (the double-float chain's forms, for the generic multiplier loop: it never
+// takes this path, since its table is already in double-float)
+__device__ __forceinline__ cdd scale_low(cdd z, double m) { return cdd_scale_dd(z, dd_from_double(m)); }
+__device__ __forceinline__ cdd dipole_low(cdd f1, cdd f2, double m, float2 dk2, int mx, int my) {
+  return dipole_mode(f1, f2, dd_from_double(m), dk2, mx, my);
+}
+__device__ __forceinline__ float2 dipole_low(float2 f1, float2 f2, double m, float2 dk2, int mx, int my) {
+  const double dk = (double)dk2.x + (double)dk2.y;
+  const double kx = dk * mx, ky = dk * my;
+  return make_float2((float)(m * (kx * (double)f1.y + ky * (double)f2.y)),
+                     (float)(-m * (kx * (double)f1.x + ky * (double)f2.x)));
+}
+
 // Twiddles in shared memory (a third buffer) for the single-precision chain:
 // its butterflies are cheap and the per-stage global twiddle loads saturated
 // the L1 pipe.  The double-float chain keeps the global table: a third
@@ -505,6 +525,48 @@ __global__ void __launch_bounds__(kFftThreads * C) fft_cols_kernel(const __grid_
     else
       fft_dif<A>(x, a.full, twg, t0, kFftThreads);
   };
+  // The multiplier on the forward-transformed column, in place (KIND 1:
+  // the D combination with the parked D1 column).  FP32 plans: a column
+  // with m_x < klo takes the FP64 entry for its modes |m_y| < klo (k = 0
+  // excepted), decided once per column so that the other columns run the
+  // plain loop.
+  auto mult_loop = [&](const S* park, auto kind_tag, auto low_tag) {
+    constexpr int KIND = decltype(kind_tag)::value;
+    constexpr bool LOW = decltype(low_tag)::value && std::is_same<A, F32>::value;
+    for (int p = t0; p < g; p += kFftThreads) {
+      const int r = __ldg(a.freq + p);
+      const int my = r <= g / 2 ? r : r - g;
+      const int amy = my < 0 ? -my : my;
+      V o = A::zero();
+      if (amy <= K && mx <= K) {
+        const size_t ti = (size_t)amy * (K + 1) + mx;
+        bool done = false;
+        if constexpr (LOW) {
+          if (amy < a.klo && (mx | amy) != 0) {
+            if constexpr (KIND == 1)
+              o = dipole_low(A::load(park + (size_t)p * a.kp + mx), A::load(x + p), a.tab64[ti], a.dk, mx, my);
+            else
+              o = scale_low(A::load(x + p), a.tab64[ti]);
+            done = true;
+          }
+        }
+        if (!done) {
+          if constexpr (KIND == 1)
+            o = dipole_mode(A::load(park + (size_t)p * a.kp + mx), A::load(x + p), mult_value(a.tab, ti, A()),
+                            a.dk, mx, my);
+          else
+            o = scale_real(A::load(x + p), mult_value(a.tab, ti, A()));
+        }
+      }
+      A::store(x + p, o);
+    }
+  };
+  auto mult_column = [&](const S* park, auto kind_tag) {
+    if (a.tab64 != nullptr && mx < a.klo)
+      mult_loop(park, kind_tag, std::true_type{});
+    else
+      mult_loop(park, kind_tag, std::false_type{});
+  };
   if (job.kind == 1) {
     load_cols(job.in[0]);
     forward();
@@ -516,27 +578,11 @@ __global__ void __launch_bounds__(kFftThreads * C) fft_cols_kernel(const __grid_
     __syncthreads();
     load_cols(job.in[1]);
     forward();
-    for (int p = t0; p < g; p += kFftThreads) {
-      const int r = __ldg(a.freq + p);
-      const int my = r <= g / 2 ? r : r - g;
-      const int amy = my < 0 ? -my : my;
-      V o = A::zero();
-      if (amy <= K && mx <= K)
-        o = dipole_mode(A::load(park + (size_t)p * a.kp + mx), A::load(x + p),
-                        mult_value(a.tab, (size_t)amy * (K + 1) + mx, A()), a.dk, mx, my);
-      A::store(x + p, o);
-    }
+    mult_column(park, std::integral_constant<int, 1>{});
   } else {
     load_cols(job.in[0]);
     forward();
-    for (int p = t0; p < g; p += kFftThreads) {
-      const int r = __ldg(a.freq + p);
-      const int my = r <= g / 2 ? r : r - g;
-      const int amy = my < 0 ? -my : my;
-      V o = A::zero();
-      if (amy <= K && mx <= K) o = scale_real(A::load(x + p), mult_value(a.tab, (size_t)amy * (K + 1) + mx, A()));
-      A::store(x + p, o);
-    }
+    mult_column(nullptr, std::integral_constant<int, 0>{});
   }
   __syncthreads();
   if (kTwSmem<A>)

@@ -84,6 +84,27 @@ __device__ __forceinline__ void multiplier_mode(const MultArgs& a, int64_t idx) 
   int row = (int)(idx / ncol), mx = (int)(idx - (int64_t)row * ncol);
   int my = row <= g / 2 ? row : row - g;
   int amy = my < 0 ? -my : my;
+  if (sizeof(R) == 4 && a.tab64 && mx < a.klo && amy < a.klo && (mx | amy) != 0) {
+    // FP32 plans, low modes: the FP64 entry, products in double, one rounding
+    const double md = a.tab64[(size_t)amy * (K + 1) + mx];
+    C* chan[2] = {(C*)a.V, (C*)a.S};
+    for (C* c : chan)
+      if (c) {
+        C z = c[idx];
+        z.x = (R)((double)z.x * md);
+        z.y = (R)((double)z.y * md);
+        c[idx] = z;
+      }
+    if (a.D1) {
+      const C z1 = ((C*)a.D1)[idx], z2 = ((const C*)a.D2)[idx];
+      const double kx = a.dk * mx, ky = a.dk * my;
+      C o;
+      o.x = (R)(md * (kx * (double)z1.y + ky * (double)z2.y));
+      o.y = (R)(-md * (kx * (double)z1.x + ky * (double)z2.x));
+      ((C*)a.D1)[idx] = o;
+    }
+    return;
+  }
   R m = 0;
   if (mx <= K && amy <= K) m = ((const R*)a.tab)[(size_t)amy * (K + 1) + mx];
   if (a.V) {
@@ -264,6 +285,8 @@ MultArgs make_mult_args(const Plan& P, int level, bool want_v, bool want_s, bool
   a.K = G.K;
   a.dk = G.dk;
   a.tab = P.precision == LP_FP64 ? (const void*)G.mtab : (const void*)G.mtab32;
+  a.tab64 = P.precision == LP_FP64 ? nullptr : G.mtab;
+  a.klo = P.precision == LP_FP64 ? 0 : kLowKFP64;
   a.V = want_v ? G.chan[0] : nullptr;
   a.S = want_s ? G.chan[1] : nullptr;
   a.D1 = want_d ? G.chan[2] : nullptr;

@@ -563,7 +563,9 @@ void history_transforms(const Plan& P, bool wv, bool ws, bool wd, cudaStream_t s
     a.tw = G.tw_dd;
     a.freq = G.freq;
     a.tab = f64 ? (const void*)G.mtab_dd : (const void*)G.mtab32;
-    a.dk = f64 ? split_host(G.dk) : make_float2((float)G.dk, 0.f);
+    a.tab64 = f64 ? nullptr : G.mtab;
+    a.klo = f64 ? 0 : kLowKFP64;
+    a.dk = f64 ? split_host(G.dk) : make_float2((float)G.dk, (float)(G.dk - (double)(float)G.dk));
     int nj = 0;
     if (wv) a.job[nj++] = FftColJob{0, {G.spec[0], nullptr}, G.spec[0]};
     if (ws) a.job[nj++] = FftColJob{0, {G.spec[1], nullptr}, G.spec[1]};

@@ -137,6 +137,8 @@ struct MultArgs {
   int g, K;
   double dk;
   const void* tab;        // double (FP64) or float (FP32) table
+  const double* tab64;    // FP32 plans: the FP64 table, taken for 0 < max(|m_x|, |m_y|) < klo
+  int klo;
   void* V;
   void* S;
   void* D1;
@@ -183,6 +185,11 @@ struct SubDDArgs {
   float2 coef[kMaxNC][kMaxW];  // weight polynomials, df64
 };
 
+// FP32 plans: modes with |m_x|, |m_y| below this take the FP64 multiplier
+// entry, the product formed in double (the low modes carry most of the
+// log kernel's weight, and its multiplier is where the terms cancel)
+constexpr int kLowKFP64 = 16;
+
 // df64 FFT chain (k_fft.cu)
 struct FftRowArgs {
   FftShape half;
@@ -203,6 +210,8 @@ struct FftColArgs {
   const float4* tw;
   const int* freq;    // frequency index of each position of the in-place forward transform's output
   const void* tab;    // deconvolved multiplier, (K+1)^2: df64 pairs (FP64) or floats without k = 0 (FP32)
+  const double* tab64;  // FP32 plans: the FP64 table, taken for 0 < max(|m_x|, |m_y|) < klo
+  int klo;
   float2 dk;          // mode spacing (df64 pair; FP32 uses .x)
   FftColJob job[3];
   int kp, K, row_lo, row_hi;
