@@ -255,7 +255,7 @@ __device__ __forceinline__ bool stencil_dd(dd u, int M, int& i0, dd& v) {
 // independent of order, so the warps of the CTA share one patch; the
 // result carries about 2^-44 of the bin's largest strength per
 // contribution, below the df64 rounding of the transforms.
-//   Phase 1 (per chunk of up to NT nodes): the CTA evaluates the 2w
+//   Phase 1 (per chunk of up to kSubDDChunk nodes): the CTA evaluates the 2w
 //   df64 weight polynomials as (node, axis) tasks, one per thread, and stores
 //   x weights and q times y weights with the stencil origins.
 //   Phase 2: each warp takes one node at a time, its lanes the w^2 cells.
@@ -265,7 +265,7 @@ template <int W, int NT>
 __device__ __forceinline__ void spread_fx_bin(const SubDDArgs& a, const float2* __restrict__ q_s, void* grid_out,
                                               int bx, int by) {
   extern __shared__ float2 smd[];
-  constexpr int NC = W * W, NP = (NC + 31) / 32, NWARP = NT / 32, CH = NT;
+  constexpr int NC = W * W, NP = (NC + 31) / 32, NWARP = NT / 32, CH = kSubDDChunk;
   constexpr int WS = 2 * W + 1;  // weight row stride (odd: conflict-free task stores)
   const int M = a.M, MM = M * M, nc = a.nc;
   const int key = by * a.nbx + bx;
@@ -436,20 +436,20 @@ __global__ void __launch_bounds__(kSubThreads) spread_sub_wave_kernel(const SubA
 }
 
 template <int W, int NT>
-__global__ void __launch_bounds__(NT, 4) spread_fx_kernel(const __grid_constant__ SubDDArgs a) {
+__global__ void __launch_bounds__(NT, kSubDDMinBlocks) spread_fx_kernel(const __grid_constant__ SubDDArgs a) {
   spread_fx_bin<W, NT>(a, a.q, a.grid, blockIdx.x, blockIdx.y);
 }
 
 // Listed bins x channels: block (b, c) spreads channel c of bin bins[b].
 template <int W, int NT>
-__global__ void __launch_bounds__(NT, 4) spread_fx_list_kernel(const __grid_constant__ SubDDArgs a,
+__global__ void __launch_bounds__(NT, kSubDDMinBlocks) spread_fx_list_kernel(const __grid_constant__ SubDDArgs a,
                                                                const int2* __restrict__ bins, FxChan ch) {
   const int2 b = bins[blockIdx.x];
   spread_fx_bin<W, NT>(a, ch.q[blockIdx.y], ch.grid[blockIdx.y], b.x, b.y);
 }
 
 template <int W, int NT>
-__global__ void __launch_bounds__(NT, 4) spread_fx_wave_kernel(const SubDDArgs* __restrict__ recs,
+__global__ void __launch_bounds__(NT, kSubDDMinBlocks) spread_fx_wave_kernel(const SubDDArgs* __restrict__ recs,
                                                                const int* __restrict__ first, int nrec) {
   const int r = wave_record(first, nrec, blockIdx.x);
   const SubDDArgs& a = recs[r];
@@ -496,11 +496,11 @@ static size_t spread_fx_smem_nt(int M, int w, int nt) {
          (size_t)2 * M * M * sizeof(int);
 }
 
-size_t spread_sub_dd_smem(int M, int w) { return spread_fx_smem_nt(M, w, kSubDDThreads); }
+size_t spread_sub_dd_smem(int M, int w) { return spread_fx_smem_nt(M, w, kSubDDChunk); }
 
 // dynamic shared memory of either binned spread for patch side M
 size_t spread_sub_smem(int M, int w, bool f64) {
-  if (f64) return spread_fx_smem_nt(M, w, kSubDDThreads);
+  if (f64) return spread_fx_smem_nt(M, w, kSubDDChunk);
   return (size_t)(((sub_ncw(w) * w + 3) & ~3) + (kSubThreads / 32) * M * M) * sizeof(float);
 }
 
@@ -528,7 +528,7 @@ void launch_spread_fx_list(const SubDDArgs& a, const int2* bins, int nbins, cons
                            cudaStream_t s) {
   if (nbins <= 0 || nch <= 0) return;
   dim3 grid(nbins, nch);
-  const size_t smem = spread_fx_smem_nt(a.M, w, kSubDDThreads);
+  const size_t smem = spread_fx_smem_nt(a.M, w, kSubDDChunk);
   switch (w) {
 #define LP_CASE(W)                                                                      \
   case W:                                                                               \
@@ -542,7 +542,7 @@ void launch_spread_fx_list(const SubDDArgs& a, const int2* bins, int nbins, cons
 
 void launch_spread_sub_dd(const SubDDArgs& a, int w, cudaStream_t s) {
   dim3 grid(a.nbx, a.nby);
-  const size_t smem = spread_fx_smem_nt(a.M, w, kSubDDThreads);
+  const size_t smem = spread_fx_smem_nt(a.M, w, kSubDDChunk);
   switch (w) {
 #define LP_CASE(W)                                                               \
   case W:                                                                        \

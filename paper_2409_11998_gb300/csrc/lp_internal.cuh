@@ -21,6 +21,8 @@ constexpr int kTile = 32;           // bin side (near-history cells) of the binn
 constexpr int kBinCandidates[2][3] = {{16, 32, 48}, {16, 24, 32}};
 constexpr int kSubThreads = 256;    // threads per CTA of the binned spread
 constexpr int kSubDDThreads = 128;  // threads per CTA of the binned df64 spread (FP64 plans)
+constexpr int kSubDDChunk = 64;     // nodes per weight chunk of that spread (one task per thread)
+constexpr int kSubDDMinBlocks = 6;  // resident CTAs per SM it is compiled for (80 registers)
 // Coefficient count of the binned spread's weight polynomials for width w
 // (the plan's fit is zero-padded; plans whose fit needs more use the
 // point-parallel spread).
