@@ -481,7 +481,7 @@ constexpr int kColBatch<F32> = 8;
 // transform (in digit-reversed order) in its own global columns meanwhile.
 // The multiplier is applied in the forward transform's order.
 template <class A, int C>
-__global__ void __launch_bounds__(kFftThreads * C) fft_cols_kernel(const __grid_constant__ FftColArgs a) {
+__device__ __forceinline__ void fft_cols_body(const FftColArgs& a) {
   using V = typename A::V;
   using S = typename A::S;
   extern __shared__ float4 sm_raw[];
@@ -596,6 +596,18 @@ __global__ void __launch_bounds__(kFftThreads * C) fft_cols_kernel(const __grid_
   }
 }
 
+template <class A, int C>
+__global__ void __launch_bounds__(kFftThreads * C) fft_cols_kernel(const __grid_constant__ FftColArgs a) {
+  fft_cols_body<A, C>(a);
+}
+
+// FP32, two columns per CTA, compiled for two resident CTAs per SM (64
+// registers): with the compiler's own choice (87) only one 512-thread CTA
+// would fit
+__global__ void __launch_bounds__(kFftThreads * 2, 2) fft_cols2_f32_kernel(const __grid_constant__ FftColArgs a) {
+  fft_cols_body<F32, 2>(a);
+}
+
 // Inverse transform of rows: one CTA per (row, job); writes the g values of
 // the row over the job's grid row (df64 pairs over the FP64 grid, or floats).
 template <class A>
@@ -686,10 +698,13 @@ size_t fft_cols_smem_c(int g, bool f64, int C) {
   return f64 ? (size_t)C * g * sizeof(float4) : (size_t)(C + 1) * g * sizeof(float2);
 }
 // Columns per CTA: FP64 two when they fit (their 16-byte values then fill
-// whole sectors; measured 0.56 -> 0.54 ms on the starfish), FP32 one (four
-// 1024-thread groups measured slower: 0.30 -> 0.32 ms).
+// whole sectors; measured 0.56 -> 0.54 ms on the starfish); FP32 two when
+// at least two CTAs fit on an SM (adjacent lanes read the two columns' 8-byte
+// values of a row as 16 contiguous bytes; four 1024-thread groups measured
+// slower: 0.30 -> 0.32 ms).
 int fft_cols_per_cta(int g, bool f64) {
   if (f64 && fft_cols_smem_c(g, f64, 2) <= 220 * 1024) return 2;
+  if (!f64 && fft_cols_smem_c(g, f64, 2) <= 110 * 1024) return 2;
   return 1;
 }
 size_t fft_cols_smem(int g, bool f64) { return fft_cols_smem_c(g, f64, 1); }
@@ -715,10 +730,10 @@ std::vector<int> fft_dif_order(const FftShape& sh) {
 
 bool fft_dd_configure() {
   const int bytes = 220 * 1024;
-  const void* fns[7] = {(const void*)fft_rows_fwd_kernel<DD>,  (const void*)fft_rows_inv_kernel<DD>,
+  const void* fns[8] = {(const void*)fft_rows_fwd_kernel<DD>,  (const void*)fft_rows_inv_kernel<DD>,
                         (const void*)fft_cols_kernel<DD, 1>,    (const void*)fft_cols_kernel<DD, 2>,
                         (const void*)fft_rows_fwd_kernel<F32>, (const void*)fft_rows_inv_kernel<F32>,
-                        (const void*)fft_cols_kernel<F32, 1>};
+                        (const void*)fft_cols_kernel<F32, 1>,   (const void*)fft_cols2_f32_kernel};
   for (const void* f : fns)
     if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return false;
   return true;
@@ -755,7 +770,10 @@ void launch_fft_cols(const FftColArgs& a, int njobs, bool f64, cudaStream_t s) {
     else
       fft_cols_kernel<DD, 1><<<grid, kFftThreads, smem, s>>>(a);
   } else {
-    fft_cols_kernel<F32, 1><<<grid, kFftThreads, smem, s>>>(a);  // fft_cols_per_cta is 1 for FP32
+    if (C == 2)
+      fft_cols2_f32_kernel<<<grid, kFftThreads * 2, smem, s>>>(a);
+    else
+      fft_cols_kernel<F32, 1><<<grid, kFftThreads, smem, s>>>(a);
   }
 }
 
