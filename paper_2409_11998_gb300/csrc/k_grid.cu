@@ -165,20 +165,59 @@ __device__ __forceinline__ void interp_target(const InterpArgs<T>& a, int64_t i)
     T kx[W], ky[W];
     es_weights<T, W>(a.es, (T)(dx - 0.5 * (W - 1)), kx);
     es_weights<T, W>(a.es, (T)(dy - 0.5 * (W - 1)), ky);
+    if constexpr (sizeof(T) == 4) {
+      // single precision: a row is read as W/2 + 1 eight-byte cell pairs from
+      // the even cell ix0 at or below ix (rows start 8-byte aligned: the
+      // pitch is even), with the x weights shifted once onto the W + 1 cells
+      // ix0 .. ix0 + W; the unused end cell (possibly the row's padding, whose
+      // bits need not be a finite float) is dropped
+      const int ix0 = ix & ~1;
+      const bool odd = (ix & 1) != 0;
+      T ks[W + 1];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const T* grid = (const T*)a.grid[l][c];
-      if (!grid) continue;
-      T s = 0;
-#pragma unroll
-      for (int b = 0; b < W; ++b) {
-        const T* row = grid + (size_t)(iy + b) * gd.pitch + ix;
-        T r = 0;
-#pragma unroll
-        for (int t = 0; t < W; ++t) r = fma(row[t], kx[t], r);
-        s = fma(r, ky[b], s);
+      for (int t = 0; t <= W; ++t) {
+        const T here = t < W ? kx[t] : T(0), prev = t > 0 ? kx[t - 1] : T(0);
+        ks[t] = odd ? prev : here;
       }
-      acc[c] += (double)s;
+      constexpr int NQ = (W + 2) / 2;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T* grid = (const T*)a.grid[l][c];
+        if (!grid) continue;
+        T s = 0;
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+          const float2* row = (const float2*)(grid + (size_t)(iy + b) * gd.pitch + ix0);
+          float2 q[NQ];
+#pragma unroll
+          for (int u = 0; u < NQ; ++u) q[u] = __ldg(row + u);
+          T r = 0;
+#pragma unroll
+          for (int t = 0; t <= W; ++t) {
+            T v = (t & 1) ? q[t / 2].y : q[t / 2].x;
+            if (t == W) v = odd ? v : T(0);
+            r = fma(v, ks[t], r);
+          }
+          s = fma(r, ky[b], s);
+        }
+        acc[c] += (double)s;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T* grid = (const T*)a.grid[l][c];
+        if (!grid) continue;
+        T s = 0;
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+          const T* row = grid + (size_t)(iy + b) * gd.pitch + ix;
+          T r = 0;
+#pragma unroll
+          for (int t = 0; t < W; ++t) r = fma(row[t], kx[t], r);
+          s = fma(r, ky[b], s);
+        }
+        acc[c] += (double)s;
+      }
     }
   }
   if (bad) {
