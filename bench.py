@@ -361,9 +361,12 @@ def roofline(info, st, nv, nb, nt, precision, n_out=3, workload="starfish"):
     else:
         kp = lambda K: (int(K) + 2) & ~1
         cols_bytes = sum(7 * g * kp(K) * 2 * b for g, K in levels)
+        # the single-precision column pass runs two columns per CTA when three
+        # columns of the near grid fit in 110 KB of shared memory
+        cols_name = "fft_cols2_f32_kernel" if 3 * int(levels[0][0]) * 8 <= 110 * 1024 else "fft_cols_kernel"
         cand = {"spread_volume": (vol_ms, "spread_sub_kernel" if binned else "spread_atomic_kernel", spread_bytes,
                                   nv * nl * (W * W + 2 * W * (nc - 1)) / 32),
-                "multiplier": (st["multiplier"], "fft_cols_kernel", cols_bytes, None),
+                "multiplier": (st["multiplier"], cols_name, cols_bytes, None),
                 "interp": (st["interp"], "interp_dd_kernel" if precision == "fp64" else "interp_kernel",
                            interp_bytes, nt * nl * (2 * W * nc + n_out * W * W) / 32)}
     dom = max(cand, key=lambda k: cand[k][0])

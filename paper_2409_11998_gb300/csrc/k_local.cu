@@ -474,7 +474,8 @@ __device__ int local_classify_one(const LocalArgs& a, int64_t i) {
       const int x0c = max(cx - 1, 0), x1c = min(cx + 1, a.hnx - 1);
       const int y0c = max(cy - 1, 0), y1c = min(cy + 1, a.hny - 1);
       int k32 = -1;
-      for (int yy = y0c; yy <= y1c; ++yy) {
+      const bool scan = a.cell_near[cy * a.hnx + cx] != 0;  // else every neighbouring cell is empty
+      for (int yy = y0c; scan && yy <= y1c; ++yy) {
         const float ty = fmaf(-(float)(yy - cy), a.hh32, ry);
         for (int xx = x0c; xx <= x1c; ++xx) {
           const float tx = fmaf(-(float)(xx - cx), a.hh32, rx);
@@ -649,6 +650,7 @@ LocalArgs make_local_args(const Plan& P, int64_t nt, const double* txy, const do
   a.hnx = P.hash_nx;
   a.hny = P.hash_ny;
   a.cell_start = P.d_cell_start;
+  a.cell_near = P.d_cell_near;
   a.cell_node = P.d_cell_node;
   a.cell_xy32 = P.d_cell_xy32;
   a.geo_coef32 = P.d_geo_coef32;

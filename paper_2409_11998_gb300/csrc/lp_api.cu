@@ -183,7 +183,7 @@ void destroy_plan(Plan& P) {
                   P.d_dy_tab, P.d_dy_rel, P.d_dy_nw, P.d_dy_sig, P.d_dy_mu,
                   P.d_dy_rad, P.d_dy_wgl, P.d_dy_cell_start, P.d_dy_cell_panel, P.d_dy_ref, P.d_vf,
                   P.d_corners, P.d_corner_q, P.d_qred, P.d_geo_coef_dd, P.d_sigma_coef_dd,
-                  P.d_mu_coef_dd, P.d_bkeys, P.d_bstart, P.d_brel_dd, P.d_bperm, P.d_bq_dd, P.d_bbins};
+                  P.d_mu_coef_dd, P.d_cell_near, P.d_bkeys, P.d_bstart, P.d_brel_dd, P.d_bperm, P.d_bq_dd, P.d_bbins};
   for (void* b : bufs) dfree(b);
   if (P.h_status) cudaFreeHost(P.h_status);
   for (auto& e : P.ev)

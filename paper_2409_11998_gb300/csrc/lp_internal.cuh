@@ -272,6 +272,7 @@ struct LocalArgs {
   double hx0, hy0, hh;
   float hh32, inv_hh32, band32, margin32;  // single-precision copies for the classification
   int hnx, hny;
+  const unsigned char* cell_near;  // per hash cell: a boundary node within its 3x3 cells
   const int* cell_start;
   const int* cell_node;
   const float2* cell_xy32;   // node coordinates relative to their cell origin
@@ -377,6 +378,7 @@ struct Plan {
   double hash_x0 = 0, hash_y0 = 0, hash_h = 0;
   int hash_nx = 0, hash_ny = 0;
   int* d_cell_start = nullptr;  // [nx*ny + 1]
+  unsigned char* d_cell_near = nullptr;  // [nx*ny] 1 where the cell's 3x3 neighbourhood holds a node
   int* d_cell_node = nullptr;   // [nb] node ids sorted by cell
   float2* d_cell_xy32 = nullptr;  // [nb] node coordinates relative to their cell's origin (FP32)
   float* d_geo_coef32 = nullptr;  // FP32 copy of d_geo_coef (Newton start)

@@ -389,6 +389,16 @@ lp_status build_boundary(Plan& P, const double* h_xy, const double* h_w, const d
     cnt[cell[j] + 1]++;
   }
   for (size_t c = 0; c + 1 < cnt.size(); ++c) cnt[c + 1] += cnt[c];
+  // cells whose 3x3 neighbourhood holds no node: every target there is far
+  // from the boundary, and the classification skips the scan
+  std::vector<unsigned char> near((size_t)nx * ny, 0);
+  for (int cy = 0; cy < ny; ++cy)
+    for (int cx = 0; cx < nx; ++cx) {
+      const int c = cy * nx + cx;
+      if (cnt[c + 1] == cnt[c]) continue;
+      for (int yy = std::max(cy - 1, 0); yy <= std::min(cy + 1, ny - 1); ++yy)
+        for (int xx = std::max(cx - 1, 0); xx <= std::min(cx + 1, nx - 1); ++xx) near[(size_t)yy * nx + xx] = 1;
+    }
   std::vector<int> fill(cnt.begin(), cnt.end() - 1);
   for (int64_t j = 0; j < nb; ++j) order[fill[cell[j]]++] = (int)j;  // stable: ascending ids
   // FP32 coordinates of each sorted node relative to its cell's origin, for
@@ -434,6 +444,7 @@ lp_status build_boundary(Plan& P, const double* h_xy, const double* h_w, const d
       !dmalloc((void**)&P.d_leg_T, (size_t)p * p * sizeof(double)) ||
       !dmalloc((void**)&P.d_tau, p * sizeof(double)) ||
       !dmalloc((void**)&P.d_cell_start, cnt.size() * sizeof(int)) ||
+      !dmalloc((void**)&P.d_cell_near, near.size()) ||
       !dmalloc((void**)&P.d_cell_node, std::max<int64_t>(nb, 1) * sizeof(int)) ||
       !dmalloc((void**)&P.d_cell_xy32, std::max<int64_t>(nb, 1) * sizeof(float2)) ||
       !dmalloc((void**)&P.d_geo_coef32, (size_t)P.n_panels * 2 * p * sizeof(float)) ||
@@ -456,6 +467,7 @@ lp_status build_boundary(Plan& P, const double* h_xy, const double* h_w, const d
   cudaMemcpy(P.d_leg_T, T.data(), T.size() * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemcpy(P.d_tau, tau.data(), p * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemcpy(P.d_cell_start, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice);
+  cudaMemcpy(P.d_cell_near, near.data(), near.size(), cudaMemcpyHostToDevice);
   if (nb) cudaMemcpy(P.d_cell_node, order.data(), nb * sizeof(int), cudaMemcpyHostToDevice);
   if (nb) cudaMemcpy(P.d_cell_xy32, rel.data(), nb * sizeof(float2), cudaMemcpyHostToDevice);
   launch_panel_coef(P, P.d_bxy, 2, 2, P.d_geo_coef, P.d_geo_ref, P.stream);

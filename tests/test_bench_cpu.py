@@ -36,7 +36,11 @@ def test_fp64_roofline_spread_or_interp():
 def test_fp32_roofline_dominant_stage():
     st = {"spread": 0.3, "spread_volume": 0.25, "multiplier": 0.28, "interp": 0.2}
     r = bench.roofline(_info(1), st, 1_000_000, 16384, 1_000_000, "fp32", workload="none")
-    assert r["kernel"] == "fft_cols_kernel" and r["bound"] == "hbm"
+    # a 2916-point near grid: three columns fit in 110 KB, two columns per CTA
+    assert r["kernel"] == "fft_cols2_f32_kernel" and r["bound"] == "hbm"
+    r6 = bench.roofline(dict(_info(1), g_nh=6144, K_nh=1536), st, 1_000_000, 16384, 1_000_000, "fp32",
+                        workload="none")
+    assert r6["kernel"] == "fft_cols_kernel"
     kp = lambda K: (K + 2) & ~1
     byts = 7 * 2916 * kp(729) * 8 + 7 * 1152 * kp(288) * 8
     assert r["hbm"]["algorithmic_bytes_per_step"] == byts and r["frac"] == r["hbm_frac"]
