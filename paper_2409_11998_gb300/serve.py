@@ -16,6 +16,13 @@ was never admitted, or was evicted, least recently used first, to make room);
 
 ``one_at_a_time=True`` gives the reference serving path: one stream, one
 request per call, lp_execute, in arrival order.
+
+A client may stop waiting (it timed out, or its process died): an arrival
+can carry the time at which its client abandons the request.  A request
+abandoned while it waits is dropped without being launched; one abandoned
+while its wave is on the GPU completes with the wave (kernels in flight are
+never interrupted) and its outputs are dropped; either way its plan is
+released as usual, and latency statistics count it apart.
 """
 from __future__ import annotations
 
@@ -39,6 +46,8 @@ class Request:
     t_done: float = -1.0
     points: int = 0
     outputs: dict | None = None
+    abandon: float = float("inf")  # seconds from the start at which the client stops waiting
+    abandoned: bool = False
 
 
 def poisson_arrivals(rate, duration, n_meshes, seed=0, mesh_weights=None):
@@ -56,14 +65,19 @@ def poisson_arrivals(rate, duration, n_meshes, seed=0, mesh_weights=None):
 
 
 def latency_stats(reqs):
+    """p50/p99/mean latency and served points/s of the completed requests;
+    abandoned requests are counted apart."""
+    n_abandoned = sum(1 for r in reqs if r.abandoned)
+    reqs = [r for r in reqs if not r.abandoned]
     lat = np.array([r.t_done - r.arrival for r in reqs])
     if lat.size == 0:
-        return {}
+        return {"requests": 0, "abandoned": n_abandoned} if n_abandoned else {}
     span = max(r.t_done for r in reqs) - min(r.arrival for r in reqs)
     pts = sum(r.points for r in reqs)
     return {"requests": int(lat.size), "p50_ms": float(np.percentile(lat, 50) * 1e3),
             "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
-            "points_per_s": float(pts / span) if span > 0 else None, "span_s": float(span)}
+            "points_per_s": float(pts / span) if span > 0 else None, "span_s": float(span),
+            **({"abandoned": n_abandoned} if n_abandoned else {})}
 
 
 class _Mesh:
@@ -88,8 +102,13 @@ class _PlanInst:
 
 class Server:
     def __init__(self, pool, precision="fp32", tol=1e-5, n_slots=2, max_wave=32,
-                 mem_budget=64 << 30, one_at_a_time=False, keep_outputs=False, device="cuda", levels="auto"):
-        import torch
+                 mem_budget=64 << 30, one_at_a_time=False, keep_outputs=False, device="cuda", levels="auto",
+                 torch_module=None):
+        # torch_module: a stand-in for the few torch stream, event and tensor
+        # calls the loop makes, for exercising the scheduling without a GPU
+        if torch_module is None:
+            import torch as torch_module
+        torch = torch_module
         self.torch = torch
         self.device = device
         self.prec = LP_FP32 if precision == "fp32" else LP_FP64
@@ -213,7 +232,9 @@ class Server:
         for r in slot["reqs"]:
             r.t_done = now
             r._keep = None
-            if not self.keep:
+            if r.abandon <= now:            # the client left while the wave ran
+                r.abandoned = True
+            if not self.keep or r.abandoned:
                 r.outputs = None
         for inst in slot["insts"]:
             inst.busy = False
@@ -222,9 +243,11 @@ class Server:
         slot["reqs"], slot["insts"] = [], []
 
     def run(self, arrivals, poll_s=5e-5):
-        """Serve the (time, mesh, scale) arrivals in real time; returns the
-        requests with their launch and completion times."""
-        reqs = [Request(i, m, t, s) for i, (t, m, s) in enumerate(sorted(arrivals))]
+        """Serve the (time, mesh, scale[, abandon]) arrivals in real time;
+        returns the requests with their launch and completion times (abandon:
+        the time at which the client stops waiting; none by default)."""
+        reqs = [Request(i, a[1], a[0], a[2], abandon=a[3] if len(a) > 3 else float("inf"))
+                for i, a in enumerate(sorted(arrivals, key=lambda a: a[0]))]
         queue = collections.deque()
         nxt = 0
         done = 0
@@ -234,6 +257,14 @@ class Server:
             while nxt < len(reqs) and reqs[nxt].arrival <= now:
                 queue.append(reqs[nxt])
                 nxt += 1
+            if any(r.abandon <= now for r in queue):
+                # clients that stopped waiting: their requests are never launched
+                left = [r for r in queue if r.abandon <= now]
+                for r in left:
+                    r.abandoned = True
+                    r.t_done = now
+                queue = collections.deque(r for r in queue if r.abandon > now)
+                done += len(left)
             progressed = False
             for si, slot in enumerate(self.slots):
                 if slot["busy"] and slot["event"].query():
