@@ -246,9 +246,11 @@ lp_status lp_execute_graph(lp_plan_t plan, int64_t n_t, const double* t_xy, cons
  *   lp_batch_execute(b, n, plans, n_t, t_xy, f_jet, V, S, D): evaluates, for
  *     every member i, exactly what lp_execute(plans[i], n_t[i], t_xy[i],
  *     f_jet[i], V[i], S[i], D[i]) evaluates (Sec. 3 and Sec. 4 per problem),
- *     with one zeroing launch, one spread launch for the boundary nodes (and
- *     the volume nodes of plans without bins), one launch for the binned
- *     volume spreads of every member and level, one interpolation launch
+ *     with one zeroing launch, one point-parallel spread launch (boundary
+ *     nodes of FP32 members, volume nodes of plans without bins), one launch
+ *     for the binned volume spreads of every member and level, one for the
+ *     binned layer spreads of FP64 members (their boundary nodes sorted into
+ *     the bins at plan time), one interpolation launch
  *     per arithmetic (df64, and the cuFFT path's), and one local classify +
  *     near launch for the whole wave; each member's transform chain is
  *     issued on one of 8 worker streams that fork from the batch stream

@@ -449,6 +449,18 @@ __global__ void __launch_bounds__(NT, kSubDDMinBlocks) spread_fx_list_kernel(con
 }
 
 template <int W, int NT>
+__global__ void __launch_bounds__(NT, kSubDDMinBlocks) spread_fx_list_wave_kernel(
+    const SubDDArgs* __restrict__ recs, const FxListRec* __restrict__ lrecs, const int* __restrict__ first,
+    int nrec) {
+  const int r = wave_record(first, nrec, blockIdx.x);
+  const FxListRec& L = lrecs[r];
+  const int key = blockIdx.x - first[r];
+  const int c = key % L.nch;
+  const int2 b = L.bins[key / L.nch];
+  spread_fx_bin<W, NT>(recs[r], L.ch.q[c], L.ch.grid[c], b.x, b.y);
+}
+
+template <int W, int NT>
 __global__ void __launch_bounds__(NT, kSubDDMinBlocks) spread_fx_wave_kernel(const SubDDArgs* __restrict__ recs,
                                                                const int* __restrict__ first, int nrec) {
   const int r = wave_record(first, nrec, blockIdx.x);
@@ -517,6 +529,8 @@ bool spread_sub_dd_configure(int w) {
            cudaFuncSetAttribute(spread_fx_wave_kernel<W, kSubDDThreads>,                                \
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&   \
            cudaFuncSetAttribute(spread_fx_list_kernel<W, kSubDDThreads>,                                \
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&   \
+           cudaFuncSetAttribute(spread_fx_list_wave_kernel<W, kSubDDThreads>,                           \
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
     LP_SUB_DD_CASES
 #undef LP_CASE
@@ -597,6 +611,20 @@ void launch_spread_sub(const SubArgs& a, int w, cudaStream_t s) {
 
 // One launch for the binned spreads of a wave: recs[nrec] in device memory,
 // first[nrec + 1] their first blocks; smem: the largest record's need.
+void launch_spread_fx_list_wave(int w, const SubDDArgs* recs, const FxListRec* lrecs, const int* first, int nrec,
+                                int nblocks, size_t smem, cudaStream_t s) {
+  if (nrec <= 0 || nblocks <= 0) return;
+  switch (w) {
+#define LP_CASE(W)                                                                                            \
+  case W:                                                                                                     \
+    spread_fx_list_wave_kernel<W, kSubDDThreads><<<nblocks, kSubDDThreads, smem, s>>>(recs, lrecs, first, nrec); \
+    break;
+    LP_SUB_DD_CASES
+#undef LP_CASE
+    default: break;
+  }
+}
+
 void launch_spread_wave(int precision, int w, const void* recs, const int* first, int nrec, int nblocks,
                         size_t smem, cudaStream_t s) {
   if (nrec <= 0 || nblocks <= 0) return;

@@ -166,6 +166,12 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
   size_t bsmem = 0;
   std::vector<InterpDDArgs> idd;
   std::vector<int> ifirst(1, 0);
+  // FP64 plans whose boundary nodes sit in the bins: the layer spreads over
+  // their listed bins, one record per plan and level
+  std::vector<SubDDArgs> ldd;
+  std::vector<FxListRec> lrec;
+  std::vector<int> lfirst(1, 0);
+  size_t lsmem = 0;
   const bool f64 = prec == LP_FP64;
   for (int i = 0; i < n; ++i) {
     const Plan& P = plans[i]->P;
@@ -214,7 +220,31 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
         bq[nq] = P.d_bq + 2 * P.nb;
         bg[nq++] = G.chan[3];
       }
-      add_spread(P.d_bxy, bq, nq, bg, P.nb);
+      if (nq && f64 && P.bbinned) {
+        SubDDArgs a = make_spread_dd_args(P, l);
+        a.rel = P.d_brel_dd;
+        a.start = P.d_bstart;
+        FxListRec r{};
+        r.bins = P.d_bbins;
+        int k = 0;
+        if (ws) {
+          r.ch.q[k] = P.d_bq_dd;
+          r.ch.grid[k++] = G.chan[1];
+        }
+        if (wd) {
+          r.ch.q[k] = P.d_bq_dd + P.nb;
+          r.ch.grid[k++] = G.chan[2];
+          r.ch.q[k] = P.d_bq_dd + 2 * P.nb;
+          r.ch.grid[k++] = G.chan[3];
+        }
+        r.nch = k;
+        ldd.push_back(a);
+        lrec.push_back(r);
+        lfirst.push_back(lfirst.back() + P.n_bbins * k);
+        lsmem = std::max(lsmem, spread_sub_smem(P.sub_M[l], P.ker.w, true));
+      } else {
+        add_spread(P.d_bxy, bq, nq, bg, P.nb);
+      }
       if (!P.own_fft) {  // plans on the FFT chain apply the multiplier inside it
         int rec = (int)mult.size();
         mult.push_back(make_mult_args(P, l, wv, ws, wd));
@@ -250,6 +280,7 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
   const size_t o_la = pk.put(loc), o_lw = pk.put(lwork);
   const size_t o_ba = f64 ? pk.put(bdd) : pk.put(b32), o_bf = pk.put(bfirst);
   const size_t o_da = pk.put(idd), o_df = pk.put(ifirst);
+  const size_t o_lda = pk.put(ldd), o_lre = pk.put(lrec), o_lfi = pk.put(lfirst);
   const int nbrec = (int)(f64 ? bdd.size() : b32.size()), ndrec = (int)idd.size();
   const size_t bytes = align_up(pk.img.size(), 256);
   if (bytes > b->buf_cap) {
@@ -286,6 +317,9 @@ lp_status lp_batch_execute(lp_batch_t b, int n, const lp_plan_t* plans, const in
   b->launches += 2;
   launch_spread_wave(prec, w, d + o_ba, (const int*)(d + o_bf), nbrec, bfirst.back(), bsmem, s);
   if (nbrec) ++b->launches;
+  launch_spread_fx_list_wave(w, (const SubDDArgs*)(d + o_lda), (const FxListRec*)(d + o_lre),
+                             (const int*)(d + o_lfi), (int)ldd.size(), lfirst.back(), lsmem, s);
+  if (!ldd.empty()) ++b->launches;
   const long long before = sum_launches(plans, n);
   cudaEventRecord(b->ev[2], s);
   // each plan's transforms: the whole FFT chain for plans on it (counted as

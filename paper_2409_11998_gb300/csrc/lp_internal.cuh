@@ -531,6 +531,16 @@ struct FxChan {
 };
 void launch_spread_fx_list(const SubDDArgs& a, const int2* bins, int nbins, const FxChan& ch, int nch, int w,
                            cudaStream_t s);
+// the same over a wave of plans: record r (SubDDArgs recs[r], its bin list
+// and channels lrecs[r]) covers blocks first[r] .. first[r + 1] - 1, one per
+// (listed bin, channel)
+struct FxListRec {
+  const int2* bins;
+  FxChan ch;
+  int nch;
+};
+void launch_spread_fx_list_wave(int w, const SubDDArgs* recs, const FxListRec* lrecs, const int* first, int nrec,
+                                int nblocks, size_t smem, cudaStream_t s);
 void launch_bin_sort_dd(const double* xy, int64_t n, const BinGeom& bg, int* keys, int* counts, int* cursor,
                         int* starts, float4* rel_s, int* perm, unsigned* status, cudaStream_t s);
 void launch_gather_q_dd(const double* q, const int* perm, int64_t n, float2* q_s, cudaStream_t s);
