@@ -739,14 +739,23 @@ bool fft_dd_configure() {
   return true;
 }
 
+// Threads per row transform: about one per radix-4 butterfly of a stage
+// (N / 4, a whole number of warps, 32 .. kFftThreads), so that the short
+// rows of small grids do not leave most of a 256-thread CTA idle; the row
+// kernels stride by blockDim.
+static int row_threads(int N) {
+  const int t = ((N / 4 + 31) / 32) * 32;
+  return std::min(kFftThreads, std::max(32, t));
+}
+
 void launch_fft_rows_fwd(const FftRowArgs& a, int nchan, bool f64, cudaStream_t s) {
   const int nrows = a.row_hi - a.row_lo;
   if (nrows <= 0 || nchan <= 0) return;
   const size_t smem = fft_rows_smem(2 * a.half.n, f64);
   if (f64)
-    fft_rows_fwd_kernel<DD><<<dim3(nrows, nchan), kFftThreads, smem, s>>>(a);
+    fft_rows_fwd_kernel<DD><<<dim3(nrows, nchan), row_threads(a.half.n), smem, s>>>(a);
   else
-    fft_rows_fwd_kernel<F32><<<dim3(nrows, nchan), kFftThreads, smem, s>>>(a);
+    fft_rows_fwd_kernel<F32><<<dim3(nrows, nchan), row_threads(a.half.n), smem, s>>>(a);
 }
 
 void launch_fft_rows_inv(const FftRowArgs& a, int nchan, bool f64, cudaStream_t s) {
@@ -754,9 +763,9 @@ void launch_fft_rows_inv(const FftRowArgs& a, int nchan, bool f64, cudaStream_t 
   if (nrows <= 0 || nchan <= 0) return;
   const size_t smem = fft_rows_smem(2 * a.half.n, f64);
   if (f64)
-    fft_rows_inv_kernel<DD><<<dim3(nrows, nchan), kFftThreads, smem, s>>>(a);
+    fft_rows_inv_kernel<DD><<<dim3(nrows, nchan), row_threads(a.half.n), smem, s>>>(a);
   else
-    fft_rows_inv_kernel<F32><<<dim3(nrows, nchan), kFftThreads, smem, s>>>(a);
+    fft_rows_inv_kernel<F32><<<dim3(nrows, nchan), row_threads(a.half.n), smem, s>>>(a);
 }
 
 void launch_fft_cols(const FftColArgs& a, int njobs, bool f64, cudaStream_t s) {
