@@ -29,7 +29,7 @@ def lp():
 
 
 def _sample(prob, n=10_000, n_near=1_000, seed=17):
-    """The survey's 10k-target subsample: uniformly drawn targets plus the
+    """A 10k-target subsample: uniformly drawn targets plus the
     band near the boundary -- the nearest targets first (on-surface points),
     then every k-th by distance so that the whole 12 sqrt(delta) band is
     covered -- plus the targets nearest to the corners of the box (the
