@@ -106,14 +106,22 @@ __global__ void __launch_bounds__(128) interp_dd_kernel(const __grid_constant__ 
 template <int W>
 __global__ void __launch_bounds__(128) interp_dd_wave_kernel(const InterpDDArgs* __restrict__ recs,
                                                              const int* __restrict__ first, int nrec) {
+  // the block's record in shared memory: the per-target code reads its
+  // weight coefficients and level data many times (from global memory each
+  // read would be a load; the single-plan kernel has them in parameter space)
+  __shared__ InterpDDArgs sa;
   int lo = 0, hi = nrec - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (first[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
   }
-  const InterpDDArgs& a = recs[lo];
+  static_assert(sizeof(InterpDDArgs) % sizeof(int) == 0, "record copied as words");
+  const int* src = (const int*)(recs + lo);
+  int* dst = (int*)&sa;
+  for (int k = threadIdx.x; k < (int)(sizeof(InterpDDArgs) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
+  __syncthreads();
   const int64_t i = (int64_t)(blockIdx.x - first[lo]) * 128 + threadIdx.x;
-  if (i < a.n) interp_dd_target<W>(a, i);
+  if (i < sa.n) interp_dd_target<W>(sa, i);
 }
 
 }  // namespace
