@@ -210,13 +210,15 @@ lp_status lp_execute(lp_plan_t plan, int64_t n_t, const double* t_xy, const doub
  * this call then runs the same kernels as lp_execute on the same data, but
  * it stages nothing (every pointer must be device memory, else LP_ERR_ARG)
  * and keeps its per-call scratch -- the list of targets near the boundary
- * -- in a static device array sized for at most 2,097,152 targets (16 MiB,
- * held by every GPU that loads the library until the process exits); larger
- * n_t is rejected with LP_ERR_ARG before anything is launched.  The call
- * must be made with the plan's device current (LP_ERR_ARG otherwise: the
- * array is per device).  The first call on each device looks up that array's
- * device address (with the device current), so make the first call on a
- * device before any stream capture.  All calls share the one array: calls
+ * -- in a static device array sized for at most 2,097,152 targets (16 MiB
+ * per device, held until the process exits); larger n_t is rejected with
+ * LP_ERR_ARG before anything is launched.  The call must be made with the
+ * plan's device current (LP_ERR_ARG otherwise: the array is per device).
+ * The first call on each device looks up that array's device address (with
+ * the device current); the CUDA driver loads modules lazily, so that lookup
+ * is when it loads the module holding the array and takes the array's 16
+ * MiB.  Make the first call on a device during set-up, before any stream
+ * capture and before the point from which nothing may be allocated.  All calls share the one array: calls
  * whose work overlaps on the GPU (two plans on different streams, say) race,
  * so serialise them.  No cudaMalloc, cudaFree or allocating library routine
  * is called. */
